@@ -1,0 +1,261 @@
+"""FP64 CPU oracle of the ProbeSDF per-ray render and its adjoint.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import this package.  The
+product path (``paper_2412_10084_gb300``) never imports it, and this package
+never imports the product: the two share only the seeded input generators of
+``synth``.
+
+The arithmetic lives in ``probesdf_oracle.c`` (plain C, FP64, one ray at a
+time); this module compiles it with gcc and marshals numpy arrays through
+ctypes.  Every function's paper passage is cited in the C source.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "probesdf_oracle.c")
+_HDR = os.path.join(_HERE, "probesdf_oracle.h")
+_BUILD_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+DIR_REFLECT = 0
+DIR_VIEW = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (FP contraction off: the FP32 sample
+    positions must be computed with exactly the stated roundings)."""
+    os.makedirs(_BUILD_DIR, exist_ok=True)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-shared", "-fPIC",
+           "-ffp-contract=off", "-fno-fast-math", "-pthread", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Model(ctypes.Structure):
+    _fields_ = [
+        ("R", ctypes.c_int32 * 3),
+        ("bmin", ctypes.c_float * 3),
+        ("bmax", ctypes.c_float * 3),
+        ("n_s", ctypes.c_int32),
+        ("sdf", ctypes.c_void_p),
+        ("feat", ctypes.c_void_p),
+        ("P", ctypes.c_int32 * 3),
+        ("sh_l", ctypes.c_int32),
+        ("n_a", ctypes.c_int32),
+        ("probes", ctypes.c_void_p),
+        ("width", ctypes.c_int32),
+        ("n_fresnel", ctypes.c_int32),
+        ("mlp", ctypes.c_void_p),
+    ]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [
+        ("tau", ctypes.c_double),
+        ("n_samples", ctypes.c_int32),
+        ("dir_mode", ctypes.c_int32),
+        ("bg", ctypes.c_double * 3),
+    ]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            lib.orc_sh_eval.argtypes = [ctypes.c_int32, P, P]
+            lib.orc_sh_grad.argtypes = [ctypes.c_int32, P, P]
+            lib.orc_render_forward.argtypes = [P, P, ctypes.c_int64, P, P, P, P, P, P, P, P,
+                                               ctypes.c_int32]
+            lib.orc_render_forward.restype = ctypes.c_int32
+            lib.orc_render_backward.argtypes = [P, P, ctypes.c_int64, P, P, P, P, P, P, P, P, P,
+                                                P, ctypes.c_int32]
+            lib.orc_render_backward.restype = ctypes.c_int32
+            lib.orc_render_trace.argtypes = [P, P, P, P, P, P, P, P, P, P]
+            lib.orc_render_trace.restype = ctypes.c_int32
+            lib.orc_point_eval.argtypes = [P, P, P, P, ctypes.c_float, P, P, P, P]
+            lib.orc_point_eval.restype = ctypes.c_int32
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+class Model:
+    """Oracle copy of a scene: every parameter promoted to FP64.
+
+    sdf [Rz,Ry,Rx], feat [Rz,Ry,Rx,n_s], probes [Pz,Py,Px,l*l,n_a], mlp flat
+    (W1[W][n_in] b1 W2[W][W] b2 W3[3][W] b3), box in FP32.
+    """
+
+    def __init__(self, sdf, feat, probes, mlp, box_min, box_max, sh_l, width, n_fresnel):
+        self.sdf = _f64(sdf)
+        self.feat = _f64(feat)
+        self.probes = _f64(probes)
+        self.mlp = _f64(mlp).ravel()
+        self.box_min = _f32(box_min)
+        self.box_max = _f32(box_max)
+        self.sh_l = int(sh_l)
+        self.width = int(width)
+        self.n_fresnel = int(n_fresnel)
+        Rz, Ry, Rx = self.sdf.shape
+        self.n_s = self.feat.shape[-1]
+        Pz, Py, Px, L2, na = self.probes.shape
+        assert L2 == self.sh_l ** 2
+        self.n_a = na
+        n_in = self.n_s + self.n_a + self.n_fresnel
+        W = self.width
+        assert self.mlp.size == W * n_in + W + W * W + W + 3 * W + 3, "mlp size"
+        s = _Model()
+        s.R[:] = (Rx, Ry, Rz)
+        s.bmin[:] = tuple(float(v) for v in self.box_min)
+        s.bmax[:] = tuple(float(v) for v in self.box_max)
+        s.n_s = self.n_s
+        s.sdf = self.sdf.ctypes.data
+        s.feat = self.feat.ctypes.data
+        s.P[:] = (Px, Py, Pz)
+        s.sh_l = self.sh_l
+        s.n_a = self.n_a
+        s.probes = self.probes.ctypes.data
+        s.width = W
+        s.n_fresnel = self.n_fresnel
+        s.mlp = self.mlp.ctypes.data
+        self._s = s
+
+    @classmethod
+    def from_scene(cls, sc):
+        return cls(sc.sdf, sc.feat, sc.probes, sc.mlp, sc.box_min, sc.box_max, sc.sh_l,
+                   sc.width, sc.n_fresnel)
+
+
+def _params(tau, n_samples, dir_mode=DIR_REFLECT, bg=(0.0, 0.0, 0.0)):
+    p = _Params()
+    p.tau = float(tau)
+    p.n_samples = int(n_samples)
+    p.dir_mode = int(dir_mode)
+    p.bg[:] = tuple(float(v) for v in bg)
+    return p
+
+
+def render_forward(model: Model, rays_o, rays_d, tau, n_samples, dir_mode=DIR_REFLECT,
+                   bg=(0.0, 0.0, 0.0), t_samples=None, n_threads=1, margin=False):
+    """rgb [n,3], depth [n], wsum [n], logT_final [n] (and the per-ray
+    smallest relative distance to a ReLU or alpha-clip kink if asked)."""
+    lib = _load()
+    o, d = _f32(rays_o).reshape(-1, 3), _f32(rays_d).reshape(-1, 3)
+    n = o.shape[0]
+    ts = None if t_samples is None else _f32(t_samples).reshape(n, n_samples + 1)
+    rgb = np.zeros((n, 3))
+    depth, wsum, logT = np.zeros(n), np.zeros(n), np.zeros(n)
+    mg = np.full(n, np.inf) if margin else None
+    p = _params(tau, n_samples, dir_mode, bg)
+    st = lib.orc_render_forward(ctypes.byref(model._s), ctypes.byref(p), n, _ptr(o), _ptr(d),
+                                _ptr(ts), _ptr(rgb), _ptr(depth), _ptr(wsum), _ptr(logT),
+                                _ptr(mg), int(n_threads))
+    if st != 0:
+        raise ValueError(f"oracle forward rejected its arguments ({st})")
+    out = {"rgb": rgb, "depth": depth, "wsum": wsum, "logT": logT}
+    if margin:
+        out["margin"] = mg
+    return out
+
+
+def render_backward(model: Model, rays_o, rays_d, d_rgb, tau, n_samples, d_depth=None,
+                    d_wsum=None, dir_mode=DIR_REFLECT, bg=(0.0, 0.0, 0.0), t_samples=None,
+                    n_threads=1):
+    """Gradients of sum(d_rgb*rgb + d_depth*depth + d_wsum*wsum) w.r.t. the
+    SDF nodes, node features, probe coefficients and MLP parameters."""
+    lib = _load()
+    o, d = _f32(rays_o).reshape(-1, 3), _f32(rays_d).reshape(-1, 3)
+    n = o.shape[0]
+    ts = None if t_samples is None else _f32(t_samples).reshape(n, n_samples + 1)
+    drgb = _f64(d_rgb).reshape(n, 3)
+    dd = None if d_depth is None else _f64(d_depth).reshape(n)
+    dw = None if d_wsum is None else _f64(d_wsum).reshape(n)
+    g_sdf = np.zeros_like(model.sdf)
+    g_feat = np.zeros_like(model.feat)
+    g_probe = np.zeros_like(model.probes)
+    g_mlp = np.zeros_like(model.mlp)
+    p = _params(tau, n_samples, dir_mode, bg)
+    st = lib.orc_render_backward(ctypes.byref(model._s), ctypes.byref(p), n, _ptr(o), _ptr(d),
+                                 _ptr(ts), _ptr(drgb), _ptr(dd), _ptr(dw), _ptr(g_sdf),
+                                 _ptr(g_feat), _ptr(g_probe), _ptr(g_mlp), int(n_threads))
+    if st != 0:
+        raise ValueError(f"oracle backward rejected its arguments ({st})")
+    return {"sdf": g_sdf, "feat": g_feat, "probes": g_probe, "mlp": g_mlp}
+
+
+def render_trace(model: Model, o, d, tau, n_samples, dir_mode=DIR_REFLECT, t_samples=None):
+    """Per-sample detail of one ray: t[N+1], s[N+1], w[N], C[N,3], normal[N,3]."""
+    lib = _load()
+    o, d = _f32(o).reshape(3), _f32(d).reshape(3)
+    ts = None if t_samples is None else _f32(t_samples).reshape(n_samples + 1)
+    t = np.zeros(n_samples + 1, np.float32)
+    s = np.zeros(n_samples + 1)
+    w = np.zeros(n_samples)
+    C = np.zeros((n_samples, 3))
+    nrm = np.zeros((n_samples, 3))
+    p = _params(tau, n_samples, dir_mode)
+    hit = lib.orc_render_trace(ctypes.byref(model._s), ctypes.byref(p), _ptr(o), _ptr(d),
+                               _ptr(ts), _ptr(t), _ptr(s), _ptr(w), _ptr(C), _ptr(nrm))
+    if hit < 0:
+        raise ValueError("oracle trace rejected its arguments")
+    return {"hit": bool(hit), "t": t, "s": s, "w": w, "C": C, "normal": nrm}
+
+
+def point_eval(model: Model, o, d, t, dir_mode=DIR_REFLECT):
+    """SDF value, gradient, MLP input vector and colour at the point o + t d."""
+    lib = _load()
+    o, d = _f32(o).reshape(3), _f32(d).reshape(3)
+    s = np.zeros(1)
+    g = np.zeros(3)
+    x = np.zeros(model.n_s + model.n_a + model.n_fresnel)
+    C = np.zeros(3)
+    p = _params(1.0, 1, dir_mode)
+    st = lib.orc_point_eval(ctypes.byref(model._s), ctypes.byref(p), _ptr(o), _ptr(d),
+                            ctypes.c_float(t), _ptr(s), _ptr(g), _ptr(x), _ptr(C))
+    if st != 0:
+        raise ValueError("oracle point_eval rejected its arguments")
+    return {"s": s[0], "g": g, "x": x, "C": C}
+
+
+def sh_eval(l, r):
+    lib = _load()
+    r = _f64(r).reshape(3)
+    Y = np.zeros(l * l)
+    lib.orc_sh_eval(int(l), _ptr(r), _ptr(Y))
+    return Y
+
+
+def sh_grad(l, r):
+    lib = _load()
+    r = _f64(r).reshape(3)
+    dY = np.zeros((l * l, 3))
+    lib.orc_sh_grad(int(l), _ptr(r), _ptr(dY))
+    return dY

@@ -1,0 +1,66 @@
+/*
+ * FP64 CPU oracle of the ProbeSDF per-ray render and adjoint.
+ * TEST INFRASTRUCTURE ONLY: used by the tests, the smoke check and the
+ * benchmark's CPU-baseline leg; never by the product path.
+ */
+#ifndef PROBESDF_ORACLE_H
+#define PROBESDF_ORACLE_H
+
+#include <stdint.h>
+
+#define ORC_MAX_NS 16
+#define ORC_MAX_NA 16
+#define ORC_MAX_K 8
+#define ORC_MAX_L2 16
+#define ORC_MAX_W 64
+#define ORC_MAX_IN 40
+
+#define ORC_DIR_REFLECT 0
+#define ORC_DIR_VIEW 1
+
+typedef struct orc_model {
+    int32_t R[3];          /* SDF / feature nodes per axis (x, y, z) */
+    float bmin[3];         /* grid box, FP32 as the kernel sees it */
+    float bmax[3];
+    int32_t n_s;           /* spatial features per node */
+    const double* sdf;     /* [Rz][Ry][Rx] */
+    const double* feat;    /* [Rz][Ry][Rx][n_s] */
+    int32_t P[3];          /* probe nodes per axis, same box */
+    int32_t sh_l;          /* SH order l (1-indexed): l*l coefficients */
+    int32_t n_a;           /* angular feature channels */
+    const double* probes;  /* [Pz][Py][Px][l*l][n_a] */
+    int32_t width;         /* MLP hidden width W */
+    int32_t n_fresnel;     /* K: Fresnel powers 1..K */
+    const double* mlp;     /* W1[W][n_in] b1[W] W2[W][W] b2[W] W3[3][W] b3[3] */
+} orc_model;
+
+typedef struct orc_params {
+    double tau;            /* NeuS logistic scale */
+    int32_t n_samples;     /* N colour samples, N+1 SDF points */
+    int32_t dir_mode;      /* ORC_DIR_REFLECT or ORC_DIR_VIEW */
+    double bg[3];          /* background colour */
+} orc_params;
+
+void orc_sh_eval(int32_t l, const double r[3], double* Y);
+void orc_sh_grad(int32_t l, const double r[3], double* dY);
+
+int32_t orc_render_forward(const orc_model* m, const orc_params* p, int64_t n_rays,
+                           const float* rays_o, const float* rays_d, const float* t_samples,
+                           double* rgb, double* depth, double* wsum, double* logT_final,
+                           double* margin, int32_t n_threads);
+
+int32_t orc_render_backward(const orc_model* m, const orc_params* p, int64_t n_rays,
+                            const float* rays_o, const float* rays_d, const float* t_samples,
+                            const double* d_rgb, const double* d_depth, const double* d_wsum,
+                            double* g_sdf, double* g_feat, double* g_probe, double* g_mlp,
+                            int32_t n_threads);
+
+int32_t orc_render_trace(const orc_model* m, const orc_params* p, const float* o, const float* d,
+                         const float* t_samples, float* t, double* s, double* w, double* C,
+                         double* normal);
+
+int32_t orc_point_eval(const orc_model* m, const orc_params* p, const float o[3],
+                       const float d[3], float t, double* s, double g[3], double* mlp_in,
+                       double C[3]);
+
+#endif

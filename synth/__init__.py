@@ -1,0 +1,363 @@
+"""Seeded synthetic inputs for the ProbeSDF render: scenes, cameras, rays,
+parameters and targets.
+
+This module holds no arithmetic of the method itself (no interpolation,
+spherical harmonics, MLP or compositing): it only builds inputs.  Both the
+CUDA path and the FP64 oracle read the arrays it returns, so they see the
+identical FP32 bytes.
+
+Workload recipes (shapes of the paper's object- and human-capture setups,
+ProbeSDF Sec. 5; no dataset content is used):
+
+* ``sphere64``   64^3 grid on [0,1]^3, SDF of a radius-0.5 sphere plus N(0,0.01)
+  noise, 3 features/node ~N(0,0.1), probes 16^3 x 9 SH x 4 ch ~N(0,0.1), MLP
+  10->16->16->3 Xavier-uniform with zero biases, 8 pinhole cameras on a
+  radius-2 sphere, 128x128 px, 512 random pixels each (4096 rays), 128 samples.
+* ``object256``  256^3 grid on [0,1]^3, smooth-min union of 32 random spheres and
+  superquadrics, probes 32^3 x 9 x 4, MLP 10->32->32->3, 49 cameras at
+  1600x1200 on a radius-2 hemisphere, 2^18 random pixels, 256 samples.
+* ``human384``   384x768x384 grid on [0,1]x[0,2]x[0,1], a posed chain of 15
+  capsules, probes 48x96x48 x 9 x 4, 64 cameras at 2048^2 on a ring, 2^19
+  rays, 256 samples.
+* ``stress512``  512^3 object-style grid, probes 64^3 x 9 x 8, MLP
+  14->32->32->3, 2^20 rays, 512 samples.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+
+def rng(seed: int) -> np.random.Generator:
+    """Counter-based generator (Philox) so every recipe is reproducible."""
+    return np.random.Generator(np.random.Philox(int(seed)))
+
+
+@dataclasses.dataclass
+class Scene:
+    sdf: np.ndarray          # float32 [Rz, Ry, Rx]
+    feat: np.ndarray         # float32 [Rz, Ry, Rx, n_s]
+    probes: np.ndarray       # float32 [Pz, Py, Px, l*l, n_a]
+    mlp: np.ndarray          # float32 flat: W1[W][n_in] b1 W2[W][W] b2 W3[3][W] b3
+    box_min: np.ndarray      # float32 [3]
+    box_max: np.ndarray      # float32 [3]
+    sh_l: int
+    width: int
+    n_fresnel: int
+
+    @property
+    def dims(self):
+        Rz, Ry, Rx = self.sdf.shape
+        return (Rx, Ry, Rz)
+
+    @property
+    def probe_dims(self):
+        Pz, Py, Px = self.probes.shape[:3]
+        return (Px, Py, Pz)
+
+    @property
+    def n_s(self):
+        return self.feat.shape[-1]
+
+    @property
+    def n_a(self):
+        return self.probes.shape[-1]
+
+
+@dataclasses.dataclass
+class Rays:
+    o: np.ndarray            # float32 [n, 3]
+    d: np.ndarray            # float32 [n, 3], unit length
+    target: np.ndarray       # float32 [n, 3] in [0, 1]
+
+
+# ----------------------------------------------------------------------------
+# Parameters
+# ----------------------------------------------------------------------------
+
+def mlp_params(n_in: int, width: int, g: np.random.Generator, n_out: int = 3) -> np.ndarray:
+    """Xavier-uniform weights, zero biases, packed W1 b1 W2 b2 W3 b3."""
+    def xavier(fo, fi):
+        a = math.sqrt(6.0 / (fi + fo))
+        return g.uniform(-a, a, size=(fo, fi))
+    parts = [xavier(width, n_in).ravel(), np.zeros(width),
+             xavier(width, width).ravel(), np.zeros(width),
+             xavier(n_out, width).ravel(), np.zeros(n_out)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def mlp_param_count(n_in: int, width: int, n_out: int = 3) -> int:
+    return width * n_in + width + width * width + width + n_out * width + n_out
+
+
+# ----------------------------------------------------------------------------
+# Scene SDFs (scene construction only)
+# ----------------------------------------------------------------------------
+
+def _node_coords(dims, box_min, box_max, zslice):
+    Rx, Ry, Rz = dims
+    xs = np.linspace(box_min[0], box_max[0], Rx)
+    ys = np.linspace(box_min[1], box_max[1], Ry)
+    zs = np.linspace(box_min[2], box_max[2], Rz)[zslice]
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    return X, Y, Z
+
+
+def _smin(a, b, k):
+    h = np.maximum(k - np.abs(a - b), 0.0) / k
+    return np.minimum(a, b) - h * h * k * 0.25
+
+
+def sphere_sdf(dims, box_min, box_max, center, radius):
+    X, Y, Z = _node_coords(dims, box_min, box_max, slice(None))
+    return np.sqrt((X - center[0]) ** 2 + (Y - center[1]) ** 2 + (Z - center[2]) ** 2) - radius
+
+
+def _random_rotation(g):
+    q = g.normal(size=4)
+    q /= np.linalg.norm(q)
+    a, b, c, d = q
+    return np.array([[a * a + b * b - c * c - d * d, 2 * (b * c - a * d), 2 * (b * d + a * c)],
+                     [2 * (b * c + a * d), a * a - b * b + c * c - d * d, 2 * (c * d - a * b)],
+                     [2 * (b * d - a * c), 2 * (c * d + a * b), a * a - b * b - c * c + d * d]])
+
+
+def object_shapes(g, n_shapes=32):
+    shapes = []
+    for i in range(n_shapes):
+        c = g.uniform(0.25, 0.75, size=3)
+        if i % 2 == 0:
+            shapes.append(("sphere", c, g.uniform(0.05, 0.2)))
+        else:
+            radii = g.uniform(0.04, 0.16, size=3)
+            expo = g.uniform(1.5, 6.0)
+            shapes.append(("superquadric", c, (radii, expo, _random_rotation(g))))
+    return shapes
+
+
+def object_sdf(dims, box_min, box_max, shapes, k=0.05, slab=32):
+    """Smooth-min (polynomial, k) union of spheres and superquadrics.  The
+    superquadric uses the usual implicit-function distance approximation."""
+    Rx, Ry, Rz = dims
+    out = np.empty((Rz, Ry, Rx), np.float32)
+    for z0 in range(0, Rz, slab):
+        X, Y, Z = _node_coords(dims, box_min, box_max, slice(z0, min(Rz, z0 + slab)))
+        P = np.stack([X, Y, Z], -1)
+        acc = None
+        for kind, c, prm in shapes:
+            q = P - c
+            if kind == "sphere":
+                dist = np.sqrt((q * q).sum(-1)) - prm
+            else:
+                radii, e, Rm = prm
+                ql = (q @ Rm) / radii
+                f = (np.abs(ql[..., 0]) ** e + np.abs(ql[..., 1]) ** e +
+                     np.abs(ql[..., 2]) ** e) ** (1.0 / e)
+                dist = (f - 1.0) * radii.min()
+            acc = dist if acc is None else _smin(acc, dist, k)
+        out[z0:z0 + acc.shape[0]] = acc
+    return out
+
+
+def capsule_body(g):
+    """A 15-capsule articulated figure in a seeded random pose, in a
+    [0,1] x [0,2] x [0,1] box (y up)."""
+    def rot(axis, ang):
+        axis = np.asarray(axis, float)
+        axis /= np.linalg.norm(axis)
+        K = np.array([[0, -axis[2], axis[1]], [axis[2], 0, -axis[0]], [-axis[1], axis[0], 0]])
+        return np.eye(3) + math.sin(ang) * K + (1 - math.cos(ang)) * K @ K
+
+    def jitter(scale=0.35):
+        return rot(g.normal(size=3), g.uniform(-scale, scale))
+
+    caps = []
+    pelvis = np.array([0.5, 0.95, 0.5]) + g.uniform(-0.03, 0.03, size=3)
+    up = np.array([0.0, 1.0, 0.0])
+    chest = pelvis + jitter(0.2) @ up * 0.45
+    caps.append((pelvis, chest, 0.13))
+    neck = chest + jitter(0.2) @ up * 0.12
+    caps.append((chest, neck, 0.05))
+    head = neck + jitter(0.3) @ up * 0.14
+    caps.append((neck + up * 0.03, head, 0.085))
+    for side in (-1.0, 1.0):
+        sh = chest + np.array([0.17 * side, -0.04, 0.0])
+        caps.append((chest, sh, 0.06))
+        elbow = sh + jitter(0.8) @ np.array([0.12 * side, -0.25, 0.0])
+        caps.append((sh, elbow, 0.045))
+        wrist = elbow + jitter(0.8) @ np.array([0.05 * side, -0.24, 0.05])
+        caps.append((elbow, wrist, 0.038))
+        hip = pelvis + np.array([0.09 * side, -0.03, 0.0])
+        knee = hip + jitter(0.4) @ np.array([0.0, -0.42, 0.03])
+        caps.append((hip, knee, 0.07))
+        ankle = knee + jitter(0.4) @ np.array([0.0, -0.40, -0.03])
+        caps.append((knee, ankle, 0.055))
+    caps.append((pelvis + np.array([-0.1, 0.0, 0.0]), pelvis + np.array([0.1, 0.0, 0.0]), 0.11))
+    assert len(caps) == 15
+    return caps
+
+
+def capsule_sdf(dims, box_min, box_max, caps, k=0.04, slab=16):
+    Rx, Ry, Rz = dims
+    out = np.empty((Rz, Ry, Rx), np.float32)
+    for z0 in range(0, Rz, slab):
+        X, Y, Z = _node_coords(dims, box_min, box_max, slice(z0, min(Rz, z0 + slab)))
+        P = np.stack([X, Y, Z], -1)
+        acc = None
+        for a, b, rad in caps:
+            ab = b - a
+            h = np.clip(((P - a) @ ab) / (ab @ ab), 0.0, 1.0)
+            q = P - a - h[..., None] * ab
+            dist = np.sqrt((q * q).sum(-1)) - rad
+            acc = dist if acc is None else _smin(acc, dist, k)
+        out[z0:z0 + acc.shape[0]] = acc
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Cameras and rays
+# ----------------------------------------------------------------------------
+
+def fibonacci_sphere(n, hemisphere=False):
+    i = np.arange(n) + 0.5
+    z = 1.0 - i / n if hemisphere else 1.0 - 2.0 * i / n
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    phi = math.pi * (3.0 - math.sqrt(5.0)) * i
+    return np.stack([r * np.cos(phi), r * np.sin(phi), z], -1)
+
+
+def look_at_cameras(positions, target, up=(0.0, 0.0, 1.0)):
+    cams = []
+    up = np.asarray(up, float)
+    for p in positions:
+        fwd = target - p
+        fwd /= np.linalg.norm(fwd)
+        u = up if abs(fwd @ up) < 0.99 else np.array([1.0, 0.0, 0.0])
+        right = np.cross(fwd, u)
+        right /= np.linalg.norm(right)
+        cup = np.cross(right, fwd)
+        cams.append((np.asarray(p, float), fwd, right, cup))
+    return cams
+
+
+def pixel_rays(cams, width, height, fov_deg, n_rays, g, per_camera=None):
+    """Random pixel rays: uniform camera choice (or a fixed count per camera),
+    uniform pixel; origins at the camera centre, FP64 unit directions rounded
+    to FP32."""
+    tan_half = math.tan(math.radians(fov_deg) * 0.5)
+    aspect = width / height
+    if per_camera is not None:
+        cam_idx = np.repeat(np.arange(len(cams)), per_camera)
+    else:
+        cam_idx = g.integers(0, len(cams), size=n_rays)
+    px = g.integers(0, width, size=cam_idx.size)
+    py = g.integers(0, height, size=cam_idx.size)
+    o = np.empty((cam_idx.size, 3))
+    d = np.empty((cam_idx.size, 3))
+    for ci, (p, fwd, right, cup) in enumerate(cams):
+        sel = cam_idx == ci
+        sx = (2.0 * (px[sel] + 0.5) / width - 1.0) * tan_half * aspect
+        sy = (1.0 - 2.0 * (py[sel] + 0.5) / height) * tan_half
+        dd = fwd[None] + sx[:, None] * right[None] + sy[:, None] * cup[None]
+        dd /= np.linalg.norm(dd, axis=1, keepdims=True)
+        o[sel] = p
+        d[sel] = dd
+    return o.astype(np.float32), d.astype(np.float32)
+
+
+def image_rays(cam, width, height, fov_deg):
+    """Every pixel of one camera, row-major."""
+    p, fwd, right, cup = cam
+    tan_half = math.tan(math.radians(fov_deg) * 0.5)
+    aspect = width / height
+    jj, ii = np.meshgrid(np.arange(height), np.arange(width), indexing="ij")
+    sx = (2.0 * (ii + 0.5) / width - 1.0) * tan_half * aspect
+    sy = (1.0 - 2.0 * (jj + 0.5) / height) * tan_half
+    dd = fwd + sx[..., None] * right + sy[..., None] * cup
+    dd /= np.linalg.norm(dd, axis=-1, keepdims=True)
+    o = np.broadcast_to(p, dd.shape)
+    return o.reshape(-1, 3).astype(np.float32), dd.reshape(-1, 3).astype(np.float32)
+
+
+# ----------------------------------------------------------------------------
+# Recipes
+# ----------------------------------------------------------------------------
+
+WORKLOADS = {
+    "sphere64": dict(seed=1235, R=(64, 64, 64), P=(16, 16, 16), box=((0, 0, 0), (1, 1, 1)),
+                     n_s=3, n_a=4, sh_l=3, width=16, K=3, n_samples=128, tau=64.0,
+                     n_rays=4096, cams=8, res=(128, 128), fov=50.0, cam_r=2.0),
+    "object256": dict(seed=1236, R=(256, 256, 256), P=(32, 32, 32), box=((0, 0, 0), (1, 1, 1)),
+                      n_s=3, n_a=4, sh_l=3, width=32, K=3, n_samples=256, tau=64.0,
+                      n_rays=1 << 18, cams=49, res=(1600, 1200), fov=45.0, cam_r=2.0),
+    "human384": dict(seed=1237, R=(384, 768, 384), P=(48, 96, 48), box=((0, 0, 0), (1, 2, 1)),
+                     n_s=3, n_a=4, sh_l=3, width=32, K=3, n_samples=256, tau=64.0,
+                     n_rays=1 << 19, cams=64, res=(2048, 2048), fov=60.0, cam_r=2.5),
+    "stress512": dict(seed=1239, R=(512, 512, 512), P=(64, 64, 64), box=((0, 0, 0), (1, 1, 1)),
+                      n_s=3, n_a=8, sh_l=3, width=32, K=3, n_samples=512, tau=64.0,
+                      n_rays=1 << 20, cams=49, res=(1600, 1200), fov=45.0, cam_r=2.0),
+}
+
+
+def _make_scene_arrays(name, g, spec, dims=None, probe_dims=None):
+    dims = tuple(dims or spec["R"])
+    probe_dims = tuple(probe_dims or spec["P"])
+    bmin = np.array(spec["box"][0], np.float64)
+    bmax = np.array(spec["box"][1], np.float64)
+    Rx, Ry, Rz = dims
+    if name == "sphere64":
+        sdf = sphere_sdf(dims, bmin, bmax, (0.5, 0.5, 0.5), 0.5)
+        sdf = sdf + g.normal(0.0, 0.01, size=sdf.shape)
+    elif name in ("object256", "stress512"):
+        sdf = object_sdf(dims, bmin, bmax, object_shapes(g, 32))
+    elif name == "human384":
+        sdf = capsule_sdf(dims, bmin, bmax, capsule_body(g))
+    else:
+        raise KeyError(name)
+    sdf = sdf.astype(np.float32)
+    feat = g.normal(0.0, 0.1, size=(Rz, Ry, Rx, spec["n_s"])).astype(np.float32)
+    Px, Py, Pz = probe_dims
+    probes = g.normal(0.0, 0.1, size=(Pz, Py, Px, spec["sh_l"] ** 2, spec["n_a"]))
+    n_in = spec["n_s"] + spec["n_a"] + spec["K"]
+    mlp = mlp_params(n_in, spec["width"], g)
+    return Scene(sdf=sdf, feat=feat, probes=probes.astype(np.float32), mlp=mlp,
+                 box_min=bmin.astype(np.float32), box_max=bmax.astype(np.float32),
+                 sh_l=spec["sh_l"], width=spec["width"], n_fresnel=spec["K"])
+
+
+def make_scene(name: str, dims=None, probe_dims=None) -> Scene:
+    spec = WORKLOADS[name]
+    return _make_scene_arrays(name, rng(spec["seed"]), spec, dims, probe_dims)
+
+
+def make_rays(name: str, n_rays: int | None = None, seed_offset: int = 0) -> Rays:
+    spec = WORKLOADS[name]
+    g = rng(spec["seed"] * 7919 + 17 + seed_offset)
+    n = int(n_rays if n_rays is not None else spec["n_rays"])
+    bmin = np.array(spec["box"][0], float)
+    bmax = np.array(spec["box"][1], float)
+    center = 0.5 * (bmin + bmax)
+    W, H = spec["res"]
+    if name == "human384":
+        ang = 2 * math.pi * (np.arange(spec["cams"]) + 0.5) / spec["cams"]
+        pos = np.stack([center[0] + spec["cam_r"] * np.cos(ang),
+                        np.full_like(ang, center[1]),
+                        center[2] + spec["cam_r"] * np.sin(ang)], -1)
+        cams = look_at_cameras(pos, center, up=(0.0, 1.0, 0.0))
+    else:
+        hemi = name != "sphere64"
+        pos = center + spec["cam_r"] * fibonacci_sphere(spec["cams"], hemisphere=hemi)
+        cams = look_at_cameras(pos, center)
+    if name == "sphere64" and n_rays is None:
+        o, d = pixel_rays(cams, W, H, spec["fov"], n, g, per_camera=n // spec["cams"])
+    else:
+        o, d = pixel_rays(cams, W, H, spec["fov"], n, g)
+    target = g.uniform(0.0, 1.0, size=(o.shape[0], 3)).astype(np.float32)
+    return Rays(o=o, d=d, target=target)
+
+
+def random_unit_vectors(n, g):
+    v = g.normal(size=(n, 3))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
