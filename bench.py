@@ -1,0 +1,379 @@
+"""Throughput of the fused ProbeSDF training step (render forward + adjoint).
+
+One step = one pass of the hot path over one batch: the forward render of
+every ray (trilinear SDF / normal / feature gathers, probe-blended SH angular
+features, Fresnel inputs, colour MLP, NeuS compositing), the L1 photometric
+loss gradient, and the adjoint kernel that recomputes every per-sample
+activation and accumulates gradients for the SDF grid, features, probes and
+MLP.  Default workload: the object-capture shape, a 256^3 grid, 32^3 probes,
+MLP 10->32->32->3, 2^18 rays x 256 samples, FP32.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank renders its own
+batch (weak scaling, replicas, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fused fwd+bwd samples/s per train step"
+
+WORKLOAD = "object256"
+WORKLOAD_DESC = ("object-capture training step: 256^3 SDF grid (smooth-min union of 32 "
+                 "spheres/superquadrics) + 3 FP32 features/node, probes 32^3 x 9 SH x 4 ch, "
+                 "MLP 10->32->32->3, 49 cameras 1600x1200 on a hemisphere, 2^18 random pixel "
+                 "rays x 256 samples, tau 64, L1 loss")
+
+# Algorithmic bytes per sample (one trilinear cell gather of the 16-byte node
+# records, gradients read-modify-written in FP32): forward 8 x 16 B; adjoint
+# 8 x 16 B recompute + 2 x 8 x 16 B gradient read-modify-write.
+BYTES_FWD = 128
+BYTES_BWD = 384
+BYTES_STEP = BYTES_FWD + BYTES_BWD
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--rays", type=int, default=1 << 18)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-rays", type=int, default=0, help="rays of the oracle sample (0 = auto)")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for name, val in zip(names, r[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.rows)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def reduce_max(value, world, device=None):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world, device=None):
+    if world > 1:
+        import torch.distributed as dist
+        if device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (the --impl reference arm and the cpu_baseline object)
+# ---------------------------------------------------------------------------
+
+def oracle_rate(sc, rays, n_rays, tau, N, threads):
+    """Oracle forward + adjoint (the same L1 step) on n_rays of the workload:
+    returns (samples/s, seconds)."""
+    import numpy as np
+
+    import oracle
+    m = oracle.Model.from_scene(sc)
+    o, d, tgt = rays.o[:n_rays], rays.d[:n_rays], rays.target[:n_rays]
+    t0 = time.perf_counter()
+    fw = oracle.render_forward(m, o, d, tau, N, n_threads=threads)
+    drgb = np.sign(fw["rgb"] - tgt) / (3.0 * n_rays)
+    oracle.render_backward(m, o, d, drgb, tau, N, n_threads=threads)
+    dt = time.perf_counter() - t0
+    return n_rays * N / dt, dt
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def auto_cpu_rays(sc, rays, tau, N, threads, target_s=12.0):
+    rate, _ = oracle_rate(sc, rays, 64, tau, N, threads)
+    n = int(rate * target_s / N)
+    return max(64, min(n, rays.o.shape[0]))
+
+
+def run_reference(args, world, rank):
+    import synth
+    if rank != 0:
+        return
+    sc = synth.make_scene(WORKLOAD)
+    rays = synth.make_rays(WORKLOAD, n_rays=args.rays)
+    tau, N = 64.0, 256
+    threads = cpu_cores()
+    per_step_s = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    n = args.cpu_rays or auto_cpu_rays(sc, rays, tau, N, threads, target_s=per_step_s)
+    for _ in range(args.warmup):
+        oracle_rate(sc, rays, n, tau, N, threads)
+    total = 0.0
+    for _ in range(args.steps):
+        _, dt = oracle_rate(sc, rays, n, tau, N, threads)
+        total += dt
+    value = args.steps * n * N / total
+    sample = f"{n} of the workload's rays x {N} samples per step, FP64 oracle forward + adjoint"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "rays_per_step": n, "samples_per_ray": N},
+        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_2412_10084_gb300 as ps
+    import synth
+
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    sc = synth.make_scene(WORKLOAD)
+    rays = synth.make_rays(WORKLOAD, n_rays=args.rays, seed_offset=rank)
+    tau, N = 64.0, 256
+    n = rays.o.shape[0]
+    samples = n * N
+    scene = ps.Scene.from_host(sc, device=device)
+    params = ps.render_params(tau, N, ps.DIR_REFLECT, sc.n_fresnel)
+    o = torch.as_tensor(rays.o, device=device)
+    d = torch.as_tensor(rays.d, device=device)
+    tgt = torch.as_tensor(rays.target, device=device)
+    gg = torch.zeros_like(scene.grid)
+    gp = torch.zeros_like(scene.probes)
+    gm = torch.zeros_like(scene.mlp)
+    stream = torch.cuda.current_stream(device)
+    ev = {k: [] for k in ("fwd0", "fwd1", "bwd1")}
+
+    def step(record=False):
+        gg.zero_()
+        gp.zero_()
+        gm.zero_()
+        if record:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        rgb, depth, wsum, logT = ps.render_forward(scene, o, d, params)
+        if record:
+            e1 = torch.cuda.Event(enable_timing=True)
+            e1.record(stream)
+        d_rgb = torch.sign(rgb - tgt) * (1.0 / (3.0 * n))  # L1 loss gradient
+        if record:
+            e2 = torch.cuda.Event(enable_timing=True)
+            e2.record(stream)
+        ps.render_backward(scene, o, d, params, d_rgb, logT, grads=(gg, gp, gm))
+        if record:
+            e3 = torch.cuda.Event(enable_timing=True)
+            e3.record(stream)
+            ev["fwd0"].append((e0, e1))
+            ev["bwd1"].append((e2, e3))
+        return rgb
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(device)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world, device)
+    torch.cuda.synchronize(device)
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(args.steps):
+        step(record=True)
+    stop.record(stream)
+    torch.cuda.synchronize(device)
+    barrier(world, device)
+    elapsed_ms = start.elapsed_time(stop)
+    clk = clocks.stop()
+    elapsed_ms = reduce_max(elapsed_ms, world, device)
+    fwd_ms = statistics.mean(a.elapsed_time(b) for a, b in ev["fwd0"])
+    bwd_ms = statistics.mean(a.elapsed_time(b) for a, b in ev["bwd1"])
+
+    # End to end through the public API with host buffers: pinned host rays and
+    # targets copied in, the loss read back, every step.
+    h_o = torch.as_tensor(rays.o).pin_memory()
+    h_d = torch.as_tensor(rays.d).pin_memory()
+    h_t = torch.as_tensor(rays.target).pin_memory()
+    scene.grid.requires_grad_(True)
+    scene.probes.requires_grad_(True)
+    scene.mlp.requires_grad_(True)
+
+    def e2e_step():
+        for p in (scene.grid, scene.probes, scene.mlp):
+            p.grad = None
+        o_ = h_o.to(device, non_blocking=True)
+        d_ = h_d.to(device, non_blocking=True)
+        t_ = h_t.to(device, non_blocking=True)
+        rgb, _, _ = ps.render(scene, o_, d_, params)
+        loss = (rgb - t_).abs().mean()
+        loss.backward()
+        return float(loss.item())
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize(device)
+    barrier(world, device)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize(device)
+    e2e_s = reduce_max(time.perf_counter() - t0, world, device)
+    scene.grid.requires_grad_(False)
+
+    if rank != 0:
+        return
+    peak, peak_kind = measured_peaks()
+    bwd_gbs = BYTES_BWD * samples / (bwd_ms * 1e-3) / 1e9
+    fwd_gbs = BYTES_FWD * samples / (fwd_ms * 1e-3) / 1e9
+    ms_per_step = elapsed_ms / args.steps
+    value = world * samples / (ms_per_step * 1e-3)
+    step_gbs = BYTES_STEP * samples / (ms_per_step * 1e-3) / 1e9
+    out = {
+        "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "rays_per_gpu": n, "samples_per_ray": N,
+                   "grid": "256^3 x 16 B packed nodes (268 MB)", "probes": "32^3 x 9 x 4 FP32",
+                   "mlp": "10->32->32->3 FP32",
+                   "l2": "inputs larger than L2: packed grid 268 MB + gradient grid 268 MB "
+                         "vs 126 MB L2; no explicit flush",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": "render_backward_kernel",
+                     "achieved": bwd_gbs, "peak": peak, "unit": "GB/s",
+                     "frac": bwd_gbs / peak, "traffic": None,
+                     "bytes_per_sample": BYTES_BWD, "peak_kind": peak_kind,
+                     "launch_ms": bwd_ms},
+        "roofline_forward": {"bound": "hbm", "kernel": "render_forward_kernel",
+                             "achieved": fwd_gbs, "peak": peak, "unit": "GB/s",
+                             "frac": fwd_gbs / peak, "bytes_per_sample": BYTES_FWD,
+                             "launch_ms": fwd_ms},
+        "roofline_step": {"achieved": step_gbs, "peak": peak, "unit": "GB/s",
+                          "frac": step_gbs / peak, "bytes_per_sample": BYTES_STEP},
+        "e2e": {"value": world * samples / (e2e_s / args.steps), "unit": "samples/s",
+                "h2d_bytes_per_step": int(h_o.numel() * 4 + h_d.numel() * 4 + h_t.numel() * 4),
+                "d2h_bytes_per_step": 4},
+        "clocks": clk,
+        "gpu_launches": 2 * args.steps,
+        "rays_per_s": world * n / (ms_per_step * 1e-3),
+    }
+    if not args.no_cpu_baseline:
+        threads = cpu_cores()
+        nr = args.cpu_rays or auto_cpu_rays(sc, rays, tau, N, threads)
+        rate, secs = oracle_rate(sc, rays, nr, tau, N, threads)
+        out["cpu_baseline"] = {"value": rate, "unit": "samples/s", "cores": threads,
+                               "kind": "oracle",
+                               "sample": f"{nr} rays x {N} samples of the same workload, FP64 "
+                                         f"forward + adjoint, {secs:.1f} s"}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * probesdf.h — C ABI of the GB300 (sm_103a) ProbeSDF per-ray render library.
+ *
+ * The library evaluates the appearance and rendering model of ProbeSDF
+ * ("Light Field Probes For Neural Surface Reconstruction", CVPR 2025) for a
+ * batch of camera rays, and its adjoint:
+ *   - an explicit SDF grid, read by trilinear interpolation, with the normal
+ *     taken from the SDF gradient (Sec. 3, Eq. 13);
+ *   - spatial features F_s interpolated from the same grid nodes (Sec. 3.1);
+ *   - angular features F_a: spherical-harmonic coefficients stored on a
+ *     coarse probe grid, blended trilinearly and evaluated in the reflected
+ *     (or view) direction (Sec. 3.2, Eqs. 5-7);
+ *   - Fresnel inputs (1 - n.v)^k (Sec. 3.1, Eq. 4);
+ *   - a 2-hidden-layer ReLU MLP with a sigmoid output (Sec. 4);
+ *   - NeuS opacities and front-to-back alpha compositing of colour, depth
+ *     and accumulated weight (Sec. 3.3, Eqs. 8-10).
+ *
+ * Conventions for every entry point:
+ *   - Every pointer marked "device" is a CUDA device pointer owned by the
+ *     caller, contiguous, 16-byte aligned, and valid on `stream` for the
+ *     duration of the work enqueued by the call.  The library never frees or
+ *     retains device memory and allocates no device memory.
+ *   - Handles (psdf_grid, psdf_probes, psdf_mlp) are small host structs that
+ *     hold a copy of the descriptor and a NON-owning device pointer to the
+ *     parameter values.  Destroying a handle frees only the host struct.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Calls are asynchronous with respect to the host.
+ *   - Errors found on the host (bad descriptor, null or misaligned pointer,
+ *     unsupported combination) return immediately with a negative status and
+ *     enqueue nothing.  A failing CUDA launch returns PSDF_ERR_CUDA; the
+ *     cudaError_t is available from psdf_last_cuda_error() on the same host
+ *     thread.  No C++ exception crosses this boundary.
+ *   - Nothing here synchronises the stream.
+ *
+ * Axes: dims[0..2] are the node counts along x, y, z; arrays are stored with
+ * x fastest ([z][y][x]).  Both grids span the same box and are node-aligned:
+ * node i along an axis sits at box_min + i (box_max - box_min) / (dims - 1).
+ */
+#ifndef PROBESDF_H
+#define PROBESDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t psdf_status;
+
+#define PSDF_OK 0
+#define PSDF_ERR_INVALID_ARG -1   /* null pointer, negative count, bad enum */
+#define PSDF_ERR_BAD_SHAPE -2     /* a dimension outside the supported range */
+#define PSDF_ERR_BAD_DTYPE -3     /* a dtype enum the call does not take */
+#define PSDF_ERR_MISALIGNED -4    /* a device pointer not 16-byte aligned */
+#define PSDF_ERR_CUDA -5          /* a CUDA call failed; see psdf_last_cuda_error */
+#define PSDF_ERR_UNSUPPORTED -6   /* a valid but not compiled-in combination */
+
+#define PSDF_F32 0
+
+#define PSDF_DIR_REFLECT 0  /* F_a looked up with r = 2(n.v)n - v (Sec. 3.1) */
+#define PSDF_DIR_VIEW 1     /* F_a looked up with v, for retro-reflective materials (Sec. 3.1) */
+
+#define PSDF_GRID_VALUES 0
+#define PSDF_GRID_GRAD 1
+
+/* SDF + spatial-feature grid (Sec. 3, "explicit SDF grid"; Sec. 3.1 F_s). */
+typedef struct psdf_grid_desc {
+    int32_t dims[3];     /* nodes along x, y, z; each in [2, 4096], product < 2^31 */
+    float box_min[3];    /* world-space box spanned by the nodes */
+    float box_max[3];    /* box_max > box_min on every axis */
+    int32_t n_feat;      /* spatial features per node (n_s); 3 is compiled in */
+    int32_t feat_dtype;  /* PSDF_F32 */
+} psdf_grid_desc;
+
+/* Light-field probe grid (Sec. 3.2): l*l SH coefficients of n_a channels. */
+typedef struct psdf_probe_desc {
+    int32_t dims[3];     /* probe nodes along x, y, z over the grid's box; each >= 2 */
+    int32_t sh_l;        /* SH order l, 1-indexed as in Eq. 5 (l*l coefficients); 3 compiled in */
+    int32_t n_ang;       /* angular channels n_a; 4 and 8 compiled in */
+    int32_t dtype;       /* PSDF_F32 */
+} psdf_probe_desc;
+
+/* Colour MLP (Sec. 4): n_in -> width -> width -> 3, ReLU, ReLU, sigmoid.
+ * n_in = n_s + n_a + n_fresnel; parameters packed row-major as
+ * W1[width][n_in] b1[width] W2[width][width] b2[width] W3[3][width] b3[3]. */
+typedef struct psdf_mlp_desc {
+    int32_t n_in;
+    int32_t width;       /* 16 and 32 compiled in */
+    int32_t dtype;       /* PSDF_F32 */
+} psdf_mlp_desc;
+
+typedef struct psdf_render_params {
+    float tau;           /* NeuS logistic scale of Eq. 10, > 0 */
+    int32_t n_samples;   /* N colour samples per ray (N+1 SDF points), in [1, 4096] */
+    int32_t dir_mode;    /* PSDF_DIR_REFLECT or PSDF_DIR_VIEW */
+    int32_t n_fresnel;   /* K: inputs (1 - n.v)^1..K (Eq. 4 uses powers of 1 - n.v); 3 compiled in */
+    float bg[3];         /* background colour added with the final transmittance */
+} psdf_render_params;
+
+typedef struct psdf_grid psdf_grid;
+typedef struct psdf_probes psdf_probes;
+typedef struct psdf_mlp psdf_mlp;
+
+/* Human-readable text of a status code (static storage). */
+const char* psdf_status_string(psdf_status status);
+
+/* cudaError_t (as int) of the last call on this host thread that returned
+ * PSDF_ERR_CUDA; 0 if none. */
+int32_t psdf_last_cuda_error(void);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int32_t psdf_version(void);
+
+/* Bytes of the packed grid layout: one 16-byte record {sdf, f0, f1, f2} per
+ * node, in the library's own node order.  The gradient buffer of
+ * psdf_render_backward has the same size and layout (FP32). */
+psdf_status psdf_grid_bytes(const psdf_grid_desc* desc, size_t* values_bytes);
+
+/* Handle over caller-owned packed values (device, psdf_grid_bytes bytes). */
+psdf_status psdf_grid_create(const psdf_grid_desc* desc, const void* values, psdf_grid** out);
+void psdf_grid_destroy(psdf_grid* grid);
+
+/* Dense <-> packed conversion on `stream`.
+ * pack:   sdf (device, FP32 [Rz][Ry][Rx]) and feat (device, FP32
+ *         [Rz][Ry][Rx][n_feat]) -> packed (device, psdf_grid_bytes bytes).
+ * unpack: packed values or gradients (device) -> the two dense arrays. */
+psdf_status psdf_grid_pack(const psdf_grid_desc* desc, const float* sdf, const float* feat,
+                           void* packed, void* stream);
+psdf_status psdf_grid_unpack(const psdf_grid_desc* desc, const void* packed, float* sdf,
+                             float* feat, void* stream);
+
+/* Probe coefficients (device, FP32 [Pz][Py][Px][l*l][n_a]); the layout is the
+ * caller's, no packing. */
+psdf_status psdf_probes_create(const psdf_probe_desc* desc, const void* coeffs,
+                               psdf_probes** out);
+void psdf_probes_destroy(psdf_probes* probes);
+
+/* MLP parameters (device, FP32, packed as in psdf_mlp_desc). */
+psdf_status psdf_mlp_param_count(const psdf_mlp_desc* desc, int64_t* count);
+psdf_status psdf_mlp_create(const psdf_mlp_desc* desc, const void* params, psdf_mlp** out);
+void psdf_mlp_destroy(psdf_mlp* mlp);
+
+/* Forward render (Eqs. 4-10, Sec. 4) of n_rays rays.
+ *   rays_o, rays_d : device FP32 [n_rays][3]; rays_d must be unit length
+ *                    (used as given; t is then a distance).
+ *   t_samples      : NULL for N evenly spaced samples over the ray's segment
+ *                    inside the box (slab test, t >= 0), or device FP32
+ *                    [n_rays][N+1] of increasing sample distances (a ray with
+ *                    t[N] <= t[0] is treated as a miss).
+ *   rgb            : device FP32 [n_rays][3] = sum_k w_k C_k + T_N bg
+ *   depth          : device FP32 [n_rays]    = sum_k w_k t_k
+ *   wsum           : device FP32 [n_rays]    = sum_k w_k
+ *   logT_final     : device FP32 [n_rays]    = log T_N, needed by the backward
+ * Rays that miss the box give rgb = bg and zeros elsewhere.  n_rays = 0 is a
+ * valid no-op. */
+psdf_status psdf_render_forward(const psdf_grid* grid, const psdf_probes* probes,
+                                const psdf_mlp* mlp, const psdf_render_params* params,
+                                const float* rays_o, const float* rays_d,
+                                const float* t_samples, int64_t n_rays, float* rgb,
+                                float* depth, float* wsum, float* logT_final, void* stream);
+
+/* Adjoint of psdf_render_forward (Sec. 3.3-3.4: gradients for the SDF
+ * values, spatial features, probe coefficients and MLP weights).  The
+ * per-sample activations are recomputed, not stored.
+ *   d_rgb          : device FP32 [n_rays][3] (required)
+ *   d_depth, d_wsum: device FP32 [n_rays] or NULL (= zero)
+ *   logT_final     : the forward's output for the same inputs
+ *   grad_grid      : device FP32, psdf_grid_bytes bytes, packed like the values
+ *   grad_probes    : device FP32 [Pz][Py][Px][l*l][n_a]
+ *   grad_mlp       : device FP32 [psdf_mlp_param_count]
+ * Gradients are ACCUMULATED (+=) with atomics, so their summation order is
+ * not fixed; zero them first for a fresh gradient.  All three gradient
+ * pointers are required. */
+psdf_status psdf_render_backward(const psdf_grid* grid, const psdf_probes* probes,
+                                 const psdf_mlp* mlp, const psdf_render_params* params,
+                                 const float* rays_o, const float* rays_d,
+                                 const float* t_samples, int64_t n_rays, const float* d_rgb,
+                                 const float* d_depth, const float* d_wsum,
+                                 const float* logT_final, float* grad_grid,
+                                 float* grad_probes, float* grad_mlp, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PROBESDF_H */

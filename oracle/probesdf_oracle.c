@@ -82,7 +82,7 @@ static void locate_f32(const float x[3], const float bmin[3], const float sc[3],
         float u = (x[a] - bmin[a]) * sc[a];
         float fl = floorf(u);
         float hi = (float)(dims[a] - 2);
-        if (fl < 0.0f) fl = 0.0f;
+        if (!(fl >= 0.0f)) fl = 0.0f; /* also maps NaN to cell 0: indices stay in bounds */
         if (fl > hi) fl = hi;
         idx[a] = (int)fl;
         frac[a] = (double)(u - fl);

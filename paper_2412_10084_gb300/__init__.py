@@ -1,0 +1,335 @@
+"""GB300 (sm_103a) ProbeSDF per-ray render and adjoint.
+
+A thin ctypes binding over ``libprobesdf.so`` (C ABI in include/probesdf.h):
+argument marshalling only, every step of the render and its adjoint runs in
+the library's CUDA kernels.  PyTorch provides device memory and streams.
+
+There is no CPU fallback: if the library cannot be built or loaded, or no
+CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+__all__ = [
+    "GridDesc", "ProbeDesc", "MlpDesc", "RenderParams", "Scene", "LibraryError",
+    "library", "grid_bytes", "mlp_param_count", "pack_grid", "unpack_grid",
+    "render_forward", "render_backward", "render", "DIR_REFLECT", "DIR_VIEW",
+]
+
+DIR_REFLECT = 0
+DIR_VIEW = 1
+F32 = 0
+
+
+class LibraryError(RuntimeError):
+    pass
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int32 * 3), ("box_min", ctypes.c_float * 3),
+                ("box_max", ctypes.c_float * 3), ("n_feat", ctypes.c_int32),
+                ("feat_dtype", ctypes.c_int32)]
+
+
+class ProbeDesc(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int32 * 3), ("sh_l", ctypes.c_int32),
+                ("n_ang", ctypes.c_int32), ("dtype", ctypes.c_int32)]
+
+
+class MlpDesc(ctypes.Structure):
+    _fields_ = [("n_in", ctypes.c_int32), ("width", ctypes.c_int32), ("dtype", ctypes.c_int32)]
+
+
+class RenderParams(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_float), ("n_samples", ctypes.c_int32),
+                ("dir_mode", ctypes.c_int32), ("n_fresnel", ctypes.c_int32),
+                ("bg", ctypes.c_float * 3)]
+
+
+_lock = threading.Lock()
+_lib = None
+_P = ctypes.c_void_p
+
+
+def library() -> ctypes.CDLL:
+    """Load (building first if needed) libprobesdf.so and declare its ABI."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        lib.psdf_status_string.restype = ctypes.c_char_p
+        lib.psdf_status_string.argtypes = [ctypes.c_int32]
+        lib.psdf_last_cuda_error.restype = ctypes.c_int32
+        lib.psdf_version.restype = ctypes.c_int32
+        lib.psdf_grid_bytes.argtypes = [_P, ctypes.POINTER(ctypes.c_size_t)]
+        lib.psdf_grid_create.argtypes = [_P, _P, ctypes.POINTER(_P)]
+        lib.psdf_grid_destroy.argtypes = [_P]
+        lib.psdf_grid_destroy.restype = None
+        lib.psdf_grid_pack.argtypes = [_P, _P, _P, _P, _P]
+        lib.psdf_grid_unpack.argtypes = [_P, _P, _P, _P, _P]
+        lib.psdf_probes_create.argtypes = [_P, _P, ctypes.POINTER(_P)]
+        lib.psdf_probes_destroy.argtypes = [_P]
+        lib.psdf_probes_destroy.restype = None
+        lib.psdf_mlp_param_count.argtypes = [_P, ctypes.POINTER(ctypes.c_int64)]
+        lib.psdf_mlp_create.argtypes = [_P, _P, ctypes.POINTER(_P)]
+        lib.psdf_mlp_destroy.argtypes = [_P]
+        lib.psdf_mlp_destroy.restype = None
+        lib.psdf_render_forward.argtypes = [_P, _P, _P, _P, _P, _P, _P, ctypes.c_int64,
+                                            _P, _P, _P, _P, _P]
+        lib.psdf_render_backward.argtypes = [_P, _P, _P, _P, _P, _P, _P, ctypes.c_int64,
+                                             _P, _P, _P, _P, _P, _P, _P, _P]
+        for name in ("psdf_grid_bytes", "psdf_grid_create", "psdf_grid_pack", "psdf_grid_unpack",
+                     "psdf_probes_create", "psdf_mlp_param_count", "psdf_mlp_create",
+                     "psdf_render_forward", "psdf_render_backward"):
+            getattr(lib, name).restype = ctypes.c_int32
+        _lib = lib
+        return lib
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        lib = library()
+        msg = lib.psdf_status_string(status).decode()
+        extra = ""
+        if status == -5:
+            extra = f" (cudaError {lib.psdf_last_cuda_error()})"
+        raise LibraryError(f"{what}: {msg}{extra}")
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _require_cuda(*tensors):
+    for t in tensors:
+        if t is not None:
+            if not t.is_cuda:
+                raise LibraryError("tensors must be on a CUDA device (there is no CPU path)")
+            if t.dtype != torch.float32:
+                raise LibraryError(f"expected float32, got {t.dtype}")
+            if not t.is_contiguous():
+                raise LibraryError("tensors must be contiguous")
+
+
+def grid_desc(dims, box_min, box_max, n_feat=3) -> GridDesc:
+    d = GridDesc()
+    d.dims[:] = tuple(int(v) for v in dims)
+    d.box_min[:] = tuple(float(v) for v in box_min)
+    d.box_max[:] = tuple(float(v) for v in box_max)
+    d.n_feat = int(n_feat)
+    d.feat_dtype = F32
+    return d
+
+
+def grid_bytes(desc: GridDesc) -> int:
+    n = ctypes.c_size_t()
+    _check(library().psdf_grid_bytes(ctypes.byref(desc), ctypes.byref(n)), "psdf_grid_bytes")
+    return n.value
+
+
+def mlp_param_count(n_in: int, width: int) -> int:
+    d = MlpDesc(n_in, width, F32)
+    n = ctypes.c_int64()
+    _check(library().psdf_mlp_param_count(ctypes.byref(d), ctypes.byref(n)),
+           "psdf_mlp_param_count")
+    return n.value
+
+
+def pack_grid(desc: GridDesc, sdf: torch.Tensor, feat: torch.Tensor) -> torch.Tensor:
+    """Dense sdf [Rz,Ry,Rx] + feat [Rz,Ry,Rx,3] (device FP32) -> packed [Rz*Ry*Rx, 4]."""
+    _require_cuda(sdf, feat)
+    out = torch.empty(grid_bytes(desc) // 4, dtype=torch.float32, device=sdf.device).view(-1, 4)
+    _check(library().psdf_grid_pack(ctypes.byref(desc), _ptr(sdf), _ptr(feat), _ptr(out),
+                                    _stream()), "psdf_grid_pack")
+    return out
+
+
+def unpack_grid(desc: GridDesc, packed: torch.Tensor):
+    """Packed values or gradients -> (sdf [Rz,Ry,Rx], feat [Rz,Ry,Rx,3])."""
+    _require_cuda(packed)
+    Rx, Ry, Rz = desc.dims
+    sdf = torch.empty((Rz, Ry, Rx), dtype=torch.float32, device=packed.device)
+    feat = torch.empty((Rz, Ry, Rx, desc.n_feat), dtype=torch.float32, device=packed.device)
+    _check(library().psdf_grid_unpack(ctypes.byref(desc), _ptr(packed), _ptr(sdf), _ptr(feat),
+                                      _stream()), "psdf_grid_unpack")
+    return sdf, feat
+
+
+@dataclasses.dataclass
+class Scene:
+    """Device-resident parameters: packed grid [R^3,4], probes
+    [Pz,Py,Px,l*l,n_a] and the packed MLP vector, with their descriptors."""
+    grid: torch.Tensor
+    probes: torch.Tensor
+    mlp: torch.Tensor
+    dims: tuple
+    box_min: tuple
+    box_max: tuple
+    sh_l: int
+    width: int
+    n_feat: int = 3
+
+    @property
+    def probe_dims(self):
+        Pz, Py, Px = self.probes.shape[:3]
+        return (Px, Py, Pz)
+
+    @property
+    def n_ang(self):
+        return self.probes.shape[-1]
+
+    def descs(self, n_fresnel):
+        gd = grid_desc(self.dims, self.box_min, self.box_max, self.n_feat)
+        pd = ProbeDesc()
+        pd.dims[:] = self.probe_dims
+        pd.sh_l = self.sh_l
+        pd.n_ang = self.n_ang
+        pd.dtype = F32
+        md = MlpDesc(self.n_feat + self.n_ang + n_fresnel, self.width, F32)
+        return gd, pd, md
+
+    @classmethod
+    def from_host(cls, sc, device="cuda"):
+        """Upload a synth.Scene-like object (numpy arrays) and pack its grid."""
+        dev = torch.device(device)
+        sdf = torch.as_tensor(sc.sdf, dtype=torch.float32, device=dev).contiguous()
+        feat = torch.as_tensor(sc.feat, dtype=torch.float32, device=dev).contiguous()
+        gd = grid_desc(sc.dims, sc.box_min, sc.box_max, sc.feat.shape[-1])
+        grid = pack_grid(gd, sdf, feat)
+        probes = torch.as_tensor(sc.probes, dtype=torch.float32, device=dev).contiguous()
+        mlp = torch.as_tensor(sc.mlp, dtype=torch.float32, device=dev).contiguous()
+        return cls(grid=grid, probes=probes, mlp=mlp, dims=tuple(sc.dims),
+                   box_min=tuple(float(v) for v in sc.box_min),
+                   box_max=tuple(float(v) for v in sc.box_max), sh_l=int(sc.sh_l),
+                   width=int(sc.width), n_feat=int(sc.feat.shape[-1]))
+
+
+def render_params(tau=64.0, n_samples=128, dir_mode=DIR_REFLECT, n_fresnel=3,
+                  bg=(0.0, 0.0, 0.0)) -> RenderParams:
+    p = RenderParams()
+    p.tau = float(tau)
+    p.n_samples = int(n_samples)
+    p.dir_mode = int(dir_mode)
+    p.n_fresnel = int(n_fresnel)
+    p.bg[:] = tuple(float(v) for v in bg)
+    return p
+
+
+class _Handles:
+    """Short-lived C handles over the scene's current device pointers."""
+
+    def __init__(self, grid, probes, mlp, gd, pd, md):
+        lib = library()
+        self.g, self.p, self.m = _P(), _P(), _P()
+        _check(lib.psdf_grid_create(ctypes.byref(gd), _ptr(grid), ctypes.byref(self.g)),
+               "psdf_grid_create")
+        _check(lib.psdf_probes_create(ctypes.byref(pd), _ptr(probes), ctypes.byref(self.p)),
+               "psdf_probes_create")
+        _check(lib.psdf_mlp_create(ctypes.byref(md), _ptr(mlp), ctypes.byref(self.m)),
+               "psdf_mlp_create")
+
+    def close(self):
+        lib = library()
+        lib.psdf_grid_destroy(self.g)
+        lib.psdf_probes_destroy(self.p)
+        lib.psdf_mlp_destroy(self.m)
+
+
+def render_forward(scene: Scene, rays_o, rays_d, params: RenderParams, t_samples=None,
+                   grid=None, probes=None, mlp=None):
+    """-> rgb [n,3], depth [n], wsum [n], logT_final [n] (device FP32)."""
+    grid = scene.grid if grid is None else grid
+    probes = scene.probes if probes is None else probes
+    mlp = scene.mlp if mlp is None else mlp
+    _require_cuda(grid, probes, mlp, rays_o, rays_d, t_samples)
+    n = rays_o.shape[0]
+    dev = rays_o.device
+    rgb = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    depth = torch.empty(n, dtype=torch.float32, device=dev)
+    wsum = torch.empty(n, dtype=torch.float32, device=dev)
+    logT = torch.empty(n, dtype=torch.float32, device=dev)
+    gd, pd, md = scene.descs(params.n_fresnel)
+    h = _Handles(grid, probes, mlp, gd, pd, md)
+    try:
+        _check(library().psdf_render_forward(h.g, h.p, h.m, ctypes.byref(params), _ptr(rays_o),
+                                             _ptr(rays_d), _ptr(t_samples), n, _ptr(rgb),
+                                             _ptr(depth), _ptr(wsum), _ptr(logT), _stream()),
+               "psdf_render_forward")
+    finally:
+        h.close()
+    return rgb, depth, wsum, logT
+
+
+def render_backward(scene: Scene, rays_o, rays_d, params: RenderParams, d_rgb, logT,
+                    d_depth=None, d_wsum=None, t_samples=None, grads=None, grid=None,
+                    probes=None, mlp=None):
+    """Accumulates into (and returns) grad_grid [R^3,4], grad_probes, grad_mlp."""
+    grid = scene.grid if grid is None else grid
+    probes = scene.probes if probes is None else probes
+    mlp = scene.mlp if mlp is None else mlp
+    _require_cuda(grid, probes, mlp, rays_o, rays_d, t_samples, d_rgb, d_depth, d_wsum, logT)
+    if grads is None:
+        grads = (torch.zeros_like(grid), torch.zeros_like(probes), torch.zeros_like(mlp))
+    gg, gp, gm = grads
+    gd, pd, md = scene.descs(params.n_fresnel)
+    h = _Handles(grid, probes, mlp, gd, pd, md)
+    try:
+        _check(library().psdf_render_backward(
+            h.g, h.p, h.m, ctypes.byref(params), _ptr(rays_o), _ptr(rays_d), _ptr(t_samples),
+            rays_o.shape[0], _ptr(d_rgb), _ptr(d_depth), _ptr(d_wsum), _ptr(logT), _ptr(gg),
+            _ptr(gp), _ptr(gm), _stream()), "psdf_render_backward")
+    finally:
+        h.close()
+    return gg, gp, gm
+
+
+class RenderFunction(torch.autograd.Function):
+    """Differentiable render: (grid, probes, mlp) -> (rgb, depth, wsum).  The
+    backward recomputes per-sample activations in the library's adjoint
+    kernel; only log T_N per ray is saved."""
+
+    @staticmethod
+    def forward(ctx, grid, probes, mlp, rays_o, rays_d, t_samples, scene, params):
+        rgb, depth, wsum, logT = render_forward(scene, rays_o, rays_d, params, t_samples,
+                                                grid=grid, probes=probes, mlp=mlp)
+        ctx.save_for_backward(grid, probes, mlp, rays_o, rays_d, logT,
+                              t_samples if t_samples is not None else torch.empty(0))
+        ctx.has_t = t_samples is not None
+        ctx.scene = scene
+        ctx.params = params
+        ctx.mark_non_differentiable(logT)
+        return rgb, depth, wsum
+
+    @staticmethod
+    def backward(ctx, d_rgb, d_depth, d_wsum):
+        grid, probes, mlp, rays_o, rays_d, logT, t_samples = ctx.saved_tensors
+        t_samples = t_samples if ctx.has_t else None
+        d_rgb = torch.zeros((rays_o.shape[0], 3), dtype=torch.float32, device=rays_o.device) \
+            if d_rgb is None else d_rgb.contiguous()
+        d_depth = None if d_depth is None else d_depth.contiguous()
+        d_wsum = None if d_wsum is None else d_wsum.contiguous()
+        gg, gp, gm = render_backward(ctx.scene, rays_o, rays_d, ctx.params, d_rgb, logT,
+                                     d_depth=d_depth, d_wsum=d_wsum, t_samples=t_samples,
+                                     grid=grid, probes=probes, mlp=mlp)
+        return gg, gp, gm, None, None, None, None, None
+
+
+def render(scene: Scene, rays_o, rays_d, params: RenderParams, t_samples=None):
+    """Differentiable w.r.t. scene.grid, scene.probes and scene.mlp."""
+    return RenderFunction.apply(scene.grid, scene.probes, scene.mlp, rays_o, rays_d, t_samples,
+                                scene, params)

@@ -1,0 +1,368 @@
+// C ABI of the ProbeSDF render library: handles, host-side validation,
+// launch configuration, dense <-> packed grid conversion.
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+#include "probesdf.h"
+
+struct psdf_grid {
+    psdf_grid_desc desc;
+    const void* values;
+};
+struct psdf_probes {
+    psdf_probe_desc desc;
+    const void* coeffs;
+};
+struct psdf_mlp {
+    psdf_mlp_desc desc;
+    const void* params;
+};
+
+namespace {
+
+thread_local int32_t g_last_cuda_error = 0;
+
+psdf_status cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return PSDF_OK;
+    g_last_cuda_error = static_cast<int32_t>(e);
+    return PSDF_ERR_CUDA;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+psdf_status check_grid_desc(const psdf_grid_desc* d)
+{
+    if (!d) return PSDF_ERR_INVALID_ARG;
+    int64_t n = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (d->dims[a] < 2 || d->dims[a] > 4096) return PSDF_ERR_BAD_SHAPE;
+        if (!(d->box_max[a] > d->box_min[a])) return PSDF_ERR_BAD_SHAPE;
+        n *= d->dims[a];
+    }
+    if (n >= (int64_t(1) << 31)) return PSDF_ERR_BAD_SHAPE;
+    if (d->feat_dtype != PSDF_F32) return PSDF_ERR_BAD_DTYPE;
+    if (d->n_feat != 3) return PSDF_ERR_UNSUPPORTED;
+    return PSDF_OK;
+}
+
+psdf_status check_probe_desc(const psdf_probe_desc* d)
+{
+    if (!d) return PSDF_ERR_INVALID_ARG;
+    int64_t n = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (d->dims[a] < 2 || d->dims[a] > 4096) return PSDF_ERR_BAD_SHAPE;
+        n *= d->dims[a];
+    }
+    if (d->sh_l < 1 || d->sh_l > 4 || d->n_ang < 1 || d->n_ang > 64) return PSDF_ERR_BAD_SHAPE;
+    if (n * d->sh_l * d->sh_l * d->n_ang >= (int64_t(1) << 31)) return PSDF_ERR_BAD_SHAPE;
+    if (d->dtype != PSDF_F32) return PSDF_ERR_BAD_DTYPE;
+    return PSDF_OK;
+}
+
+psdf_status check_mlp_desc(const psdf_mlp_desc* d)
+{
+    if (!d) return PSDF_ERR_INVALID_ARG;
+    if (d->n_in < 1 || d->n_in > 64 || d->width < 1 || d->width > 256) return PSDF_ERR_BAD_SHAPE;
+    if (d->dtype != PSDF_F32) return PSDF_ERR_BAD_DTYPE;
+    return PSDF_OK;
+}
+
+int64_t mlp_params(const psdf_mlp_desc* d)
+{
+    const int64_t W = d->width, n = d->n_in;
+    return W * n + W + W * W + W + 3 * W + 3;
+}
+
+struct Resolved {
+    psdf::RenderArgs args;
+    psdf::KernelShape shape;
+};
+
+psdf_status resolve(const psdf_grid* grid, const psdf_probes* probes, const psdf_mlp* mlp,
+                    const psdf_render_params* p, const float* rays_o, const float* rays_d,
+                    const float* t_samples, int64_t n_rays, Resolved& r)
+{
+    if (!grid || !probes || !mlp || !p) return PSDF_ERR_INVALID_ARG;
+    if (n_rays < 0) return PSDF_ERR_INVALID_ARG;
+    if (n_rays > 0 && (!rays_o || !rays_d)) return PSDF_ERR_INVALID_ARG;
+    if (!(p->tau > 0.0f) || p->n_samples < 1 || p->n_samples > 4096) return PSDF_ERR_BAD_SHAPE;
+    if (p->dir_mode != PSDF_DIR_REFLECT && p->dir_mode != PSDF_DIR_VIEW)
+        return PSDF_ERR_INVALID_ARG;
+    if (p->n_fresnel < 0 || p->n_fresnel > 8) return PSDF_ERR_BAD_SHAPE;
+    const psdf_grid_desc& gd = grid->desc;
+    const psdf_probe_desc& pd = probes->desc;
+    const psdf_mlp_desc& md = mlp->desc;
+    if (md.n_in != gd.n_feat + pd.n_ang + p->n_fresnel) return PSDF_ERR_BAD_SHAPE;
+    if (!grid->values || !probes->coeffs || !mlp->params) return PSDF_ERR_INVALID_ARG;
+    if (!aligned16(grid->values) || !aligned16(probes->coeffs) || !aligned16(mlp->params))
+        return PSDF_ERR_MISALIGNED;
+    if (!aligned16(rays_o) || !aligned16(rays_d) || !aligned16(t_samples))
+        return PSDF_ERR_MISALIGNED;
+    r.shape.na = pd.n_ang;
+    r.shape.l2 = pd.sh_l * pd.sh_l;
+    r.shape.width = md.width;
+    r.shape.k = p->n_fresnel;
+    bool known = false;
+#define PSDF_KNOWN(NA, L2, W, K)                                                             \
+    if (r.shape.na == NA && r.shape.l2 == L2 && r.shape.width == W && r.shape.k == K) known = true;
+    PSDF_FOR_EACH_SHAPE(PSDF_KNOWN)
+#undef PSDF_KNOWN
+    if (!known) return PSDF_ERR_UNSUPPORTED;
+
+    psdf::RenderArgs& A = r.args;
+    std::memset(&A, 0, sizeof(A));
+    A.grid.nodes = static_cast<const float4*>(grid->values);
+    for (int a = 0; a < 3; ++a) {
+        A.grid.R[a] = gd.dims[a];
+        A.grid.bmin[a] = gd.box_min[a];
+        A.grid.bmax[a] = gd.box_max[a];
+        // (R - 1) / (bmax - bmin) in FP32; the sample positions depend on these bits
+        const volatile float ext = gd.box_max[a] - gd.box_min[a];
+        A.grid.sc[a] = static_cast<float>(gd.dims[a] - 1) / ext;
+        A.probes.P[a] = pd.dims[a];
+        A.probes.sc[a] = static_cast<float>(pd.dims[a] - 1) / ext;
+    }
+    A.probes.coeffs = static_cast<const float4*>(probes->coeffs);
+    A.mlp = static_cast<const float*>(mlp->params);
+    A.tau = p->tau;
+    A.n_samples = p->n_samples;
+    A.dir_mode = p->dir_mode;
+    for (int c = 0; c < 3; ++c) A.bg[c] = p->bg[c];
+    A.rays_o = rays_o;
+    A.rays_d = rays_d;
+    A.t_samples = t_samples;
+    A.n_rays = n_rays;
+    return PSDF_OK;
+}
+
+// Persistent-grid size: every SM filled to its occupancy, capped by the work.
+int grid_size(int64_t n_rays, int ctas_per_sm, int warps_per_cta)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+    if (ctas_per_sm <= 0) ctas_per_sm = 1;
+    const int64_t full = int64_t(sms) * ctas_per_sm;
+    const int64_t need = (n_rays + warps_per_cta - 1) / warps_per_cta;
+    return static_cast<int>(need < full ? need : full);
+}
+
+__global__ void pack_kernel(const float* __restrict__ sdf, const float* __restrict__ feat,
+                            float4* __restrict__ out, int64_t n)
+{
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x)
+        out[i] = make_float4(sdf[i], feat[3 * i], feat[3 * i + 1], feat[3 * i + 2]);
+}
+
+__global__ void unpack_kernel(const float4* __restrict__ in, float* __restrict__ sdf,
+                              float* __restrict__ feat, int64_t n)
+{
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const float4 v = in[i];
+        if (sdf) sdf[i] = v.x;
+        if (feat) {
+            feat[3 * i] = v.y;
+            feat[3 * i + 1] = v.z;
+            feat[3 * i + 2] = v.w;
+        }
+    }
+}
+
+}  // namespace
+
+namespace psdf {
+
+cudaError_t launch_pack(const float* sdf, const float* feat, float4* packed, int64_t n_nodes,
+                        cudaStream_t stream)
+{
+    const int threads = 256;
+    const int64_t blocks = (n_nodes + threads - 1) / threads;
+    pack_kernel<<<(int)(blocks < 65535 * 16 ? blocks : 65535 * 16), threads, 0, stream>>>(
+        sdf, feat, packed, n_nodes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const float4* packed, float* sdf, float* feat, int64_t n_nodes,
+                          cudaStream_t stream)
+{
+    const int threads = 256;
+    const int64_t blocks = (n_nodes + threads - 1) / threads;
+    unpack_kernel<<<(int)(blocks < 65535 * 16 ? blocks : 65535 * 16), threads, 0, stream>>>(
+        packed, sdf, feat, n_nodes);
+    return cudaGetLastError();
+}
+
+}  // namespace psdf
+
+extern "C" {
+
+const char* psdf_status_string(psdf_status s)
+{
+    switch (s) {
+        case PSDF_OK: return "ok";
+        case PSDF_ERR_INVALID_ARG: return "invalid argument";
+        case PSDF_ERR_BAD_SHAPE: return "shape outside the supported range";
+        case PSDF_ERR_BAD_DTYPE: return "unsupported dtype";
+        case PSDF_ERR_MISALIGNED: return "device pointer not 16-byte aligned";
+        case PSDF_ERR_CUDA: return "CUDA error";
+        case PSDF_ERR_UNSUPPORTED: return "combination not compiled in";
+        default: return "unknown status";
+    }
+}
+
+int32_t psdf_last_cuda_error(void) { return g_last_cuda_error; }
+
+int32_t psdf_version(void) { return 100; }
+
+psdf_status psdf_grid_bytes(const psdf_grid_desc* desc, size_t* values_bytes)
+{
+    const psdf_status st = check_grid_desc(desc);
+    if (st != PSDF_OK) return st;
+    if (!values_bytes) return PSDF_ERR_INVALID_ARG;
+    *values_bytes = sizeof(float) * 4 * size_t(desc->dims[0]) * desc->dims[1] * desc->dims[2];
+    return PSDF_OK;
+}
+
+psdf_status psdf_grid_create(const psdf_grid_desc* desc, const void* values, psdf_grid** out)
+{
+    const psdf_status st = check_grid_desc(desc);
+    if (st != PSDF_OK) return st;
+    if (!values || !out) return PSDF_ERR_INVALID_ARG;
+    if (!aligned16(values)) return PSDF_ERR_MISALIGNED;
+    psdf_grid* g = new (std::nothrow) psdf_grid;
+    if (!g) return PSDF_ERR_INVALID_ARG;
+    g->desc = *desc;
+    g->values = values;
+    *out = g;
+    return PSDF_OK;
+}
+
+void psdf_grid_destroy(psdf_grid* grid) { delete grid; }
+
+psdf_status psdf_grid_pack(const psdf_grid_desc* desc, const float* sdf, const float* feat,
+                           void* packed, void* stream)
+{
+    const psdf_status st = check_grid_desc(desc);
+    if (st != PSDF_OK) return st;
+    if (!sdf || !feat || !packed) return PSDF_ERR_INVALID_ARG;
+    if (!aligned16(packed)) return PSDF_ERR_MISALIGNED;
+    const int64_t n = int64_t(desc->dims[0]) * desc->dims[1] * desc->dims[2];
+    return cuda_status(psdf::launch_pack(sdf, feat, static_cast<float4*>(packed), n,
+                                         static_cast<cudaStream_t>(stream)));
+}
+
+psdf_status psdf_grid_unpack(const psdf_grid_desc* desc, const void* packed, float* sdf,
+                             float* feat, void* stream)
+{
+    const psdf_status st = check_grid_desc(desc);
+    if (st != PSDF_OK) return st;
+    if (!packed || (!sdf && !feat)) return PSDF_ERR_INVALID_ARG;
+    if (!aligned16(packed)) return PSDF_ERR_MISALIGNED;
+    const int64_t n = int64_t(desc->dims[0]) * desc->dims[1] * desc->dims[2];
+    return cuda_status(psdf::launch_unpack(static_cast<const float4*>(packed), sdf, feat, n,
+                                           static_cast<cudaStream_t>(stream)));
+}
+
+psdf_status psdf_probes_create(const psdf_probe_desc* desc, const void* coeffs,
+                               psdf_probes** out)
+{
+    const psdf_status st = check_probe_desc(desc);
+    if (st != PSDF_OK) return st;
+    if (!coeffs || !out) return PSDF_ERR_INVALID_ARG;
+    if (!aligned16(coeffs)) return PSDF_ERR_MISALIGNED;
+    psdf_probes* p = new (std::nothrow) psdf_probes;
+    if (!p) return PSDF_ERR_INVALID_ARG;
+    p->desc = *desc;
+    p->coeffs = coeffs;
+    *out = p;
+    return PSDF_OK;
+}
+
+void psdf_probes_destroy(psdf_probes* probes) { delete probes; }
+
+psdf_status psdf_mlp_param_count(const psdf_mlp_desc* desc, int64_t* count)
+{
+    const psdf_status st = check_mlp_desc(desc);
+    if (st != PSDF_OK) return st;
+    if (!count) return PSDF_ERR_INVALID_ARG;
+    *count = mlp_params(desc);
+    return PSDF_OK;
+}
+
+psdf_status psdf_mlp_create(const psdf_mlp_desc* desc, const void* params, psdf_mlp** out)
+{
+    const psdf_status st = check_mlp_desc(desc);
+    if (st != PSDF_OK) return st;
+    if (!params || !out) return PSDF_ERR_INVALID_ARG;
+    if (!aligned16(params)) return PSDF_ERR_MISALIGNED;
+    psdf_mlp* m = new (std::nothrow) psdf_mlp;
+    if (!m) return PSDF_ERR_INVALID_ARG;
+    m->desc = *desc;
+    m->params = params;
+    *out = m;
+    return PSDF_OK;
+}
+
+void psdf_mlp_destroy(psdf_mlp* mlp) { delete mlp; }
+
+psdf_status psdf_render_forward(const psdf_grid* grid, const psdf_probes* probes,
+                                const psdf_mlp* mlp, const psdf_render_params* params,
+                                const float* rays_o, const float* rays_d,
+                                const float* t_samples, int64_t n_rays, float* rgb,
+                                float* depth, float* wsum, float* logT_final, void* stream)
+{
+    Resolved r;
+    psdf_status st = resolve(grid, probes, mlp, params, rays_o, rays_d, t_samples, n_rays, r);
+    if (st != PSDF_OK) return st;
+    if (n_rays > 0 && (!rgb || !depth || !wsum || !logT_final)) return PSDF_ERR_INVALID_ARG;
+    if (!aligned16(rgb) || !aligned16(depth) || !aligned16(wsum) || !aligned16(logT_final))
+        return PSDF_ERR_MISALIGNED;
+    if (n_rays == 0) return PSDF_OK;
+    r.args.rgb = rgb;
+    r.args.depth = depth;
+    r.args.wsum = wsum;
+    r.args.logT = logT_final;
+    const int ctas = grid_size(n_rays, psdf::forward_ctas_per_sm(r.shape), psdf::kFwdThreads / 32);
+    return cuda_status(
+        psdf::launch_forward(r.args, r.shape, ctas, static_cast<cudaStream_t>(stream)));
+}
+
+psdf_status psdf_render_backward(const psdf_grid* grid, const psdf_probes* probes,
+                                 const psdf_mlp* mlp, const psdf_render_params* params,
+                                 const float* rays_o, const float* rays_d,
+                                 const float* t_samples, int64_t n_rays, const float* d_rgb,
+                                 const float* d_depth, const float* d_wsum,
+                                 const float* logT_final, float* grad_grid,
+                                 float* grad_probes, float* grad_mlp, void* stream)
+{
+    Resolved r;
+    psdf_status st = resolve(grid, probes, mlp, params, rays_o, rays_d, t_samples, n_rays, r);
+    if (st != PSDF_OK) return st;
+    if (!grad_grid || !grad_probes || !grad_mlp) return PSDF_ERR_INVALID_ARG;
+    if (n_rays > 0 && (!d_rgb || !logT_final)) return PSDF_ERR_INVALID_ARG;
+    if (!aligned16(d_rgb) || !aligned16(d_depth) || !aligned16(d_wsum) ||
+        !aligned16(logT_final) || !aligned16(grad_grid) || !aligned16(grad_probes) ||
+        !aligned16(grad_mlp))
+        return PSDF_ERR_MISALIGNED;
+    if (n_rays == 0) return PSDF_OK;
+    r.args.logT = const_cast<float*>(logT_final);
+    r.args.d_rgb = d_rgb;
+    r.args.d_depth = d_depth;
+    r.args.d_wsum = d_wsum;
+    r.args.grad_grid = grad_grid;
+    r.args.grad_probes = grad_probes;
+    r.args.grad_mlp = grad_mlp;
+    const int ctas =
+        grid_size(n_rays, psdf::backward_ctas_per_sm(r.shape), psdf::kBwdThreads / 32);
+    return cuda_status(
+        psdf::launch_backward(r.args, r.shape, ctas, static_cast<cudaStream_t>(stream)));
+}
+
+}  // extern "C"

@@ -1,0 +1,308 @@
+// Device-side building blocks of the ProbeSDF per-ray render (sm_103a).
+//
+// One warp renders one ray; lane l holds sample k = 32 c + l of chunk c.
+// Everything here is per lane; the warp-level scans live in the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace psdf {
+
+constexpr int kWarp = 32;
+constexpr float kNormalEps = 1e-12f;  // n = g / sqrt(|g|^2 + eps^2)
+
+// Kernel view of the packed SDF + feature grid: one float4 {sdf, f0, f1, f2}
+// per node, x fastest.
+struct GridView {
+    const float4* __restrict__ nodes;
+    int R[3];
+    float bmin[3];
+    float bmax[3];
+    float sc[3];  // (R - 1) / (bmax - bmin), FP32-rounded on the host
+};
+
+// Probe coefficients, [Pz][Py][Px][L2][NA] FP32, viewed as float4 groups of
+// four channels.
+struct ProbeView {
+    const float4* __restrict__ coeffs;
+    int P[3];
+    float sc[3];
+};
+
+struct RenderArgs {
+    GridView grid;
+    ProbeView probes;
+    const float* __restrict__ mlp;  // W1 b1 W2 b2 W3 b3
+    float tau;
+    int n_samples;
+    int dir_mode;  // 0 reflect, 1 view
+    float bg[3];
+    const float* __restrict__ rays_o;
+    const float* __restrict__ rays_d;
+    const float* __restrict__ t_samples;  // nullable [n_rays][N+1]
+    int64_t n_rays;
+    // forward outputs / backward inputs
+    float* rgb;
+    float* depth;
+    float* wsum;
+    float* logT;
+    // backward
+    const float* __restrict__ d_rgb;
+    const float* __restrict__ d_depth;
+    const float* __restrict__ d_wsum;
+    float* grad_grid;
+    float* grad_probes;
+    float* grad_mlp;
+};
+
+// ---------------------------------------------------------------------------
+// Sample positions.  These decide integer cell indices, so they use explicit
+// round-to-nearest intrinsics (never contracted into FMAs) in a fixed order;
+// any IEEE-754 FP32 implementation of the same sequence gives the same bits.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ bool ray_box(const float o[3], const float d[3], const GridView& g,
+                                        float& tn, float& tf)
+{
+    float t_enter = -INFINITY, t_exit = INFINITY;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.0f) {
+            if (o[a] < g.bmin[a] || o[a] > g.bmax[a]) return false;
+            continue;
+        }
+        const float t0 = __fdiv_rn(__fsub_rn(g.bmin[a], o[a]), d[a]);
+        const float t1 = __fdiv_rn(__fsub_rn(g.bmax[a], o[a]), d[a]);
+        const float lo = t0 < t1 ? t0 : t1;
+        const float hi = t0 < t1 ? t1 : t0;
+        if (lo > t_enter) t_enter = lo;
+        if (hi < t_exit) t_exit = hi;
+    }
+    tn = t_enter > 0.0f ? t_enter : 0.0f;
+    tf = t_exit;
+    return tf > tn;
+}
+
+__device__ __forceinline__ float sample_t(int k, float dt, float tn)
+{
+    return __fmaf_rn(static_cast<float>(k), dt, tn);
+}
+
+// Cell of a point along one axis: floor(u) clamped to [0, R-2]; the fraction
+// u - i is exact.
+__device__ __forceinline__ void locate_axis(float x, float bmin, float sc, int R, int& i,
+                                            float& f)
+{
+    const float u = __fmul_rn(__fsub_rn(x, bmin), sc);
+    float fl = floorf(u);
+    const float hi = static_cast<float>(R - 2);
+    fl = fl >= 0.0f ? fl : 0.0f;  // also maps NaN to cell 0: every index stays in bounds
+    fl = fl > hi ? hi : fl;
+    i = static_cast<int>(fl);
+    f = __fsub_rn(u, fl);
+}
+
+struct Cell {
+    int base;  // linear index of corner (0,0,0)
+    float f[3];
+};
+
+__device__ __forceinline__ Cell locate(const float x[3], const float bmin[3], const float sc[3],
+                                       const int R[3])
+{
+    Cell c;
+    int i[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) locate_axis(x[a], bmin[a], sc[a], R[a], i[a], c.f[a]);
+    c.base = (i[2] * R[1] + i[1]) * R[0] + i[0];
+    return c;
+}
+
+__device__ __forceinline__ void point_at(const float o[3], const float d[3], float t, float x[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[a] = __fmaf_rn(t, d[a], o[a]);
+}
+
+// ---------------------------------------------------------------------------
+// Trilinear gathers (Sec. 3.1): 8 corner records of 16 bytes each.
+// ---------------------------------------------------------------------------
+
+struct Corners {
+    float4 v[8];  // corner c = cx + 2 cy + 4 cz
+};
+
+__device__ __forceinline__ void gather_corners(const GridView& g, const Cell& c, Corners& k)
+{
+    const int sx = 1, sy = g.R[0], sz = g.R[0] * g.R[1];
+    const float4* p = g.nodes + c.base;
+    k.v[0] = __ldg(p);
+    k.v[1] = __ldg(p + sx);
+    k.v[2] = __ldg(p + sy);
+    k.v[3] = __ldg(p + sx + sy);
+    k.v[4] = __ldg(p + sz);
+    k.v[5] = __ldg(p + sz + sx);
+    k.v[6] = __ldg(p + sz + sy);
+    k.v[7] = __ldg(p + sz + sy + sx);
+}
+
+__device__ __forceinline__ void corner_weights(const float f[3], float w[8])
+{
+    const float x0 = 1.0f - f[0], x1 = f[0];
+    const float y0 = 1.0f - f[1], y1 = f[1];
+    const float z0 = 1.0f - f[2], z1 = f[2];
+    w[0] = x0 * y0 * z0;
+    w[1] = x1 * y0 * z0;
+    w[2] = x0 * y1 * z0;
+    w[3] = x1 * y1 * z0;
+    w[4] = x0 * y0 * z1;
+    w[5] = x1 * y0 * z1;
+    w[6] = x0 * y1 * z1;
+    w[7] = x1 * y1 * z1;
+}
+
+// SDF value only (the extra point N of a ray's last full chunk).
+__device__ __forceinline__ float sdf_value(const GridView& g, const Cell& c)
+{
+    const int sx = 1, sy = g.R[0], sz = g.R[0] * g.R[1];
+    const float* p = reinterpret_cast<const float*>(g.nodes + c.base);
+    float w[8];
+    corner_weights(c.f, w);
+    const int off[8] = {0, sx, sy, sx + sy, sz, sz + sx, sz + sy, sz + sy + sx};
+    float s = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s = fmaf(w[q], __ldg(p + 4 * off[q]), s);
+    return s;
+}
+
+// Value, analytic gradient (world units) and 3 features at a point.
+__device__ __forceinline__ void sdf_full(const GridView& g, const Cell& c, const Corners& k,
+                                         float& s, float grad[3], float feat[3])
+{
+    float w[8];
+    corner_weights(c.f, w);
+    s = 0.0f;
+    feat[0] = feat[1] = feat[2] = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        s = fmaf(w[q], k.v[q].x, s);
+        feat[0] = fmaf(w[q], k.v[q].y, feat[0]);
+        feat[1] = fmaf(w[q], k.v[q].z, feat[1]);
+        feat[2] = fmaf(w[q], k.v[q].w, feat[2]);
+    }
+    const float fx = c.f[0], fy = c.f[1], fz = c.f[2];
+    const float x0 = 1.0f - fx, y0 = 1.0f - fy, z0 = 1.0f - fz;
+    // d/du_x: differences along x weighted by the (y, z) bilinear weights
+    const float gx = (y0 * z0) * (k.v[1].x - k.v[0].x) + (fy * z0) * (k.v[3].x - k.v[2].x) +
+                     (y0 * fz) * (k.v[5].x - k.v[4].x) + (fy * fz) * (k.v[7].x - k.v[6].x);
+    const float gy = (x0 * z0) * (k.v[2].x - k.v[0].x) + (fx * z0) * (k.v[3].x - k.v[1].x) +
+                     (x0 * fz) * (k.v[6].x - k.v[4].x) + (fx * fz) * (k.v[7].x - k.v[5].x);
+    const float gz = (x0 * y0) * (k.v[4].x - k.v[0].x) + (fx * y0) * (k.v[5].x - k.v[1].x) +
+                     (x0 * fy) * (k.v[6].x - k.v[2].x) + (fx * fy) * (k.v[7].x - k.v[3].x);
+    grad[0] = gx * g.sc[0];
+    grad[1] = gy * g.sc[1];
+    grad[2] = gz * g.sc[2];
+}
+
+// ---------------------------------------------------------------------------
+// Real spherical harmonics, orthonormal, no Condon-Shortley phase (Eq. 5),
+// ordered by degree then m = -deg..deg.  L2 = l*l with l 1-indexed.
+// ---------------------------------------------------------------------------
+
+template <int L2>
+__device__ __forceinline__ void sh_basis(const float r[3], float Y[L2])
+{
+    const float x = r[0], y = r[1], z = r[2];
+    Y[0] = 0.28209479177387814f;
+    if constexpr (L2 > 1) {
+        Y[1] = 0.48860251190291992f * y;
+        Y[2] = 0.48860251190291992f * z;
+        Y[3] = 0.48860251190291992f * x;
+    }
+    if constexpr (L2 > 4) {
+        Y[4] = 1.0925484305920792f * (x * y);
+        Y[5] = 1.0925484305920792f * (y * z);
+        Y[6] = 0.31539156525252005f * (3.0f * z * z - 1.0f);
+        Y[7] = 1.0925484305920792f * (x * z);
+        Y[8] = 0.54627421529603959f * (x * x - y * y);
+    }
+    if constexpr (L2 > 9) {
+        Y[9] = 0.59004358992664352f * y * (3.0f * x * x - y * y);
+        Y[10] = 2.8906114426405538f * (x * y * z);
+        Y[11] = 0.45704579946446572f * y * (5.0f * z * z - 1.0f);
+        Y[12] = 0.37317633259011540f * z * (5.0f * z * z - 3.0f);
+        Y[13] = 0.45704579946446572f * x * (5.0f * z * z - 1.0f);
+        Y[14] = 1.4453057213202769f * z * (x * x - y * y);
+        Y[15] = 0.59004358992664352f * x * (x * x - 3.0f * y * y);
+    }
+}
+
+// dr = sum_j dY_j * grad Y_j(r)
+template <int L2>
+__device__ __forceinline__ void sh_basis_vjp(const float r[3], const float dY[L2], float dr[3])
+{
+    const float x = r[0], y = r[1], z = r[2];
+    dr[0] = dr[1] = dr[2] = 0.0f;
+    if constexpr (L2 > 1) {
+        const float c = 0.48860251190291992f;
+        dr[1] += c * dY[1];
+        dr[2] += c * dY[2];
+        dr[0] += c * dY[3];
+    }
+    if constexpr (L2 > 4) {
+        const float a = 1.0925484305920792f, b = 0.31539156525252005f,
+                    e = 0.54627421529603959f;
+        dr[0] += a * (y * dY[4] + z * dY[7]) + 2.0f * e * x * dY[8];
+        dr[1] += a * (x * dY[4] + z * dY[5]) - 2.0f * e * y * dY[8];
+        dr[2] += a * (y * dY[5] + x * dY[7]) + 6.0f * b * z * dY[6];
+    }
+    if constexpr (L2 > 9) {
+        const float c33 = 0.59004358992664352f, c32 = 2.8906114426405538f,
+                    c31 = 0.45704579946446572f, c30 = 0.37317633259011540f,
+                    c32b = 1.4453057213202769f;
+        dr[0] += c33 * 6.0f * x * y * dY[9] + c32 * y * z * dY[10] +
+                 c31 * (5.0f * z * z - 1.0f) * dY[13] + c32b * 2.0f * x * z * dY[14] +
+                 c33 * (3.0f * x * x - 3.0f * y * y) * dY[15];
+        dr[1] += c33 * (3.0f * x * x - 3.0f * y * y) * dY[9] + c32 * x * z * dY[10] +
+                 c31 * (5.0f * z * z - 1.0f) * dY[11] - c32b * 2.0f * y * z * dY[14] -
+                 c33 * 6.0f * x * y * dY[15];
+        dr[2] += c32 * x * y * dY[10] + c31 * 10.0f * y * z * dY[11] +
+                 c30 * (15.0f * z * z - 3.0f) * dY[12] + c31 * 10.0f * x * z * dY[13] +
+                 c32b * (x * x - y * y) * dY[14];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// NeuS helpers (Eqs. 9-10).
+// ---------------------------------------------------------------------------
+
+// log Phi_tau(s) = -softplus(-tau s)
+__device__ __forceinline__ float log_phi(float tau, float s)
+{
+    const float z = -tau * s;
+    return -(fmaxf(z, 0.0f) + log1pf(expf(-fabsf(z))));
+}
+
+// d log Phi / ds = tau * (1 - Phi(s)) = tau * sigmoid(-tau s)
+__device__ __forceinline__ float dlog_phi(float tau, float s)
+{
+    return tau / (1.0f + expf(tau * s));
+}
+
+__device__ __forceinline__ float sigmoidf(float z) { return 1.0f / (1.0f + expf(-z)); }
+
+// Vector reduction into global memory (no return value).
+__device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b),
+                 "f"(c), "f"(d)
+                 : "memory");
+}
+
+__device__ __forceinline__ void red_add(float* addr, float a)
+{
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(addr), "f"(a) : "memory");
+}
+
+}  // namespace psdf

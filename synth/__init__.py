@@ -137,27 +137,44 @@ def object_shapes(g, n_shapes=32):
     return shapes
 
 
-def object_sdf(dims, box_min, box_max, shapes, k=0.05, slab=32):
+def _torch_coords(dims, box_min, box_max, z0, z1):
+    import torch
+    Rx, Ry, Rz = dims
+    xs = torch.linspace(float(box_min[0]), float(box_max[0]), Rx, dtype=torch.float64)
+    ys = torch.linspace(float(box_min[1]), float(box_max[1]), Ry, dtype=torch.float64)
+    zs = torch.linspace(float(box_min[2]), float(box_max[2]), Rz, dtype=torch.float64)[z0:z1]
+    Z, Y, X = torch.meshgrid(zs, ys, xs, indexing="ij")
+    return torch.stack([X, Y, Z], -1)
+
+
+def _torch_smin(a, b, k):
+    import torch
+    h = torch.clamp(k - (a - b).abs(), min=0.0) / k
+    return torch.minimum(a, b) - h * h * k * 0.25
+
+
+def object_sdf(dims, box_min, box_max, shapes, k=0.05, slab=16):
     """Smooth-min (polynomial, k) union of spheres and superquadrics.  The
-    superquadric uses the usual implicit-function distance approximation."""
+    superquadric uses the usual implicit-function distance approximation.
+    Evaluated with torch on the host (multithreaded), FP64, stored FP32."""
+    import torch
     Rx, Ry, Rz = dims
     out = np.empty((Rz, Ry, Rx), np.float32)
     for z0 in range(0, Rz, slab):
-        X, Y, Z = _node_coords(dims, box_min, box_max, slice(z0, min(Rz, z0 + slab)))
-        P = np.stack([X, Y, Z], -1)
+        z1 = min(Rz, z0 + slab)
+        P = _torch_coords(dims, box_min, box_max, z0, z1)
         acc = None
         for kind, c, prm in shapes:
-            q = P - c
+            q = P - torch.as_tensor(c, dtype=torch.float64)
             if kind == "sphere":
-                dist = np.sqrt((q * q).sum(-1)) - prm
+                dist = q.norm(dim=-1) - prm
             else:
                 radii, e, Rm = prm
-                ql = (q @ Rm) / radii
-                f = (np.abs(ql[..., 0]) ** e + np.abs(ql[..., 1]) ** e +
-                     np.abs(ql[..., 2]) ** e) ** (1.0 / e)
-                dist = (f - 1.0) * radii.min()
-            acc = dist if acc is None else _smin(acc, dist, k)
-        out[z0:z0 + acc.shape[0]] = acc
+                ql = (q @ torch.as_tensor(Rm, dtype=torch.float64)) / torch.as_tensor(radii)
+                f = ql.abs().pow(e).sum(-1).pow(1.0 / e)
+                dist = (f - 1.0) * float(radii.min())
+            acc = dist if acc is None else _torch_smin(acc, dist, k)
+        out[z0:z1] = acc.numpy().astype(np.float32)
     return out
 
 
@@ -200,19 +217,21 @@ def capsule_body(g):
 
 
 def capsule_sdf(dims, box_min, box_max, caps, k=0.04, slab=16):
+    import torch
     Rx, Ry, Rz = dims
     out = np.empty((Rz, Ry, Rx), np.float32)
     for z0 in range(0, Rz, slab):
-        X, Y, Z = _node_coords(dims, box_min, box_max, slice(z0, min(Rz, z0 + slab)))
-        P = np.stack([X, Y, Z], -1)
+        z1 = min(Rz, z0 + slab)
+        P = _torch_coords(dims, box_min, box_max, z0, z1)
         acc = None
         for a, b, rad in caps:
-            ab = b - a
-            h = np.clip(((P - a) @ ab) / (ab @ ab), 0.0, 1.0)
-            q = P - a - h[..., None] * ab
-            dist = np.sqrt((q * q).sum(-1)) - rad
-            acc = dist if acc is None else _smin(acc, dist, k)
-        out[z0:z0 + acc.shape[0]] = acc
+            a_ = torch.as_tensor(a, dtype=torch.float64)
+            ab = torch.as_tensor(b - a, dtype=torch.float64)
+            h = torch.clamp(((P - a_) @ ab) / float(ab @ ab), 0.0, 1.0)
+            q = P - a_ - h[..., None] * ab
+            dist = q.norm(dim=-1) - rad
+            acc = dist if acc is None else _torch_smin(acc, dist, k)
+        out[z0:z1] = acc.numpy().astype(np.float32)
     return out
 
 

@@ -1,0 +1,90 @@
+"""Host-only checks of the C ABI library (no GPU needed, no kernel launched):
+it builds for sm_103a, loads, exports every symbol include/*.h declares, and
+rejects bad arguments on the host before any CUDA call."""
+import ctypes
+import glob
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(psdf_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2412_10084_gb300 import build
+    return ctypes.CDLL(build.build())
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("psdf_render_forward", "psdf_render_backward", "psdf_grid_create",
+                     "psdf_probes_create", "psdf_mlp_create", "psdf_grid_pack",
+                     "psdf_grid_unpack"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_and_version(lib):
+    lib.psdf_status_string.restype = ctypes.c_char_p
+    assert lib.psdf_status_string(0) == b"ok"
+    assert b"aligned" in lib.psdf_status_string(-4)
+    assert lib.psdf_version() >= 100
+
+
+def test_host_validation_without_gpu(lib):
+    import paper_2412_10084_gb300 as ps
+    gd = ps.grid_desc((64, 64, 64), (0, 0, 0), (1, 1, 1))
+    assert ps.grid_bytes(gd) == 64 ** 3 * 16
+    assert ps.mlp_param_count(10, 32) == 32 * 10 + 32 + 32 * 32 + 32 + 96 + 3
+    bad = ps.grid_desc((1, 64, 64), (0, 0, 0), (1, 1, 1))
+    with pytest.raises(ps.LibraryError, match="shape"):
+        ps.grid_bytes(bad)
+    flat = ps.grid_desc((8, 8, 8), (0, 0, 0), (1, 0, 1))
+    with pytest.raises(ps.LibraryError, match="shape"):
+        ps.grid_bytes(flat)
+    h = ctypes.c_void_p()
+    lib.psdf_grid_create.argtypes = [ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.POINTER(ctypes.c_void_p)]
+    assert lib.psdf_grid_create(ctypes.byref(gd), ctypes.c_void_p(0x1008), ctypes.byref(h)) == -4
+    assert lib.psdf_grid_create(ctypes.byref(gd), None, ctypes.byref(h)) == -1
+    lib.psdf_render_forward.argtypes = [ctypes.c_void_p] * 7 + [ctypes.c_int64] + \
+        [ctypes.c_void_p] * 5
+    assert lib.psdf_render_forward(None, None, None, None, None, None, None, 0,
+                                   None, None, None, None, None) == -1
+
+
+def test_kernel_sh_constants_match_closed_form():
+    """The SH constants typed into the kernels equal the Cartesian coefficients
+    of the orthonormal real basis of Eq. 5 (normalisation
+    sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!), times sqrt 2 for m != 0)."""
+    src = open(os.path.join(ROOT, "paper_2412_10084_gb300", "csrc", "render_common.cuh")).read()
+    body = src[src.index("sh_basis(const float"):src.index("sh_basis_vjp")]
+    consts = sorted({float(v) for v in re.findall(r"(\d\.\d{10,})f", body)})
+
+    # Cartesian coefficients of the real SH, degrees 0..3
+    closed = sorted({
+        0.5 * math.sqrt(1 / math.pi), math.sqrt(3 / (4 * math.pi)),
+        0.5 * math.sqrt(15 / math.pi), 0.25 * math.sqrt(5 / math.pi),
+        0.25 * math.sqrt(15 / math.pi), 0.25 * math.sqrt(35 / (2 * math.pi)),
+        0.5 * math.sqrt(105 / math.pi), 0.25 * math.sqrt(21 / (2 * math.pi)),
+        0.25 * math.sqrt(7 / math.pi), 0.25 * math.sqrt(105 / math.pi)})
+    assert len(consts) == len(closed)
+    for a, b in zip(consts, closed):
+        assert abs(a - b) <= 1e-15 * b

@@ -1,0 +1,307 @@
+"""Parity of the CUDA render and adjoint with the FP64 oracle (GPU only).
+
+Every comparison calls the C ABI through the Python binding on cuda:0 and
+the oracle on the same seeded FP32 inputs.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from helpers import (GRAD_RTOL, RGB_DEPTH_RTOL, clean_rays, oracle_backward, oracle_forward,
+                     rel_err_elementwise, rel_err_tensor)
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    import paper_2412_10084_gb300 as ps
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+
+
+def gpu_forward(scene, o, d, params, t_samples=None):
+    rgb, depth, wsum, logT = ps.render_forward(scene, dev(o), dev(d), params,
+                                               None if t_samples is None else dev(t_samples))
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy().astype(np.float64)
+            for k, v in (("rgb", rgb), ("depth", depth), ("wsum", wsum), ("logT", logT))}
+
+
+def gpu_backward(scene, o, d, params, drgb, ddepth=None, dwsum=None, t_samples=None):
+    o_, d_ = dev(o), dev(d)
+    ts = None if t_samples is None else dev(t_samples)
+    _, _, _, logT = ps.render_forward(scene, o_, d_, params, ts)
+    gg, gp, gm = ps.render_backward(scene, o_, d_, params, dev(drgb), logT,
+                                    d_depth=None if ddepth is None else dev(ddepth),
+                                    d_wsum=None if dwsum is None else dev(dwsum), t_samples=ts)
+    gd, _, _ = scene.descs(params.n_fresnel)
+    gsdf, gfeat = ps.unpack_grid(gd, gg)
+    torch.cuda.synchronize()
+    return {"sdf": gsdf.cpu().numpy(), "feat": gfeat.cpu().numpy(),
+            "probes": gp.cpu().numpy(), "mlp": gm.cpu().numpy()}
+
+
+def check_forward(sc, o, d, tau, N, dir_mode=0, bg=(0, 0, 0), t_samples=None):
+    scene = ps.Scene.from_host(sc)
+    params = ps.render_params(tau, N, dir_mode, sc.n_fresnel, bg)
+    g = gpu_forward(scene, o, d, params, t_samples)
+    r = oracle_forward(sc, o, d, tau, N, dir_mode=dir_mode, bg=bg, t_samples=t_samples)
+    errs = {k: rel_err_elementwise(g[k], r[k]) for k in ("rgb", "depth", "wsum")}
+    errs["logT"] = float(np.max(np.abs(g["logT"] - r["logT"]) /
+                                np.maximum(np.abs(r["logT"]), 1.0)))
+    for k, e in errs.items():
+        assert e <= RGB_DEPTH_RTOL, (k, e)
+    return g, r
+
+
+def check_backward(sc, o, d, tau, N, dir_mode=0, bg=(0, 0, 0), seed=5, with_depth=False,
+                   t_samples=None, min_kept=0.5):
+    keep = clean_rays(sc, o, d, tau, N, dir_mode=dir_mode, bg=bg, t_samples=t_samples)
+    assert keep.size >= min_kept * o.shape[0], (keep.size, o.shape[0])
+    o, d = o[keep], d[keep]
+    if t_samples is not None:
+        t_samples = t_samples[keep]
+    g = synth.rng(seed)
+    n = o.shape[0]
+    drgb = (g.normal(size=(n, 3)) / n).astype(np.float32)
+    ddepth = (g.normal(size=n) / n).astype(np.float32) if with_depth else None
+    dwsum = (g.normal(size=n) / n).astype(np.float32) if with_depth else None
+    scene = ps.Scene.from_host(sc)
+    params = ps.render_params(tau, N, dir_mode, sc.n_fresnel, bg)
+    gg = gpu_backward(scene, o, d, params, drgb, ddepth, dwsum, t_samples)
+    gr = oracle_backward(sc, o, d, drgb.astype(np.float64), tau, N, dir_mode=dir_mode, bg=bg,
+                         d_depth=ddepth, d_wsum=dwsum, t_samples=t_samples)
+    errs = {k: rel_err_tensor(gg[k], gr[k]) for k in ("sdf", "feat", "probes", "mlp")}
+    for k, e in errs.items():
+        assert e <= GRAD_RTOL, (k, e, errs)
+    return errs
+
+
+# ---------------------------------------------------------------------------
+# The small configuration: 64^3 sphere + noise, 4096 rays x 128 samples
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def sphere64():
+    sc = synth.make_scene("sphere64")
+    rays = synth.make_rays("sphere64")
+    return sc, rays
+
+
+def test_forward_parity_sphere64(sphere64):
+    sc, rays = sphere64
+    g, r = check_forward(sc, rays.o, rays.d, 64.0, 128)
+    assert np.sum(r["wsum"] > 0.5) > 200  # the batch does hit the surface
+
+
+def test_backward_parity_sphere64(sphere64):
+    sc, rays = sphere64
+    check_backward(sc, rays.o, rays.d, 64.0, 128)
+
+
+def test_backward_parity_with_depth_and_wsum_cotangents(sphere64):
+    sc, rays = sphere64
+    check_backward(sc, rays.o[:1500], rays.d[:1500], 64.0, 128, bg=(0.2, 0.5, 0.9),
+                   with_depth=True)
+
+
+# ---------------------------------------------------------------------------
+# Ragged shapes, modes and edge cases
+# ---------------------------------------------------------------------------
+
+def test_ragged_samples_and_rays_view_mode():
+    sc = synth.make_scene("sphere64", dims=(40, 33, 37), probe_dims=(7, 6, 5))
+    rays = synth.make_rays("sphere64", n_rays=777, seed_offset=3)
+    check_forward(sc, rays.o, rays.d, 48.0, 100, dir_mode=1, bg=(0.3, 0.1, 0.7))
+    check_backward(sc, rays.o, rays.d, 48.0, 100, dir_mode=1, bg=(0.3, 0.1, 0.7),
+                   with_depth=True)
+
+
+@pytest.mark.parametrize("N", [1, 31, 32, 33, 64])
+def test_sample_counts_around_chunk_boundaries(N):
+    sc = synth.make_scene("sphere64", dims=(24, 24, 24), probe_dims=(6, 6, 6))
+    rays = synth.make_rays("sphere64", n_rays=300, seed_offset=N)
+    check_forward(sc, rays.o, rays.d, 32.0, N)
+    check_backward(sc, rays.o, rays.d, 32.0, N, with_depth=True)
+
+
+def test_width32_and_eight_channels():
+    spec = dict(synth.WORKLOADS["stress512"])
+    g = synth.rng(77)
+    sc = synth.make_scene("sphere64", dims=(30, 30, 30), probe_dims=(5, 5, 5))
+    sc.probes = g.normal(0, 0.1, size=(5, 5, 5, 9, 8)).astype(np.float32)
+    sc.width = 32
+    sc.mlp = synth.mlp_params(3 + 8 + 3, 32, g)
+    rays = synth.make_rays("sphere64", n_rays=600, seed_offset=9)
+    check_forward(sc, rays.o, rays.d, 64.0, 96)
+    check_backward(sc, rays.o, rays.d, 64.0, 96)
+    assert spec["n_a"] == 8
+
+
+def test_explicit_sample_distances():
+    sc = synth.make_scene("sphere64", dims=(32, 32, 32), probe_dims=(8, 8, 8))
+    rays = synth.make_rays("sphere64", n_rays=256, seed_offset=11)
+    g = synth.rng(12)
+    N = 48
+    # sorted random distances inside [1.2, 2.8] (the sphere scene spans ~[1.5, 2.5])
+    t = np.sort(g.uniform(1.2, 2.8, size=(256, N + 1)), axis=1).astype(np.float32)
+    t[:5] = 0.0  # treated as misses
+    check_forward(sc, rays.o, rays.d, 64.0, N, t_samples=t)
+    check_backward(sc, rays.o, rays.d, 64.0, N, t_samples=t)
+
+
+def test_empty_batch_and_misses():
+    sc = synth.make_scene("sphere64", dims=(16, 16, 16), probe_dims=(4, 4, 4))
+    scene = ps.Scene.from_host(sc)
+    params = ps.render_params(64.0, 32, 0, 3, (0.25, 0.5, 0.75))
+    e = torch.empty((0, 3), dtype=torch.float32, device="cuda")
+    rgb, depth, wsum, logT = ps.render_forward(scene, e, e, params)
+    assert rgb.shape == (0, 3)
+    gg, gp, gm = ps.render_backward(scene, e, e, params, e, logT)
+    assert float(gg.abs().sum()) == 0.0
+    o = np.array([[2.0, 2.0, 2.0], [-1.0, 0.5, 0.5], [0.5, 0.5, 3.0]], np.float32)
+    d = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]], np.float32)
+    out = gpu_forward(scene, o, d, params)
+    np.testing.assert_array_equal(out["rgb"], np.tile([0.25, 0.5, 0.75], (3, 1)))
+    assert np.all(out["wsum"] == 0) and np.all(out["depth"] == 0)
+
+
+def test_host_validation_errors():
+    sc = synth.make_scene("sphere64", dims=(16, 16, 16), probe_dims=(4, 4, 4))
+    scene = ps.Scene.from_host(sc)
+    o = dev(np.zeros((4, 3)))
+    with pytest.raises(ps.LibraryError, match="shape"):
+        ps.render_forward(scene, o, o, ps.render_params(64.0, 0))
+    with pytest.raises(ps.LibraryError, match="shape"):
+        ps.render_forward(scene, o, o, ps.render_params(-1.0, 8))
+    with pytest.raises(ps.LibraryError):
+        ps.render_forward(scene, o, o, ps.render_params(64.0, 8, n_fresnel=2))
+    with pytest.raises(ps.LibraryError, match="CPU"):
+        ps.render_forward(scene, o.cpu(), o.cpu(), ps.render_params(64.0, 8))
+
+
+def test_pack_unpack_roundtrip_exact():
+    sc = synth.make_scene("sphere64", dims=(19, 17, 23), probe_dims=(4, 4, 4))
+    scene = ps.Scene.from_host(sc)
+    gd, _, _ = scene.descs(3)
+    sdf, feat = ps.unpack_grid(gd, scene.grid)
+    np.testing.assert_array_equal(sdf.cpu().numpy(), sc.sdf)
+    np.testing.assert_array_equal(feat.cpu().numpy(), sc.feat)
+
+
+# ---------------------------------------------------------------------------
+# Invariants and determinism at the full object-capture size
+# (256^3 grid, 32^3 probes, W = 32, 2^18 rays x 256 samples: the benchmark's launch)
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def object256():
+    sc = synth.make_scene("object256")
+    rays = synth.make_rays("object256")
+    return sc, rays
+
+
+def test_full_size_forward_sampled_parity_and_invariants(object256):
+    sc, rays = object256
+    scene = ps.Scene.from_host(sc)
+    params = ps.render_params(64.0, 256, 0, 3)
+    o, d = dev(rays.o), dev(rays.d)
+    rgb, depth, wsum, logT = ps.render_forward(scene, o, d, params)
+    rgb2, depth2, wsum2, logT2 = ps.render_forward(scene, o, d, params)
+    torch.cuda.synchronize()
+    assert torch.equal(rgb, rgb2) and torch.equal(depth, depth2) and torch.equal(wsum, wsum2)
+    for t in (rgb, depth, wsum, logT):
+        assert torch.isfinite(t).all()
+    assert float(wsum.min()) >= 0.0 and float(wsum.max()) <= 1.0 + 1e-6
+    assert float(rgb.min()) >= 0.0 and float(rgb.max()) <= 1.0 + 1e-6
+    idx = synth.rng(3).choice(rays.o.shape[0], 256, replace=False)
+    r = oracle_forward(sc, rays.o[idx], rays.d[idx], 64.0, 256)
+    for k, v in (("rgb", rgb), ("depth", depth), ("wsum", wsum)):
+        e = rel_err_elementwise(v.cpu().numpy()[idx], r[k])
+        assert e <= RGB_DEPTH_RTOL, (k, e)
+
+
+def test_full_size_backward_subset_parity(object256):
+    sc, rays = object256
+    idx = synth.rng(4).choice(rays.o.shape[0], 384, replace=False)
+    check_backward(sc, rays.o[idx], rays.d[idx], 64.0, 256, min_kept=0.3)
+
+
+def test_full_size_backward_runs_and_is_finite(object256):
+    sc, rays = object256
+    scene = ps.Scene.from_host(sc)
+    params = ps.render_params(64.0, 256, 0, 3)
+    o, d = dev(rays.o), dev(rays.d)
+    target = dev(rays.target)
+    scene.grid.requires_grad_(True)
+    scene.probes.requires_grad_(True)
+    scene.mlp.requires_grad_(True)
+    rgb, depth, wsum = ps.render(scene, o, d, params)
+    loss = (rgb - target).abs().mean()
+    loss.backward()
+    torch.cuda.synchronize()
+    for p in (scene.grid, scene.probes, scene.mlp):
+        assert p.grad is not None and torch.isfinite(p.grad).all()
+        assert float(p.grad.abs().max()) > 0.0
+
+
+# ---------------------------------------------------------------------------
+# Autograd wrapper and FP32 finite differences on the GPU itself
+# ---------------------------------------------------------------------------
+
+def test_autograd_function_matches_direct_backward(sphere64):
+    sc, rays = sphere64
+    scene = ps.Scene.from_host(sc)
+    params = ps.render_params(64.0, 128, 0, 3)
+    o, d = dev(rays.o), dev(rays.d)
+    drgb = dev(synth.rng(8).normal(size=(rays.o.shape[0], 3)) / 4096)
+    grid = scene.grid.clone().requires_grad_(True)
+    probes = scene.probes.clone().requires_grad_(True)
+    mlp = scene.mlp.clone().requires_grad_(True)
+    rgb, _, _ = ps.RenderFunction.apply(grid, probes, mlp, o, d, None, scene, params)
+    (rgb * drgb).sum().backward()
+    _, _, _, logT = ps.render_forward(scene, o, d, params)
+    gg, gp, gm = ps.render_backward(scene, o, d, params, drgb, logT)
+    for a, b in ((grid.grad, gg), (probes.grad, gp), (mlp.grad, gm)):
+        scale = float(b.abs().max())
+        assert float((a - b).abs().max()) <= 1e-5 * scale
+
+
+def test_gpu_central_differences():
+    """FP32 gradients against central differences of the FP32 forward on the GPU
+    (h = 1e-3 on 64 random parameters; relative 1e-2, the FP32 round-off bound)."""
+    sc = synth.make_scene("sphere64", dims=(20, 20, 20), probe_dims=(5, 5, 5))
+    rays = synth.make_rays("sphere64", n_rays=512, seed_offset=21)
+    keep = clean_rays(sc, rays.o, rays.d, 16.0, 48, margin=1e-2)
+    o, d = dev(rays.o[keep]), dev(rays.d[keep])
+    n = o.shape[0]
+    scene = ps.Scene.from_host(sc)
+    params = ps.render_params(16.0, 48, 0, 3)
+    wts = dev(synth.rng(22).normal(size=(n, 3)))
+
+    def loss():
+        rgb, _, _, _ = ps.render_forward(scene, o, d, params)
+        return float((rgb.double() * wts.double()).sum())
+
+    _, _, _, logT = ps.render_forward(scene, o, d, params)
+    gg, gp, gm = ps.render_backward(scene, o, d, params, wts, logT)
+    g = synth.rng(23)
+    h = 1e-3
+    checked = 0
+    for tensor, grad in ((scene.grid, gg), (scene.probes, gp), (scene.mlp, gm)):
+        flat, gflat = tensor.view(-1), grad.view(-1)
+        nz = torch.nonzero(gflat.abs() > 1e-3 * gflat.abs().max()).view(-1).cpu().numpy()
+        for i in g.choice(nz, min(22, nz.size), replace=False):
+            old = float(flat[i])
+            flat[i] = old + h
+            lp = loss()
+            flat[i] = old - h
+            lm = loss()
+            flat[i] = old
+            fd = (lp - lm) / (2 * h)
+            an = float(gflat[i])
+            assert abs(fd - an) <= 1e-2 * abs(an) + 2e-3 * float(gflat.abs().max()), (i, fd, an)
+            checked += 1
+    assert checked >= 60
