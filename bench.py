@@ -173,7 +173,12 @@ def cpu_cores():
 
 
 def auto_cpu_rays(sc, rays, tau, N, threads, target_s=12.0):
-    rate, _ = oracle_rate(sc, rays, 64, tau, N, threads)
+    """Rays of the oracle sample sized to about target_s seconds of CPU work."""
+    n = max(256, 16 * threads)
+    rate, dt = oracle_rate(sc, rays, n, tau, N, threads)
+    while dt < 1.0 and n < rays.o.shape[0]:
+        n = min(4 * n, rays.o.shape[0])
+        rate, dt = oracle_rate(sc, rays, n, tau, N, threads)
     n = int(rate * target_s / N)
     return max(64, min(n, rays.o.shape[0]))
 
@@ -236,7 +241,7 @@ def run_ours(args, world, rank, local):
     gp = torch.zeros_like(scene.probes)
     gm = torch.zeros_like(scene.mlp)
     stream = torch.cuda.current_stream(device)
-    ev = {k: [] for k in ("fwd0", "fwd1", "bwd1")}
+    ev = {k: [] for k in ("fwd0", "bwd1")}
 
     def step(record=False):
         gg.zero_()

@@ -271,7 +271,7 @@ render_backward_kernel(RenderArgs A)
             float lam = 0.0f;
             bool unclipped = false;
             if (active) {
-                const float diff = log_phi(tau, s_next) - log_phi(tau, S.s);
+                const float diff = log_transmittance(tau, S.s, s_next);
                 unclipped = diff < 0.0f;
                 lam = unclipped ? diff : 0.0f;
             }

@@ -284,6 +284,19 @@ __device__ __forceinline__ float log_phi(float tau, float s)
     return -(fmaxf(z, 0.0f) + log1pf(expf(-fabsf(z))));
 }
 
+// log(1 - alpha) before the clip of Eq. 9: log Phi(s1) - log Phi(s0).  With
+// z = -tau s this is softplus(z0) - softplus(z1) = log1p(sigmoid(z1) expm1(z0 - z1)),
+// which keeps full relative accuracy when s1 is close to s0 (a grazing ray),
+// where the difference of the two logarithms cancels in FP32.  When the
+// argument nears -1 (a large drop deep inside the surface) the plain
+// difference is already accurate and avoids log1p(-1).
+__device__ __forceinline__ float log_transmittance(float tau, float s0, float s1)
+{
+    const float p = expm1f(tau * (s1 - s0)) / (1.0f + expf(tau * s1));
+    if (p > -0.5f) return log1pf(p);
+    return log_phi(tau, s1) - log_phi(tau, s0);
+}
+
 // d log Phi / ds = tau * (1 - Phi(s)) = tau * sigmoid(-tau s)
 __device__ __forceinline__ float dlog_phi(float tau, float s)
 {

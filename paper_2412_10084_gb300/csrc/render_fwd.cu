@@ -67,7 +67,7 @@ render_forward_kernel(RenderArgs A)
             // Eq. 9 in log space: log(1 - alpha_k) = min(log Phi(s_k+1) - log Phi(s_k), 0)
             float lam = 0.0f;
             if (active) {
-                const float diff = log_phi(A.tau, s_next) - log_phi(A.tau, S.s);
+                const float diff = log_transmittance(A.tau, S.s, s_next);
                 lam = diff < 0.0f ? diff : 0.0f;
             }
             // exclusive warp scan of lam -> log T_k within the chunk (Eq. 8)
