@@ -241,6 +241,7 @@ def run_ours(args, world, rank, local):
     gp = torch.zeros_like(scene.probes)
     gm = torch.zeros_like(scene.mlp)
     stream = torch.cuda.current_stream(device)
+    occ = ps.render_occupancy(scene, params)
     ev = {k: [] for k in ("fwd0", "bwd1")}
 
     def step(record=False):
@@ -354,6 +355,7 @@ def run_ours(args, world, rank, local):
                 "h2d_bytes_per_step": int(h_o.numel() * 4 + h_d.numel() * 4 + h_t.numel() * 4),
                 "d2h_bytes_per_step": 4},
         "clocks": clk,
+        "ctas_per_sm": {"forward": occ[0], "backward": occ[1]},
         "gpu_launches": 2 * args.steps,
         "rays_per_s": world * n / (ms_per_step * 1e-3),
     }

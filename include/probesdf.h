@@ -112,6 +112,13 @@ int32_t psdf_last_cuda_error(void);
 /* Library version, major * 10000 + minor * 100 + patch. */
 int32_t psdf_version(void);
 
+/* Synchronises `stream`, then reads and clears the device status word of the
+ * current device into *flags: 0 = no device-side error since the last call;
+ * bit 0 = a kernel gave up waiting for its tensor-core work (the kernel
+ * stopped early; its outputs are not valid).  Kernels never trap: they
+ * record the condition here and return. */
+psdf_status psdf_device_status(void* stream, int32_t* flags);
+
 /* Bytes of the packed grid layout: one 16-byte record {sdf, f0, f1, f2} per
  * node, in the library's own node order.  The gradient buffer of
  * psdf_render_backward has the same size and layout (FP32). */
@@ -179,6 +186,13 @@ psdf_status psdf_render_backward(const psdf_grid* grid, const psdf_probes* probe
                                  const float* d_depth, const float* d_wsum,
                                  const float* logT_final, float* grad_grid,
                                  float* grad_probes, float* grad_mlp, void* stream);
+
+/* Resident CTAs per SM that psdf_render_forward / psdf_render_backward launch
+ * with for these objects (each CTA renders 4 rays at a time).  Host query,
+ * no kernel is launched. */
+psdf_status psdf_render_occupancy(const psdf_grid* grid, const psdf_probes* probes,
+                                  const psdf_mlp* mlp, const psdf_render_params* params,
+                                  int32_t* forward_ctas_per_sm, int32_t* backward_ctas_per_sm);
 
 #ifdef __cplusplus
 }

@@ -21,7 +21,7 @@ from . import build as _build
 __all__ = [
     "GridDesc", "ProbeDesc", "MlpDesc", "RenderParams", "Scene", "LibraryError",
     "library", "grid_bytes", "mlp_param_count", "pack_grid", "unpack_grid",
-    "render_forward", "render_backward", "render", "DIR_REFLECT", "DIR_VIEW",
+    "render_forward", "render_backward", "render", "device_status", "DIR_REFLECT", "DIR_VIEW",
 ]
 
 DIR_REFLECT = 0
@@ -71,6 +71,8 @@ def library() -> ctypes.CDLL:
         lib.psdf_status_string.argtypes = [ctypes.c_int32]
         lib.psdf_last_cuda_error.restype = ctypes.c_int32
         lib.psdf_version.restype = ctypes.c_int32
+        lib.psdf_device_status.argtypes = [_P, ctypes.POINTER(ctypes.c_int32)]
+        lib.psdf_device_status.restype = ctypes.c_int32
         lib.psdf_grid_bytes.argtypes = [_P, ctypes.POINTER(ctypes.c_size_t)]
         lib.psdf_grid_create.argtypes = [_P, _P, ctypes.POINTER(_P)]
         lib.psdf_grid_destroy.argtypes = [_P]
@@ -88,9 +90,11 @@ def library() -> ctypes.CDLL:
                                             _P, _P, _P, _P, _P]
         lib.psdf_render_backward.argtypes = [_P, _P, _P, _P, _P, _P, _P, ctypes.c_int64,
                                              _P, _P, _P, _P, _P, _P, _P, _P]
+        lib.psdf_render_occupancy.argtypes = [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_int32),
+                                              ctypes.POINTER(ctypes.c_int32)]
         for name in ("psdf_grid_bytes", "psdf_grid_create", "psdf_grid_pack", "psdf_grid_unpack",
                      "psdf_probes_create", "psdf_mlp_param_count", "psdf_mlp_create",
-                     "psdf_render_forward", "psdf_render_backward"):
+                     "psdf_render_forward", "psdf_render_backward", "psdf_render_occupancy"):
             getattr(lib, name).restype = ctypes.c_int32
         _lib = lib
         return lib
@@ -104,6 +108,15 @@ def _check(status: int, what: str):
         if status == -5:
             extra = f" (cudaError {lib.psdf_last_cuda_error()})"
         raise LibraryError(f"{what}: {msg}{extra}")
+
+
+def device_status(stream=None) -> int:
+    """Synchronises the stream, then reads and clears the device status word
+    (0 = no kernel gave up waiting on its tensor-core work)."""
+    flags = ctypes.c_int32()
+    _check(library().psdf_device_status(_stream(stream), ctypes.byref(flags)),
+           "psdf_device_status")
+    return flags.value
 
 
 def _ptr(t):
@@ -296,6 +309,20 @@ def render_backward(scene: Scene, rays_o, rays_d, params: RenderParams, d_rgb, l
     finally:
         h.close()
     return gg, gp, gm
+
+
+def render_occupancy(scene: Scene, params: RenderParams):
+    """(forward, backward) resident CTAs per SM of the render kernels."""
+    gd, pd, md = scene.descs(params.n_fresnel)
+    h = _Handles(scene.grid, scene.probes, scene.mlp, gd, pd, md)
+    f, b = ctypes.c_int32(), ctypes.c_int32()
+    try:
+        _check(library().psdf_render_occupancy(h.g, h.p, h.m, ctypes.byref(params),
+                                               ctypes.byref(f), ctypes.byref(b)),
+               "psdf_render_occupancy")
+    finally:
+        h.close()
+    return f.value, b.value
 
 
 class RenderFunction(torch.autograd.Function):

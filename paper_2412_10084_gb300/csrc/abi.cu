@@ -2,6 +2,7 @@
 // launch configuration, dense <-> packed grid conversion.
 #include <cstdint>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <new>
 
@@ -21,9 +22,27 @@ struct psdf_mlp {
     const void* params;
 };
 
+// Device status word (per device, static storage): kernels OR error bits into
+// it; psdf_device_status reads and clears it.
+__device__ int g_device_status;
+
 namespace {
 
 thread_local int32_t g_last_cuda_error = 0;
+
+// Address of g_device_status on the current device (looked up once per device).
+int* device_status_ptr()
+{
+    static int* ptrs[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!ptrs[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_device_status) != cudaSuccess) return nullptr;
+        ptrs[dev] = static_cast<int*>(p);
+    }
+    return ptrs[dev];
+}
 
 psdf_status cuda_status(cudaError_t e)
 {
@@ -136,6 +155,8 @@ psdf_status resolve(const psdf_grid* grid, const psdf_probes* probes, const psdf
     A.rays_d = rays_d;
     A.t_samples = t_samples;
     A.n_rays = n_rays;
+    A.status = device_status_ptr();
+    if (!A.status) return cuda_status(cudaErrorInvalidDevice);
     return PSDF_OK;
 }
 
@@ -179,6 +200,27 @@ __global__ void unpack_kernel(const float4* __restrict__ in, float* __restrict__
 
 namespace psdf {
 
+int resident_ctas(const cudaFuncAttributes& fa, int threads, size_t dyn_smem, unsigned tmem_cols)
+{
+    int dev = 0, regs_sm = 0, smem_sm = 0, thr_sm = 0, blk_sm = 0, reserved = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    cudaDeviceGetAttribute(&blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    const int warps = (threads + 31) / 32;
+    // registers are allocated per warp in units of 256
+    const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+    int n = blk_sm > 0 ? blk_sm : 32;
+    if (regs_warp > 0) n = std::min(n, regs_sm / (regs_warp * warps));
+    const size_t smem = dyn_smem + fa.sharedSizeBytes + static_cast<size_t>(reserved);
+    if (smem > 0) n = std::min<int>(n, static_cast<int>(smem_sm / smem));
+    n = std::min(n, thr_sm / threads);
+    if (tmem_cols > 0) n = std::min<int>(n, static_cast<int>(512 / tmem_cols));
+    return n;
+}
+
 cudaError_t launch_pack(const float* sdf, const float* feat, float4* packed, int64_t n_nodes,
                         cudaStream_t stream)
 {
@@ -219,7 +261,23 @@ const char* psdf_status_string(psdf_status s)
 
 int32_t psdf_last_cuda_error(void) { return g_last_cuda_error; }
 
-int32_t psdf_version(void) { return 100; }
+int32_t psdf_version(void) { return 200; }
+
+psdf_status psdf_device_status(void* stream, int32_t* flags)
+{
+    if (!flags) return PSDF_ERR_INVALID_ARG;
+    int* p = device_status_ptr();
+    if (!p) return cuda_status(cudaErrorInvalidDevice);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, p, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    *flags = v;
+    return PSDF_OK;
+}
 
 psdf_status psdf_grid_bytes(const psdf_grid_desc* desc, size_t* values_bytes)
 {
@@ -329,7 +387,10 @@ psdf_status psdf_render_forward(const psdf_grid* grid, const psdf_probes* probes
     r.args.depth = depth;
     r.args.wsum = wsum;
     r.args.logT = logT_final;
-    const int ctas = grid_size(n_rays, psdf::forward_ctas_per_sm(r.shape), psdf::kFwdThreads / 32);
+    int per_sm = 0;
+    st = cuda_status(psdf::forward_ctas_per_sm(r.shape, &per_sm));
+    if (st != PSDF_OK) return st;
+    const int ctas = grid_size(n_rays, per_sm, psdf::kFwdThreads / 32);
     return cuda_status(
         psdf::launch_forward(r.args, r.shape, ctas, static_cast<cudaStream_t>(stream)));
 }
@@ -359,10 +420,30 @@ psdf_status psdf_render_backward(const psdf_grid* grid, const psdf_probes* probe
     r.args.grad_grid = grad_grid;
     r.args.grad_probes = grad_probes;
     r.args.grad_mlp = grad_mlp;
-    const int ctas =
-        grid_size(n_rays, psdf::backward_ctas_per_sm(r.shape), psdf::kBwdThreads / 32);
+    int per_sm = 0;
+    st = cuda_status(psdf::backward_ctas_per_sm(r.shape, &per_sm));
+    if (st != PSDF_OK) return st;
+    const int ctas = grid_size(n_rays, per_sm, psdf::kBwdThreads / 32);
     return cuda_status(
         psdf::launch_backward(r.args, r.shape, ctas, static_cast<cudaStream_t>(stream)));
+}
+
+psdf_status psdf_render_occupancy(const psdf_grid* grid, const psdf_probes* probes,
+                                  const psdf_mlp* mlp, const psdf_render_params* params,
+                                  int32_t* forward_ctas_per_sm, int32_t* backward_ctas_per_sm)
+{
+    Resolved r;
+    psdf_status st = resolve(grid, probes, mlp, params, nullptr, nullptr, nullptr, 0, r);
+    if (st != PSDF_OK) return st;
+    if (!forward_ctas_per_sm || !backward_ctas_per_sm) return PSDF_ERR_INVALID_ARG;
+    int f = 0, b = 0;
+    st = cuda_status(psdf::forward_ctas_per_sm(r.shape, &f));
+    if (st != PSDF_OK) return st;
+    st = cuda_status(psdf::backward_ctas_per_sm(r.shape, &b));
+    if (st != PSDF_OK) return st;
+    *forward_ctas_per_sm = f;
+    *backward_ctas_per_sm = b;
+    return PSDF_OK;
 }
 
 }  // extern "C"

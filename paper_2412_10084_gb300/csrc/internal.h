@@ -26,8 +26,13 @@ cudaError_t launch_forward(const RenderArgs& A, const KernelShape& ks, int grid_
                            cudaStream_t stream);
 cudaError_t launch_backward(const RenderArgs& A, const KernelShape& ks, int grid_ctas,
                             cudaStream_t stream);
-int forward_ctas_per_sm(const KernelShape& ks);
-int backward_ctas_per_sm(const KernelShape& ks);
+// Resident CTAs per SM of a kernel from its registers and shared memory, the
+// device's per-SM limits and the tensor-memory columns each CTA allocates.
+int resident_ctas(const cudaFuncAttributes& fa, int threads, size_t dyn_smem, unsigned tmem_cols);
+
+// Resident CTAs per SM (occupancy, capped by tensor-memory columns).
+cudaError_t forward_ctas_per_sm(const KernelShape& ks, int* n);
+cudaError_t backward_ctas_per_sm(const KernelShape& ks, int* n);
 
 cudaError_t launch_pack(const float* sdf, const float* feat, float4* packed, int64_t n_nodes,
                         cudaStream_t stream);

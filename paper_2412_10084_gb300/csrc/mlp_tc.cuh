@@ -1,0 +1,123 @@
+// Colour MLP (Sec. 4) on the tcgen05 tensor cores, FP32-equivalent accuracy.
+//
+// A CTA of 4 warps batches its 128 samples (4 rays x 32 samples) into M = 128
+// tiles.  Every FP32 operand x is split into hi = fp16(x) and lo = fp16(x - hi)
+// (about 22 significant bits); each layer is A_hi B_hi + A_hi B_lo + A_lo B_hi,
+// accumulated in FP32 in tensor memory.  Layer 3 (width -> 3) stays on the
+// CUDA cores.  The adjoint reads the same tiles transposed (MN-major).
+#pragma once
+
+#include "sample_eval.cuh"
+#include "tc_sm100.cuh"
+
+namespace psdf {
+
+template <class C>
+struct MlpTC {
+    static constexpr int W = C::W;
+    static constexpr int K1 = 16;           // layer-1 K: n_in padded to 16
+    static_assert(C::NIN < K1, "n_in + a bias column must fit in 16");
+    static_assert(W == 16 || W == 32, "hidden width 16 or 32");
+    static constexpr int kW1 = W * K1 * 2;  // bytes of one split of W1 [W][16]
+    static constexpr int kW2 = W * W * 2;   // bytes of one split of W2 [W][W]
+    static constexpr int kWeightBytes = 2 * (kW1 + kW2);
+    // FP32 parameters kept for the CUDA-core parts: b1[W] b2[W] W3T[W][4] b3[4]
+    static constexpr int kB1 = 0, kB2 = W, kW3T = 2 * W, kB3 = 6 * W, kF32 = 6 * W + 4;
+    static constexpr uint32_t kIdescL = tc::idesc_f16(128, W, 0, 0);
+};
+
+// Cooperative load of the packed FP32 parameters into the split weight tiles
+// (hi at w, lo at w + kW1 / + kW2) and the FP32 block.
+template <class C>
+__device__ __forceinline__ void load_mlp_tc(const float* __restrict__ g, uint8_t* wt, float* f32)
+{
+    using M = MlpTC<C>;
+    constexpr int W = C::W;
+    uint8_t* w1h = wt;
+    uint8_t* w1l = wt + M::kW1;
+    uint8_t* w2h = wt + 2 * M::kW1;
+    uint8_t* w2l = w2h + M::kW2;
+    for (int i = threadIdx.x; i < W * M::K1; i += blockDim.x) {
+        const int o = i / M::K1, j = i % M::K1;
+        const float v = j < C::NIN ? g[C::gW1 + o * C::NIN + j] : 0.0f;
+        __half h, l;
+        tc::split2(v, h, l);
+        const uint32_t off = tc::tile_off(o, j, M::K1);
+        *reinterpret_cast<__half*>(w1h + off) = h;
+        *reinterpret_cast<__half*>(w1l + off) = l;
+    }
+    for (int i = threadIdx.x; i < W * W; i += blockDim.x) {
+        const int o = i / W, j = i % W;
+        __half h, l;
+        tc::split2(g[C::gW2 + i], h, l);
+        const uint32_t off = tc::tile_off(o, j, W);
+        *reinterpret_cast<__half*>(w2h + off) = h;
+        *reinterpret_cast<__half*>(w2l + off) = l;
+    }
+    for (int i = threadIdx.x; i < M::kF32; i += blockDim.x) {
+        float v;
+        if (i < M::kB2) {
+            v = g[C::gB1 + i];
+        } else if (i < M::kW3T) {
+            v = g[C::gB2 + (i - M::kB2)];
+        } else if (i < M::kB3) {
+            const int o = (i - M::kW3T) / 4, c = (i - M::kW3T) % 4;
+            v = c < 3 ? g[C::gW3 + c * W + o] : 0.0f;
+        } else {
+            const int c = i - M::kB3;
+            v = c < 3 ? g[C::gB3 + c] : 0.0f;
+        }
+        f32[i] = v;
+    }
+}
+
+// The three split products of one K-major x K-major k-step.
+__device__ __forceinline__ void mma3(uint32_t d, const uint8_t* a_hi, const uint8_t* a_lo,
+                                     const uint8_t* b_hi, const uint8_t* b_lo, uint32_t a_lbo,
+                                     uint32_t a_sbo, uint32_t b_lbo, uint32_t b_sbo,
+                                     uint32_t idesc, bool accumulate)
+{
+    const uint64_t ah = tc::desc(a_hi, a_lbo, a_sbo), al = tc::desc(a_lo, a_lbo, a_sbo);
+    const uint64_t bh = tc::desc(b_hi, b_lbo, b_sbo), bl = tc::desc(b_lo, b_lbo, b_sbo);
+    tc::mma_f16(d, ah, bh, idesc, accumulate);
+    tc::mma_f16(d, ah, bl, idesc, true);
+    tc::mma_f16(d, al, bh, idesc, true);
+}
+
+// Layer 3 (W -> 3) and the sigmoid on the CUDA cores: h2 already ReLU'd.
+template <class C>
+__device__ __forceinline__ void mlp_layer3(const float* f32, const float* h2, float col[3])
+{
+    using M = MlpTC<C>;
+    const float4 b3 = *reinterpret_cast<const float4*>(f32 + M::kB3);
+    float z0 = b3.x, z1 = b3.y, z2 = b3.z;
+#pragma unroll
+    for (int o = 0; o < C::W; ++o) {
+        const float4 w3 = *reinterpret_cast<const float4*>(f32 + M::kW3T + 4 * o);
+        z0 = fmaf(w3.x, h2[o], z0);
+        z1 = fmaf(w3.y, h2[o], z1);
+        z2 = fmaf(w3.z, h2[o], z2);
+    }
+    col[0] = sigmoidf(z0);
+    col[1] = sigmoidf(z1);
+    col[2] = sigmoidf(z2);
+}
+
+// Writes a row of `n` FP32 values (n a multiple of 8) as split FP16 into
+// columns [c0, c0 + n) of a tile with C columns.
+template <int NV>
+__device__ __forceinline__ void store_row(uint8_t* hi, uint8_t* lo, int row, int c0, int C,
+                                          const float* v)
+{
+#pragma unroll
+    for (int g = 0; g < NV; g += 8) tc::store8(hi, lo, row, c0 + g, C, v + g);
+}
+
+template <int NV>
+__device__ __forceinline__ void zero_row(uint8_t* hi, uint8_t* lo, int row, int c0, int C)
+{
+#pragma unroll
+    for (int g = 0; g < NV; g += 8) tc::zero8(hi, lo, row, c0 + g, C);
+}
+
+}  // namespace psdf

@@ -1,168 +1,88 @@
-// Adjoint of the ProbeSDF render (Sec. 3.3-3.4), FP32, sm_103a.
+// Adjoint of the ProbeSDF render (Sec. 3.3-3.4), sm_103a.
 //
-// Each warp walks its ray's 32-sample chunks back to front starting from the
-// saved log T_N, recomputing every per-sample activation (nothing per sample
-// is stored by the forward).  Per chunk:
-//   - transmittance from a warp suffix-sum of the clipped log-opacities;
-//   - the suffix term of dL/dalpha_k = T_k (G_k - S_k) from a warp scan of
-//     the affine recurrence S_k = alpha_{k+1} G_{k+1} + (1 - alpha_{k+1}) S_{k+1};
-//   - MLP backward per lane, the weight gradient as a lane-transposed pass
-//     over the chunk's activation rows in shared memory (one CTA-level
-//     shared-memory accumulator, flushed to global memory once per CTA);
-//   - SDF / feature gradients as one 16-byte vector reduction per corner;
-//   - probe gradients reduced over runs of samples that share a probe cell
-//     (consecutive along a ray) before the global reductions.
+// Same CTA organisation as the forward: 4 warps, one ray per warp, lockstep
+// 32-sample chunks forming M = 128 tiles, but chunks are walked back to front
+// starting from the saved log T_N, and every per-sample activation is
+// recomputed (nothing per sample is stored by the forward).  Per chunk:
+//   P0  recompute geometry and features -> input row of the XH tile;
+//   P1  layer 1 (tensor cores); warp suffix sum of the clipped log-opacities
+//       gives log T_k;
+//   P2  layer 2 (tensor cores) and layer 3; the suffix term of
+//       dL/dalpha_k = T_k (G_k - S_k) from a warp scan of the affine recurrence
+//       S_k = alpha_{k+1} G_{k+1} + (1 - alpha_{k+1}) S_{k+1}; sigmoid and layer-3
+//       adjoints on the CUDA cores -> dz2 row of the DZ tile;
+//   P3  dh1 = dz2 W2 (tensor cores, W2 read transposed) -> dz1 row;
+//   P4  dx = dz1 W1 (tensor cores) and the weight gradient
+//       [dz1 | dz2]^T [x, 1 | h1] as an M = 64 MMA over the transposed tiles,
+//       accumulated in tensor memory for the whole kernel;
+//   P5  angular, Fresnel, normal and spatial-feature adjoints; SDF + feature
+//       gradients as one 16-byte vector reduction per corner; probe gradients
+//       summed over runs of samples sharing a probe cell.
+// MLP-path gradients in the FP16 tiles are carried scaled by per-CTA powers of
+// two, from rigorous bounds (largest dL/drgb among the CTA's rays and column
+// sums of |W3| and |W2|), so they never overflow and keep their precision.
 #include "internal.h"
-#include "sample_eval.cuh"
+#include "mlp_tc.cuh"
 
 namespace psdf {
 
 template <class C>
 struct BwdLayout {
-    static constexpr int HS = C::W + 4;                  // row stride of h1/h2/dz rows
-    static constexpr int PST = ((8 + C::L2 + C::NA + 1) + 3) & ~3;  // probe staging row
+    using M = MlpTC<C>;
+    static constexpr int W = C::W;
+    static constexpr int K1 = M::K1;
+    static constexpr int XHC = K1 + W;   // XH tile: [x (n_in), 1, 0.. | h1 (W)]
+    static constexpr int DZC = 64;       // DZ tile: [dz1 (W) | dz2 (W) | unused]
+    static constexpr int kXH = 128 * XHC * 2;
+    static constexpr int kDZ = 128 * DZC * 2;
+    static constexpr uint32_t kSboXH = (XHC / 8) * 128;
+    static constexpr uint32_t kSboDZ = (DZC / 8) * 128;
+    static constexpr int PST = ((8 + C::L2 + C::NA + 1) + 3) & ~3;  // probe staging row (floats)
     static constexpr int kParamsPad = (C::kParams + 3) & ~3;
-    static constexpr int kMlpPad = (C::kMlpSmem + 3) & ~3;
-    // per-warp region
-    static constexpr int kXs = 0;
-    static constexpr int kH1 = kXs + 32 * C::NINP;
-    static constexpr int kH2 = kH1 + 32 * HS;
-    static constexpr int kDz1 = kH2 + 32 * HS;
-    static constexpr int kDz2 = kDz1 + 32 * HS;
-    static constexpr int kDz3 = kDz2 + 32 * HS;
-    static constexpr int kPst = kDz3 + 32 * 4;
-    static constexpr int kWarpFloats = kPst + 32 * PST;
-    static constexpr int kWarps = kBwdThreads / 32;
-    static constexpr int kSmemFloats = kMlpPad + kParamsPad + kWarps * kWarpFloats;
-    static constexpr size_t kSmemBytes = sizeof(float) * kSmemFloats;
+    static constexpr int oW = 0;
+    static constexpr int oF32 = oW + M::kWeightBytes;
+    static constexpr int oXH = (oF32 + 4 * M::kF32 + 127) & ~127;
+    static constexpr int oDZ = oXH + 2 * kXH;
+    static constexpr int oG = oDZ + 2 * kDZ;
+    static constexpr int oMisc = oG + 4 * kParamsPad;
+    static constexpr int kBytes = oMisc + 64;
+    static constexpr uint32_t kTmemCols = 128;  // z1/dh1 at 0, z2/dx at 32, dW at 64
+    static_assert(128 * PST * 4 <= 2 * kDZ, "probe staging aliases the DZ tiles");
+    static_assert(XHC <= 64, "dW accumulator fits columns 64..127");
 };
 
-__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
-__device__ __forceinline__ void st4(float* p, float a, float b, float c, float d)
+__device__ __forceinline__ float warp_max(float v)
 {
-    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+    return v;
 }
 
-// Lane-transposed accumulation of the MLP weight gradient over the chunk's
-// nact activation rows; results are added to the CTA accumulator gacc
-// (packed global layout).
-template <class C, class Lay>
-__device__ __forceinline__ void accumulate_dw(const float* xs, const float* h1s, const float* h2s,
-                                              const float* dz1s, const float* dz2s,
-                                              const float* dz3s, int nact, int lane, float* gacc)
+// Reduce-scatter of 16 elements over the warp: on return lane l holds the
+// warp sum of element (l % 16).
+__device__ __forceinline__ float reduce_scatter16(float* v, int lane)
 {
-    constexpr int W = C::W, NINP = C::NINP, NIN = C::NIN, HS = Lay::HS;
-    if constexpr (W == 32) {
-        const int o = lane;
-        float a1[NINP], a2[W], a3[3] = {0.f, 0.f, 0.f};
-        float db1 = 0.f, db2 = 0.f, db3 = 0.f;
 #pragma unroll
-        for (int i = 0; i < NINP; ++i) a1[i] = 0.f;
+    for (int m = 8, half = 8; m > 0; m >>= 1, half >>= 1) {
+        const bool upper = (lane & m) != 0;
 #pragma unroll
-        for (int i = 0; i < W; ++i) a2[i] = 0.f;
-        for (int s = 0; s < nact; ++s) {
-            const float d1 = dz1s[s * HS + o];
-            const float d2 = dz2s[s * HS + o];
-            const float h2o = h2s[s * HS + o];
-            const float4 d3 = ld4(dz3s + 4 * s);
-#pragma unroll
-            for (int q = 0; q < NINP / 4; ++q) {
-                const float4 xv = ld4(xs + s * NINP + 4 * q);
-                a1[4 * q + 0] = fmaf(d1, xv.x, a1[4 * q + 0]);
-                a1[4 * q + 1] = fmaf(d1, xv.y, a1[4 * q + 1]);
-                a1[4 * q + 2] = fmaf(d1, xv.z, a1[4 * q + 2]);
-                a1[4 * q + 3] = fmaf(d1, xv.w, a1[4 * q + 3]);
-            }
-#pragma unroll
-            for (int q = 0; q < W / 4; ++q) {
-                const float4 hv = ld4(h1s + s * HS + 4 * q);
-                a2[4 * q + 0] = fmaf(d2, hv.x, a2[4 * q + 0]);
-                a2[4 * q + 1] = fmaf(d2, hv.y, a2[4 * q + 1]);
-                a2[4 * q + 2] = fmaf(d2, hv.z, a2[4 * q + 2]);
-                a2[4 * q + 3] = fmaf(d2, hv.w, a2[4 * q + 3]);
-            }
-            a3[0] = fmaf(d3.x, h2o, a3[0]);
-            a3[1] = fmaf(d3.y, h2o, a3[1]);
-            a3[2] = fmaf(d3.z, h2o, a3[2]);
-            db1 += d1;
-            db2 += d2;
-            db3 += lane == 0 ? d3.x : (lane == 1 ? d3.y : d3.z);
-        }
-#pragma unroll
-        for (int i = 0; i < NIN; ++i) atomicAdd(gacc + C::gW1 + o * NIN + i, a1[i]);
-        atomicAdd(gacc + C::gB1 + o, db1);
-#pragma unroll
-        for (int i = 0; i < W; ++i) atomicAdd(gacc + C::gW2 + o * W + i, a2[i]);
-        atomicAdd(gacc + C::gB2 + o, db2);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) atomicAdd(gacc + C::gW3 + c * W + o, a3[c]);
-        if (lane < 3) atomicAdd(gacc + C::gB3 + lane, db3);
-    } else {
-        static_assert(W == 16, "hidden width 16 or 32");
-        const int o = lane & 15;
-        if (lane < 16) {
-            // W1 row o, b1[o], W3 column o, b3
-            float a1[NINP], a3[3] = {0.f, 0.f, 0.f};
-            float db1 = 0.f, db3 = 0.f;
-#pragma unroll
-            for (int i = 0; i < NINP; ++i) a1[i] = 0.f;
-            for (int s = 0; s < nact; ++s) {
-                const float d1 = dz1s[s * HS + o];
-                const float h2o = h2s[s * HS + o];
-                const float4 d3 = ld4(dz3s + 4 * s);
-#pragma unroll
-                for (int q = 0; q < NINP / 4; ++q) {
-                    const float4 xv = ld4(xs + s * NINP + 4 * q);
-                    a1[4 * q + 0] = fmaf(d1, xv.x, a1[4 * q + 0]);
-                    a1[4 * q + 1] = fmaf(d1, xv.y, a1[4 * q + 1]);
-                    a1[4 * q + 2] = fmaf(d1, xv.z, a1[4 * q + 2]);
-                    a1[4 * q + 3] = fmaf(d1, xv.w, a1[4 * q + 3]);
-                }
-                a3[0] = fmaf(d3.x, h2o, a3[0]);
-                a3[1] = fmaf(d3.y, h2o, a3[1]);
-                a3[2] = fmaf(d3.z, h2o, a3[2]);
-                db1 += d1;
-                db3 += lane == 0 ? d3.x : (lane == 1 ? d3.y : d3.z);
-            }
-#pragma unroll
-            for (int i = 0; i < NIN; ++i) atomicAdd(gacc + C::gW1 + o * NIN + i, a1[i]);
-            atomicAdd(gacc + C::gB1 + o, db1);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) atomicAdd(gacc + C::gW3 + c * W + o, a3[c]);
-            if (lane < 3) atomicAdd(gacc + C::gB3 + lane, db3);
-        } else {
-            // W2 row o, b2[o]
-            float a2[W];
-            float db2 = 0.f;
-#pragma unroll
-            for (int i = 0; i < W; ++i) a2[i] = 0.f;
-            for (int s = 0; s < nact; ++s) {
-                const float d2 = dz2s[s * HS + o];
-#pragma unroll
-                for (int q = 0; q < W / 4; ++q) {
-                    const float4 hv = ld4(h1s + s * HS + 4 * q);
-                    a2[4 * q + 0] = fmaf(d2, hv.x, a2[4 * q + 0]);
-                    a2[4 * q + 1] = fmaf(d2, hv.y, a2[4 * q + 1]);
-                    a2[4 * q + 2] = fmaf(d2, hv.z, a2[4 * q + 2]);
-                    a2[4 * q + 3] = fmaf(d2, hv.w, a2[4 * q + 3]);
-                }
-                db2 += d2;
-            }
-#pragma unroll
-            for (int i = 0; i < W; ++i) atomicAdd(gacc + C::gW2 + o * W + i, a2[i]);
-            atomicAdd(gacc + C::gB2 + o, db2);
+        for (int j = 0; j < half; ++j) {
+            const float send = upper ? v[j] : v[j + half];
+            const float keep = upper ? v[j + half] : v[j];
+            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, m);
         }
     }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
 }
 
 // Probe-coefficient gradient (Eqs. 6-7): dL/db_ijc = sum_k w_i(k) Y_j(k) dF_a,c(k).
 // Samples of a chunk that share a probe cell are consecutive; lane (corner i,
 // channel c) sums each run and issues one reduction per coefficient.
-template <class C, class Lay>
+template <class C, int PST>
 __device__ __forceinline__ void scatter_probe_grad(const RenderArgs& A, const float* pst, int nact,
                                                    int lane)
 {
-    constexpr int L2 = C::L2, NA = C::NA, PST = Lay::PST;
+    constexpr int L2 = C::L2, NA = C::NA;
     constexpr int CPL = (8 * NA) / 32;
     static_assert((8 * NA) % 32 == 0, "8 corners x channels must fill whole warps");
     const int Px = A.probes.P[0], Pxy = A.probes.P[0] * A.probes.P[1];
@@ -202,80 +122,166 @@ __device__ __forceinline__ void scatter_probe_grad(const RenderArgs& A, const fl
 }
 
 template <class C>
-__global__ void __launch_bounds__(kBwdThreads)
+__global__ void __launch_bounds__(kBwdThreads, 3)
 render_backward_kernel(RenderArgs A)
 {
-    using Lay = BwdLayout<C>;
-    constexpr int W = C::W, NINP = C::NINP, HS = Lay::HS, NA = C::NA, L2 = C::L2;
-    extern __shared__ __align__(16) float smem[];
-    float* sw = smem;
-    float* gacc = smem + Lay::kMlpPad;
-    const int warp_in_cta = threadIdx.x >> 5;
-    float* wreg = gacc + Lay::kParamsPad + warp_in_cta * Lay::kWarpFloats;
-    float* xs = wreg + Lay::kXs;
-    float* h1s = wreg + Lay::kH1;
-    float* h2s = wreg + Lay::kH2;
-    float* dz1s = wreg + Lay::kDz1;
-    float* dz2s = wreg + Lay::kDz2;
-    float* dz3s = wreg + Lay::kDz3;
-    float* pst = wreg + Lay::kPst;
+    using M = MlpTC<C>;
+    using L = BwdLayout<C>;
+    constexpr int W = C::W, L2 = C::L2, NA = C::NA, NIN = C::NIN, K1 = M::K1;
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint8_t* wt = smem + L::oW;
+    uint8_t* w1h = wt;
+    uint8_t* w1l = wt + M::kW1;
+    uint8_t* w2h = wt + 2 * M::kW1;
+    uint8_t* w2l = w2h + M::kW2;
+    float* f32 = reinterpret_cast<float*>(smem + L::oF32);
+    uint8_t* xhh = smem + L::oXH;
+    uint8_t* xhl = xhh + L::kXH;
+    uint8_t* dzh = smem + L::oDZ;
+    uint8_t* dzl = dzh + L::kDZ;
+    float* gacc = reinterpret_cast<float*>(smem + L::oG);
+    float* red = reinterpret_cast<float*>(smem + L::oMisc);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::oMisc + 32);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::oMisc + 40);
 
-    load_mlp_smem<C>(A.mlp, sw);
-    for (int i = threadIdx.x; i < Lay::kParamsPad; i += blockDim.x) gacc[i] = 0.0f;
-    __syncthreads();
-
-    const int lane = threadIdx.x & 31;
-    const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const unsigned FULL = 0xffffffffu;
     const int N = A.n_samples;
     const float tau = A.tau;
-    const unsigned FULL = 0xffffffffu;
+    const int64_t stride = int64_t(gridDim.x) * 4;
+    int64_t ray = int64_t(blockIdx.x) * 4 + warp;
 
-    for (int64_t ray = warp0; ray < A.n_rays; ray += nwarps) {
-        const RayIn R = load_ray(A, ray);
-        const RaySpan sp = ray_span(A, R, ray);
-        if (!sp.hit) continue;
-        const float drgb[3] = {__ldg(A.d_rgb + 3 * ray), __ldg(A.d_rgb + 3 * ray + 1),
-                               __ldg(A.d_rgb + 3 * ray + 2)};
-        const float ddepth = A.d_depth ? __ldg(A.d_depth + ray) : 0.0f;
-        const float dwsum = A.d_wsum ? __ldg(A.d_wsum + ray) : 0.0f;
-        float logT_end = __ldg(A.logT + ray);  // log T at the point after the chunk
+    load_mlp_tc<C>(A.mlp, wt, f32);
+    for (int i = tid; i < L::kParamsPad; i += blockDim.x) gacc[i] = 0.0f;
+    if (warp == 0) tc::tmem_alloc(tslot, L::kTmemCols);
+    if (tid == 0) tc::mbar_init(mbar, 1);
+    {
+        // gradient scale: the largest |dL/drgb| over the rays this CTA renders
+        float m = 0.0f;
+        for (int64_t r = ray + int64_t(lane) * stride; r < A.n_rays; r += 32 * stride)
+            m = fmaxf(m, fmaxf(fabsf(__ldg(A.d_rgb + 3 * r)),
+                               fmaxf(fabsf(__ldg(A.d_rgb + 3 * r + 1)),
+                                     fabsf(__ldg(A.d_rgb + 3 * r + 2)))));
+        m = warp_max(m);
+        if (lane == 0) red[warp] = m;
+    }
+    tc::fence_smem_to_async();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t t_row = tmem + (static_cast<uint32_t>(32 * warp) << 16);
+    // Power-of-two scales of the dz2 and dz1 tiles.  With |w| <= 1 and
+    // sigmoid' <= 1/4: |dz3| <= M/4 (M = largest |dL/drgb| of the CTA),
+    // |dz2_i| <= B2 = M/4 * sum_c |W3[c][i]|, |dz1_i| <= B1 = max_i sum_o |W2[o][i]| * B2.
+    // Scaling each bound to <= 2^12 keeps every value finite in FP16 while
+    // values down to ~1e-5 of the bound keep both halves of the split normal.
+    float s1 = 1.0f, inv_s1 = 1.0f, s2 = 1.0f, inv_s2 = 1.0f;
+    {
+        const float m = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
+        float c3 = 0.0f, c2 = 0.0f;
+        for (int i = 0; i < W; ++i) {
+            const float4 w3 = *reinterpret_cast<const float4*>(f32 + M::kW3T + 4 * i);
+            c3 = fmaxf(c3, fabsf(w3.x) + fabsf(w3.y) + fabsf(w3.z));
+        }
+        for (int i = 0; i < W; ++i) {
+            float cs = 0.0f;
+            for (int o = 0; o < W; ++o) cs += fabsf(__ldg(A.mlp + C::gW2 + o * W + i));
+            c2 = fmaxf(c2, cs);
+        }
+        const float b2 = 0.25f * m * c3, b1 = b2 * c2;
+        int e;
+        if (b2 > 0.0f && b2 < 1e30f) {
+            frexpf(b2, &e);
+            s2 = ldexpf(1.0f, 12 - e);
+            inv_s2 = ldexpf(1.0f, e - 12);
+        }
+        if (b1 > 0.0f && b1 < 1e30f) {
+            frexpf(b1, &e);
+            s1 = ldexpf(1.0f, 12 - e);
+            inv_s1 = ldexpf(1.0f, e - 12);
+        }
+    }
+    uint32_t phase = 0;
+    bool bad = false, any_chunk = false, dw_started = false;
+    float acc3[3] = {0.f, 0.f, 0.f}, accb3 = 0.0f;  // dW3 column (lane % W) and db3 (lane < 3)
+
+    for (;;) {
+        RayIn R;
+        RaySpan sp;
+        bool have = false;
+        while (ray < A.n_rays) {
+            R = load_ray(A, ray);
+            sp = ray_span(A, R, ray);
+            if (sp.hit) {
+                have = true;
+                break;
+            }
+            ray += stride;
+        }
+        if (!__syncthreads_or(have)) break;
+        any_chunk = true;
+
+        float drgb[3] = {0.f, 0.f, 0.f}, ddepth = 0.f, dwsum = 0.f, logT_end = 0.f;
+        if (have) {
+            drgb[0] = __ldg(A.d_rgb + 3 * ray);
+            drgb[1] = __ldg(A.d_rgb + 3 * ray + 1);
+            drgb[2] = __ldg(A.d_rgb + 3 * ray + 2);
+            ddepth = A.d_depth ? __ldg(A.d_depth + ray) : 0.0f;
+            dwsum = A.d_wsum ? __ldg(A.d_wsum + ray) : 0.0f;
+            logT_end = __ldg(A.logT + ray);
+        }
         float s_carry = drgb[0] * A.bg[0] + drgb[1] * A.bg[1] + drgb[2] * A.bg[2];
         const int nch = (N + 31) >> 5;
 
         for (int ch = nch - 1; ch >= 0; --ch) {
             const int base = ch * 32;
             const int k = base + lane;
-            const bool active = k < N;
-            const int nact = min(32, N - base);
-            const float t = span_t(sp, active ? k : N - 1);
-
-            SampleGeom<C> S;
-            eval_geometry<C>(A, R.o, R.d, t, S);
-            float col[3];
-            mlp_forward<C, true>(sw, S.x, col, xs + lane * NINP, h1s + lane * HS,
-                                 h2s + lane * HS);
-
-            // s at point k+1 (extra gather for the chunk's last sample)
-            float s_next = __shfl_down_sync(FULL, S.s, 1);
+            const bool active = have && k < N;
+            const int nact = have ? min(32, N - base) : 0;
             const bool extra = active && (lane == 31 || k + 1 >= N);
+
+            // ---- P0: recompute geometry and features -> XH columns [0, 16) ----
+            SampleGeom<C> S;
+            float t = 0.0f, lam = 0.0f, s_next = 0.0f;
+            bool unclipped = false;
             Cell c1;
             c1.base = 0;
-            c1.f[0] = c1.f[1] = c1.f[2] = 0.f;
-            if (extra) {
-                float xw[3];
-                point_at(R.o, R.d, span_t(sp, k + 1), xw);
-                c1 = locate(xw, A.grid.bmin, A.grid.sc, A.grid.R);
-                s_next = sdf_value(A.grid, c1);
+            c1.f[0] = c1.f[1] = c1.f[2] = 0.0f;
+            if (have) {
+                t = span_t(sp, k < N ? k : N - 1);
+                eval_geometry<C>(A, R.o, R.d, t, S);
+                float xin[K1];
+#pragma unroll
+                for (int i = 0; i < K1; ++i) xin[i] = i < NIN ? S.x[i] : (i == NIN ? 1.0f : 0.0f);
+                store_row<K1>(xhh, xhl, tid, 0, L::XHC, xin);
+                s_next = __shfl_down_sync(FULL, S.s, 1);
+                if (extra) {
+                    float xw[3];
+                    point_at(R.o, R.d, span_t(sp, k + 1), xw);
+                    c1 = locate(xw, A.grid.bmin, A.grid.sc, A.grid.R);
+                    s_next = sdf_value(A.grid, c1);
+                }
+                if (active) {
+                    const float diff = log_transmittance(tau, S.s, s_next);
+                    unclipped = diff < 0.0f;
+                    lam = unclipped ? diff : 0.0f;
+                }
+            } else {
+                zero_row<K1>(xhh, xhl, tid, 0, L::XHC);
+                S.s = 0.0f;
             }
-            float lam = 0.0f;
-            bool unclipped = false;
-            if (active) {
-                const float diff = log_transmittance(tau, S.s, s_next);
-                unclipped = diff < 0.0f;
-                lam = unclipped ? diff : 0.0f;
+            tc::fence_smem_to_async();
+            tc::fence_before();
+            if (__syncthreads_or(bad)) goto done;
+            tc::fence_after();
+
+            // ---- P1: layer 1; log T_k from a suffix sum of lam ----
+            if (tid == 0) {
+                mma3(tmem + 0, xhh, xhl, w1h, w1l, 128, L::kSboXH, 128, (K1 / 8) * 128,
+                     M::kIdescL, false);
+                tc::commit(mbar);
             }
-            // inclusive suffix sum of lam over the chunk: log T_k = log T_end - suf
             float suf = lam;
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
@@ -286,11 +292,58 @@ render_backward_kernel(RenderArgs A)
             const float Tk = expf(logTk);
             const float Tk1 = expf(logTk + lam);
             const float alpha = -expm1f(lam);
+            bad |= !tc::mbar_wait(mbar, phase);
+            phase ^= 1;
+            tc::fence_after();
+            uint32_t mask1 = 0;
+            {
+                float z[W];
+                tc::tmem_ld<W>(t_row + 0, z);
+#pragma unroll
+                for (int o = 0; o < W; ++o) {
+                    const float h = z[o] + f32[M::kB1 + o];
+                    mask1 |= (h > 0.0f ? 1u : 0u) << o;
+                    z[o] = fmaxf(h, 0.0f);
+                }
+                if (!have) {
+#pragma unroll
+                    for (int o = 0; o < W; ++o) z[o] = 0.0f;
+                }
+                store_row<W>(xhh, xhl, tid, K1, L::XHC, z);
+            }
+            tc::fence_smem_to_async();
+            tc::fence_before();
+            __syncthreads();
+            tc::fence_after();
+
+            // ---- P2: layer 2 + 3; compositing adjoint; dz3 -> dz2 ----
+            if (tid == 0) {
+#pragma unroll
+                for (int s = 0; s < W / 16; ++s)
+                    mma3(tmem + 32, xhh + 256 + s * 256, xhl + 256 + s * 256, w2h + s * 256,
+                         w2l + s * 256, 128, L::kSboXH, 128, (W / 8) * 128, M::kIdescL, s > 0);
+                tc::commit(mbar);
+            }
+            bad |= !tc::mbar_wait(mbar, phase);
+            phase ^= 1;
+            tc::fence_after();
+            float h2[W];
+            uint32_t mask2 = 0;
+            float col[3];
+            {
+                tc::tmem_ld<W>(t_row + 32, h2);
+#pragma unroll
+                for (int o = 0; o < W; ++o) {
+                    const float h = h2[o] + f32[M::kB2 + o];
+                    mask2 |= (h > 0.0f ? 1u : 0u) << o;
+                    h2[o] = fmaxf(h, 0.0f);
+                }
+                mlp_layer3<C>(f32, h2, col);
+            }
             const float w = active ? Tk * alpha : 0.0f;
             const float G = active ? drgb[0] * col[0] + drgb[1] * col[1] + drgb[2] * col[2] +
                                          ddepth * t + dwsum
                                    : 0.0f;
-            // suffix recurrence S_k = a_{k+1} S_{k+1} + b_{k+1}, a = 1 - alpha, b = alpha G
             const float a_own = active ? expf(lam) : 1.0f;
             const float b_own = active ? alpha * G : 0.0f;
             float Am = __shfl_down_sync(FULL, a_own, 1);
@@ -315,183 +368,242 @@ render_backward_kernel(RenderArgs A)
             if (lane == 0) dlam_prev = 0.0f;
             const float ds_own = active ? (dlam_prev - dlam) * dlog_phi(tau, S.s) : 0.0f;
 
-            // ---- colour path: sigmoid, MLP backward ----
             float dz3[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) dz3[c] = w * drgb[c] * col[c] * (1.0f - col[c]);
-            st4(dz3s + 4 * lane, dz3[0], dz3[1], dz3[2], 0.0f);
-            float dh1[W];
+            // dW3 and db3 on the CUDA cores: warp reduce-scatter of dz3 (x) h2 in
+            // 16-column slices; lane l accumulates column 16 * (l / 16) + l % 16
 #pragma unroll
-            for (int i = 0; i < W; ++i) dh1[i] = 0.0f;
-            const float* h2row = h2s + lane * HS;
-            float* dz2row = dz2s + lane * HS;
+            for (int c = 0; c < 3; ++c) {
 #pragma unroll
-            for (int o4 = 0; o4 < W / 4; ++o4) {
-                const float4 hv = ld4(h2row + 4 * o4);
-                const float hh[4] = {hv.x, hv.y, hv.z, hv.w};
-                float dz2v[4];
+                for (int hs = 0; hs < W / 16; ++hs) {
+                    float v[16];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int o = 4 * o4 + u;
-                    const float4 w3 = ld4(sw + C::kW3T + 4 * o);
+                    for (int i = 0; i < 16; ++i) v[i] = dz3[c] * h2[16 * hs + i];
+                    const float r = reduce_scatter16(v, lane);
+                    if ((lane >> 4) == hs) acc3[c] += r;
+                }
+                float sb = dz3[c];
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) sb += __shfl_xor_sync(FULL, sb, off);
+                if (lane == c) accb3 += sb;
+            }
+            {
+                float dz2[W];
+#pragma unroll
+                for (int i = 0; i < W; ++i) {
+                    const float4 w3 = *reinterpret_cast<const float4*>(f32 + M::kW3T + 4 * i);
                     const float dh2 = w3.x * dz3[0] + w3.y * dz3[1] + w3.z * dz3[2];
-                    const float dz2 = hh[u] > 0.0f ? dh2 : 0.0f;
-                    dz2v[u] = dz2;
-                    const float4* wr = reinterpret_cast<const float4*>(sw + C::kW2 + o * W);
-#pragma unroll
-                    for (int q = 0; q < W / 4; ++q) {
-                        const float4 w4 = wr[q];
-                        dh1[4 * q + 0] = fmaf(w4.x, dz2, dh1[4 * q + 0]);
-                        dh1[4 * q + 1] = fmaf(w4.y, dz2, dh1[4 * q + 1]);
-                        dh1[4 * q + 2] = fmaf(w4.z, dz2, dh1[4 * q + 2]);
-                        dh1[4 * q + 3] = fmaf(w4.w, dz2, dh1[4 * q + 3]);
-                    }
+                    dz2[i] = ((mask2 >> i) & 1u) ? dh2 * s2 : 0.0f;
                 }
-                st4(dz2row + 4 * o4, dz2v[0], dz2v[1], dz2v[2], dz2v[3]);
+                store_row<W>(dzh, dzl, tid, W, L::DZC, dz2);
             }
-            float dx[NINP];
-#pragma unroll
-            for (int i = 0; i < NINP; ++i) dx[i] = 0.0f;
-            const float* h1row = h1s + lane * HS;
-            float* dz1row = dz1s + lane * HS;
-#pragma unroll
-            for (int i4 = 0; i4 < W / 4; ++i4) {
-                const float4 hv = ld4(h1row + 4 * i4);
-                const float hh[4] = {hv.x, hv.y, hv.z, hv.w};
-                float dz1v[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int i = 4 * i4 + u;
-                    const float dz1 = hh[u] > 0.0f ? dh1[i] : 0.0f;
-                    dz1v[u] = dz1;
-                    const float4* wr = reinterpret_cast<const float4*>(sw + C::kW1 + i * NINP);
-#pragma unroll
-                    for (int q = 0; q < NINP / 4; ++q) {
-                        const float4 w4 = wr[q];
-                        dx[4 * q + 0] = fmaf(w4.x, dz1, dx[4 * q + 0]);
-                        dx[4 * q + 1] = fmaf(w4.y, dz1, dx[4 * q + 1]);
-                        dx[4 * q + 2] = fmaf(w4.z, dz1, dx[4 * q + 2]);
-                        dx[4 * q + 3] = fmaf(w4.w, dz1, dx[4 * q + 3]);
-                    }
-                }
-                st4(dz1row + 4 * i4, dz1v[0], dz1v[1], dz1v[2], dz1v[3]);
-            }
+            tc::fence_smem_to_async();
+            tc::fence_before();
+            __syncthreads();
+            tc::fence_after();
 
-            // ---- angular features: dY, probe-gradient staging ----
-            float wq[8];
-            corner_weights(S.pcell.f, wq);
-            int pidx[8];
-            probe_corner_index(A.probes, S.pcell, pidx);
-            float dY[L2];
+            // ---- P3: dh1 = dz2 W2 (W2 read as its transpose) -> dz1 ----
+            if (tid == 0) {
+                const uint32_t idesc = tc::idesc_f16(128, W, 0, 1);
 #pragma unroll
-            for (int j = 0; j < L2; ++j) dY[j] = 0.0f;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const float4* b = A.probes.coeffs + (size_t)pidx[q] * (L2 * C::NA4);
-#pragma unroll
-                for (int j = 0; j < L2; ++j) {
-                    float acc = 0.0f;
-#pragma unroll
-                    for (int cg = 0; cg < C::NA4; ++cg) {
-                        const float4 bb = __ldg(b + j * C::NA4 + cg);
-                        acc = fmaf(bb.x, dx[3 + 4 * cg + 0], acc);
-                        acc = fmaf(bb.y, dx[3 + 4 * cg + 1], acc);
-                        acc = fmaf(bb.z, dx[3 + 4 * cg + 2], acc);
-                        acc = fmaf(bb.w, dx[3 + 4 * cg + 3], acc);
-                    }
-                    dY[j] = fmaf(wq[q], acc, dY[j]);
-                }
+                for (int s = 0; s < W / 16; ++s)
+                    mma3(tmem + 0, dzh + (W / 8) * 128 + s * 256, dzl + (W / 8) * 128 + s * 256,
+                         w2h + s * 2 * (W / 8) * 128, w2l + s * 2 * (W / 8) * 128, 128,
+                         L::kSboDZ, (W / 8) * 128, 128, idesc, s > 0);
+                tc::commit(mbar);
             }
+            bad |= !tc::mbar_wait(mbar, phase);
+            phase ^= 1;
+            tc::fence_after();
             {
-                float* row = pst + lane * Lay::PST;
+                float dh1[W];
+                tc::tmem_ld<W>(t_row + 0, dh1);
+                const float r12 = s1 * inv_s2;  // dh1 arrives scaled by s2; dz1 is stored scaled by s1
 #pragma unroll
-                for (int q = 0; q < 8; ++q) row[q] = wq[q];
-#pragma unroll
-                for (int j = 0; j < L2; ++j) row[8 + j] = S.Y[j];
-#pragma unroll
-                for (int c = 0; c < NA; ++c) row[8 + L2 + c] = active ? dx[3 + c] : 0.0f;
-                row[8 + L2 + NA] = __int_as_float(S.pcell.base);
+                for (int i = 0; i < W; ++i) dh1[i] = ((mask1 >> i) & 1u) ? dh1[i] * r12 : 0.0f;
+                store_row<W>(dzh, dzl, tid, 0, L::DZC, dh1);
             }
+            tc::fence_smem_to_async();
+            tc::fence_before();
+            __syncthreads();
+            tc::fence_after();
 
-            // ---- normal path: r(n), Fresnel(n), n(g) ----
-            float dr[3];
-            sh_basis_vjp<L2>(S.r, dY, dr);
-            const float v[3] = {-R.d[0], -R.d[1], -R.d[2]};
-            float dn[3] = {0.f, 0.f, 0.f};
-            if (A.dir_mode != 1) {
-                const float drn = dr[0] * S.n[0] + dr[1] * S.n[1] + dr[2] * S.n[2];
+            // ---- P4: dx = dz1 W1 (transposed W1) and the weight gradient ----
+            if (tid == 0) {
+                const uint32_t idx = tc::idesc_f16(128, 16, 0, 1);
 #pragma unroll
-                for (int a = 0; a < 3; ++a) dn[a] = 2.0f * drn * v[a] + 2.0f * S.ndv * dr[a];
+                for (int s = 0; s < W / 16; ++s)
+                    mma3(tmem + 32, dzh + s * 256, dzl + s * 256, w1h + s * 512, w1l + s * 512,
+                         128, L::kSboDZ, 256, 128, idx, s > 0);
+                const uint32_t idw = tc::idesc_f16(64, L::XHC, 1, 1);
+#pragma unroll
+                for (int s = 0; s < 8; ++s)
+                    mma3(tmem + 64, dzh + s * 2 * L::kSboDZ, dzl + s * 2 * L::kSboDZ,
+                         xhh + s * 2 * L::kSboXH, xhl + s * 2 * L::kSboXH, L::kSboDZ, 128,
+                         L::kSboXH, 128, idw, dw_started || s > 0);
+                dw_started = true;
+                tc::commit(mbar);
             }
-            {
-                const float om = 1.0f - S.ndv;
-                float dndv = 0.0f, pw = 1.0f;
+            bad |= !tc::mbar_wait(mbar, phase);
+            phase ^= 1;
+            tc::fence_after();
+            float dx[16];
+            tc::tmem_ld<16>(t_row + 32, dx);
 #pragma unroll
-                for (int kk = 1; kk <= C::K; ++kk) {
-                    dndv -= dx[3 + NA + kk - 1] * static_cast<float>(kk) * pw;
-                    pw *= om;
-                }
-#pragma unroll
-                for (int a = 0; a < 3; ++a) dn[a] = fmaf(dndv, v[a], dn[a]);
-            }
-            const float ndn = S.n[0] * dn[0] + S.n[1] * dn[1] + S.n[2] * dn[2];
-            const float irho = 1.0f / S.rho;
-            const float gxs = (dn[0] - S.n[0] * ndn) * irho * A.grid.sc[0];
-            const float gys = (dn[1] - S.n[1] * ndn) * irho * A.grid.sc[1];
-            const float gzs = (dn[2] - S.n[2] * ndn) * irho * A.grid.sc[2];
+            for (int i = 0; i < 16; ++i) dx[i] *= inv_s1;
+            tc::fence_before();
+            __syncthreads();  // tiles are free from here on
 
-            // ---- SDF + feature node gradients: one vector reduction per corner ----
-            if (active) {
-                const float fx = S.cell.f[0], fy = S.cell.f[1], fz = S.cell.f[2];
-                const int sy = A.grid.R[0], sz = A.grid.R[0] * A.grid.R[1];
+            // ---- P5: angular / Fresnel / normal adjoints and grid reductions ----
+            float* pst = reinterpret_cast<float*>(dzh) + warp * 32 * L::PST;
+            if (have) {
+                float wq[8];
+                corner_weights(S.pcell.f, wq);
+                int pidx[8];
+                probe_corner_index(A.probes, S.pcell, pidx);
+                float dY[L2];
+#pragma unroll
+                for (int j = 0; j < L2; ++j) dY[j] = 0.0f;
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
-                    const int cx = q & 1, cy = (q >> 1) & 1, cz = (q >> 2) & 1;
-                    const float wx = cx ? fx : 1.0f - fx, sgx = cx ? 1.0f : -1.0f;
-                    const float wy = cy ? fy : 1.0f - fy, sgy = cy ? 1.0f : -1.0f;
-                    const float wz = cz ? fz : 1.0f - fz, sgz = cz ? 1.0f : -1.0f;
-                    const float wc = wx * wy * wz;
-                    const float dsdf = ds_own * wc + gxs * sgx * wy * wz + gys * wx * sgy * wz +
-                                       gzs * wx * wy * sgz;
-                    float* dst = A.grad_grid + 4 * (size_t)(S.cell.base + cx + cy * sy + cz * sz);
-                    red_add_v4(dst, dsdf, wc * dx[0], wc * dx[1], wc * dx[2]);
-                }
-            }
-            if (extra) {
-                const float ds1 = dlam * dlog_phi(tau, s_next);
-                float w1[8];
-                corner_weights(c1.f, w1);
-                const int sy = A.grid.R[0], sz = A.grid.R[0] * A.grid.R[1];
+                    const float4* b = A.probes.coeffs + (size_t)pidx[q] * (L2 * C::NA4);
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int cx = q & 1, cy = (q >> 1) & 1, cz = (q >> 2) & 1;
-                    red_add(A.grad_grid + 4 * (size_t)(c1.base + cx + cy * sy + cz * sz),
-                            ds1 * w1[q]);
+                    for (int j = 0; j < L2; ++j) {
+                        float acc = 0.0f;
+#pragma unroll
+                        for (int cg = 0; cg < C::NA4; ++cg) {
+                            const float4 bb = __ldg(b + j * C::NA4 + cg);
+                            acc = fmaf(bb.x, dx[3 + 4 * cg + 0], acc);
+                            acc = fmaf(bb.y, dx[3 + 4 * cg + 1], acc);
+                            acc = fmaf(bb.z, dx[3 + 4 * cg + 2], acc);
+                            acc = fmaf(bb.w, dx[3 + 4 * cg + 3], acc);
+                        }
+                        dY[j] = fmaf(wq[q], acc, dY[j]);
+                    }
                 }
+                {
+                    float Y[L2];
+                    sh_basis<L2>(S.r, Y);
+                    float* row = pst + lane * L::PST;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) row[q] = wq[q];
+#pragma unroll
+                    for (int j = 0; j < L2; ++j) row[8 + j] = Y[j];
+#pragma unroll
+                    for (int c = 0; c < NA; ++c) row[8 + L2 + c] = active ? dx[3 + c] : 0.0f;
+                    row[8 + L2 + NA] = __int_as_float(S.pcell.base);
+                }
+                float dr[3];
+                sh_basis_vjp<L2>(S.r, dY, dr);
+                const float v[3] = {-R.d[0], -R.d[1], -R.d[2]};
+                float dn[3] = {0.f, 0.f, 0.f};
+                if (A.dir_mode != 1) {
+                    const float drn = dr[0] * S.n[0] + dr[1] * S.n[1] + dr[2] * S.n[2];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) dn[a] = 2.0f * drn * v[a] + 2.0f * S.ndv * dr[a];
+                }
+                {
+                    const float om = 1.0f - S.ndv;
+                    float dndv = 0.0f, pw = 1.0f;
+#pragma unroll
+                    for (int kk = 1; kk <= C::K; ++kk) {
+                        dndv -= dx[3 + NA + kk - 1] * static_cast<float>(kk) * pw;
+                        pw *= om;
+                    }
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) dn[a] = fmaf(dndv, v[a], dn[a]);
+                }
+                const float ndn = S.n[0] * dn[0] + S.n[1] * dn[1] + S.n[2] * dn[2];
+                const float irho = 1.0f / S.rho;
+                const float gxs = (dn[0] - S.n[0] * ndn) * irho * A.grid.sc[0];
+                const float gys = (dn[1] - S.n[1] * ndn) * irho * A.grid.sc[1];
+                const float gzs = (dn[2] - S.n[2] * ndn) * irho * A.grid.sc[2];
+                const int sy = A.grid.R[0], sz = A.grid.R[0] * A.grid.R[1];
+                if (active) {
+                    const float fx = S.cell.f[0], fy = S.cell.f[1], fz = S.cell.f[2];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int cx = q & 1, cy = (q >> 1) & 1, cz = (q >> 2) & 1;
+                        const float wx = cx ? fx : 1.0f - fx, sgx = cx ? 1.0f : -1.0f;
+                        const float wy = cy ? fy : 1.0f - fy, sgy = cy ? 1.0f : -1.0f;
+                        const float wz = cz ? fz : 1.0f - fz, sgz = cz ? 1.0f : -1.0f;
+                        const float wc = wx * wy * wz;
+                        const float dsdf = ds_own * wc + gxs * sgx * wy * wz +
+                                           gys * wx * sgy * wz + gzs * wx * wy * sgz;
+                        float* dst =
+                            A.grad_grid + 4 * (size_t)(S.cell.base + cx + cy * sy + cz * sz);
+                        red_add_v4(dst, dsdf, wc * dx[0], wc * dx[1], wc * dx[2]);
+                    }
+                }
+                if (extra) {
+                    const float ds1 = dlam * dlog_phi(tau, s_next);
+                    float w1[8];
+                    corner_weights(c1.f, w1);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int cx = q & 1, cy = (q >> 1) & 1, cz = (q >> 2) & 1;
+                        red_add(A.grad_grid + 4 * (size_t)(c1.base + cx + cy * sy + cz * sz),
+                                ds1 * w1[q]);
+                    }
+                }
+                __syncwarp();
+                scatter_probe_grad<C, L::PST>(A, pst, nact, lane);
+                logT_end = __shfl_sync(FULL, logTk, 0);
+                s_carry = next_carry;
             }
-
-            __syncwarp();
-            accumulate_dw<C, Lay>(xs, h1s, h2s, dz1s, dz2s, dz3s, nact, lane, gacc);
-            scatter_probe_grad<C, Lay>(A, pst, nact, lane);
-            __syncwarp();
-
-            logT_end = __shfl_sync(FULL, logTk, 0);
-            s_carry = next_carry;
         }
+        if (have) ray += stride;
     }
+done:
+    // every thread reaches this point together (the loop exits and the jump
+    // above are CTA-uniform), so the flag can be made uniform here
+    bad = __syncthreads_or(bad);
+    if (bad) {
+        tc::mbar_wait(mbar, phase);
+        if (tid == 0) atomicOr(A.status, 1);
+    }
+    tc::fence_before();
     __syncthreads();
-    for (int i = threadIdx.x; i < C::kParams; i += blockDim.x) red_add(A.grad_mlp + i, gacc[i]);
+    tc::fence_after();
+    if (any_chunk && !bad) {
+        // dW1, db1, dW2, db2 from the tensor-memory accumulator (M = 64 layout:
+        // row r lives in lane 32 (r / 16) + r % 16)
+        float v[L::XHC];
+        tc::tmem_ld<L::XHC>(t_row + 64, v);
+        const int r = 16 * warp + lane;
+        if (lane < 16) {
+            if (r < W) {  // dz1 rows, scaled by s1
+#pragma unroll
+                for (int j = 0; j < NIN; ++j) gacc[C::gW1 + r * NIN + j] += v[j] * inv_s1;
+                gacc[C::gB1 + r] += v[NIN] * inv_s1;
+            } else if (r < 2 * W) {  // dz2 rows, scaled by s2
+#pragma unroll
+                for (int i = 0; i < W; ++i) gacc[C::gW2 + (r - W) * W + i] += v[K1 + i] * inv_s2;
+                gacc[C::gB2 + (r - W)] += v[NIN] * inv_s2;
+            }
+        }
+        if (lane < W) {  // lane l holds column l (16-column slices, see P2)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) atomicAdd(gacc + C::gW3 + c * W + lane, acc3[c]);
+        }
+        if (lane < 3) atomicAdd(gacc + C::gB3 + lane, accb3);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, L::kTmemCols);
+    if (any_chunk)
+        for (int i = tid; i < C::kParams; i += blockDim.x) red_add(A.grad_mlp + i, gacc[i]);
 }
 
 template <class C>
 cudaError_t launch_backward_t(const RenderArgs& A, int grid_ctas, cudaStream_t stream)
 {
-    using Lay = BwdLayout<C>;
+    using L = BwdLayout<C>;
     cudaError_t e = cudaFuncSetAttribute(render_backward_kernel<C>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Lay::kSmemBytes);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
     if (e != cudaSuccess) return e;
-    render_backward_kernel<C><<<grid_ctas, kBwdThreads, Lay::kSmemBytes, stream>>>(A);
+    render_backward_kernel<C><<<grid_ctas, kBwdThreads, L::kBytes, stream>>>(A);
     return cudaGetLastError();
 }
 
@@ -506,22 +618,29 @@ cudaError_t launch_backward(const RenderArgs& A, const KernelShape& ks, int grid
     return cudaErrorInvalidValue;
 }
 
-int backward_ctas_per_sm(const KernelShape& ks)
+template <class C>
+cudaError_t backward_occupancy_t(int* n)
 {
-    int n = 0;
+    using L = BwdLayout<C>;
+    cudaError_t e = cudaFuncSetAttribute(render_backward_kernel<C>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, render_backward_kernel<C>);
+    if (e != cudaSuccess) return e;
+    *n = resident_ctas(fa, kBwdThreads, L::kBytes, L::kTmemCols);
+    return *n > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
+}
+
+cudaError_t backward_ctas_per_sm(const KernelShape& ks, int* n)
+{
+    *n = 0;
 #define PSDF_BWD_OCC(NA, L2, W, K)                                                           \
-    if (ks.na == NA && ks.l2 == L2 && ks.width == W && ks.k == K) {                          \
-        using C_ = Cfg<NA, L2, W, K>;                                                        \
-        cudaFuncSetAttribute(render_backward_kernel<C_>,                                     \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,                    \
-                             (int)BwdLayout<C_>::kSmemBytes);                                \
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_backward_kernel<C_>,        \
-                                                      kBwdThreads,                           \
-                                                      BwdLayout<C_>::kSmemBytes);            \
-    }
+    if (ks.na == NA && ks.l2 == L2 && ks.width == W && ks.k == K)                            \
+        return backward_occupancy_t<Cfg<NA, L2, W, K>>(n);
     PSDF_FOR_EACH_SHAPE(PSDF_BWD_OCC)
 #undef PSDF_BWD_OCC
-    return n;
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace psdf

@@ -54,6 +54,7 @@ struct RenderArgs {
     float* grad_grid;
     float* grad_probes;
     float* grad_mlp;
+    int* status;  // device status word: bit 0 = a tensor-core wait ran out
 };
 
 // ---------------------------------------------------------------------------

@@ -1,34 +1,84 @@
-// Forward ProbeSDF render (Sec. 3, Eqs. 4-10; Sec. 4), FP32, sm_103a.
+// Forward ProbeSDF render (Sec. 3, Eqs. 4-10; Sec. 4), sm_103a.
 //
-// Persistent grid; each warp takes rays in a grid-stride loop and walks a ray
-// in chunks of 32 samples (lane = sample).  Per chunk: one trilinear gather
-// of 8 packed 16-byte node records per sample, the probe blend, the MLP
-// (weights broadcast from shared memory), then a warp scan of the clipped
-// log-opacities gives the transmittance of every sample of the chunk; the
-// chunk total is carried to the next chunk with compensated summation.
+// Persistent CTAs of 4 warps.  Each warp takes rays in a grid-stride loop
+// (misses are written out at once) and walks its ray in chunks of 32 samples,
+// lane = sample.  The 4 warps advance chunk by chunk in lockstep so that their
+// 128 samples form one M = 128 tile for the tensor-core MLP:
+//   P0  trilinear gather of 8 packed 16-byte node records per sample, normal,
+//       SH of the lookup direction, probe blend, Fresnel powers -> MLP input
+//       row (split FP16) in shared memory;
+//   P1  layer 1 on the tensor cores; meanwhile the warp scan of the clipped
+//       log-opacities gives every sample's transmittance (Eq. 8);
+//   P2  ReLU epilogue -> layer 2 on the tensor cores -> layer 3 and sigmoid on
+//       the CUDA cores; the chunk's weights, colours and depths are summed.
+// The log-transmittance carry between chunks uses compensated summation.
 #include "internal.h"
-#include "sample_eval.cuh"
+#include "mlp_tc.cuh"
 
 namespace psdf {
+
+template <class C>
+struct FwdLayout {
+    using M = MlpTC<C>;
+    static constexpr int K1 = M::K1;
+    static constexpr int kXT = 128 * K1 * 2;   // one split of the input tile [128][16]
+    static constexpr int kHT = 128 * C::W * 2; // one split of the hidden tile [128][W]
+    static constexpr int oW = 0;
+    static constexpr int oF32 = oW + M::kWeightBytes;
+    static constexpr int oX = (oF32 + 4 * M::kF32 + 127) & ~127;
+    static constexpr int oH = oX + 2 * kXT;
+    static constexpr int oBar = oH + 2 * kHT;
+    static constexpr int kBytes = oBar + 16;
+    static constexpr uint32_t kTmemCols = 64;  // layer 1 at column 0, layer 2 at 32
+};
 
 template <class C>
 __global__ void __launch_bounds__(kFwdThreads)
 render_forward_kernel(RenderArgs A)
 {
-    __shared__ __align__(16) float sw[C::kMlpSmem];
-    load_mlp_smem<C>(A.mlp, sw);
+    using M = MlpTC<C>;
+    using L = FwdLayout<C>;
+    constexpr int W = C::W;
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint8_t* wt = smem + L::oW;
+    float* f32 = reinterpret_cast<float*>(smem + L::oF32);
+    uint8_t* xh = smem + L::oX;
+    uint8_t* xl = xh + L::kXT;
+    uint8_t* hh = smem + L::oH;
+    uint8_t* hl = hh + L::kHT;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::oBar);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::oBar + 8);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    load_mlp_tc<C>(A.mlp, wt, f32);
+    if (warp == 0) tc::tmem_alloc(tslot, L::kTmemCols);
+    if (tid == 0) tc::mbar_init(mbar, 1);
+    tc::fence_smem_to_async();
+    tc::fence_before();
     __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t t_row = tmem + (static_cast<uint32_t>(32 * warp) << 16);
+    uint32_t phase = 0;
+    bool bad = false;
 
-    const int lane = threadIdx.x & 31;
-    const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-    const int N = A.n_samples;
     const unsigned FULL = 0xffffffffu;
+    const int N = A.n_samples;
+    const int64_t stride = int64_t(gridDim.x) * 4;
+    int64_t ray = int64_t(blockIdx.x) * 4 + warp;
 
-    for (int64_t ray = warp0; ray < A.n_rays; ray += nwarps) {
-        const RayIn R = load_ray(A, ray);
-        const RaySpan sp = ray_span(A, R, ray);
-        if (!sp.hit) {
+    for (;;) {
+        // this warp's next ray that hits the box; misses are finished here
+        RayIn R;
+        RaySpan sp;
+        bool have = false;
+        while (ray < A.n_rays) {
+            R = load_ray(A, ray);
+            sp = ray_span(A, R, ray);
+            if (sp.hit) {
+                have = true;
+                break;
+            }
             if (lane == 0) {
                 A.rgb[3 * ray + 0] = A.bg[0];
                 A.rgb[3 * ray + 1] = A.bg[1];
@@ -37,40 +87,49 @@ render_forward_kernel(RenderArgs A)
                 A.wsum[ray] = 0.0f;
                 A.logT[ray] = 0.0f;
             }
-            continue;
+            ray += stride;
         }
+        if (!__syncthreads_or(have)) break;
+
         float acc_r = 0.f, acc_g = 0.f, acc_b = 0.f, acc_d = 0.f, acc_w = 0.f;
         float carry = 0.f, comp = 0.f;  // Kahan sum of log T over chunks
-
         for (int base = 0; base < N; base += 32) {
             const int k = base + lane;
-            const bool active = k < N;
-            const int kc = active ? k : N - 1;  // colour sample evaluated by this lane
-            const float t = span_t(sp, kc);
-
-            SampleGeom<C> S;
-            eval_geometry<C>(A, R.o, R.d, t, S);
-            float col[3];
-            mlp_forward<C, false>(sw, S.x, col, nullptr, nullptr, nullptr);
-
-            // s at point k+1: the next lane's point, or an extra gather for the
-            // chunk's last lane.
-            float s_next = __shfl_down_sync(FULL, S.s, 1);
-            if (lane == 31 || k + 1 >= N) {
-                if (active) {
+            const bool active = have && k < N;
+            float t = 0.0f, lam = 0.0f;
+            // ---- P0: geometry, angular and spatial features -> input row ----
+            if (have) {
+                t = span_t(sp, k < N ? k : N - 1);
+                SampleGeom<C> S;
+                eval_geometry<C>(A, R.o, R.d, t, S);
+                float xin[M::K1];
+#pragma unroll
+                for (int i = 0; i < M::K1; ++i) xin[i] = i < C::NIN ? S.x[i] : 0.0f;
+                store_row<M::K1>(xh, xl, tid, 0, M::K1, xin);
+                float s_next = __shfl_down_sync(FULL, S.s, 1);
+                if (active && (lane == 31 || k + 1 >= N)) {
                     float xw[3];
                     point_at(R.o, R.d, span_t(sp, k + 1), xw);
-                    const Cell c1 = locate(xw, A.grid.bmin, A.grid.sc, A.grid.R);
-                    s_next = sdf_value(A.grid, c1);
+                    s_next = sdf_value(A.grid, locate(xw, A.grid.bmin, A.grid.sc, A.grid.R));
                 }
+                if (active) {
+                    const float diff = log_transmittance(A.tau, S.s, s_next);
+                    lam = diff < 0.0f ? diff : 0.0f;
+                }
+            } else {
+                zero_row<M::K1>(xh, xl, tid, 0, M::K1);
             }
-            // Eq. 9 in log space: log(1 - alpha_k) = min(log Phi(s_k+1) - log Phi(s_k), 0)
-            float lam = 0.0f;
-            if (active) {
-                const float diff = log_transmittance(A.tau, S.s, s_next);
-                lam = diff < 0.0f ? diff : 0.0f;
+            tc::fence_smem_to_async();
+            tc::fence_before();
+            if (__syncthreads_or(bad)) goto done;
+            tc::fence_after();
+            // ---- P1: layer 1 on the tensor cores ----
+            if (tid == 0) {
+                mma3(tmem + 0, xh, xl, wt, wt + M::kW1, 128, (M::K1 / 8) * 128, 128,
+                     (M::K1 / 8) * 128, M::kIdescL, false);
+                tc::commit(mbar);
             }
-            // exclusive warp scan of lam -> log T_k within the chunk (Eq. 8)
+            // transmittance of the chunk (Eq. 8): exclusive warp scan of lam
             float incl = lam;
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
@@ -80,45 +139,99 @@ render_forward_kernel(RenderArgs A)
             float excl = __shfl_up_sync(FULL, incl, 1);
             if (lane == 0) excl = 0.0f;
             const float total = __shfl_sync(FULL, incl, 31);
-            if (active) {
-                const float T = expf((carry - comp) + excl);
-                const float w = T * -expm1f(lam);
-                acc_r = fmaf(w, col[0], acc_r);
-                acc_g = fmaf(w, col[1], acc_g);
-                acc_b = fmaf(w, col[2], acc_b);
-                acc_d = fmaf(w, t, acc_d);
-                acc_w += w;
+            const float wgt = active ? expf((carry - comp) + excl) * -expm1f(lam) : 0.0f;
+            {
+                const float y = total - comp;
+                const float tt = carry + y;
+                comp = (tt - carry) - y;
+                carry = tt;
             }
-            const float y = total - comp;
-            const float tt = carry + y;
-            comp = (tt - carry) - y;
-            carry = tt;
-        }
+            bad |= !tc::mbar_wait(mbar, phase);
+            phase ^= 1;
+            tc::fence_after();
+            {
+                float z[W];
+                tc::tmem_ld<W>(t_row + 0, z);
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            acc_r += __shfl_xor_sync(FULL, acc_r, off);
-            acc_g += __shfl_xor_sync(FULL, acc_g, off);
-            acc_b += __shfl_xor_sync(FULL, acc_b, off);
-            acc_d += __shfl_xor_sync(FULL, acc_d, off);
-            acc_w += __shfl_xor_sync(FULL, acc_w, off);
+                for (int o = 0; o < W; ++o) z[o] = fmaxf(z[o] + f32[M::kB1 + o], 0.0f);
+                store_row<W>(hh, hl, tid, 0, W, z);
+            }
+            tc::fence_smem_to_async();
+            tc::fence_before();
+            __syncthreads();
+            tc::fence_after();
+            // ---- P2: layer 2 on the tensor cores, layer 3 on the CUDA cores ----
+            if (tid == 0) {
+#pragma unroll
+                for (int s = 0; s < W / 16; ++s)
+                    mma3(tmem + 32, hh + s * 256, hl + s * 256, wt + 2 * M::kW1 + s * 256,
+                         wt + 2 * M::kW1 + M::kW2 + s * 256, 128, (W / 8) * 128, 128,
+                         (W / 8) * 128, M::kIdescL, s > 0);
+                tc::commit(mbar);
+            }
+            bad |= !tc::mbar_wait(mbar, phase);
+            phase ^= 1;
+            tc::fence_after();
+            {
+                float z[W];
+                tc::tmem_ld<W>(t_row + 32, z);
+#pragma unroll
+                for (int o = 0; o < W; ++o) z[o] = fmaxf(z[o] + f32[M::kB2 + o], 0.0f);
+                float col[3];
+                mlp_layer3<C>(f32, z, col);
+                if (active) {
+                    acc_r = fmaf(wgt, col[0], acc_r);
+                    acc_g = fmaf(wgt, col[1], acc_g);
+                    acc_b = fmaf(wgt, col[2], acc_b);
+                    acc_d = fmaf(wgt, t, acc_d);
+                    acc_w += wgt;
+                }
+            }
+            tc::fence_before();
         }
-        if (lane == 0) {
-            const float logT = carry - comp;
-            const float TN = expf(logT);
-            A.rgb[3 * ray + 0] = fmaf(TN, A.bg[0], acc_r);
-            A.rgb[3 * ray + 1] = fmaf(TN, A.bg[1], acc_g);
-            A.rgb[3 * ray + 2] = fmaf(TN, A.bg[2], acc_b);
-            A.depth[ray] = acc_d;
-            A.wsum[ray] = acc_w;
-            A.logT[ray] = logT;
+        if (have) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                acc_r += __shfl_xor_sync(FULL, acc_r, off);
+                acc_g += __shfl_xor_sync(FULL, acc_g, off);
+                acc_b += __shfl_xor_sync(FULL, acc_b, off);
+                acc_d += __shfl_xor_sync(FULL, acc_d, off);
+                acc_w += __shfl_xor_sync(FULL, acc_w, off);
+            }
+            if (lane == 0) {
+                const float logT = carry - comp;
+                const float TN = expf(logT);
+                A.rgb[3 * ray + 0] = fmaf(TN, A.bg[0], acc_r);
+                A.rgb[3 * ray + 1] = fmaf(TN, A.bg[1], acc_g);
+                A.rgb[3 * ray + 2] = fmaf(TN, A.bg[2], acc_b);
+                A.depth[ray] = acc_d;
+                A.wsum[ray] = acc_w;
+                A.logT[ray] = logT;
+            }
+            ray += stride;
         }
     }
+done:
+    bad = __syncthreads_or(bad);
+    if (bad) {
+        // an MMA never signalled completion: give it one more bounded wait
+        // before the tensor memory is released, and report the failure
+        tc::mbar_wait(mbar, phase);
+        if (tid == 0) atomicOr(A.status, 1);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, L::kTmemCols);
 }
 
 template <class C>
 cudaError_t launch_forward_t(const RenderArgs& A, int grid_ctas, cudaStream_t stream)
 {
-    render_forward_kernel<C><<<grid_ctas, kFwdThreads, 0, stream>>>(A);
+    using L = FwdLayout<C>;
+    cudaError_t e = cudaFuncSetAttribute(render_forward_kernel<C>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
+    if (e != cudaSuccess) return e;
+    render_forward_kernel<C><<<grid_ctas, kFwdThreads, L::kBytes, stream>>>(A);
     return cudaGetLastError();
 }
 
@@ -133,16 +246,29 @@ cudaError_t launch_forward(const RenderArgs& A, const KernelShape& ks, int grid_
     return cudaErrorInvalidValue;
 }
 
-int forward_ctas_per_sm(const KernelShape& ks)
+template <class C>
+cudaError_t forward_occupancy_t(int* n)
 {
-    int n = 0;
+    using L = FwdLayout<C>;
+    cudaError_t e = cudaFuncSetAttribute(render_forward_kernel<C>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, render_forward_kernel<C>);
+    if (e != cudaSuccess) return e;
+    *n = resident_ctas(fa, kFwdThreads, L::kBytes, L::kTmemCols);
+    return *n > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
+}
+
+cudaError_t forward_ctas_per_sm(const KernelShape& ks, int* n)
+{
+    *n = 0;
 #define PSDF_FWD_OCC(NA, L2, W, K)                                                           \
     if (ks.na == NA && ks.l2 == L2 && ks.width == W && ks.k == K)                            \
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                       \
-            &n, render_forward_kernel<Cfg<NA, L2, W, K>>, kFwdThreads, 0);
+        return forward_occupancy_t<Cfg<NA, L2, W, K>>(n);
     PSDF_FOR_EACH_SHAPE(PSDF_FWD_OCC)
 #undef PSDF_FWD_OCC
-    return n;
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace psdf

@@ -1,6 +1,6 @@
-// Per-sample colour evaluation shared by the forward and backward kernels:
-// geometry (Sec. 3, Eq. 13), probe-blended SH angular features (Eqs. 5-7),
-// Fresnel inputs (Eq. 4) and the colour MLP (Sec. 4), FP32 SIMT.
+// Per-sample evaluation shared by the forward and backward kernels: geometry
+// (Sec. 3, Eq. 13), probe-blended SH angular features (Eqs. 5-7) and Fresnel
+// inputs (Eq. 4), FP32 on the CUDA cores; the MLP input row is their concatenation.
 #pragma once
 
 #include "render_common.cuh"
@@ -17,15 +17,6 @@ struct Cfg {
     static constexpr int NIN = NS + NA + K;
     static constexpr int NINP = (NIN + 3) & ~3;  // MLP input row, padded to float4
     static constexpr int NA4 = NA / 4;           // float4 groups per SH coefficient
-    // MLP parameters in shared memory, rows padded to float4:
-    //   W1 [W][NINP], b1 [W], W2 [W][W], b2 [W], W3T [W][4] (W3 transposed), b3 [4]
-    static constexpr int kW1 = 0;
-    static constexpr int kB1 = kW1 + W * NINP;
-    static constexpr int kW2 = kB1 + W;
-    static constexpr int kB2 = kW2 + W * W;
-    static constexpr int kW3T = kB2 + W;
-    static constexpr int kB3 = kW3T + 4 * W;
-    static constexpr int kMlpSmem = kB3 + 4;  // floats
     // packed (global) parameter offsets: W1[W][NIN] b1 W2[W][W] b2 W3[3][W] b3[3]
     static constexpr int gW1 = 0;
     static constexpr int gB1 = W * NIN;
@@ -37,32 +28,6 @@ struct Cfg {
     static_assert(NA % 4 == 0, "angular channels are read as float4 groups");
     static_assert(W % 4 == 0, "hidden width must be a multiple of 4");
 };
-
-// Cooperative copy of the packed parameters into the padded smem layout.
-template <class C>
-__device__ __forceinline__ void load_mlp_smem(const float* __restrict__ g, float* s)
-{
-    for (int i = threadIdx.x; i < C::kMlpSmem; i += blockDim.x) {
-        float v = 0.0f;
-        if (i < C::kB1) {
-            const int o = i / C::NINP, c = i % C::NINP;
-            v = c < C::NIN ? g[C::gW1 + o * C::NIN + c] : 0.0f;
-        } else if (i < C::kW2) {
-            v = g[C::gB1 + (i - C::kB1)];
-        } else if (i < C::kB2) {
-            v = g[C::gW2 + (i - C::kW2)];
-        } else if (i < C::kW3T) {
-            v = g[C::gB2 + (i - C::kB2)];
-        } else if (i < C::kB3) {
-            const int o = (i - C::kW3T) / 4, c = (i - C::kW3T) % 4;
-            v = c < 3 ? g[C::gW3 + c * C::W + o] : 0.0f;
-        } else {
-            const int c = i - C::kB3;
-            v = c < 3 ? g[C::gB3 + c] : 0.0f;
-        }
-        s[i] = v;
-    }
-}
 
 // Geometry and appearance inputs of one colour sample.
 template <class C>
@@ -165,66 +130,6 @@ __device__ __forceinline__ void eval_geometry(const RenderArgs& A, const float o
     }
 #pragma unroll
     for (int i = C::NIN; i < C::NINP; ++i) S.x[i] = 0.0f;
-}
-
-// Colour MLP (Sec. 4): n_in -> W -> W -> 3, ReLU, ReLU, sigmoid.  Weights are
-// read from shared memory as warp-uniform float4 broadcasts.  If STORE, the
-// input, h1 and h2 rows of this lane are written to shared memory for the
-// weight-gradient pass.
-template <class C, bool STORE>
-__device__ __forceinline__ void mlp_forward(const float* __restrict__ sw, const float x[C::NINP],
-                                            float col[3], float* xrow, float* h1row,
-                                            float* h2row)
-{
-    float h1[C::W];
-#pragma unroll
-    for (int o = 0; o < C::W; ++o) {
-        const float4* wr = reinterpret_cast<const float4*>(sw + C::kW1 + o * C::NINP);
-        float z = sw[C::kB1 + o];
-#pragma unroll
-        for (int q = 0; q < C::NINP / 4; ++q) {
-            const float4 w4 = wr[q];
-            z = fmaf(w4.x, x[4 * q + 0], z);
-            z = fmaf(w4.y, x[4 * q + 1], z);
-            z = fmaf(w4.z, x[4 * q + 2], z);
-            z = fmaf(w4.w, x[4 * q + 3], z);
-        }
-        h1[o] = fmaxf(z, 0.0f);
-    }
-    const float4 b3 = *reinterpret_cast<const float4*>(sw + C::kB3);
-    float z3[3] = {b3.x, b3.y, b3.z};
-#pragma unroll
-    for (int o = 0; o < C::W; ++o) {
-        const float4* wr = reinterpret_cast<const float4*>(sw + C::kW2 + o * C::W);
-        float z = sw[C::kB2 + o];
-#pragma unroll
-        for (int q = 0; q < C::W / 4; ++q) {
-            const float4 w4 = wr[q];
-            z = fmaf(w4.x, h1[4 * q + 0], z);
-            z = fmaf(w4.y, h1[4 * q + 1], z);
-            z = fmaf(w4.z, h1[4 * q + 2], z);
-            z = fmaf(w4.w, h1[4 * q + 3], z);
-        }
-        const float h2 = fmaxf(z, 0.0f);
-        const float4 w3 = *reinterpret_cast<const float4*>(sw + C::kW3T + 4 * o);
-        z3[0] = fmaf(w3.x, h2, z3[0]);
-        z3[1] = fmaf(w3.y, h2, z3[1]);
-        z3[2] = fmaf(w3.z, h2, z3[2]);
-        if constexpr (STORE) h2row[o] = h2;
-    }
-    col[0] = sigmoidf(z3[0]);
-    col[1] = sigmoidf(z3[1]);
-    col[2] = sigmoidf(z3[2]);
-    if constexpr (STORE) {
-#pragma unroll
-        for (int q = 0; q < C::NINP / 4; ++q)
-            reinterpret_cast<float4*>(xrow)[q] =
-                make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
-#pragma unroll
-        for (int q = 0; q < C::W / 4; ++q)
-            reinterpret_cast<float4*>(h1row)[q] =
-                make_float4(h1[4 * q], h1[4 * q + 1], h1[4 * q + 2], h1[4 * q + 3]);
-    }
 }
 
 // Ray record (broadcast by every lane of the warp).
