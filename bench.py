@@ -237,9 +237,7 @@ def run_ours(args, world, rank, local):
     o = torch.as_tensor(rays.o, device=device)
     d = torch.as_tensor(rays.d, device=device)
     tgt = torch.as_tensor(rays.target, device=device)
-    gg = torch.zeros_like(scene.grid)
-    gp = torch.zeros_like(scene.probes)
-    gm = torch.zeros_like(scene.mlp)
+    gg, gp, gm = scene.grad_buffers()
     stream = torch.cuda.current_stream(device)
     occ = ps.render_occupancy(scene, params)
     ev = {k: [] for k in ("fwd0", "bwd1")}

@@ -57,6 +57,8 @@ typedef int32_t psdf_status;
 #define PSDF_ERR_UNSUPPORTED -6   /* a valid but not compiled-in combination */
 
 #define PSDF_F32 0
+#define PSDF_BF16 1
+#define PSDF_F16 2
 
 #define PSDF_DIR_REFLECT 0  /* F_a looked up with r = 2(n.v)n - v (Sec. 3.1) */
 #define PSDF_DIR_VIEW 1     /* F_a looked up with v, for retro-reflective materials (Sec. 3.1) */
@@ -70,7 +72,7 @@ typedef struct psdf_grid_desc {
     float box_min[3];    /* world-space box spanned by the nodes */
     float box_max[3];    /* box_max > box_min on every axis */
     int32_t n_feat;      /* spatial features per node (n_s); 3 is compiled in */
-    int32_t feat_dtype;  /* PSDF_F32 */
+    int32_t feat_dtype;  /* PSDF_F32 or PSDF_BF16 (storage of the features; SDF stays FP32) */
 } psdf_grid_desc;
 
 /* Light-field probe grid (Sec. 3.2): l*l SH coefficients of n_a channels. */
@@ -78,7 +80,7 @@ typedef struct psdf_probe_desc {
     int32_t dims[3];     /* probe nodes along x, y, z over the grid's box; each >= 2 */
     int32_t sh_l;        /* SH order l, 1-indexed as in Eq. 5 (l*l coefficients); 3 compiled in */
     int32_t n_ang;       /* angular channels n_a; 4 and 8 compiled in */
-    int32_t dtype;       /* PSDF_F32 */
+    int32_t dtype;       /* PSDF_F32 or PSDF_F16 (storage of the coefficients) */
 } psdf_probe_desc;
 
 /* Colour MLP (Sec. 4): n_in -> width -> width -> 3, ReLU, ReLU, sigmoid.
@@ -87,7 +89,9 @@ typedef struct psdf_probe_desc {
 typedef struct psdf_mlp_desc {
     int32_t n_in;
     int32_t width;       /* 16 and 32 compiled in */
-    int32_t dtype;       /* PSDF_F32 */
+    int32_t dtype;       /* arithmetic: PSDF_F32 (FP32-equivalent: FP16 hi/lo split on the
+                            tensor cores, FP32 accumulation) or PSDF_F16 (FP16 operands, FP32
+                            accumulation); the parameters are FP32 in memory either way */
 } psdf_mlp_desc;
 
 typedef struct psdf_render_params {
@@ -119,10 +123,13 @@ int32_t psdf_version(void);
  * record the condition here and return. */
 psdf_status psdf_device_status(void* stream, int32_t* flags);
 
-/* Bytes of the packed grid layout: one 16-byte record {sdf, f0, f1, f2} per
- * node, in the library's own node order.  The gradient buffer of
- * psdf_render_backward has the same size and layout (FP32). */
-psdf_status psdf_grid_bytes(const psdf_grid_desc* desc, size_t* values_bytes);
+/* Bytes of the packed grid values and of the grid gradient buffer.
+ * Values, PSDF_F32 features: one 16-byte record {sdf, f0, f1, f2} per node.
+ * Values, PSDF_BF16 features: an FP32 SDF array, then (at the next 16-byte
+ * boundary) one 8-byte record {f0, f1, f2, 0} of BF16 per node.
+ * Gradient (either case): one FP32 record {dsdf, df0, df1, df2} per node.
+ * Node order is x fastest. */
+psdf_status psdf_grid_bytes(const psdf_grid_desc* desc, size_t* values_bytes, size_t* grad_bytes);
 
 /* Handle over caller-owned packed values (device, psdf_grid_bytes bytes). */
 psdf_status psdf_grid_create(const psdf_grid_desc* desc, const void* values, psdf_grid** out);
@@ -130,15 +137,17 @@ void psdf_grid_destroy(psdf_grid* grid);
 
 /* Dense <-> packed conversion on `stream`.
  * pack:   sdf (device, FP32 [Rz][Ry][Rx]) and feat (device, FP32
- *         [Rz][Ry][Rx][n_feat]) -> packed (device, psdf_grid_bytes bytes).
- * unpack: packed values or gradients (device) -> the two dense arrays. */
+ *         [Rz][Ry][Rx][n_feat]) -> packed values (device, values_bytes);
+ *         BF16 features are rounded to nearest even.
+ * unpack: packed values (which = PSDF_GRID_VALUES) or a gradient buffer
+ *         (PSDF_GRID_GRAD) -> the dense arrays (either may be NULL). */
 psdf_status psdf_grid_pack(const psdf_grid_desc* desc, const float* sdf, const float* feat,
                            void* packed, void* stream);
-psdf_status psdf_grid_unpack(const psdf_grid_desc* desc, const void* packed, float* sdf,
-                             float* feat, void* stream);
+psdf_status psdf_grid_unpack(const psdf_grid_desc* desc, int32_t which, const void* packed,
+                             float* sdf, float* feat, void* stream);
 
-/* Probe coefficients (device, FP32 [Pz][Py][Px][l*l][n_a]); the layout is the
- * caller's, no packing. */
+/* Probe coefficients (device, [Pz][Py][Px][l*l][n_a], FP32 or FP16 per the
+ * descriptor); the layout is the caller's, no packing. */
 psdf_status psdf_probes_create(const psdf_probe_desc* desc, const void* coeffs,
                                psdf_probes** out);
 void psdf_probes_destroy(psdf_probes* probes);
@@ -173,8 +182,8 @@ psdf_status psdf_render_forward(const psdf_grid* grid, const psdf_probes* probes
  *   d_rgb          : device FP32 [n_rays][3] (required)
  *   d_depth, d_wsum: device FP32 [n_rays] or NULL (= zero)
  *   logT_final     : the forward's output for the same inputs
- *   grad_grid      : device FP32, psdf_grid_bytes bytes, packed like the values
- *   grad_probes    : device FP32 [Pz][Py][Px][l*l][n_a]
+ *   grad_grid      : device FP32, grad_bytes of psdf_grid_bytes, {dsdf, df0..2} per node
+ *   grad_probes    : device FP32 [Pz][Py][Px][l*l][n_a] (FP32 whatever the storage)
  *   grad_mlp       : device FP32 [psdf_mlp_param_count]
  * Gradients are ACCUMULATED (+=) with atomics, so their summation order is
  * not fixed; zero them first for a fresh gradient.  All three gradient

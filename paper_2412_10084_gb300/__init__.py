@@ -20,13 +20,17 @@ from . import build as _build
 
 __all__ = [
     "GridDesc", "ProbeDesc", "MlpDesc", "RenderParams", "Scene", "LibraryError",
-    "library", "grid_bytes", "mlp_param_count", "pack_grid", "unpack_grid",
+    "library", "grid_bytes", "mlp_param_count", "pack_grid", "unpack_grid", "BF16", "F16", "F32",
     "render_forward", "render_backward", "render", "device_status", "DIR_REFLECT", "DIR_VIEW",
 ]
 
 DIR_REFLECT = 0
 DIR_VIEW = 1
 F32 = 0
+BF16 = 1
+F16 = 2
+GRID_VALUES = 0
+GRID_GRAD = 1
 
 
 class LibraryError(RuntimeError):
@@ -73,12 +77,13 @@ def library() -> ctypes.CDLL:
         lib.psdf_version.restype = ctypes.c_int32
         lib.psdf_device_status.argtypes = [_P, ctypes.POINTER(ctypes.c_int32)]
         lib.psdf_device_status.restype = ctypes.c_int32
-        lib.psdf_grid_bytes.argtypes = [_P, ctypes.POINTER(ctypes.c_size_t)]
+        lib.psdf_grid_bytes.argtypes = [_P, ctypes.POINTER(ctypes.c_size_t),
+                                         ctypes.POINTER(ctypes.c_size_t)]
         lib.psdf_grid_create.argtypes = [_P, _P, ctypes.POINTER(_P)]
         lib.psdf_grid_destroy.argtypes = [_P]
         lib.psdf_grid_destroy.restype = None
         lib.psdf_grid_pack.argtypes = [_P, _P, _P, _P, _P]
-        lib.psdf_grid_unpack.argtypes = [_P, _P, _P, _P, _P]
+        lib.psdf_grid_unpack.argtypes = [_P, ctypes.c_int32, _P, _P, _P, _P]
         lib.psdf_probes_create.argtypes = [_P, _P, ctypes.POINTER(_P)]
         lib.psdf_probes_destroy.argtypes = [_P]
         lib.psdf_probes_destroy.restype = None
@@ -128,31 +133,33 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _require_cuda(*tensors):
+def _require_cuda(*tensors, dtypes=(torch.float32,)):
     for t in tensors:
         if t is not None:
             if not t.is_cuda:
                 raise LibraryError("tensors must be on a CUDA device (there is no CPU path)")
-            if t.dtype != torch.float32:
-                raise LibraryError(f"expected float32, got {t.dtype}")
+            if t.dtype not in dtypes:
+                raise LibraryError(f"expected {dtypes}, got {t.dtype}")
             if not t.is_contiguous():
                 raise LibraryError("tensors must be contiguous")
 
 
-def grid_desc(dims, box_min, box_max, n_feat=3) -> GridDesc:
+def grid_desc(dims, box_min, box_max, n_feat=3, feat_dtype=F32) -> GridDesc:
     d = GridDesc()
     d.dims[:] = tuple(int(v) for v in dims)
     d.box_min[:] = tuple(float(v) for v in box_min)
     d.box_max[:] = tuple(float(v) for v in box_max)
     d.n_feat = int(n_feat)
-    d.feat_dtype = F32
+    d.feat_dtype = int(feat_dtype)
     return d
 
 
-def grid_bytes(desc: GridDesc) -> int:
-    n = ctypes.c_size_t()
-    _check(library().psdf_grid_bytes(ctypes.byref(desc), ctypes.byref(n)), "psdf_grid_bytes")
-    return n.value
+def grid_bytes(desc: GridDesc):
+    """(packed value bytes, gradient bytes) of a grid."""
+    n, g = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(library().psdf_grid_bytes(ctypes.byref(desc), ctypes.byref(n), ctypes.byref(g)),
+           "psdf_grid_bytes")
+    return n.value, g.value
 
 
 def mlp_param_count(n_in: int, width: int) -> int:
@@ -164,22 +171,32 @@ def mlp_param_count(n_in: int, width: int) -> int:
 
 
 def pack_grid(desc: GridDesc, sdf: torch.Tensor, feat: torch.Tensor) -> torch.Tensor:
-    """Dense sdf [Rz,Ry,Rx] + feat [Rz,Ry,Rx,3] (device FP32) -> packed [Rz*Ry*Rx, 4]."""
+    """Dense sdf [Rz,Ry,Rx] + feat [Rz,Ry,Rx,3] (device FP32) -> packed values:
+    float32 [R^3, 4] for FP32 features, a uint8 buffer for BF16 features."""
     _require_cuda(sdf, feat)
-    out = torch.empty(grid_bytes(desc) // 4, dtype=torch.float32, device=sdf.device).view(-1, 4)
+    nbytes, _ = grid_bytes(desc)
+    if desc.feat_dtype == F32:
+        out = torch.empty(nbytes // 4, dtype=torch.float32, device=sdf.device).view(-1, 4)
+    else:
+        out = torch.empty(nbytes, dtype=torch.uint8, device=sdf.device)
     _check(library().psdf_grid_pack(ctypes.byref(desc), _ptr(sdf), _ptr(feat), _ptr(out),
                                     _stream()), "psdf_grid_pack")
     return out
 
 
-def unpack_grid(desc: GridDesc, packed: torch.Tensor):
-    """Packed values or gradients -> (sdf [Rz,Ry,Rx], feat [Rz,Ry,Rx,3])."""
-    _require_cuda(packed)
+def unpack_grid(desc: GridDesc, packed: torch.Tensor, which: int = None):
+    """Packed values or a gradient buffer -> (sdf [Rz,Ry,Rx], feat [Rz,Ry,Rx,3]).
+    `which` defaults to values for a uint8 buffer or when the layout is FP32,
+    and must be GRID_GRAD for a float32 gradient of a BF16-feature grid."""
+    _require_cuda(packed, dtypes=(torch.float32, torch.uint8))
+    if which is None:
+        which = GRID_VALUES if (packed.dtype == torch.uint8 or desc.feat_dtype == F32) \
+            else GRID_GRAD
     Rx, Ry, Rz = desc.dims
     sdf = torch.empty((Rz, Ry, Rx), dtype=torch.float32, device=packed.device)
     feat = torch.empty((Rz, Ry, Rx, desc.n_feat), dtype=torch.float32, device=packed.device)
-    _check(library().psdf_grid_unpack(ctypes.byref(desc), _ptr(packed), _ptr(sdf), _ptr(feat),
-                                      _stream()), "psdf_grid_unpack")
+    _check(library().psdf_grid_unpack(ctypes.byref(desc), int(which), _ptr(packed), _ptr(sdf),
+                                      _ptr(feat), _stream()), "psdf_grid_unpack")
     return sdf, feat
 
 
@@ -196,6 +213,9 @@ class Scene:
     sh_l: int
     width: int
     n_feat: int = 3
+    feat_dtype: int = F32    # storage of the spatial features (F32 or BF16)
+    probe_dtype: int = F32   # storage of the probe coefficients (F32 or F16)
+    mlp_dtype: int = F32     # MLP arithmetic (F32-equivalent or F16)
 
     @property
     def probe_dims(self):
@@ -207,29 +227,42 @@ class Scene:
         return self.probes.shape[-1]
 
     def descs(self, n_fresnel):
-        gd = grid_desc(self.dims, self.box_min, self.box_max, self.n_feat)
+        gd = grid_desc(self.dims, self.box_min, self.box_max, self.n_feat, self.feat_dtype)
         pd = ProbeDesc()
         pd.dims[:] = self.probe_dims
         pd.sh_l = self.sh_l
         pd.n_ang = self.n_ang
-        pd.dtype = F32
-        md = MlpDesc(self.n_feat + self.n_ang + n_fresnel, self.width, F32)
+        pd.dtype = self.probe_dtype
+        md = MlpDesc(self.n_feat + self.n_ang + n_fresnel, self.width, self.mlp_dtype)
         return gd, pd, md
 
+    def grad_buffers(self):
+        """Zeroed FP32 gradient buffers: grid [R^3, 4], probes, MLP."""
+        gd, _, _ = self.descs(3)
+        _, gbytes = grid_bytes(gd)
+        dev = self.mlp.device
+        return (torch.zeros(gbytes // 16, 4, dtype=torch.float32, device=dev),
+                torch.zeros(self.probes.shape, dtype=torch.float32, device=dev),
+                torch.zeros_like(self.mlp))
+
     @classmethod
-    def from_host(cls, sc, device="cuda"):
-        """Upload a synth.Scene-like object (numpy arrays) and pack its grid."""
+    def from_host(cls, sc, device="cuda", feat_dtype=F32, probe_dtype=F32, mlp_dtype=F32):
+        """Upload a synth.Scene-like object (numpy arrays) and pack its grid in
+        the requested storage precision."""
         dev = torch.device(device)
         sdf = torch.as_tensor(sc.sdf, dtype=torch.float32, device=dev).contiguous()
         feat = torch.as_tensor(sc.feat, dtype=torch.float32, device=dev).contiguous()
-        gd = grid_desc(sc.dims, sc.box_min, sc.box_max, sc.feat.shape[-1])
+        gd = grid_desc(sc.dims, sc.box_min, sc.box_max, sc.feat.shape[-1], feat_dtype)
         grid = pack_grid(gd, sdf, feat)
-        probes = torch.as_tensor(sc.probes, dtype=torch.float32, device=dev).contiguous()
+        probes = torch.as_tensor(sc.probes, dtype=torch.float32, device=dev)
+        if probe_dtype == F16:
+            probes = probes.half()
         mlp = torch.as_tensor(sc.mlp, dtype=torch.float32, device=dev).contiguous()
-        return cls(grid=grid, probes=probes, mlp=mlp, dims=tuple(sc.dims),
+        return cls(grid=grid, probes=probes.contiguous(), mlp=mlp, dims=tuple(sc.dims),
                    box_min=tuple(float(v) for v in sc.box_min),
                    box_max=tuple(float(v) for v in sc.box_max), sh_l=int(sc.sh_l),
-                   width=int(sc.width), n_feat=int(sc.feat.shape[-1]))
+                   width=int(sc.width), n_feat=int(sc.feat.shape[-1]), feat_dtype=feat_dtype,
+                   probe_dtype=probe_dtype, mlp_dtype=mlp_dtype)
 
 
 def render_params(tau=64.0, n_samples=128, dir_mode=DIR_REFLECT, n_fresnel=3,
@@ -269,7 +302,8 @@ def render_forward(scene: Scene, rays_o, rays_d, params: RenderParams, t_samples
     grid = scene.grid if grid is None else grid
     probes = scene.probes if probes is None else probes
     mlp = scene.mlp if mlp is None else mlp
-    _require_cuda(grid, probes, mlp, rays_o, rays_d, t_samples)
+    _require_cuda(grid, probes, mlp, dtypes=(torch.float32, torch.float16, torch.uint8))
+    _require_cuda(rays_o, rays_d, t_samples)
     n = rays_o.shape[0]
     dev = rays_o.device
     rgb = torch.empty((n, 3), dtype=torch.float32, device=dev)
@@ -295,9 +329,11 @@ def render_backward(scene: Scene, rays_o, rays_d, params: RenderParams, d_rgb, l
     grid = scene.grid if grid is None else grid
     probes = scene.probes if probes is None else probes
     mlp = scene.mlp if mlp is None else mlp
-    _require_cuda(grid, probes, mlp, rays_o, rays_d, t_samples, d_rgb, d_depth, d_wsum, logT)
+    _require_cuda(grid, probes, mlp, dtypes=(torch.float32, torch.float16, torch.uint8))
+    _require_cuda(rays_o, rays_d, t_samples, d_rgb, d_depth, d_wsum, logT)
     if grads is None:
-        grads = (torch.zeros_like(grid), torch.zeros_like(probes), torch.zeros_like(mlp))
+        grads = scene.grad_buffers()
+    _require_cuda(*grads)
     gg, gp, gm = grads
     gd, pd, md = scene.descs(params.n_fresnel)
     h = _Handles(grid, probes, mlp, gd, pd, md)
@@ -326,16 +362,24 @@ def render_occupancy(scene: Scene, params: RenderParams):
 
 
 class RenderFunction(torch.autograd.Function):
-    """Differentiable render: (grid, probes, mlp) -> (rgb, depth, wsum).  The
+    """Differentiable render: (grid, probes, mlp) -> (rgb, depth, wsum).
+
+    grid_p / probes_p are the differentiable FP32 parameters: the storage
+    tensors themselves for FP32 storage, or FP32 master copies ([R^3, 4]
+    records and [Pz,Py,Px,l*l,n_a]) when the scene stores BF16 features or
+    FP16 probes; the kernels read the scene's storage either way.  The
     backward recomputes per-sample activations in the library's adjoint
     kernel; only log T_N per ray is saved."""
 
     @staticmethod
-    def forward(ctx, grid, probes, mlp, rays_o, rays_d, t_samples, scene, params):
+    def forward(ctx, grid_p, probes_p, mlp, rays_o, rays_d, t_samples, scene, params):
+        grid = grid_p if scene.feat_dtype == F32 else scene.grid
+        probes = probes_p if scene.probe_dtype == F32 else scene.probes
         rgb, depth, wsum, logT = render_forward(scene, rays_o, rays_d, params, t_samples,
                                                 grid=grid, probes=probes, mlp=mlp)
-        ctx.save_for_backward(grid, probes, mlp, rays_o, rays_d, logT,
+        ctx.save_for_backward(mlp, rays_o, rays_d, logT,
                               t_samples if t_samples is not None else torch.empty(0))
+        ctx.storage = (grid, probes)
         ctx.has_t = t_samples is not None
         ctx.scene = scene
         ctx.params = params
@@ -344,7 +388,8 @@ class RenderFunction(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, d_rgb, d_depth, d_wsum):
-        grid, probes, mlp, rays_o, rays_d, logT, t_samples = ctx.saved_tensors
+        mlp, rays_o, rays_d, logT, t_samples = ctx.saved_tensors
+        grid, probes = ctx.storage
         t_samples = t_samples if ctx.has_t else None
         d_rgb = torch.zeros((rays_o.shape[0], 3), dtype=torch.float32, device=rays_o.device) \
             if d_rgb is None else d_rgb.contiguous()
@@ -356,7 +401,10 @@ class RenderFunction(torch.autograd.Function):
         return gg, gp, gm, None, None, None, None, None
 
 
-def render(scene: Scene, rays_o, rays_d, params: RenderParams, t_samples=None):
-    """Differentiable w.r.t. scene.grid, scene.probes and scene.mlp."""
-    return RenderFunction.apply(scene.grid, scene.probes, scene.mlp, rays_o, rays_d, t_samples,
-                                scene, params)
+def render(scene: Scene, rays_o, rays_d, params: RenderParams, t_samples=None, masters=None):
+    """Differentiable w.r.t. the scene's FP32 parameters: scene.grid,
+    scene.probes and scene.mlp, or, for reduced-precision storage, the FP32
+    masters=(grid [R^3,4], probes) that the storage was packed from."""
+    grid_p, probes_p = (scene.grid, scene.probes) if masters is None else masters
+    return RenderFunction.apply(grid_p, probes_p, scene.mlp, rays_o, rays_d, t_samples, scene,
+                                params)

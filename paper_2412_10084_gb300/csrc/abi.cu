@@ -63,9 +63,20 @@ psdf_status check_grid_desc(const psdf_grid_desc* d)
         n *= d->dims[a];
     }
     if (n >= (int64_t(1) << 31)) return PSDF_ERR_BAD_SHAPE;
-    if (d->feat_dtype != PSDF_F32) return PSDF_ERR_BAD_DTYPE;
+    if (d->feat_dtype != PSDF_F32 && d->feat_dtype != PSDF_BF16) return PSDF_ERR_BAD_DTYPE;
     if (d->n_feat != 3) return PSDF_ERR_UNSUPPORTED;
     return PSDF_OK;
+}
+
+int64_t grid_nodes(const psdf_grid_desc* d)
+{
+    return int64_t(d->dims[0]) * d->dims[1] * d->dims[2];
+}
+
+// Byte offset of the BF16 feature records in the BF16-feature layout.
+size_t bf16_feat_offset(const psdf_grid_desc* d)
+{
+    return (static_cast<size_t>(grid_nodes(d)) * 4 + 15) & ~size_t(15);
 }
 
 psdf_status check_probe_desc(const psdf_probe_desc* d)
@@ -78,7 +89,8 @@ psdf_status check_probe_desc(const psdf_probe_desc* d)
     }
     if (d->sh_l < 1 || d->sh_l > 4 || d->n_ang < 1 || d->n_ang > 64) return PSDF_ERR_BAD_SHAPE;
     if (n * d->sh_l * d->sh_l * d->n_ang >= (int64_t(1) << 31)) return PSDF_ERR_BAD_SHAPE;
-    if (d->dtype != PSDF_F32) return PSDF_ERR_BAD_DTYPE;
+    if (d->dtype != PSDF_F32 && d->dtype != PSDF_F16) return PSDF_ERR_BAD_DTYPE;
+    if (d->dtype == PSDF_F16 && d->n_ang % 4 != 0) return PSDF_ERR_UNSUPPORTED;
     return PSDF_OK;
 }
 
@@ -86,7 +98,7 @@ psdf_status check_mlp_desc(const psdf_mlp_desc* d)
 {
     if (!d) return PSDF_ERR_INVALID_ARG;
     if (d->n_in < 1 || d->n_in > 64 || d->width < 1 || d->width > 256) return PSDF_ERR_BAD_SHAPE;
-    if (d->dtype != PSDF_F32) return PSDF_ERR_BAD_DTYPE;
+    if (d->dtype != PSDF_F32 && d->dtype != PSDF_F16) return PSDF_ERR_BAD_DTYPE;
     return PSDF_OK;
 }
 
@@ -125,16 +137,25 @@ psdf_status resolve(const psdf_grid* grid, const psdf_probes* probes, const psdf
     r.shape.l2 = pd.sh_l * pd.sh_l;
     r.shape.width = md.width;
     r.shape.k = p->n_fresnel;
+    r.shape.fb = gd.feat_dtype == PSDF_BF16;
+    r.shape.ph = pd.dtype == PSDF_F16;
+    r.shape.mh = md.dtype == PSDF_F16;
     bool known = false;
-#define PSDF_KNOWN(NA, L2, W, K)                                                             \
-    if (r.shape.na == NA && r.shape.l2 == L2 && r.shape.width == W && r.shape.k == K) known = true;
+#define PSDF_KNOWN(NA, L2, W, K, FB, PH, MH) \
+    if (r.shape.match(NA, L2, W, K, FB, PH, MH)) known = true;
     PSDF_FOR_EACH_SHAPE(PSDF_KNOWN)
 #undef PSDF_KNOWN
     if (!known) return PSDF_ERR_UNSUPPORTED;
 
     psdf::RenderArgs& A = r.args;
     std::memset(&A, 0, sizeof(A));
-    A.grid.nodes = static_cast<const float4*>(grid->values);
+    if (r.shape.fb) {
+        const uint8_t* base = static_cast<const uint8_t*>(grid->values);
+        A.grid.sdf = reinterpret_cast<const float*>(base);
+        A.grid.feat16 = reinterpret_cast<const uint2*>(base + bf16_feat_offset(&gd));
+    } else {
+        A.grid.nodes = static_cast<const float4*>(grid->values);
+    }
     for (int a = 0; a < 3; ++a) {
         A.grid.R[a] = gd.dims[a];
         A.grid.bmin[a] = gd.box_min[a];
@@ -145,7 +166,10 @@ psdf_status resolve(const psdf_grid* grid, const psdf_probes* probes, const psdf
         A.probes.P[a] = pd.dims[a];
         A.probes.sc[a] = static_cast<float>(pd.dims[a] - 1) / ext;
     }
-    A.probes.coeffs = static_cast<const float4*>(probes->coeffs);
+    if (r.shape.ph)
+        A.probes.coeffs16 = static_cast<const uint2*>(probes->coeffs);
+    else
+        A.probes.coeffs = static_cast<const float4*>(probes->coeffs);
     A.mlp = static_cast<const float*>(mlp->params);
     A.tau = p->tau;
     A.n_samples = p->n_samples;
@@ -196,6 +220,43 @@ __global__ void unpack_kernel(const float4* __restrict__ in, float* __restrict__
     }
 }
 
+__device__ __forceinline__ uint32_t bf16_bits(float v)
+{
+    // round to nearest even; NaN stays NaN
+    const uint32_t u = __float_as_uint(v);
+    if ((u & 0x7fffffffu) > 0x7f800000u) return (u >> 16) | 0x40u;
+    return (u + 0x7fffu + ((u >> 16) & 1u)) >> 16;
+}
+
+__global__ void pack_bf16_kernel(const float* __restrict__ sdf, const float* __restrict__ feat,
+                                 float* __restrict__ out_sdf, uint2* __restrict__ out_feat,
+                                 int64_t n)
+{
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        out_sdf[i] = sdf[i];
+        const uint32_t f0 = bf16_bits(feat[3 * i]), f1 = bf16_bits(feat[3 * i + 1]);
+        const uint32_t f2 = bf16_bits(feat[3 * i + 2]);
+        out_feat[i] = make_uint2(f0 | (f1 << 16), f2);
+    }
+}
+
+__global__ void unpack_bf16_kernel(const float* __restrict__ in_sdf,
+                                   const uint2* __restrict__ in_feat, float* __restrict__ sdf,
+                                   float* __restrict__ feat, int64_t n)
+{
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        if (sdf) sdf[i] = in_sdf[i];
+        if (feat) {
+            const uint2 f = in_feat[i];
+            feat[3 * i] = __uint_as_float(f.x << 16);
+            feat[3 * i + 1] = __uint_as_float(f.x & 0xffff0000u);
+            feat[3 * i + 2] = __uint_as_float(f.y << 16);
+        }
+    }
+}
+
 }  // namespace
 
 namespace psdf {
@@ -228,6 +289,31 @@ cudaError_t launch_pack(const float* sdf, const float* feat, float4* packed, int
     const int64_t blocks = (n_nodes + threads - 1) / threads;
     pack_kernel<<<(int)(blocks < 65535 * 16 ? blocks : 65535 * 16), threads, 0, stream>>>(
         sdf, feat, packed, n_nodes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_bf16(const float* sdf, const float* feat, void* packed, size_t feat_off,
+                             int64_t n_nodes, cudaStream_t stream)
+{
+    const int threads = 256;
+    const int64_t blocks = (n_nodes + threads - 1) / threads;
+    uint8_t* base = static_cast<uint8_t*>(packed);
+    pack_bf16_kernel<<<(int)(blocks < 65535 * 16 ? blocks : 65535 * 16), threads, 0, stream>>>(
+        sdf, feat, reinterpret_cast<float*>(base), reinterpret_cast<uint2*>(base + feat_off),
+        n_nodes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_bf16(const void* packed, size_t feat_off, float* sdf, float* feat,
+                               int64_t n_nodes, cudaStream_t stream)
+{
+    const int threads = 256;
+    const int64_t blocks = (n_nodes + threads - 1) / threads;
+    const uint8_t* base = static_cast<const uint8_t*>(packed);
+    unpack_bf16_kernel<<<(int)(blocks < 65535 * 16 ? blocks : 65535 * 16), threads, 0,
+                         stream>>>(reinterpret_cast<const float*>(base),
+                                   reinterpret_cast<const uint2*>(base + feat_off), sdf, feat,
+                                   n_nodes);
     return cudaGetLastError();
 }
 
@@ -279,12 +365,14 @@ psdf_status psdf_device_status(void* stream, int32_t* flags)
     return PSDF_OK;
 }
 
-psdf_status psdf_grid_bytes(const psdf_grid_desc* desc, size_t* values_bytes)
+psdf_status psdf_grid_bytes(const psdf_grid_desc* desc, size_t* values_bytes, size_t* grad_bytes)
 {
     const psdf_status st = check_grid_desc(desc);
     if (st != PSDF_OK) return st;
-    if (!values_bytes) return PSDF_ERR_INVALID_ARG;
-    *values_bytes = sizeof(float) * 4 * size_t(desc->dims[0]) * desc->dims[1] * desc->dims[2];
+    if (!values_bytes || !grad_bytes) return PSDF_ERR_INVALID_ARG;
+    const size_t n = static_cast<size_t>(grid_nodes(desc));
+    *values_bytes = desc->feat_dtype == PSDF_BF16 ? bf16_feat_offset(desc) + 8 * n : 16 * n;
+    *grad_bytes = 16 * n;
     return PSDF_OK;
 }
 
@@ -311,19 +399,26 @@ psdf_status psdf_grid_pack(const psdf_grid_desc* desc, const float* sdf, const f
     if (st != PSDF_OK) return st;
     if (!sdf || !feat || !packed) return PSDF_ERR_INVALID_ARG;
     if (!aligned16(packed)) return PSDF_ERR_MISALIGNED;
-    const int64_t n = int64_t(desc->dims[0]) * desc->dims[1] * desc->dims[2];
+    const int64_t n = grid_nodes(desc);
+    if (desc->feat_dtype == PSDF_BF16)
+        return cuda_status(psdf::launch_pack_bf16(sdf, feat, packed, bf16_feat_offset(desc), n,
+                                                  static_cast<cudaStream_t>(stream)));
     return cuda_status(psdf::launch_pack(sdf, feat, static_cast<float4*>(packed), n,
                                          static_cast<cudaStream_t>(stream)));
 }
 
-psdf_status psdf_grid_unpack(const psdf_grid_desc* desc, const void* packed, float* sdf,
-                             float* feat, void* stream)
+psdf_status psdf_grid_unpack(const psdf_grid_desc* desc, int32_t which, const void* packed,
+                             float* sdf, float* feat, void* stream)
 {
     const psdf_status st = check_grid_desc(desc);
     if (st != PSDF_OK) return st;
     if (!packed || (!sdf && !feat)) return PSDF_ERR_INVALID_ARG;
+    if (which != PSDF_GRID_VALUES && which != PSDF_GRID_GRAD) return PSDF_ERR_INVALID_ARG;
     if (!aligned16(packed)) return PSDF_ERR_MISALIGNED;
-    const int64_t n = int64_t(desc->dims[0]) * desc->dims[1] * desc->dims[2];
+    const int64_t n = grid_nodes(desc);
+    if (which == PSDF_GRID_VALUES && desc->feat_dtype == PSDF_BF16)
+        return cuda_status(psdf::launch_unpack_bf16(packed, bf16_feat_offset(desc), sdf, feat, n,
+                                                    static_cast<cudaStream_t>(stream)));
     return cuda_status(psdf::launch_unpack(static_cast<const float4*>(packed), sdf, feat, n,
                                            static_cast<cudaStream_t>(stream)));
 }

@@ -11,16 +11,26 @@ constexpr int kFwdThreads = 128;
 constexpr int kBwdThreads = 128;
 
 // Compile-time shape of a render kernel: angular channels, SH coefficients,
-// MLP width, Fresnel powers (3 spatial features are fixed by the record).
+// MLP width, Fresnel powers (3 spatial features), and storage precision:
+// BF16 features (fb), FP16 probes (ph), plain-FP16 MLP (mh).
 struct KernelShape {
-    int na, l2, width, k;
+    int na, l2, width, k, fb, ph, mh;
+    bool match(int na_, int l2_, int w_, int k_, int fb_, int ph_, int mh_) const
+    {
+        return na == na_ && l2 == l2_ && width == w_ && k == k_ && fb == fb_ && ph == ph_ &&
+               mh == mh_;
+    }
 };
 
-// Shapes compiled into the library.
+// Shapes compiled into the library: the FP32 path (widths 16/32, 4 or 8
+// angular channels), the reduced-precision path (BF16 features, FP16 probes,
+// FP16 MLP), and BF16 features with FP32 probes and MLP.
 #define PSDF_FOR_EACH_SHAPE(X) \
-    X(4, 9, 16, 3)             \
-    X(4, 9, 32, 3)             \
-    X(8, 9, 32, 3)
+    X(4, 9, 16, 3, 0, 0, 0)    \
+    X(4, 9, 32, 3, 0, 0, 0)    \
+    X(8, 9, 32, 3, 0, 0, 0)    \
+    X(4, 9, 32, 3, 1, 1, 1)    \
+    X(8, 9, 32, 3, 1, 0, 0)
 
 cudaError_t launch_forward(const RenderArgs& A, const KernelShape& ks, int grid_ctas,
                            cudaStream_t stream);
@@ -38,5 +48,10 @@ cudaError_t launch_pack(const float* sdf, const float* feat, float4* packed, int
                         cudaStream_t stream);
 cudaError_t launch_unpack(const float4* packed, float* sdf, float* feat, int64_t n_nodes,
                           cudaStream_t stream);
+// BF16-feature layout: FP32 SDF array, then {f0, f1, f2, 0} BF16 records at feat_off bytes.
+cudaError_t launch_pack_bf16(const float* sdf, const float* feat, void* packed, size_t feat_off,
+                             int64_t n_nodes, cudaStream_t stream);
+cudaError_t launch_unpack_bf16(const void* packed, size_t feat_off, float* sdf, float* feat,
+                               int64_t n_nodes, cudaStream_t stream);
 
 }  // namespace psdf

@@ -42,12 +42,12 @@ struct BwdLayout {
     static constexpr int oW = 0;
     static constexpr int oF32 = oW + M::kWeightBytes;
     static constexpr int oXH = (oF32 + 4 * M::kF32 + 127) & ~127;
-    static constexpr int oDZ = oXH + 2 * kXH;
-    static constexpr int oG = oDZ + 2 * kDZ;
+    static constexpr int oDZ = oXH + M::kSplit * kXH;
+    static constexpr int oG = oDZ + M::kSplit * kDZ;
     static constexpr int oMisc = oG + 4 * kParamsPad;
     static constexpr int kBytes = oMisc + 64;
     static constexpr uint32_t kTmemCols = 128;  // z1/dh1 at 0, z2/dx at 32, dW at 64
-    static_assert(128 * PST * 4 <= 2 * kDZ, "probe staging aliases the DZ tiles");
+    static_assert(128 * PST * 4 <= M::kSplit * kDZ, "probe staging aliases the DZ tiles");
     static_assert(XHC <= 64, "dW accumulator fits columns 64..127");
 };
 
@@ -130,10 +130,10 @@ render_backward_kernel(RenderArgs A)
     constexpr int W = C::W, L2 = C::L2, NA = C::NA, NIN = C::NIN, K1 = M::K1;
     extern __shared__ __align__(128) uint8_t smem[];
     uint8_t* wt = smem + L::oW;
-    uint8_t* w1h = wt;
-    uint8_t* w1l = wt + M::kW1;
-    uint8_t* w2h = wt + 2 * M::kW1;
-    uint8_t* w2l = w2h + M::kW2;
+    uint8_t* w1h = M::w1h(wt);
+    uint8_t* w1l = M::w1l(wt);
+    uint8_t* w2h = M::w2h(wt);
+    uint8_t* w2l = M::w2l(wt);
     float* f32 = reinterpret_cast<float*>(smem + L::oF32);
     uint8_t* xhh = smem + L::oXH;
     uint8_t* xhl = xhh + L::kXH;
@@ -254,7 +254,7 @@ render_backward_kernel(RenderArgs A)
                 float xin[K1];
 #pragma unroll
                 for (int i = 0; i < K1; ++i) xin[i] = i < NIN ? S.x[i] : (i == NIN ? 1.0f : 0.0f);
-                store_row<K1>(xhh, xhl, tid, 0, L::XHC, xin);
+                store_row<K1, M::kSplit>(xhh, xhl, tid, 0, L::XHC, xin);
                 s_next = __shfl_down_sync(FULL, S.s, 1);
                 if (extra) {
                     float xw[3];
@@ -268,7 +268,7 @@ render_backward_kernel(RenderArgs A)
                     lam = unclipped ? diff : 0.0f;
                 }
             } else {
-                zero_row<K1>(xhh, xhl, tid, 0, L::XHC);
+                zero_row<K1, M::kSplit>(xhh, xhl, tid, 0, L::XHC);
                 S.s = 0.0f;
             }
             tc::fence_smem_to_async();
@@ -278,7 +278,7 @@ render_backward_kernel(RenderArgs A)
 
             // ---- P1: layer 1; log T_k from a suffix sum of lam ----
             if (tid == 0) {
-                mma3(tmem + 0, xhh, xhl, w1h, w1l, 128, L::kSboXH, 128, (K1 / 8) * 128,
+                mma_k<M::kSplit>(tmem + 0, xhh, xhl, w1h, w1l, 128, L::kSboXH, 128, (K1 / 8) * 128,
                      M::kIdescL, false);
                 tc::commit(mbar);
             }
@@ -309,7 +309,7 @@ render_backward_kernel(RenderArgs A)
 #pragma unroll
                     for (int o = 0; o < W; ++o) z[o] = 0.0f;
                 }
-                store_row<W>(xhh, xhl, tid, K1, L::XHC, z);
+                store_row<W, M::kSplit>(xhh, xhl, tid, K1, L::XHC, z);
             }
             tc::fence_smem_to_async();
             tc::fence_before();
@@ -320,7 +320,7 @@ render_backward_kernel(RenderArgs A)
             if (tid == 0) {
 #pragma unroll
                 for (int s = 0; s < W / 16; ++s)
-                    mma3(tmem + 32, xhh + 256 + s * 256, xhl + 256 + s * 256, w2h + s * 256,
+                    mma_k<M::kSplit>(tmem + 32, xhh + 256 + s * 256, xhl + 256 + s * 256, w2h + s * 256,
                          w2l + s * 256, 128, L::kSboXH, 128, (W / 8) * 128, M::kIdescL, s > 0);
                 tc::commit(mbar);
             }
@@ -396,7 +396,7 @@ render_backward_kernel(RenderArgs A)
                     const float dh2 = w3.x * dz3[0] + w3.y * dz3[1] + w3.z * dz3[2];
                     dz2[i] = ((mask2 >> i) & 1u) ? dh2 * s2 : 0.0f;
                 }
-                store_row<W>(dzh, dzl, tid, W, L::DZC, dz2);
+                store_row<W, M::kSplit>(dzh, dzl, tid, W, L::DZC, dz2);
             }
             tc::fence_smem_to_async();
             tc::fence_before();
@@ -408,7 +408,7 @@ render_backward_kernel(RenderArgs A)
                 const uint32_t idesc = tc::idesc_f16(128, W, 0, 1);
 #pragma unroll
                 for (int s = 0; s < W / 16; ++s)
-                    mma3(tmem + 0, dzh + (W / 8) * 128 + s * 256, dzl + (W / 8) * 128 + s * 256,
+                    mma_k<M::kSplit>(tmem + 0, dzh + (W / 8) * 128 + s * 256, dzl + (W / 8) * 128 + s * 256,
                          w2h + s * 2 * (W / 8) * 128, w2l + s * 2 * (W / 8) * 128, 128,
                          L::kSboDZ, (W / 8) * 128, 128, idesc, s > 0);
                 tc::commit(mbar);
@@ -422,7 +422,7 @@ render_backward_kernel(RenderArgs A)
                 const float r12 = s1 * inv_s2;  // dh1 arrives scaled by s2; dz1 is stored scaled by s1
 #pragma unroll
                 for (int i = 0; i < W; ++i) dh1[i] = ((mask1 >> i) & 1u) ? dh1[i] * r12 : 0.0f;
-                store_row<W>(dzh, dzl, tid, 0, L::DZC, dh1);
+                store_row<W, M::kSplit>(dzh, dzl, tid, 0, L::DZC, dh1);
             }
             tc::fence_smem_to_async();
             tc::fence_before();
@@ -434,12 +434,12 @@ render_backward_kernel(RenderArgs A)
                 const uint32_t idx = tc::idesc_f16(128, 16, 0, 1);
 #pragma unroll
                 for (int s = 0; s < W / 16; ++s)
-                    mma3(tmem + 32, dzh + s * 256, dzl + s * 256, w1h + s * 512, w1l + s * 512,
+                    mma_k<M::kSplit>(tmem + 32, dzh + s * 256, dzl + s * 256, w1h + s * 512, w1l + s * 512,
                          128, L::kSboDZ, 256, 128, idx, s > 0);
                 const uint32_t idw = tc::idesc_f16(64, L::XHC, 1, 1);
 #pragma unroll
                 for (int s = 0; s < 8; ++s)
-                    mma3(tmem + 64, dzh + s * 2 * L::kSboDZ, dzl + s * 2 * L::kSboDZ,
+                    mma_k<M::kSplit>(tmem + 64, dzh + s * 2 * L::kSboDZ, dzl + s * 2 * L::kSboDZ,
                          xhh + s * 2 * L::kSboXH, xhl + s * 2 * L::kSboXH, L::kSboDZ, 128,
                          L::kSboXH, 128, idw, dw_started || s > 0);
                 dw_started = true;
@@ -467,13 +467,12 @@ render_backward_kernel(RenderArgs A)
                 for (int j = 0; j < L2; ++j) dY[j] = 0.0f;
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
-                    const float4* b = A.probes.coeffs + (size_t)pidx[q] * (L2 * C::NA4);
 #pragma unroll
                     for (int j = 0; j < L2; ++j) {
                         float acc = 0.0f;
 #pragma unroll
                         for (int cg = 0; cg < C::NA4; ++cg) {
-                            const float4 bb = __ldg(b + j * C::NA4 + cg);
+                            const float4 bb = probe_coeffs<C>(A.probes, pidx[q], j, cg);
                             acc = fmaf(bb.x, dx[3 + 4 * cg + 0], acc);
                             acc = fmaf(bb.y, dx[3 + 4 * cg + 1], acc);
                             acc = fmaf(bb.z, dx[3 + 4 * cg + 2], acc);
@@ -610,9 +609,9 @@ cudaError_t launch_backward_t(const RenderArgs& A, int grid_ctas, cudaStream_t s
 cudaError_t launch_backward(const RenderArgs& A, const KernelShape& ks, int grid_ctas,
                             cudaStream_t stream)
 {
-#define PSDF_BWD_CASE(NA, L2, W, K)                                                          \
-    if (ks.na == NA && ks.l2 == L2 && ks.width == W && ks.k == K)                            \
-        return launch_backward_t<Cfg<NA, L2, W, K>>(A, grid_ctas, stream);
+#define PSDF_BWD_CASE(NA, L2, W, K, FB, PH, MH)                                              \
+    if (ks.match(NA, L2, W, K, FB, PH, MH))                                                  \
+        return launch_backward_t<Cfg<NA, L2, W, K, FB, PH, MH>>(A, grid_ctas, stream);
     PSDF_FOR_EACH_SHAPE(PSDF_BWD_CASE)
 #undef PSDF_BWD_CASE
     return cudaErrorInvalidValue;
@@ -635,9 +634,9 @@ cudaError_t backward_occupancy_t(int* n)
 cudaError_t backward_ctas_per_sm(const KernelShape& ks, int* n)
 {
     *n = 0;
-#define PSDF_BWD_OCC(NA, L2, W, K)                                                           \
-    if (ks.na == NA && ks.l2 == L2 && ks.width == W && ks.k == K)                            \
-        return backward_occupancy_t<Cfg<NA, L2, W, K>>(n);
+#define PSDF_BWD_OCC(NA, L2, W, K, FB, PH, MH)                                               \
+    if (ks.match(NA, L2, W, K, FB, PH, MH))                                                  \
+        return backward_occupancy_t<Cfg<NA, L2, W, K, FB, PH, MH>>(n);
     PSDF_FOR_EACH_SHAPE(PSDF_BWD_OCC)
 #undef PSDF_BWD_OCC
     return cudaErrorInvalidValue;

@@ -15,7 +15,9 @@ constexpr float kNormalEps = 1e-12f;  // n = g / sqrt(|g|^2 + eps^2)
 // Kernel view of the packed SDF + feature grid: one float4 {sdf, f0, f1, f2}
 // per node, x fastest.
 struct GridView {
-    const float4* __restrict__ nodes;
+    const float4* __restrict__ nodes;   // FP32 records {sdf, f0, f1, f2}
+    const float* __restrict__ sdf;      // BF16-feature layout: FP32 SDF per node ...
+    const uint2* __restrict__ feat16;   // ... and {f0, f1, f2, 0} as BF16 per node
     int R[3];
     float bmin[3];
     float bmax[3];
@@ -25,7 +27,8 @@ struct GridView {
 // Probe coefficients, [Pz][Py][Px][L2][NA] FP32, viewed as float4 groups of
 // four channels.
 struct ProbeView {
-    const float4* __restrict__ coeffs;
+    const float4* __restrict__ coeffs;    // FP32 coefficients, 4 channels per float4
+    const uint2* __restrict__ coeffs16;   // FP16 coefficients, 4 channels per uint2
     int P[3];
     float sc[3];
 };
@@ -163,17 +166,35 @@ __device__ __forceinline__ void corner_weights(const float f[3], float w[8])
     w[7] = x1 * y1 * z1;
 }
 
+__device__ __forceinline__ float bf16_lo(uint32_t u) { return __uint_as_float(u << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
+
+// Corner records of the BF16-feature layout, widened to the FP32 record form.
+__device__ __forceinline__ void gather_corners_bf16(const GridView& g, const Cell& c, Corners& k)
+{
+    const int sx = 1, sy = g.R[0], sz = g.R[0] * g.R[1];
+    const int off[8] = {0, sx, sy, sx + sy, sz, sz + sx, sz + sy, sz + sy + sx};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const float s = __ldg(g.sdf + c.base + off[q]);
+        const uint2 f = __ldg(g.feat16 + c.base + off[q]);
+        k.v[q] = make_float4(s, bf16_lo(f.x), bf16_hi(f.x), bf16_lo(f.y));
+    }
+}
+
 // SDF value only (the extra point N of a ray's last full chunk).
 __device__ __forceinline__ float sdf_value(const GridView& g, const Cell& c)
 {
     const int sx = 1, sy = g.R[0], sz = g.R[0] * g.R[1];
-    const float* p = reinterpret_cast<const float*>(g.nodes + c.base);
+    const bool split = g.sdf != nullptr;  // BF16-feature layout: SDF in its own array
+    const float* p = split ? g.sdf + c.base : reinterpret_cast<const float*>(g.nodes + c.base);
+    const int st = split ? 1 : 4;
     float w[8];
     corner_weights(c.f, w);
     const int off[8] = {0, sx, sy, sx + sy, sz, sz + sx, sz + sy, sz + sy + sx};
     float s = 0.0f;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) s = fmaf(w[q], __ldg(p + 4 * off[q]), s);
+    for (int q = 0; q < 8; ++q) s = fmaf(w[q], __ldg(p + st * off[q]), s);
     return s;
 }
 

@@ -26,8 +26,8 @@ struct FwdLayout {
     static constexpr int oW = 0;
     static constexpr int oF32 = oW + M::kWeightBytes;
     static constexpr int oX = (oF32 + 4 * M::kF32 + 127) & ~127;
-    static constexpr int oH = oX + 2 * kXT;
-    static constexpr int oBar = oH + 2 * kHT;
+    static constexpr int oH = oX + M::kSplit * kXT;
+    static constexpr int oBar = oH + M::kSplit * kHT;
     static constexpr int kBytes = oBar + 16;
     static constexpr uint32_t kTmemCols = 64;  // layer 1 at column 0, layer 2 at 32
 };
@@ -105,7 +105,7 @@ render_forward_kernel(RenderArgs A)
                 float xin[M::K1];
 #pragma unroll
                 for (int i = 0; i < M::K1; ++i) xin[i] = i < C::NIN ? S.x[i] : 0.0f;
-                store_row<M::K1>(xh, xl, tid, 0, M::K1, xin);
+                store_row<M::K1, M::kSplit>(xh, xl, tid, 0, M::K1, xin);
                 float s_next = __shfl_down_sync(FULL, S.s, 1);
                 if (active && (lane == 31 || k + 1 >= N)) {
                     float xw[3];
@@ -117,7 +117,7 @@ render_forward_kernel(RenderArgs A)
                     lam = diff < 0.0f ? diff : 0.0f;
                 }
             } else {
-                zero_row<M::K1>(xh, xl, tid, 0, M::K1);
+                zero_row<M::K1, M::kSplit>(xh, xl, tid, 0, M::K1);
             }
             tc::fence_smem_to_async();
             tc::fence_before();
@@ -125,8 +125,8 @@ render_forward_kernel(RenderArgs A)
             tc::fence_after();
             // ---- P1: layer 1 on the tensor cores ----
             if (tid == 0) {
-                mma3(tmem + 0, xh, xl, wt, wt + M::kW1, 128, (M::K1 / 8) * 128, 128,
-                     (M::K1 / 8) * 128, M::kIdescL, false);
+                mma_k<M::kSplit>(tmem + 0, xh, xl, M::w1h(wt), M::w1l(wt), 128,
+                                 (M::K1 / 8) * 128, 128, (M::K1 / 8) * 128, M::kIdescL, false);
                 tc::commit(mbar);
             }
             // transmittance of the chunk (Eq. 8): exclusive warp scan of lam
@@ -154,7 +154,7 @@ render_forward_kernel(RenderArgs A)
                 tc::tmem_ld<W>(t_row + 0, z);
 #pragma unroll
                 for (int o = 0; o < W; ++o) z[o] = fmaxf(z[o] + f32[M::kB1 + o], 0.0f);
-                store_row<W>(hh, hl, tid, 0, W, z);
+                store_row<W, M::kSplit>(hh, hl, tid, 0, W, z);
             }
             tc::fence_smem_to_async();
             tc::fence_before();
@@ -164,9 +164,9 @@ render_forward_kernel(RenderArgs A)
             if (tid == 0) {
 #pragma unroll
                 for (int s = 0; s < W / 16; ++s)
-                    mma3(tmem + 32, hh + s * 256, hl + s * 256, wt + 2 * M::kW1 + s * 256,
-                         wt + 2 * M::kW1 + M::kW2 + s * 256, 128, (W / 8) * 128, 128,
-                         (W / 8) * 128, M::kIdescL, s > 0);
+                    mma_k<M::kSplit>(tmem + 32, hh + s * 256, hl + s * 256,
+                                     M::w2h(wt) + s * 256, M::w2l(wt) + s * 256, 128,
+                                     (W / 8) * 128, 128, (W / 8) * 128, M::kIdescL, s > 0);
                 tc::commit(mbar);
             }
             bad |= !tc::mbar_wait(mbar, phase);
@@ -238,9 +238,9 @@ cudaError_t launch_forward_t(const RenderArgs& A, int grid_ctas, cudaStream_t st
 cudaError_t launch_forward(const RenderArgs& A, const KernelShape& ks, int grid_ctas,
                            cudaStream_t stream)
 {
-#define PSDF_FWD_CASE(NA, L2, W, K)                                                          \
-    if (ks.na == NA && ks.l2 == L2 && ks.width == W && ks.k == K)                            \
-        return launch_forward_t<Cfg<NA, L2, W, K>>(A, grid_ctas, stream);
+#define PSDF_FWD_CASE(NA, L2, W, K, FB, PH, MH)                                              \
+    if (ks.match(NA, L2, W, K, FB, PH, MH))                                                  \
+        return launch_forward_t<Cfg<NA, L2, W, K, FB, PH, MH>>(A, grid_ctas, stream);
     PSDF_FOR_EACH_SHAPE(PSDF_FWD_CASE)
 #undef PSDF_FWD_CASE
     return cudaErrorInvalidValue;
@@ -263,9 +263,9 @@ cudaError_t forward_occupancy_t(int* n)
 cudaError_t forward_ctas_per_sm(const KernelShape& ks, int* n)
 {
     *n = 0;
-#define PSDF_FWD_OCC(NA, L2, W, K)                                                           \
-    if (ks.na == NA && ks.l2 == L2 && ks.width == W && ks.k == K)                            \
-        return forward_occupancy_t<Cfg<NA, L2, W, K>>(n);
+#define PSDF_FWD_OCC(NA, L2, W, K, FB, PH, MH)                                                \
+    if (ks.match(NA, L2, W, K, FB, PH, MH))                                                  \
+        return forward_occupancy_t<Cfg<NA, L2, W, K, FB, PH, MH>>(n);
     PSDF_FOR_EACH_SHAPE(PSDF_FWD_OCC)
 #undef PSDF_FWD_OCC
     return cudaErrorInvalidValue;

@@ -3,12 +3,22 @@
 // inputs (Eq. 4), FP32 on the CUDA cores; the MLP input row is their concatenation.
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include "render_common.cuh"
 
 namespace psdf {
 
-template <int NA_, int L2_, int W_, int K_>
+// Compile-time shape and storage precision of a render kernel.
+//   FB: spatial features stored as BF16 (SDF stays FP32)
+//   PH: probe coefficients stored as FP16
+//   MH: MLP on the tensor cores in plain FP16 (else the FP32-equivalent
+//       hi/lo split)
+template <int NA_, int L2_, int W_, int K_, int FB_ = 0, int PH_ = 0, int MH_ = 0>
 struct Cfg {
+    static constexpr int FB = FB_;
+    static constexpr int PH = PH_;
+    static constexpr int MH = MH_;
     static constexpr int NS = 3;
     static constexpr int NA = NA_;
     static constexpr int L2 = L2_;
@@ -28,6 +38,30 @@ struct Cfg {
     static_assert(NA % 4 == 0, "angular channels are read as float4 groups");
     static_assert(W % 4 == 0, "hidden width must be a multiple of 4");
 };
+
+template <class C>
+__device__ __forceinline__ void gather_corners_t(const GridView& g, const Cell& c, Corners& k)
+{
+    if constexpr (C::FB)
+        gather_corners_bf16(g, c, k);
+    else
+        gather_corners(g, c, k);
+}
+
+// Channels [4 cg, 4 cg + 4) of SH coefficient j of probe `probe`.
+template <class C>
+__device__ __forceinline__ float4 probe_coeffs(const ProbeView& p, int probe, int j, int cg)
+{
+    const size_t i = (static_cast<size_t>(probe) * C::L2 + j) * C::NA4 + cg;
+    if constexpr (C::PH) {
+        const uint2 u = __ldg(p.coeffs16 + i);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    } else {
+        return __ldg(p.coeffs + i);
+    }
+}
 
 // Geometry and appearance inputs of one colour sample.
 template <class C>
@@ -66,7 +100,7 @@ __device__ __forceinline__ void eval_geometry(const RenderArgs& A, const float o
     point_at(o, d, t, xw);
     S.cell = locate(xw, A.grid.bmin, A.grid.sc, A.grid.R);
     Corners k;
-    gather_corners(A.grid, S.cell, k);
+    gather_corners_t<C>(A.grid, S.cell, k);
     float fs[3];
     sdf_full(A.grid, S.cell, k, S.s, S.g, fs);
 
@@ -96,7 +130,6 @@ __device__ __forceinline__ void eval_geometry(const RenderArgs& A, const float o
     for (int c = 0; c < C::NA; ++c) fa[c] = 0.0f;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        const float4* b = A.probes.coeffs + (size_t)pidx[q] * (C::L2 * C::NA4);
         float part[C::NA];
 #pragma unroll
         for (int c = 0; c < C::NA; ++c) part[c] = 0.0f;
@@ -104,7 +137,7 @@ __device__ __forceinline__ void eval_geometry(const RenderArgs& A, const float o
         for (int j = 0; j < C::L2; ++j) {
 #pragma unroll
             for (int cg = 0; cg < C::NA4; ++cg) {
-                const float4 bb = __ldg(b + j * C::NA4 + cg);
+                const float4 bb = probe_coeffs<C>(A.probes, pidx[q], j, cg);
                 part[4 * cg + 0] = fmaf(bb.x, S.Y[j], part[4 * cg + 0]);
                 part[4 * cg + 1] = fmaf(bb.y, S.Y[j], part[4 * cg + 1]);
                 part[4 * cg + 2] = fmaf(bb.z, S.Y[j], part[4 * cg + 2]);

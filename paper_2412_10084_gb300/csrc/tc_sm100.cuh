@@ -192,6 +192,24 @@ __device__ __forceinline__ void store8(uint8_t* hi_tile, uint8_t* lo_tile, int r
     *reinterpret_cast<uint4*>(lo_tile + off) = lv;
 }
 
+// Writes 8 consecutive columns as plain FP16 (hi tile only).
+__device__ __forceinline__ void store8_hi(uint8_t* hi_tile, int row, int c0, int C, const float* v)
+{
+    uint4 hv;
+    const __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
+    const __half2 c = __floats2half2_rn(v[4], v[5]), d = __floats2half2_rn(v[6], v[7]);
+    hv.x = *reinterpret_cast<const uint32_t*>(&a);
+    hv.y = *reinterpret_cast<const uint32_t*>(&b);
+    hv.z = *reinterpret_cast<const uint32_t*>(&c);
+    hv.w = *reinterpret_cast<const uint32_t*>(&d);
+    *reinterpret_cast<uint4*>(hi_tile + tile_off(row, c0, C)) = hv;
+}
+
+__device__ __forceinline__ void zero8_hi(uint8_t* hi_tile, int row, int c0, int C)
+{
+    *reinterpret_cast<uint4*>(hi_tile + tile_off(row, c0, C)) = make_uint4(0, 0, 0, 0);
+}
+
 // Zeroes 8 consecutive columns of a row in both tiles.
 __device__ __forceinline__ void zero8(uint8_t* hi_tile, uint8_t* lo_tile, int row, int c0, int C)
 {

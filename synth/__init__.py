@@ -212,6 +212,7 @@ def capsule_body(g):
         ankle = knee + jitter(0.4) @ np.array([0.0, -0.40, -0.03])
         caps.append((knee, ankle, 0.055))
     caps.append((pelvis + np.array([-0.1, 0.0, 0.0]), pelvis + np.array([0.1, 0.0, 0.0]), 0.11))
+    caps.append((chest + np.array([-0.13, -0.03, 0.0]), chest + np.array([0.13, -0.03, 0.0]), 0.09))
     assert len(caps) == 15
     return caps
 
@@ -313,7 +314,7 @@ WORKLOADS = {
                       n_rays=1 << 18, cams=49, res=(1600, 1200), fov=45.0, cam_r=2.0),
     "human384": dict(seed=1237, R=(384, 768, 384), P=(48, 96, 48), box=((0, 0, 0), (1, 2, 1)),
                      n_s=3, n_a=4, sh_l=3, width=32, K=3, n_samples=256, tau=64.0,
-                     n_rays=1 << 19, cams=64, res=(2048, 2048), fov=60.0, cam_r=2.5),
+                     n_rays=1 << 19, cams=64, res=(2048, 2048), fov=45.0, cam_r=2.5),
     "stress512": dict(seed=1239, R=(512, 512, 512), P=(64, 64, 64), box=((0, 0, 0), (1, 1, 1)),
                       n_s=3, n_a=8, sh_l=3, width=32, K=3, n_samples=512, tau=64.0,
                       n_rays=1 << 20, cams=49, res=(1600, 1200), fov=45.0, cam_r=2.0),

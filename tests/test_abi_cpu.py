@@ -51,7 +51,10 @@ def test_status_strings_and_version(lib):
 def test_host_validation_without_gpu(lib):
     import paper_2412_10084_gb300 as ps
     gd = ps.grid_desc((64, 64, 64), (0, 0, 0), (1, 1, 1))
-    assert ps.grid_bytes(gd) == 64 ** 3 * 16
+    assert ps.grid_bytes(gd) == (64 ** 3 * 16, 64 ** 3 * 16)
+    gb = ps.grid_desc((33, 33, 33), (0, 0, 0), (1, 1, 1), feat_dtype=ps.BF16)
+    n = 33 ** 3
+    assert ps.grid_bytes(gb) == (((4 * n + 15) // 16) * 16 + 8 * n, 16 * n)
     assert ps.mlp_param_count(10, 32) == 32 * 10 + 32 + 32 * 32 + 32 + 96 + 3
     bad = ps.grid_desc((1, 64, 64), (0, 0, 0), (1, 1, 1))
     with pytest.raises(ps.LibraryError, match="shape"):

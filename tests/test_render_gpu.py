@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 import torch
 
+import copy
 import os
 
 import synth
@@ -198,6 +199,93 @@ def test_launch_occupancy():
     scene = ps.Scene.from_host(sc)
     f, b = ps.render_occupancy(scene, ps.render_params(64.0, 32, 0, 3))
     assert f >= 2 and b >= 2, (f, b)
+
+
+# ---------------------------------------------------------------------------
+# Reduced-precision storage and arithmetic
+# ---------------------------------------------------------------------------
+
+RP_RGB_ABS = 2e-3      # reduced precision: |rgb - ref| <= 2e-3 (absolute)
+RP_GRAD_RTOL = 2e-2    # reduced precision: per tensor max|g - g_ref| <= 2e-2 max|g_ref|
+
+
+def stored_values(sc, feat_bf16=False, probe_f16=False):
+    """The scene with features / probes rounded to their storage precision:
+    the values the kernels read, given to the oracle."""
+    out = copy.copy(sc)
+    if feat_bf16:
+        out.feat = torch.as_tensor(sc.feat).bfloat16().float().numpy()
+    if probe_f16:
+        out.probes = sc.probes.astype(np.float16).astype(np.float32)
+    return out
+
+
+def psnr(a, b):
+    mse = float(np.mean((np.asarray(a, np.float64) - np.asarray(b, np.float64)) ** 2))
+    return float("inf") if mse == 0 else 10.0 * np.log10(1.0 / mse)
+
+
+def test_reduced_precision_human_shape():
+    """BF16 features, FP16 probes, FP16 MLP on the tensor cores (FP32 accumulation)
+    on a human-capture shaped scene, against the FP64 oracle of the stored values."""
+    sc = synth.make_scene("human384", dims=(48, 96, 48), probe_dims=(6, 12, 6))
+    rays = synth.make_rays("human384", n_rays=1024)
+    ref_sc = stored_values(sc, feat_bf16=True, probe_f16=True)
+    scene = ps.Scene.from_host(sc, feat_dtype=ps.BF16, probe_dtype=ps.F16, mlp_dtype=ps.F16)
+    params = ps.render_params(64.0, 128, 0, 3)
+    g = gpu_forward(scene, rays.o, rays.d, params)
+    r = oracle_forward(ref_sc, rays.o, rays.d, 64.0, 128)
+    err = float(np.max(np.abs(g["rgb"] - r["rgb"])))
+    assert np.sum(r["wsum"] > 0.5) > 50
+    assert err <= RP_RGB_ABS, err
+    log_errors("reduced precision forward", {"rgb_max_abs": err, "psnr_vs_oracle": psnr(g["rgb"], r["rgb"]),
+                                             "depth_rel": rel_err_elementwise(g["depth"], r["depth"])})
+    keep = clean_rays(ref_sc, rays.o, rays.d, 64.0, 128)[:600]
+    o, d = rays.o[keep], rays.d[keep]
+    n = o.shape[0]
+    drgb = (synth.rng(5).normal(size=(n, 3)) / n).astype(np.float32)
+    gg = gpu_backward(scene, o, d, params, drgb)
+    gr = oracle_backward(ref_sc, o, d, drgb.astype(np.float64), 64.0, 128)
+    errs = {k: rel_err_tensor(gg[k], gr[k]) for k in ("sdf", "feat", "probes", "mlp")}
+    log_errors("reduced precision backward", errs)
+    for k, e in errs.items():
+        assert e <= RP_GRAD_RTOL, (k, e, errs)
+
+
+def test_bf16_features_with_fp32_mlp():
+    """BF16 feature storage with FP32 probes and the FP32-equivalent MLP (the
+    adjoint-stress configuration) meets the FP32 tolerances on the stored values."""
+    g = synth.rng(78)
+    sc = synth.make_scene("sphere64", dims=(30, 30, 30), probe_dims=(5, 5, 5))
+    sc.probes = g.normal(0, 0.1, size=(5, 5, 5, 9, 8)).astype(np.float32)
+    sc.width = 32
+    sc.mlp = synth.mlp_params(3 + 8 + 3, 32, g)
+    rays = synth.make_rays("sphere64", n_rays=600, seed_offset=19)
+    ref_sc = stored_values(sc, feat_bf16=True)
+    scene = ps.Scene.from_host(sc, feat_dtype=ps.BF16)
+    params = ps.render_params(64.0, 96, 0, 3)
+    gf = gpu_forward(scene, rays.o, rays.d, params)
+    rf = oracle_forward(ref_sc, rays.o, rays.d, 64.0, 96)
+    for k in ("rgb", "depth", "wsum"):
+        assert rel_err_elementwise(gf[k], rf[k]) <= RGB_DEPTH_RTOL, k
+    keep = clean_rays(ref_sc, rays.o, rays.d, 64.0, 96)
+    o, d = rays.o[keep], rays.d[keep]
+    n = o.shape[0]
+    drgb = (synth.rng(6).normal(size=(n, 3)) / n).astype(np.float32)
+    gg = gpu_backward(scene, o, d, params, drgb)
+    gr = oracle_backward(ref_sc, o, d, drgb.astype(np.float64), 64.0, 96)
+    for k in ("sdf", "feat", "probes", "mlp"):
+        assert rel_err_tensor(gg[k], gr[k]) <= GRAD_RTOL, k
+
+
+def test_bf16_pack_roundtrip():
+    sc = synth.make_scene("sphere64", dims=(19, 17, 23), probe_dims=(4, 4, 4))
+    scene = ps.Scene.from_host(sc, feat_dtype=ps.BF16)
+    gd, _, _ = scene.descs(3)
+    sdf, feat = ps.unpack_grid(gd, scene.grid)
+    np.testing.assert_array_equal(sdf.cpu().numpy(), sc.sdf)
+    np.testing.assert_array_equal(feat.cpu().numpy(),
+                                  torch.as_tensor(sc.feat).bfloat16().float().numpy())
 
 
 def test_pack_unpack_roundtrip_exact():
