@@ -29,18 +29,40 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fused fwd+bwd samples/s per train step"
 
-WORKLOAD = "object256"
-WORKLOAD_DESC = ("object-capture training step: 256^3 SDF grid (smooth-min union of 32 "
-                 "spheres/superquadrics) + 3 FP32 features/node, probes 32^3 x 9 SH x 4 ch, "
-                 "MLP 10->32->32->3, 49 cameras 1600x1200 on a hemisphere, 2^18 random pixel "
-                 "rays x 256 samples, tau 64, L1 loss")
+# Workloads (synthetic stand-ins shaped like the paper's captures).  The
+# default, object256, is the headline training step.
+WORKLOADS = {
+    "object256": dict(
+        desc=("object-capture training step: 256^3 SDF grid (smooth-min union of 32 "
+              "spheres/superquadrics) + 3 FP32 features/node, probes 32^3 x 9 SH x 4 ch FP32, "
+              "MLP 10->32->32->3 (FP32-equivalent on tensor cores), 49 cameras 1600x1200 on a "
+              "hemisphere, 2^18 random pixel rays x 256 samples, tau 64, L1 loss"),
+        feat="f32", probe="f32", mlp="f32", dtype="f32"),
+    "human384": dict(
+        desc=("human-capture training step in reduced precision: 384x768x384 SDF grid (posed "
+              "15-capsule body) FP32 + 3 BF16 features/node, probes 48x96x48 x 9 SH x 4 ch "
+              "FP16, MLP 10->32->32->3 FP16 on tensor cores with FP32 accumulation, 64 cameras "
+              "2048x2048 on a ring, 2^19 random pixel rays x 256 samples, tau 64, L1 loss"),
+        feat="bf16", probe="f16", mlp="f16", dtype="bf16/f16"),
+    "stress512": dict(
+        desc=("adjoint stress: 512^3 SDF grid FP32 + 3 BF16 features/node, probes 64^3 x 9 SH "
+              "x 8 ch FP32, MLP 14->32->32->3 FP32-equivalent, 2^20 rays x 512 samples"),
+        feat="bf16", probe="f32", mlp="f32", dtype="f32/bf16"),
+    "sphere64": dict(
+        desc=("small configuration: 64^3 sphere + N(0,0.01) SDF, 3 FP32 features, probes "
+              "16^3 x 9 x 4, MLP 10->16->16->3, 4096 rays x 128 samples"),
+        feat="f32", probe="f32", mlp="f32", dtype="f32"),
+}
 
-# Algorithmic bytes per sample (one trilinear cell gather of the 16-byte node
-# records, gradients read-modify-written in FP32): forward 8 x 16 B; adjoint
-# 8 x 16 B recompute + 2 x 8 x 16 B gradient read-modify-write.
-BYTES_FWD = 128
-BYTES_BWD = 384
-BYTES_STEP = BYTES_FWD + BYTES_BWD
+
+def bytes_per_sample(feat):
+    """Algorithmic bytes per sample: one trilinear cell gather (8 nodes of
+    4 B SDF + 3 features at storage precision) per pass; the adjoint recomputes
+    it and read-modify-writes 8 FP32 gradient records {sdf, f0, f1, f2}."""
+    b_node = 4 + 3 * (2 if feat == "bf16" else 4)
+    fwd = 8 * b_node
+    bwd = 8 * b_node + 2 * 8 * 16
+    return fwd, bwd
 
 
 def parse():
@@ -49,7 +71,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--rays", type=int, default=1 << 18)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="object256")
+    ap.add_argument("--rays", type=int, default=0, help="rays per step (0 = the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rays", type=int, default=0, help="rays of the oracle sample (0 = auto)")
     return ap.parse_args()
@@ -187,9 +210,10 @@ def run_reference(args, world, rank):
     import synth
     if rank != 0:
         return
-    sc = synth.make_scene(WORKLOAD)
-    rays = synth.make_rays(WORKLOAD, n_rays=args.rays)
-    tau, N = 64.0, 256
+    spec = synth.WORKLOADS[args.workload]
+    sc = synth.make_scene(args.workload)
+    rays = synth.make_rays(args.workload, n_rays=args.rays or None)
+    tau, N = spec["tau"], spec["n_samples"]
     threads = cpu_cores()
     per_step_s = max(2.0, 120.0 / max(1, args.steps + args.warmup))
     n = args.cpu_rays or auto_cpu_rays(sc, rays, tau, N, threads, target_s=per_step_s)
@@ -206,7 +230,8 @@ def run_reference(args, world, rank):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "rays_per_step": n, "samples_per_ray": N},
+        "config": {"workload": WORKLOADS[args.workload]["desc"], "rays_per_step": n,
+                   "samples_per_ray": N},
         "cpu_baseline": {"value": value, "unit": "samples/s", "cores": threads,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
@@ -227,13 +252,25 @@ def run_ours(args, world, rank, local):
 
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
-    sc = synth.make_scene(WORKLOAD)
-    rays = synth.make_rays(WORKLOAD, n_rays=args.rays, seed_offset=rank)
-    tau, N = 64.0, 256
+    wl = WORKLOADS[args.workload]
+    spec = synth.WORKLOADS[args.workload]
+    sc = synth.make_scene(args.workload)
+    rays = synth.make_rays(args.workload, n_rays=args.rays or None, seed_offset=rank)
+    tau, N = spec["tau"], spec["n_samples"]
     n = rays.o.shape[0]
     samples = n * N
-    scene = ps.Scene.from_host(sc, device=device)
+    dt = {"f32": ps.F32, "bf16": ps.BF16, "f16": ps.F16}
+    scene = ps.Scene.from_host(sc, device=device, feat_dtype=dt[wl["feat"]],
+                               probe_dtype=dt[wl["probe"]], mlp_dtype=dt[wl["mlp"]])
+    masters = None
+    if scene.feat_dtype != ps.F32 or scene.probe_dtype != ps.F32:
+        gd32 = ps.grid_desc(sc.dims, sc.box_min, sc.box_max, 3, ps.F32)
+        masters = (ps.pack_grid(gd32, torch.as_tensor(sc.sdf, device=device),
+                                torch.as_tensor(sc.feat, device=device)),
+                   torch.as_tensor(sc.probes, device=device).contiguous())
     params = ps.render_params(tau, N, ps.DIR_REFLECT, sc.n_fresnel)
+    BYTES_FWD, BYTES_BWD = bytes_per_sample(wl["feat"])
+    BYTES_STEP = BYTES_FWD + BYTES_BWD
     o = torch.as_tensor(rays.o, device=device)
     d = torch.as_tensor(rays.d, device=device)
     tgt = torch.as_tensor(rays.target, device=device)
@@ -293,17 +330,17 @@ def run_ours(args, world, rank, local):
     h_o = torch.as_tensor(rays.o).pin_memory()
     h_d = torch.as_tensor(rays.d).pin_memory()
     h_t = torch.as_tensor(rays.target).pin_memory()
-    scene.grid.requires_grad_(True)
-    scene.probes.requires_grad_(True)
-    scene.mlp.requires_grad_(True)
+    diff = [scene.mlp] + (list(masters) if masters else [scene.grid, scene.probes])
+    for p in diff:
+        p.requires_grad_(True)
 
     def e2e_step():
-        for p in (scene.grid, scene.probes, scene.mlp):
+        for p in diff:
             p.grad = None
         o_ = h_o.to(device, non_blocking=True)
         d_ = h_d.to(device, non_blocking=True)
         t_ = h_t.to(device, non_blocking=True)
-        rgb, _, _ = ps.render(scene, o_, d_, params)
+        rgb, _, _ = ps.render(scene, o_, d_, params, masters=masters)
         loss = (rgb - t_).abs().mean()
         loss.backward()
         return float(loss.item())
@@ -317,7 +354,8 @@ def run_ours(args, world, rank, local):
         e2e_step()
     torch.cuda.synchronize(device)
     e2e_s = reduce_max(time.perf_counter() - t0, world, device)
-    scene.grid.requires_grad_(False)
+    for p in diff:
+        p.requires_grad_(False)
 
     if rank != 0:
         return
@@ -330,13 +368,12 @@ def run_ours(args, world, rank, local):
     out = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": wl["dtype"],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "rays_per_gpu": n, "samples_per_ray": N,
-                   "grid": "256^3 x 16 B packed nodes (268 MB)", "probes": "32^3 x 9 x 4 FP32",
-                   "mlp": "10->32->32->3 FP32",
-                   "l2": "inputs larger than L2: packed grid 268 MB + gradient grid 268 MB "
-                         "vs 126 MB L2; no explicit flush",
+        "config": {"workload": wl["desc"], "name": args.workload, "rays_per_gpu": n,
+                   "samples_per_ray": N,
+                   "l2": f"inputs larger than L2: grid {scene.grid.numel() * scene.grid.element_size() / 1e6:.0f} MB "
+                         f"+ gradient grid {sc.sdf.size * 16 / 1e6:.0f} MB vs 126 MB L2; no explicit flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": "render_backward_kernel",
                      "achieved": bwd_gbs, "peak": peak, "unit": "GB/s",
