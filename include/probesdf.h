@@ -203,6 +203,62 @@ psdf_status psdf_render_occupancy(const psdf_grid* grid, const psdf_probes* prob
                                   const psdf_mlp* mlp, const psdf_render_params* params,
                                   int32_t* forward_ctas_per_sm, int32_t* backward_ctas_per_sm);
 
+/* ---------------------------------------------------------------------------
+ * Learned sample proposal.  The paper has no counterpart: it marches its
+ * sparse grid.  A per-ray MLP [(o - box centre) / box extent, d, coarse
+ * occupancy at the centres of B equal bins of [t_n, t_f]] -> W -> W -> B
+ * (ReLU hidden layers, softmax) predicts how the render's weight is spread
+ * over the bins; the density p' = (1 - mix) p + mix / B (uniform when
+ * max p' < theta) is inverted at the quantiles k / n_out, k = 0..n_out, to
+ * give t_samples for psdf_render_forward.  Compiled shape: B = 8, W = 32
+ * (1800 parameters).  Parameters are FP32, packed W1[W][6+B] b1 W2[W][W] b2
+ * W3[B][W] b3[B].
+ * ------------------------------------------------------------------------- */
+
+typedef struct psdf_proposal_desc {
+    int32_t occ_res[3];  /* occupancy cells along x, y, z over the grid's box; each >= 2 */
+    int32_t n_bins;      /* B; 8 is compiled in */
+    int32_t width;       /* W; 32 is compiled in */
+    float mix;           /* in [0, 1) */
+    float theta;         /* uniform fallback threshold on max p' */
+} psdf_proposal_desc;
+
+psdf_status psdf_proposal_param_count(const psdf_proposal_desc* desc, int64_t* count);
+
+/* Coarse occupancy of the grid's SDF: cell c of occ_res cells along an axis
+ * covers the nodes floor(c (R-1)/res) .. ceil((c+1)(R-1)/res); occ = 1 where
+ * the smallest |sdf| over them is below `threshold` (world units), else 0.
+ *   occ : device FP32 [res_z][res_y][res_x] */
+psdf_status psdf_occupancy_build(const psdf_grid* grid, const int32_t occ_res[3],
+                                 float threshold, float* occ, void* stream);
+
+/* Per-bin sums of the weights w_k of a uniform march with params->n_samples
+ * samples (SDF only, Eqs. 8-10): hist [n_rays][n_bins] (device FP32);
+ * n_samples must be a multiple of n_bins, n_bins <= 32. */
+psdf_status psdf_weight_histogram(const psdf_grid* grid, const psdf_render_params* params,
+                                  const float* rays_o, const float* rays_d, int64_t n_rays,
+                                  int32_t n_bins, float* hist, void* stream);
+
+/* Proposal forward and sample placement:
+ *   params    : device FP32 [psdf_proposal_param_count]
+ *   occ       : device FP32 occupancy of psdf_occupancy_build
+ *   t_samples : device FP32 [n_rays][n_out + 1] (rays missing the box get zeros)
+ *   probs     : device FP32 [n_rays][B] mixed density p', or NULL */
+psdf_status psdf_proposal_forward(const psdf_grid* grid, const psdf_proposal_desc* desc,
+                                  const float* params, const float* occ, const float* rays_o,
+                                  const float* rays_d, int64_t n_rays, int32_t n_out,
+                                  float* t_samples, float* probs, void* stream);
+
+/* Training signal: for rays whose target mass sum(hist) >= min_mass, the
+ * cross-entropy of hist / sum(hist) against the proposal's softmax; the
+ * gradient of scale * sum_rays loss is ACCUMULATED into grad_params (device
+ * FP32); loss (device FP32 [n_rays], 0 for skipped rays) may be NULL. */
+psdf_status psdf_proposal_backward(const psdf_grid* grid, const psdf_proposal_desc* desc,
+                                   const float* params, const float* occ, const float* rays_o,
+                                   const float* rays_d, int64_t n_rays, const float* hist,
+                                   float min_mass, float scale, float* grad_params, float* loss,
+                                   void* stream);
+
 #ifdef __cplusplus
 }
 #endif

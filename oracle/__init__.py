@@ -73,6 +73,18 @@ class _Params(ctypes.Structure):
     ]
 
 
+class _Proposal(ctypes.Structure):
+    _fields_ = [
+        ("occ_res", ctypes.c_int32 * 3),
+        ("occ", ctypes.c_void_p),
+        ("width", ctypes.c_int32),
+        ("n_bins", ctypes.c_int32),
+        ("params", ctypes.c_void_p),
+        ("mix", ctypes.c_double),
+        ("theta", ctypes.c_double),
+    ]
+
+
 def _load():
     global _lib
     with _lock:
@@ -91,6 +103,17 @@ def _load():
             lib.orc_render_trace.restype = ctypes.c_int32
             lib.orc_point_eval.argtypes = [P, P, P, P, ctypes.c_float, P, P, P, P]
             lib.orc_point_eval.restype = ctypes.c_int32
+            lib.orc_occupancy.argtypes = [P, P, ctypes.c_double, P]
+            lib.orc_occupancy.restype = ctypes.c_int32
+            lib.orc_proposal_forward.argtypes = [P, P, ctypes.c_int64, P, P, ctypes.c_int32, P,
+                                                 P, P, P]
+            lib.orc_proposal_forward.restype = ctypes.c_int32
+            lib.orc_weight_histogram.argtypes = [P, P, ctypes.c_int64, P, P, ctypes.c_int32, P,
+                                                 ctypes.c_int32]
+            lib.orc_weight_histogram.restype = ctypes.c_int32
+            lib.orc_proposal_backward.argtypes = [P, P, ctypes.c_int64, P, P, P, ctypes.c_double,
+                                                  ctypes.c_double, P, P]
+            lib.orc_proposal_backward.restype = ctypes.c_int32
             _lib = lib
     return _lib
 
@@ -259,3 +282,89 @@ def sh_grad(l, r):
     dY = np.zeros((l * l, 3))
     lib.orc_sh_grad(int(l), _ptr(r), _ptr(dY))
     return dY
+
+
+# ----------------------------------------------------------------------------
+# Learned sample proposal (not part of the paper)
+# ----------------------------------------------------------------------------
+
+class Proposal:
+    """Oracle copy of a proposal network: occupancy [rz, ry, rx] and packed
+    parameters W1[W][6+B] b1 W2[W][W] b2 W3[B][W] b3, promoted to FP64."""
+
+    def __init__(self, occ, params, width=32, n_bins=8, mix=0.1, theta=0.2):
+        self.occ = _f64(occ)
+        self.params = _f64(params).ravel()
+        rz, ry, rx = self.occ.shape
+        nin = 6 + n_bins
+        assert self.params.size == width * nin + width + width * width + width + n_bins * width + n_bins
+        s = _Proposal()
+        s.occ_res[:] = (rx, ry, rz)
+        s.occ = self.occ.ctypes.data
+        s.width = int(width)
+        s.n_bins = int(n_bins)
+        s.params = self.params.ctypes.data
+        s.mix = float(mix)
+        s.theta = float(theta)
+        self._s = s
+        self.n_bins = int(n_bins)
+
+
+def occupancy(model: Model, res, threshold):
+    """[rz, ry, rx] in {0, 1}: cells whose covered nodes reach |sdf| < threshold."""
+    lib = _load()
+    rx, ry, rz = (int(v) for v in res)
+    out = np.zeros((rz, ry, rx))
+    r = (ctypes.c_int32 * 3)(rx, ry, rz)
+    st = lib.orc_occupancy(ctypes.byref(model._s), r, float(threshold), _ptr(out))
+    if st != 0:
+        raise ValueError("oracle occupancy rejected its arguments")
+    return out
+
+
+def proposal_forward(model: Model, prop: Proposal, rays_o, rays_d, n_out):
+    """logits [n, B], mixed density p' [n, B], t_samples [n, n_out + 1] and
+    margin [n]: the smallest |pre-activation| of a hidden unit per ray."""
+    lib = _load()
+    o, d = _f32(rays_o).reshape(-1, 3), _f32(rays_d).reshape(-1, 3)
+    n = o.shape[0]
+    B = prop.n_bins
+    logits, probs = np.zeros((n, B)), np.zeros((n, B))
+    t = np.zeros((n, n_out + 1))
+    mg = np.zeros(n)
+    st = lib.orc_proposal_forward(ctypes.byref(model._s), ctypes.byref(prop._s), n, _ptr(o),
+                                  _ptr(d), int(n_out), _ptr(logits), _ptr(probs), _ptr(t),
+                                  _ptr(mg))
+    if st != 0:
+        raise ValueError("oracle proposal_forward rejected its arguments")
+    return {"logits": logits, "probs": probs, "t": t, "margin": mg}
+
+
+def weight_histogram(model: Model, rays_o, rays_d, tau, n_samples, n_bins):
+    """[n, n_bins] per-bin sums of the uniform render's weights."""
+    lib = _load()
+    o, d = _f32(rays_o).reshape(-1, 3), _f32(rays_d).reshape(-1, 3)
+    n = o.shape[0]
+    out = np.zeros((n, n_bins))
+    p = _params(tau, n_samples)
+    st = lib.orc_weight_histogram(ctypes.byref(model._s), ctypes.byref(p), n, _ptr(o), _ptr(d),
+                                  int(n_bins), _ptr(out), 1)
+    if st != 0:
+        raise ValueError("oracle weight_histogram rejected its arguments")
+    return out
+
+
+def proposal_backward(model: Model, prop: Proposal, rays_o, rays_d, hist, min_mass, scale):
+    """(gradient of scale * sum loss w.r.t. the parameters, per-ray loss)."""
+    lib = _load()
+    o, d = _f32(rays_o).reshape(-1, 3), _f32(rays_d).reshape(-1, 3)
+    n = o.shape[0]
+    h = _f64(hist).reshape(n, prop.n_bins)
+    g = np.zeros_like(prop.params)
+    loss = np.zeros(n)
+    st = lib.orc_proposal_backward(ctypes.byref(model._s), ctypes.byref(prop._s), n, _ptr(o),
+                                   _ptr(d), _ptr(h), float(min_mass), float(scale), _ptr(g),
+                                   _ptr(loss))
+    if st != 0:
+        raise ValueError("oracle proposal_backward rejected its arguments")
+    return g, loss

@@ -785,3 +785,279 @@ int32_t orc_point_eval(const orc_model* m, const orc_params* p, const float o[3]
     for (int c = 0; c < 3; ++c) C[c] = S.C[c];
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Learned sample proposal.  Not part of the paper: a per-ray MLP predicts  */
+/* how the render's weight is spread over B equal bins of the ray's segment */
+/* in the box, and the samples are placed at quantiles of that density.     */
+/* ------------------------------------------------------------------------ */
+
+/* Coarse occupancy: cell c of res cells along an axis covers the fine nodes
+ * floor(c (R-1) / res) .. ceil((c+1) (R-1) / res); it is occupied (1) when
+ * the smallest |s| over those nodes is below `threshold`. */
+int32_t orc_occupancy(const orc_model* m, const int32_t res[3], double threshold, double* occ)
+{
+    for (int a = 0; a < 3; ++a)
+        if (res[a] < 1) return -2;
+    for (int cz = 0; cz < res[2]; ++cz)
+        for (int cy = 0; cy < res[1]; ++cy)
+            for (int cx = 0; cx < res[0]; ++cx) {
+                const int c[3] = {cx, cy, cz};
+                int lo[3], hi[3];
+                for (int a = 0; a < 3; ++a) {
+                    const int64_t span = (int64_t)(m->R[a] - 1);
+                    lo[a] = (int)((c[a] * span) / res[a]);
+                    hi[a] = (int)(((c[a] + 1) * span + res[a] - 1) / res[a]);
+                    if (hi[a] > m->R[a] - 1) hi[a] = m->R[a] - 1;
+                }
+                double mn = INFINITY;
+                for (int iz = lo[2]; iz <= hi[2]; ++iz)
+                    for (int iy = lo[1]; iy <= hi[1]; ++iy)
+                        for (int ix = lo[0]; ix <= hi[0]; ++ix) {
+                            const double v = fabs(m->sdf[node_index(m->R, ix, iy, iz)]);
+                            if (v < mn) mn = v;
+                        }
+                occ[((size_t)cz * res[1] + cy) * res[0] + cx] = mn < threshold ? 1.0 : 0.0;
+            }
+    return 0;
+}
+
+/* Occupancy at a point: trilinear blend of cell-centred values, clamped to
+ * the outer cell centres. */
+static double occ_sample(const orc_model* m, const orc_proposal* pr, const double x[3])
+{
+    int i[3];
+    double f[3];
+    for (int a = 0; a < 3; ++a) {
+        const int r = pr->occ_res[a];
+        double u = (x[a] - (double)m->bmin[a]) / ((double)m->bmax[a] - (double)m->bmin[a]) * r - 0.5;
+        if (u < 0.0) u = 0.0;
+        if (u > r - 1) u = r - 1;
+        int fl = (int)floor(u);
+        if (fl > r - 2) fl = r - 2;
+        if (fl < 0) fl = 0;
+        i[a] = fl;
+        f[a] = r > 1 ? u - fl : 0.0;
+    }
+    double v = 0.0;
+    for (int c = 0; c < 8; ++c) {
+        const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
+        const int jx = pr->occ_res[0] > 1 ? i[0] + cx : 0;
+        const int jy = pr->occ_res[1] > 1 ? i[1] + cy : 0;
+        const int jz = pr->occ_res[2] > 1 ? i[2] + cz : 0;
+        const double w = (cx ? f[0] : 1 - f[0]) * (cy ? f[1] : 1 - f[1]) * (cz ? f[2] : 1 - f[2]);
+        v += w * pr->occ[((size_t)jz * pr->occ_res[1] + jy) * pr->occ_res[0] + jx];
+    }
+    return v;
+}
+
+typedef struct {
+    int hit;
+    float tn, tf;
+    double x[ORC_MAX_IN], z1[ORC_MAX_W], h1[ORC_MAX_W], z2[ORC_MAX_W], h2[ORC_MAX_W];
+    double logit[ORC_MAX_IN], p[ORC_MAX_IN];
+} prop_state;
+
+/* Proposal MLP input [(o - centre)/extent, d, occupancy at the B bin centres]
+ * -> W -> W -> B logits (ReLU hidden layers), softmax. */
+static void proposal_eval(const orc_model* m, const orc_proposal* pr, const float* o,
+                          const float* d, prop_state* st)
+{
+    const int B = pr->n_bins, W = pr->width, nin = 6 + B;
+    st->hit = ray_box_f32(o, d, m->bmin, m->bmax, &st->tn, &st->tf);
+    for (int a = 0; a < 3; ++a) {
+        const double c = 0.5 * ((double)m->bmin[a] + (double)m->bmax[a]);
+        const double e = (double)m->bmax[a] - (double)m->bmin[a];
+        st->x[a] = ((double)o[a] - c) / e;
+        st->x[3 + a] = (double)d[a];
+    }
+    for (int b = 0; b < B; ++b) {
+        double occ = 0.0;
+        if (st->hit) {
+            const double tb = (double)st->tn + (b + 0.5) * ((double)st->tf - (double)st->tn) / B;
+            double xw[3];
+            for (int a = 0; a < 3; ++a) xw[a] = (double)o[a] + tb * (double)d[a];
+            occ = occ_sample(m, pr, xw);
+        }
+        st->x[6 + b] = occ;
+    }
+    const double* W1 = pr->params;
+    const double* b1 = W1 + W * nin;
+    const double* W2 = b1 + W;
+    const double* b2 = W2 + W * W;
+    const double* W3 = b2 + W;
+    const double* b3 = W3 + B * W;
+    for (int u = 0; u < W; ++u) {
+        double z = b1[u];
+        for (int i = 0; i < nin; ++i) z += W1[u * nin + i] * st->x[i];
+        st->z1[u] = z;
+        st->h1[u] = relu(z);
+    }
+    for (int u = 0; u < W; ++u) {
+        double z = b2[u];
+        for (int i = 0; i < W; ++i) z += W2[u * W + i] * st->h1[i];
+        st->z2[u] = z;
+        st->h2[u] = relu(z);
+    }
+    double mx = -INFINITY;
+    for (int b = 0; b < B; ++b) {
+        double z = b3[b];
+        for (int i = 0; i < W; ++i) z += W3[b * W + i] * st->h2[i];
+        st->logit[b] = z;
+        if (z > mx) mx = z;
+    }
+    double sum = 0.0;
+    for (int b = 0; b < B; ++b) {
+        st->p[b] = exp(st->logit[b] - mx);
+        sum += st->p[b];
+    }
+    for (int b = 0; b < B; ++b) st->p[b] /= sum;
+}
+
+int32_t orc_proposal_forward(const orc_model* m, const orc_proposal* pr, int64_t n_rays,
+                             const float* rays_o, const float* rays_d, int32_t n_out,
+                             double* logits, double* probs, double* t_samples, double* margin)
+{
+    const int B = pr->n_bins;
+    if (B < 1 || B > ORC_MAX_IN - 6 || pr->width < 1 || pr->width > ORC_MAX_W || n_out < 1)
+        return -2;
+    prop_state st;
+    for (int64_t r = 0; r < n_rays; ++r) {
+        proposal_eval(m, pr, rays_o + 3 * r, rays_d + 3 * r, &st);
+        if (margin) {
+            /* smallest |pre-activation| of a hidden unit: how far the ray is
+             * from a ReLU kink, where FP32 and FP64 may switch a unit apart */
+            double mg = INFINITY;
+            for (int u = 0; u < pr->width; ++u) {
+                if (fabs(st.z1[u]) < mg) mg = fabs(st.z1[u]);
+                if (fabs(st.z2[u]) < mg) mg = fabs(st.z2[u]);
+            }
+            margin[r] = mg;
+        }
+        /* mixed density p' = (1 - mix) p + mix / B, uniform if its peak is below theta */
+        double q[ORC_MAX_IN], qmax = 0.0;
+        for (int b = 0; b < B; ++b) {
+            q[b] = (1.0 - pr->mix) * st.p[b] + pr->mix / B;
+            if (q[b] > qmax) qmax = q[b];
+        }
+        if (qmax < pr->theta)
+            for (int b = 0; b < B; ++b) q[b] = 1.0 / B;
+        for (int b = 0; b < B; ++b) {
+            if (logits) logits[r * B + b] = st.logit[b];
+            if (probs) probs[r * B + b] = q[b];
+        }
+        if (!t_samples) continue;
+        double* t = t_samples + r * (n_out + 1);
+        if (!st.hit) {
+            for (int k = 0; k <= n_out; ++k) t[k] = 0.0;
+            continue;
+        }
+        /* samples at the quantiles k / n_out of the piecewise-constant density */
+        const double tn = st.tn, tf = st.tf, db = (tf - tn) / B;
+        for (int k = 0; k <= n_out; ++k) {
+            const double u = (double)k / n_out;
+            double c = 0.0;
+            int b = 0;
+            while (b < B - 1 && c + q[b] <= u) {
+                c += q[b];
+                ++b;
+            }
+            double frac = (u - c) / q[b];
+            if (frac > 1.0) frac = 1.0;
+            t[k] = tn + (b + frac) * db;
+        }
+        t[0] = tn;
+        t[n_out] = tf;
+    }
+    return 0;
+}
+
+/* Per-bin sums of the uniform render's weights w_k (the proposal's target). */
+int32_t orc_weight_histogram(const orc_model* m, const orc_params* p, int64_t n_rays,
+                             const float* rays_o, const float* rays_d, int32_t n_bins,
+                             double* hist, int32_t n_threads)
+{
+    (void)n_threads;
+    const int err = check_model(m, p);
+    if (err) return err;
+    const int N = p->n_samples;
+    if (n_bins < 1 || N % n_bins) return -2;
+    ray_work rw;
+    alloc_work(p, &rw);
+    for (int64_t r = 0; r < n_rays; ++r) {
+        double rgb[3], depth, wsum, logT;
+        const int hit = forward_ray(m, p, rays_o + 3 * r, rays_d + 3 * r, NULL, &rw, rgb, &depth,
+                                    &wsum, &logT, NULL);
+        for (int b = 0; b < n_bins; ++b) hist[r * n_bins + b] = 0.0;
+        if (!hit) continue;
+        for (int k = 0; k < N; ++k) hist[r * n_bins + k / (N / n_bins)] += rw.w[k];
+    }
+    free_work(&rw);
+    return 0;
+}
+
+/* Cross-entropy of the target bins hist / sum(hist) against the proposal's
+ * softmax, for rays whose target mass is at least min_mass; gradients of
+ * scale * sum_r loss_r with respect to the proposal parameters. */
+int32_t orc_proposal_backward(const orc_model* m, const orc_proposal* pr, int64_t n_rays,
+                              const float* rays_o, const float* rays_d, const double* hist,
+                              double min_mass, double scale, double* g_params, double* loss)
+{
+    const int B = pr->n_bins, W = pr->width, nin = 6 + B;
+    const double* W1 = pr->params;
+    const double* b1 = W1 + W * nin;
+    const double* W2 = b1 + W;
+    const double* b2 = W2 + W * W;
+    const double* W3 = b2 + W;
+    (void)b1;
+    (void)b2;
+    double* gW1 = g_params;
+    double* gb1 = gW1 + W * nin;
+    double* gW2 = gb1 + W;
+    double* gb2 = gW2 + W * W;
+    double* gW3 = gb2 + W;
+    double* gb3 = gW3 + B * W;
+    prop_state st;
+    for (int64_t r = 0; r < n_rays; ++r) {
+        if (loss) loss[r] = 0.0;
+        double mass = 0.0;
+        for (int b = 0; b < B; ++b) mass += hist[r * B + b];
+        if (!(mass >= min_mass)) continue;
+        proposal_eval(m, pr, rays_o + 3 * r, rays_d + 3 * r, &st);
+        double dl[ORC_MAX_IN], dh2[ORC_MAX_W], dz2[ORC_MAX_W], dh1[ORC_MAX_W], dz1[ORC_MAX_W];
+        double ce = 0.0;
+        for (int b = 0; b < B; ++b) {
+            const double tgt = hist[r * B + b] / mass;
+            ce -= tgt * log(st.p[b]);
+            dl[b] = scale * (st.p[b] - tgt);
+        }
+        if (loss) loss[r] = ce;
+        for (int b = 0; b < B; ++b) {
+            gb3[b] += dl[b];
+            for (int i = 0; i < W; ++i) gW3[b * W + i] += dl[b] * st.h2[i];
+        }
+        for (int i = 0; i < W; ++i) {
+            double a = 0.0;
+            for (int b = 0; b < B; ++b) a += W3[b * W + i] * dl[b];
+            dh2[i] = a;
+            dz2[i] = st.z2[i] > 0.0 ? a : 0.0;
+        }
+        for (int u = 0; u < W; ++u) {
+            gb2[u] += dz2[u];
+            for (int i = 0; i < W; ++i) gW2[u * W + i] += dz2[u] * st.h1[i];
+        }
+        for (int i = 0; i < W; ++i) {
+            double a = 0.0;
+            for (int u = 0; u < W; ++u) a += W2[u * W + i] * dz2[u];
+            dh1[i] = a;
+            dz1[i] = st.z1[i] > 0.0 ? a : 0.0;
+        }
+        for (int u = 0; u < W; ++u) {
+            gb1[u] += dz1[u];
+            for (int i = 0; i < nin; ++i) gW1[u * nin + i] += dz1[u] * st.x[i];
+        }
+        (void)dh1;
+        (void)dh2;
+    }
+    return 0;
+}

@@ -63,4 +63,28 @@ int32_t orc_point_eval(const orc_model* m, const orc_params* p, const float o[3]
                        const float d[3], float t, double* s, double g[3], double* mlp_in,
                        double C[3]);
 
+/* ---- Learned sample proposal (not in the paper: places the render's
+ * samples where a small per-ray MLP expects the surface) ---- */
+
+typedef struct orc_proposal {
+    int32_t occ_res[3];     /* coarse occupancy cells along x, y, z (over the grid box) */
+    const double* occ;      /* [res_z][res_y][res_x] in {0, 1} */
+    int32_t width;          /* hidden width */
+    int32_t n_bins;         /* bins of [t_n, t_f] */
+    const double* params;   /* W1[W][6+B] b1[W] W2[W][W] b2[W] W3[B][W] b3[B] */
+    double mix;             /* p' = (1 - mix) softmax + mix / B */
+    double theta;           /* uniform fallback if max p' < theta */
+} orc_proposal;
+
+int32_t orc_occupancy(const orc_model* m, const int32_t res[3], double threshold, double* occ);
+int32_t orc_proposal_forward(const orc_model* m, const orc_proposal* pr, int64_t n_rays,
+                             const float* rays_o, const float* rays_d, int32_t n_out,
+                             double* logits, double* probs, double* t_samples, double* margin);
+int32_t orc_weight_histogram(const orc_model* m, const orc_params* p, int64_t n_rays,
+                             const float* rays_o, const float* rays_d, int32_t n_bins,
+                             double* hist, int32_t n_threads);
+int32_t orc_proposal_backward(const orc_model* m, const orc_proposal* pr, int64_t n_rays,
+                              const float* rays_o, const float* rays_d, const double* hist,
+                              double min_mass, double scale, double* g_params, double* loss);
+
 #endif

@@ -22,6 +22,8 @@ __all__ = [
     "GridDesc", "ProbeDesc", "MlpDesc", "RenderParams", "Scene", "LibraryError",
     "library", "grid_bytes", "mlp_param_count", "pack_grid", "unpack_grid", "BF16", "F16", "F32",
     "render_forward", "render_backward", "render", "device_status", "DIR_REFLECT", "DIR_VIEW",
+    "ProposalDesc", "proposal_desc", "proposal_param_count", "occupancy_build",
+    "weight_histogram", "proposal_forward", "proposal_backward",
 ]
 
 DIR_REFLECT = 0
@@ -56,6 +58,11 @@ class RenderParams(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_float), ("n_samples", ctypes.c_int32),
                 ("dir_mode", ctypes.c_int32), ("n_fresnel", ctypes.c_int32),
                 ("bg", ctypes.c_float * 3)]
+
+
+class ProposalDesc(ctypes.Structure):
+    _fields_ = [("occ_res", ctypes.c_int32 * 3), ("n_bins", ctypes.c_int32),
+                ("width", ctypes.c_int32), ("mix", ctypes.c_float), ("theta", ctypes.c_float)]
 
 
 _lock = threading.Lock()
@@ -97,9 +104,19 @@ def library() -> ctypes.CDLL:
                                              _P, _P, _P, _P, _P, _P, _P, _P]
         lib.psdf_render_occupancy.argtypes = [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_int32),
                                               ctypes.POINTER(ctypes.c_int32)]
+        lib.psdf_proposal_param_count.argtypes = [_P, ctypes.POINTER(ctypes.c_int64)]
+        lib.psdf_occupancy_build.argtypes = [_P, _P, ctypes.c_float, _P, _P]
+        lib.psdf_weight_histogram.argtypes = [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32,
+                                              _P, _P]
+        lib.psdf_proposal_forward.argtypes = [_P, _P, _P, _P, _P, _P, ctypes.c_int64,
+                                              ctypes.c_int32, _P, _P, _P]
+        lib.psdf_proposal_backward.argtypes = [_P, _P, _P, _P, _P, _P, ctypes.c_int64, _P,
+                                               ctypes.c_float, ctypes.c_float, _P, _P, _P]
         for name in ("psdf_grid_bytes", "psdf_grid_create", "psdf_grid_pack", "psdf_grid_unpack",
                      "psdf_probes_create", "psdf_mlp_param_count", "psdf_mlp_create",
-                     "psdf_render_forward", "psdf_render_backward", "psdf_render_occupancy"):
+                     "psdf_render_forward", "psdf_render_backward", "psdf_render_occupancy",
+                     "psdf_proposal_param_count", "psdf_occupancy_build", "psdf_weight_histogram",
+                     "psdf_proposal_forward", "psdf_proposal_backward"):
             getattr(lib, name).restype = ctypes.c_int32
         _lib = lib
         return lib
@@ -408,3 +425,95 @@ def render(scene: Scene, rays_o, rays_d, params: RenderParams, t_samples=None, m
     grid_p, probes_p = (scene.grid, scene.probes) if masters is None else masters
     return RenderFunction.apply(grid_p, probes_p, scene.mlp, rays_o, rays_d, t_samples, scene,
                                 params)
+
+
+# ---------------------------------------------------------------------------
+# Learned sample proposal (the paper marches its sparse grid instead)
+# ---------------------------------------------------------------------------
+
+def proposal_desc(occ_res=(32, 32, 32), n_bins=8, width=32, mix=0.1, theta=0.2) -> ProposalDesc:
+    d = ProposalDesc()
+    d.occ_res[:] = tuple(int(v) for v in occ_res)
+    d.n_bins = int(n_bins)
+    d.width = int(width)
+    d.mix = float(mix)
+    d.theta = float(theta)
+    return d
+
+
+def proposal_param_count(desc: ProposalDesc) -> int:
+    n = ctypes.c_int64()
+    _check(library().psdf_proposal_param_count(ctypes.byref(desc), ctypes.byref(n)),
+           "psdf_proposal_param_count")
+    return n.value
+
+
+class _GridHandle:
+    def __init__(self, scene: Scene):
+        gd, _, _ = scene.descs(3)
+        self.h = _P()
+        _check(library().psdf_grid_create(ctypes.byref(gd), _ptr(scene.grid),
+                                          ctypes.byref(self.h)), "psdf_grid_create")
+
+    def __enter__(self):
+        return self.h
+
+    def __exit__(self, *exc):
+        library().psdf_grid_destroy(self.h)
+
+
+def occupancy_build(scene: Scene, occ_res, threshold: float) -> torch.Tensor:
+    """[res_z, res_y, res_x] FP32 in {0, 1}: cells near the zero level set."""
+    rx, ry, rz = (int(v) for v in occ_res)
+    occ = torch.empty((rz, ry, rx), dtype=torch.float32, device=scene.grid.device)
+    res = (ctypes.c_int32 * 3)(rx, ry, rz)
+    with _GridHandle(scene) as g:
+        _check(library().psdf_occupancy_build(g, res, float(threshold), _ptr(occ), _stream()),
+               "psdf_occupancy_build")
+    return occ
+
+
+def weight_histogram(scene: Scene, rays_o, rays_d, params: RenderParams, n_bins=8):
+    """[n, n_bins] per-bin sums of the uniform march's weights (SDF only)."""
+    _require_cuda(rays_o, rays_d)
+    n = rays_o.shape[0]
+    hist = torch.empty((n, n_bins), dtype=torch.float32, device=rays_o.device)
+    with _GridHandle(scene) as g:
+        _check(library().psdf_weight_histogram(g, ctypes.byref(params), _ptr(rays_o),
+                                               _ptr(rays_d), n, int(n_bins), _ptr(hist),
+                                               _stream()), "psdf_weight_histogram")
+    return hist
+
+
+def proposal_forward(scene: Scene, desc: ProposalDesc, params, occ, rays_o, rays_d, n_out,
+                     want_probs=True):
+    """(t_samples [n, n_out + 1], mixed density p' [n, B] or None)."""
+    _require_cuda(params, occ, rays_o, rays_d)
+    n = rays_o.shape[0]
+    t = torch.empty((n, n_out + 1), dtype=torch.float32, device=rays_o.device)
+    probs = (torch.empty((n, desc.n_bins), dtype=torch.float32, device=rays_o.device)
+             if want_probs else None)
+    with _GridHandle(scene) as g:
+        _check(library().psdf_proposal_forward(g, ctypes.byref(desc), _ptr(params), _ptr(occ),
+                                               _ptr(rays_o), _ptr(rays_d), n, int(n_out),
+                                               _ptr(t), _ptr(probs), _stream()),
+               "psdf_proposal_forward")
+    return t, probs
+
+
+def proposal_backward(scene: Scene, desc: ProposalDesc, params, occ, rays_o, rays_d, hist,
+                      min_mass=1e-3, scale=1.0, grad=None, want_loss=True):
+    """(grad [param count] with the gradient of scale * sum(loss) ADDED,
+    per-ray cross-entropy loss [n] or None)."""
+    _require_cuda(params, occ, rays_o, rays_d, hist, grad)
+    n = rays_o.shape[0]
+    if grad is None:
+        grad = torch.zeros_like(params)
+    loss = torch.empty(n, dtype=torch.float32, device=rays_o.device) if want_loss else None
+    with _GridHandle(scene) as g:
+        _check(library().psdf_proposal_backward(g, ctypes.byref(desc), _ptr(params), _ptr(occ),
+                                                _ptr(rays_o), _ptr(rays_d), n, _ptr(hist),
+                                                float(min_mass), float(scale), _ptr(grad),
+                                                _ptr(loss), _stream()),
+               "psdf_proposal_backward")
+    return grad, loss

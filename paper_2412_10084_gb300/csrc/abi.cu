@@ -8,6 +8,7 @@
 
 #include "internal.h"
 #include "probesdf.h"
+#include "proposal.h"
 
 struct psdf_grid {
     psdf_grid_desc desc;
@@ -539,6 +540,162 @@ psdf_status psdf_render_occupancy(const psdf_grid* grid, const psdf_probes* prob
     *forward_ctas_per_sm = f;
     *backward_ctas_per_sm = b;
     return PSDF_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Learned sample proposal
+// ---------------------------------------------------------------------------
+
+namespace {
+
+psdf_status check_proposal_desc(const psdf_proposal_desc* d)
+{
+    if (!d) return PSDF_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (d->occ_res[a] < 2 || d->occ_res[a] > 1024) return PSDF_ERR_BAD_SHAPE;
+    if (d->n_bins != psdf::proposal_bins() || d->width != psdf::proposal_width())
+        return PSDF_ERR_UNSUPPORTED;
+    if (!(d->mix >= 0.0f && d->mix < 1.0f) || !(d->theta >= 0.0f)) return PSDF_ERR_INVALID_ARG;
+    return PSDF_OK;
+}
+
+psdf_status grid_view(const psdf_grid* grid, psdf::GridView& g)
+{
+    if (!grid || !grid->values) return PSDF_ERR_INVALID_ARG;
+    const psdf_grid_desc& gd = grid->desc;
+    std::memset(&g, 0, sizeof(g));
+    if (gd.feat_dtype == PSDF_BF16) {
+        const uint8_t* base = static_cast<const uint8_t*>(grid->values);
+        g.sdf = reinterpret_cast<const float*>(base);
+        g.feat16 = reinterpret_cast<const uint2*>(base + bf16_feat_offset(&gd));
+    } else {
+        g.nodes = static_cast<const float4*>(grid->values);
+    }
+    for (int a = 0; a < 3; ++a) {
+        g.R[a] = gd.dims[a];
+        g.bmin[a] = gd.box_min[a];
+        g.bmax[a] = gd.box_max[a];
+        const volatile float ext = gd.box_max[a] - gd.box_min[a];
+        g.sc[a] = static_cast<float>(gd.dims[a] - 1) / ext;
+    }
+    return PSDF_OK;
+}
+
+}  // namespace
+
+psdf_status psdf_proposal_param_count(const psdf_proposal_desc* desc, int64_t* count)
+{
+    const psdf_status st = check_proposal_desc(desc);
+    if (st != PSDF_OK) return st;
+    if (!count) return PSDF_ERR_INVALID_ARG;
+    *count = psdf::proposal_param_count();
+    return PSDF_OK;
+}
+
+psdf_status psdf_occupancy_build(const psdf_grid* grid, const int32_t occ_res[3],
+                                 float threshold, float* occ, void* stream)
+{
+    psdf::GridView g;
+    psdf_status st = grid_view(grid, g);
+    if (st != PSDF_OK) return st;
+    if (!occ_res || !occ) return PSDF_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (occ_res[a] < 1 || occ_res[a] > 1024) return PSDF_ERR_BAD_SHAPE;
+    if (!aligned16(occ)) return PSDF_ERR_MISALIGNED;
+    const int res[3] = {occ_res[0], occ_res[1], occ_res[2]};
+    return cuda_status(psdf::launch_occupancy(g, res, threshold, occ,
+                                              static_cast<cudaStream_t>(stream)));
+}
+
+psdf_status psdf_weight_histogram(const psdf_grid* grid, const psdf_render_params* params,
+                                  const float* rays_o, const float* rays_d, int64_t n_rays,
+                                  int32_t n_bins, float* hist, void* stream)
+{
+    if (!params || n_rays < 0) return PSDF_ERR_INVALID_ARG;
+    if (!(params->tau > 0.0f) || params->n_samples < 1 || params->n_samples > 4096)
+        return PSDF_ERR_BAD_SHAPE;
+    if (n_bins < 1 || n_bins > 32 || params->n_samples % n_bins) return PSDF_ERR_BAD_SHAPE;
+    psdf::RenderArgs A;
+    std::memset(&A, 0, sizeof(A));
+    psdf_status st = grid_view(grid, A.grid);
+    if (st != PSDF_OK) return st;
+    if (n_rays > 0 && (!rays_o || !rays_d || !hist)) return PSDF_ERR_INVALID_ARG;
+    if (!aligned16(rays_o) || !aligned16(rays_d) || !aligned16(hist)) return PSDF_ERR_MISALIGNED;
+    if (n_rays == 0) return PSDF_OK;
+    A.tau = params->tau;
+    A.n_samples = params->n_samples;
+    A.rays_o = rays_o;
+    A.rays_d = rays_d;
+    A.n_rays = n_rays;
+    return cuda_status(
+        psdf::launch_histogram(A, n_bins, hist, static_cast<cudaStream_t>(stream)));
+}
+
+namespace {
+
+psdf_status proposal_launch(const psdf_grid* grid, const psdf_proposal_desc* desc,
+                            const float* params, const float* occ, const float* rays_o,
+                            const float* rays_d, int64_t n_rays, psdf::ProposalLaunch& L)
+{
+    psdf_status st = check_proposal_desc(desc);
+    if (st != PSDF_OK) return st;
+    std::memset(&L, 0, sizeof(L));
+    st = grid_view(grid, L.grid);
+    if (st != PSDF_OK) return st;
+    if (!params || !occ || n_rays < 0) return PSDF_ERR_INVALID_ARG;
+    if (n_rays > 0 && (!rays_o || !rays_d)) return PSDF_ERR_INVALID_ARG;
+    if (!aligned16(params) || !aligned16(occ) || !aligned16(rays_o) || !aligned16(rays_d))
+        return PSDF_ERR_MISALIGNED;
+    for (int a = 0; a < 3; ++a) L.occ_res[a] = desc->occ_res[a];
+    L.occ = occ;
+    L.params = params;
+    L.mix = desc->mix;
+    L.theta = desc->theta;
+    L.rays_o = rays_o;
+    L.rays_d = rays_d;
+    L.n_rays = n_rays;
+    return PSDF_OK;
+}
+
+}  // namespace
+
+psdf_status psdf_proposal_forward(const psdf_grid* grid, const psdf_proposal_desc* desc,
+                                  const float* params, const float* occ, const float* rays_o,
+                                  const float* rays_d, int64_t n_rays, int32_t n_out,
+                                  float* t_samples, float* probs, void* stream)
+{
+    psdf::ProposalLaunch L;
+    psdf_status st = proposal_launch(grid, desc, params, occ, rays_o, rays_d, n_rays, L);
+    if (st != PSDF_OK) return st;
+    if (n_out < 1 || n_out > 4096) return PSDF_ERR_BAD_SHAPE;
+    if (n_rays > 0 && !t_samples) return PSDF_ERR_INVALID_ARG;
+    if (!aligned16(t_samples) || !aligned16(probs)) return PSDF_ERR_MISALIGNED;
+    if (n_rays == 0) return PSDF_OK;
+    L.n_out = n_out;
+    L.t_samples = t_samples;
+    L.probs = probs;
+    return cuda_status(psdf::launch_proposal_forward(L, static_cast<cudaStream_t>(stream)));
+}
+
+psdf_status psdf_proposal_backward(const psdf_grid* grid, const psdf_proposal_desc* desc,
+                                   const float* params, const float* occ, const float* rays_o,
+                                   const float* rays_d, int64_t n_rays, const float* hist,
+                                   float min_mass, float scale, float* grad_params, float* loss,
+                                   void* stream)
+{
+    psdf::ProposalLaunch L;
+    psdf_status st = proposal_launch(grid, desc, params, occ, rays_o, rays_d, n_rays, L);
+    if (st != PSDF_OK) return st;
+    if (!grad_params || (n_rays > 0 && !hist)) return PSDF_ERR_INVALID_ARG;
+    if (!aligned16(hist) || !aligned16(grad_params) || !aligned16(loss)) return PSDF_ERR_MISALIGNED;
+    if (n_rays == 0) return PSDF_OK;
+    L.hist = hist;
+    L.min_mass = min_mass;
+    L.scale = scale;
+    L.grad = grad_params;
+    L.loss = loss;
+    return cuda_status(psdf::launch_proposal_backward(L, static_cast<cudaStream_t>(stream)));
 }
 
 }  // extern "C"

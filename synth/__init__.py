@@ -381,3 +381,8 @@ def make_rays(name: str, n_rays: int | None = None, seed_offset: int = 0) -> Ray
 def random_unit_vectors(n, g):
     v = g.normal(size=(n, 3))
     return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def proposal_params(g: np.random.Generator, width: int = 32, n_bins: int = 8) -> np.ndarray:
+    """Xavier-uniform initial parameters of the proposal MLP (6 + B -> W -> W -> B)."""
+    return mlp_params(6 + n_bins, width, g, n_out=n_bins)

@@ -519,3 +519,104 @@ def test_oracle_reproduces_committed_fixture():
         g = gold["grad_" + k]
         np.testing.assert_allclose(now["grad_" + k][g["index"]], g["value"], rtol=1e-10,
                                    atol=1e-15)
+
+
+# ----------------------------------------------------------------------------
+# Learned sample proposal (not in the paper): pins of its oracle
+# ----------------------------------------------------------------------------
+
+def _proposal_fixture(seed=81, logit_scale=1.0):
+    sc = tiny_scene(R=(16, 16, 16), P=(4, 4, 4))
+    m = oracle.Model.from_scene(sc)
+    occ = oracle.occupancy(m, (6, 6, 6), 2.0 / 15)
+    g = synth.rng(seed)
+    params = synth.proposal_params(g).astype(np.float64)
+    params[-8 - 8 * 32:] *= logit_scale
+    return sc, m, occ, params
+
+
+def test_proposal_uniform_density_gives_uniform_quantiles():
+    sc, m, occ, params = _proposal_fixture()
+    params[-8 - 8 * 32:] = 0.0  # W3 = 0, b3 = 0: every logit 0
+    prop = oracle.Proposal(occ, params, mix=0.1, theta=0.0)
+    o, d = rays_into_box(40, 82)
+    out = oracle.proposal_forward(m, prop, o, d, 24)
+    np.testing.assert_allclose(out["probs"], 1.0 / 8, atol=1e-15)
+    for i in range(40):
+        tr = oracle.render_trace(m, o[i], d[i], 10.0, 24)  # uniform sample positions
+        if not tr["hit"]:
+            assert np.all(out["t"][i] == 0)
+            continue
+        tn, tf = float(tr["t"][0]), float(tr["t"][-1])
+        np.testing.assert_allclose(out["t"][i], tn + (tf - tn) * np.arange(25) / 24, atol=1e-12)
+
+
+def test_proposal_quantile_placement_follows_density():
+    sc, m, occ, params = _proposal_fixture(logit_scale=8.0)
+    prop = oracle.Proposal(occ, params, mix=0.1, theta=0.0)
+    o, d = rays_into_box(30, 83)
+    n_out = 400
+    out = oracle.proposal_forward(m, prop, o, d, n_out)
+    for i in range(30):
+        t = out["t"][i]
+        if t[-1] <= t[0]:
+            continue
+        assert np.all(np.diff(t) >= 0)
+        edges = t[0] + (t[-1] - t[0]) * np.arange(9) / 8
+        # fraction of the n_out sample intervals falling in each bin = the density
+        counts = np.histogram(0.5 * (t[1:] + t[:-1]), bins=edges)[0] / n_out
+        np.testing.assert_allclose(counts, out["probs"][i], atol=2.0 / n_out)
+        # the piecewise-linear CDF of the bin density reaches k / n_out at t_k
+        cdf = np.interp(t, edges, np.concatenate([[0.0], np.cumsum(out["probs"][i])]))
+        np.testing.assert_allclose(cdf, np.arange(n_out + 1) / n_out, atol=1e-6)
+        assert abs(out["probs"][i].sum() - 1) < 1e-12 and out["probs"][i].min() >= 0.1 / 8 - 1e-15
+
+
+def test_weight_histogram_sums_to_wsum():
+    sc = tiny_scene(R=(12, 12, 12))
+    m = oracle.Model.from_scene(sc)
+    o, d = rays_into_box(50, 84)
+    h = oracle.weight_histogram(m, o, d, 32.0, 48, 8)
+    fw = oracle.render_forward(m, o, d, 32.0, 48)
+    np.testing.assert_allclose(h.sum(1), fw["wsum"], atol=1e-13)
+    tr = oracle.render_trace(m, o[0], d[0], 32.0, 48)
+    np.testing.assert_allclose(h[0], tr["w"].reshape(8, 6).sum(1), atol=1e-15)
+
+
+def test_occupancy_of_a_sphere_shell():
+    R = (24, 24, 24)
+    X, Y, Z = np.meshgrid(*(np.linspace(0, 1, k) for k in R), indexing="ij")
+    dist = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2)
+    sc = tiny_scene(R=R, sdf=(dist - 0.3).transpose(2, 1, 0))
+    m = oracle.Model.from_scene(sc)
+    thr = 2.0 / 23
+    occ = oracle.occupancy(m, (8, 8, 8), thr)
+    cs = (np.arange(8) + 0.5) / 8
+    CZ, CY, CX = np.meshgrid(cs, cs, cs, indexing="ij")
+    shell = np.abs(np.sqrt((CX - 0.5) ** 2 + (CY - 0.5) ** 2 + (CZ - 0.5) ** 2) - 0.3)
+    half_diag = np.sqrt(3) * (0.5 / 8 + 1.0 / 23)
+    assert np.all(occ[shell < thr - half_diag] == 1)       # cells straddling the shell
+    assert np.all(occ[shell > thr + half_diag] == 0)       # cells far from it
+    assert 0 < occ.mean() < 0.8
+
+
+def test_proposal_gradient_central_differences():
+    sc, m, occ, params = _proposal_fixture(seed=85)
+    o, d = rays_into_box(24, 86)
+    hist = oracle.weight_histogram(m, o, d, 16.0, 32, 8)
+    keep = hist.sum(1) > 1e-3
+    o, d, hist = o[keep], d[keep], hist[keep]
+    prop = oracle.Proposal(occ, params)
+    g, loss = oracle.proposal_backward(m, prop, o, d, hist, 1e-3, 0.5)
+    flat = prop.params
+    h = 1e-6
+    idx = synth.rng(87).choice(flat.size, 300, replace=False)
+    for i in idx:
+        old = flat[i]
+        flat[i] = old + h
+        lp = oracle.proposal_backward(m, prop, o, d, hist, 1e-3, 0.5)[1].sum()
+        flat[i] = old - h
+        lm = oracle.proposal_backward(m, prop, o, d, hist, 1e-3, 0.5)[1].sum()
+        flat[i] = old
+        fd = 0.5 * (lp - lm) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * np.abs(g).max() + 1e-9, (i, fd, g[i])
