@@ -204,33 +204,63 @@ psdf_status psdf_render_occupancy(const psdf_grid* grid, const psdf_probes* prob
                                   int32_t* forward_ctas_per_sm, int32_t* backward_ctas_per_sm);
 
 /* ---------------------------------------------------------------------------
+ * Optimiser.  The paper trains its grids, probes and MLP with Adam (Sec. 3.4);
+ * this is the update of Kingma & Ba (2015, Algorithm 1) with bias correction:
+ *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
+ *   p -= lr * (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps)
+ * (evaluated as lr_t m / (sqrt(v) + eps_t), lr_t and eps_t folded on the host).
+ *   param, grad, m, v : device FP32 [n], m and v zero before step 1
+ *   step              : 1-based update count (>= 1)
+ *   clear_grad        : nonzero to zero grad in the same pass (the render's
+ *                       and the proposal's backward calls accumulate)
+ * Elementwise and in place; the four arrays must not overlap.
+ * ------------------------------------------------------------------------- */
+
+psdf_status psdf_adam_step(float* param, float* grad, float* m, float* v, int64_t n, float lr,
+                           float beta1, float beta2, float eps, int32_t step, int32_t clear_grad,
+                           void* stream);
+
+/* ---------------------------------------------------------------------------
  * Learned sample proposal.  The paper has no counterpart: it marches its
- * sparse grid.  A per-ray MLP [(o - box centre) / box extent, d, coarse
- * occupancy at the centres of B equal bins of [t_n, t_f]] -> W -> W -> B
- * (ReLU hidden layers, softmax) predicts how the render's weight is spread
- * over the bins; the density p' = (1 - mix) p + mix / B (uniform when
- * max p' < theta) is inverted at the quantiles k / n_out, k = 0..n_out, to
- * give t_samples for psdf_render_forward.  Compiled shape: B = 8, W = 32
- * (1800 parameters).  Parameters are FP32, packed W1[W][6+B] b1 W2[W][W] b2
- * W3[B][W] b3[B].
+ * sparse grid.  A per-ray MLP [(o - box centre) / box extent, d, first
+ * occupied position, occupied fraction of each of B equal bins of
+ * [t_n, t_f], B step inputs] -> W -> W -> B (ReLU hidden layers, softmax) predicts how the
+ * render's weight is spread over the bins; the density p' = (1 - mix) p +
+ * mix r, where r puts 1/4 evenly on all bins and 3/4 evenly on the bins that
+ * hold an occupied point or neighbour one that does (r = 1/B when no bin
+ * does), and p' = 1/B when max p' < theta, is inverted at the quantiles k / n_out, k = 0..n_out, to
+ * give t_samples for psdf_render_forward.  The occupancy inputs look up the B n_sub points
+ * t = t_n + (k + 1/2) (t_f - t_n) / (B n_sub), k = 0..B n_sub - 1, in the coarse
+ * occupancy grid (the cell containing each point): bin b's input is the set
+ * share of its n_sub points, the first-position input is (k* + 1/2) / (B n_sub)
+ * for the first set point k* (1 when none is), and B step inputs
+ * clamp(B first - b, 0, 1) give the share of each bin before that point.
+ * Compiled shapes: B = 8 or 16, W = 32.  Parameters are FP32, packed
+ * W1[W][7+2B] b1 W2[W][W] b2 W3[B][W] b3[B].
  * ------------------------------------------------------------------------- */
 
 typedef struct psdf_proposal_desc {
-    int32_t occ_res[3];  /* occupancy cells along x, y, z over the grid's box; each >= 2 */
-    int32_t n_bins;      /* B; 8 is compiled in */
+    int32_t occ_res[3];  /* occupancy cells along x, y, z over the grid's box; each in [2, 64] */
+    int32_t n_bins;      /* B; 8 and 16 are compiled in */
     int32_t width;       /* W; 32 is compiled in */
+    int32_t n_sub;       /* occupancy look-ups per bin, in [1, 32] */
     float mix;           /* in [0, 1) */
     float theta;         /* uniform fallback threshold on max p' */
 } psdf_proposal_desc;
 
 psdf_status psdf_proposal_param_count(const psdf_proposal_desc* desc, int64_t* count);
 
+/* 32-bit words of an occupancy bitmask with occ_res cells (each in [2, 64]). */
+psdf_status psdf_occupancy_words(const int32_t occ_res[3], int64_t* words);
+
 /* Coarse occupancy of the grid's SDF: cell c of occ_res cells along an axis
- * covers the nodes floor(c (R-1)/res) .. ceil((c+1)(R-1)/res); occ = 1 where
- * the smallest |sdf| over them is below `threshold` (world units), else 0.
- *   occ : device FP32 [res_z][res_y][res_x] */
+ * covers the nodes floor(c (R-1)/res) .. ceil((c+1)(R-1)/res); it is set where
+ * the smallest |sdf| over them is below `threshold` (world units).
+ *   occ_bits : device [psdf_occupancy_words] words; cell
+ *              i = (z res_y + y) res_x + x is bit (i & 31) of word i >> 5
+ *              (bits past the last cell are 0). */
 psdf_status psdf_occupancy_build(const psdf_grid* grid, const int32_t occ_res[3],
-                                 float threshold, float* occ, void* stream);
+                                 float threshold, uint32_t* occ_bits, void* stream);
 
 /* Per-bin sums of the weights w_k of a uniform march with params->n_samples
  * samples (SDF only, Eqs. 8-10): hist [n_rays][n_bins] (device FP32);
@@ -241,20 +271,23 @@ psdf_status psdf_weight_histogram(const psdf_grid* grid, const psdf_render_param
 
 /* Proposal forward and sample placement:
  *   params    : device FP32 [psdf_proposal_param_count]
- *   occ       : device FP32 occupancy of psdf_occupancy_build
+ *   occ_bits  : device occupancy bitmask of psdf_occupancy_build for desc->occ_res
  *   t_samples : device FP32 [n_rays][n_out + 1] (rays missing the box get zeros)
  *   probs     : device FP32 [n_rays][B] mixed density p', or NULL */
 psdf_status psdf_proposal_forward(const psdf_grid* grid, const psdf_proposal_desc* desc,
-                                  const float* params, const float* occ, const float* rays_o,
+                                  const float* params, const uint32_t* occ_bits,
+                                  const float* rays_o,
                                   const float* rays_d, int64_t n_rays, int32_t n_out,
                                   float* t_samples, float* probs, void* stream);
 
-/* Training signal: for rays whose target mass sum(hist) >= min_mass, the
- * cross-entropy of hist / sum(hist) against the proposal's softmax; the
- * gradient of scale * sum_rays loss is ACCUMULATED into grad_params (device
- * FP32); loss (device FP32 [n_rays], 0 for skipped rays) may be NULL. */
+/* Training signal: for rays whose weight mass sum(hist) >= min_mass, the
+ * mass-weighted cross-entropy loss = -sum_b hist_b log p_b against the
+ * proposal's softmax p (d loss / d logit_b = mass p_b - hist_b); the gradient
+ * of scale * sum_rays loss is ACCUMULATED into grad_params (device FP32);
+ * loss (device FP32 [n_rays], 0 for skipped rays) may be NULL. */
 psdf_status psdf_proposal_backward(const psdf_grid* grid, const psdf_proposal_desc* desc,
-                                   const float* params, const float* occ, const float* rays_o,
+                                   const float* params, const uint32_t* occ_bits,
+                                   const float* rays_o,
                                    const float* rays_d, int64_t n_rays, const float* hist,
                                    float min_mass, float scale, float* grad_params, float* loss,
                                    void* stream);

@@ -79,6 +79,7 @@ class _Proposal(ctypes.Structure):
         ("occ", ctypes.c_void_p),
         ("width", ctypes.c_int32),
         ("n_bins", ctypes.c_int32),
+        ("n_sub", ctypes.c_int32),
         ("params", ctypes.c_void_p),
         ("mix", ctypes.c_double),
         ("theta", ctypes.c_double),
@@ -290,19 +291,20 @@ def sh_grad(l, r):
 
 class Proposal:
     """Oracle copy of a proposal network: occupancy [rz, ry, rx] and packed
-    parameters W1[W][6+B] b1 W2[W][W] b2 W3[B][W] b3, promoted to FP64."""
+    parameters W1[W][7+2B] b1 W2[W][W] b2 W3[B][W] b3, promoted to FP64."""
 
-    def __init__(self, occ, params, width=32, n_bins=8, mix=0.1, theta=0.2):
+    def __init__(self, occ, params, width=32, n_bins=8, mix=0.1, theta=0.2, n_sub=8):
         self.occ = _f64(occ)
         self.params = _f64(params).ravel()
         rz, ry, rx = self.occ.shape
-        nin = 6 + n_bins
+        nin = 7 + 2 * n_bins
         assert self.params.size == width * nin + width + width * width + width + n_bins * width + n_bins
         s = _Proposal()
         s.occ_res[:] = (rx, ry, rz)
         s.occ = self.occ.ctypes.data
         s.width = int(width)
         s.n_bins = int(n_bins)
+        s.n_sub = int(n_sub)
         s.params = self.params.ctypes.data
         s.mix = float(mix)
         s.theta = float(theta)
@@ -355,7 +357,8 @@ def weight_histogram(model: Model, rays_o, rays_d, tau, n_samples, n_bins):
 
 
 def proposal_backward(model: Model, prop: Proposal, rays_o, rays_d, hist, min_mass, scale):
-    """(gradient of scale * sum loss w.r.t. the parameters, per-ray loss)."""
+    """(gradient of scale * sum loss w.r.t. the parameters, per-ray loss
+    -sum_b hist_b log p_b)."""
     lib = _load()
     o, d = _f32(rays_o).reshape(-1, 3), _f32(rays_d).reshape(-1, 3)
     n = o.shape[0]

@@ -822,33 +822,46 @@ int32_t orc_occupancy(const orc_model* m, const int32_t res[3], double threshold
     return 0;
 }
 
-/* Occupancy at a point: trilinear blend of cell-centred values, clamped to
- * the outer cell centres. */
-static double occ_sample(const orc_model* m, const orc_proposal* pr, const double x[3])
+/* Occupancy features of a ray: the segment [t_n, t_f] is cut into B n_sub
+ * equal sub-intervals whose centres are looked up in the occupancy cell that
+ * contains them.  frac[b] is the occupied share of bin b's n_sub points,
+ * *first the position (j + 1/2) / (B n_sub) of the first occupied point j
+ * (1 when none is) and step[b] = clamp(B *first - b, 0, 1) the share of bin b
+ * that lies before it.  The positions and cell indices decide integers, so they
+ * are computed in FP32 with the roundings the kernel uses (FP contraction off,
+ * fmaf a fused multiply-add). */
+static void ray_occupancy(const orc_model* m, const orc_proposal* pr, const float o[3],
+                          const float d[3], float tn, float tf, double* frac, double* first,
+                          double* step)
 {
-    int i[3];
-    double f[3];
-    for (int a = 0; a < 3; ++a) {
-        const int r = pr->occ_res[a];
-        double u = (x[a] - (double)m->bmin[a]) / ((double)m->bmax[a] - (double)m->bmin[a]) * r - 0.5;
-        if (u < 0.0) u = 0.0;
-        if (u > r - 1) u = r - 1;
-        int fl = (int)floor(u);
-        if (fl > r - 2) fl = r - 2;
-        if (fl < 0) fl = 0;
-        i[a] = fl;
-        f[a] = r > 1 ? u - fl : 0.0;
+    const int B = pr->n_bins, S = pr->n_sub;
+    const float seg = (tf - tn) / (float)(B * S);
+    float inv[3];
+    for (int a = 0; a < 3; ++a) inv[a] = (float)pr->occ_res[a] / (m->bmax[a] - m->bmin[a]);
+    *first = 1.0;
+    for (int b = 0; b < B; ++b) {
+        int count = 0;
+        for (int j = 0; j < S; ++j) {
+            const float t = fmaf((float)(b * S + j) + 0.5f, seg, tn);
+            int c[3];
+            for (int a = 0; a < 3; ++a) {
+                const float x = fmaf(t, d[a], o[a]);
+                float u = (x - m->bmin[a]) * inv[a];
+                u = fminf(fmaxf(u, 0.0f), (float)(pr->occ_res[a] - 1));
+                c[a] = (int)floorf(u);
+            }
+            const size_t cell = ((size_t)c[2] * pr->occ_res[1] + c[1]) * pr->occ_res[0] + c[0];
+            if (pr->occ[cell] > 0.5) {
+                if (*first == 1.0) *first = (b * S + j + 0.5) / (B * S);
+                ++count;
+            }
+        }
+        frac[b] = (double)count / S;
     }
-    double v = 0.0;
-    for (int c = 0; c < 8; ++c) {
-        const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
-        const int jx = pr->occ_res[0] > 1 ? i[0] + cx : 0;
-        const int jy = pr->occ_res[1] > 1 ? i[1] + cy : 0;
-        const int jz = pr->occ_res[2] > 1 ? i[2] + cz : 0;
-        const double w = (cx ? f[0] : 1 - f[0]) * (cy ? f[1] : 1 - f[1]) * (cz ? f[2] : 1 - f[2]);
-        v += w * pr->occ[((size_t)jz * pr->occ_res[1] + jy) * pr->occ_res[0] + jx];
+    for (int b = 0; b < B; ++b) {
+        const double v = B * *first - b;
+        step[b] = v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
     }
-    return v;
 }
 
 typedef struct {
@@ -858,12 +871,14 @@ typedef struct {
     double logit[ORC_MAX_IN], p[ORC_MAX_IN];
 } prop_state;
 
-/* Proposal MLP input [(o - centre)/extent, d, occupancy at the B bin centres]
+/* Proposal MLP input [(o - centre)/extent, d, first occupied position,
+ * occupied fraction of the B bins, share of each bin before the first
+ * occupied point]
  * -> W -> W -> B logits (ReLU hidden layers), softmax. */
 static void proposal_eval(const orc_model* m, const orc_proposal* pr, const float* o,
                           const float* d, prop_state* st)
 {
-    const int B = pr->n_bins, W = pr->width, nin = 6 + B;
+    const int B = pr->n_bins, W = pr->width, nin = 7 + 2 * B;
     st->hit = ray_box_f32(o, d, m->bmin, m->bmax, &st->tn, &st->tf);
     for (int a = 0; a < 3; ++a) {
         const double c = 0.5 * ((double)m->bmin[a] + (double)m->bmax[a]);
@@ -871,15 +886,14 @@ static void proposal_eval(const orc_model* m, const orc_proposal* pr, const floa
         st->x[a] = ((double)o[a] - c) / e;
         st->x[3 + a] = (double)d[a];
     }
-    for (int b = 0; b < B; ++b) {
-        double occ = 0.0;
-        if (st->hit) {
-            const double tb = (double)st->tn + (b + 0.5) * ((double)st->tf - (double)st->tn) / B;
-            double xw[3];
-            for (int a = 0; a < 3; ++a) xw[a] = (double)o[a] + tb * (double)d[a];
-            occ = occ_sample(m, pr, xw);
+    if (st->hit) {
+        ray_occupancy(m, pr, o, d, st->tn, st->tf, st->x + 7, st->x + 6, st->x + 7 + B);
+    } else {
+        st->x[6] = 1.0;
+        for (int b = 0; b < B; ++b) {
+            st->x[7 + b] = 0.0;
+            st->x[7 + B + b] = 1.0;
         }
-        st->x[6 + b] = occ;
     }
     const double* W1 = pr->params;
     const double* b1 = W1 + W * nin;
@@ -919,7 +933,8 @@ int32_t orc_proposal_forward(const orc_model* m, const orc_proposal* pr, int64_t
                              double* logits, double* probs, double* t_samples, double* margin)
 {
     const int B = pr->n_bins;
-    if (B < 1 || B > ORC_MAX_IN - 6 || pr->width < 1 || pr->width > ORC_MAX_W || n_out < 1)
+    if (B < 1 || 7 + 2 * B > ORC_MAX_IN || pr->width < 1 || pr->width > ORC_MAX_W || n_out < 1 ||
+        pr->n_sub < 1)
         return -2;
     prop_state st;
     for (int64_t r = 0; r < n_rays; ++r) {
@@ -934,10 +949,21 @@ int32_t orc_proposal_forward(const orc_model* m, const orc_proposal* pr, int64_t
             }
             margin[r] = mg;
         }
-        /* mixed density p' = (1 - mix) p + mix / B, uniform if its peak is below theta */
+        /* mixed density p' = (1 - mix) p + mix r: r puts a quarter of the mix
+         * share on every bin and three quarters evenly on the bins that hold
+         * an occupied point or neighbour a bin that does (all of it uniformly
+         * when none does); p' is uniform when its peak is below theta */
+        double near[ORC_MAX_IN], nr = 0.0;
+        for (int b = 0; b < B; ++b) {
+            const int nb = st.x[7 + b] > 0.0 || (b > 0 && st.x[6 + b] > 0.0) ||
+                           (b + 1 < B && st.x[8 + b] > 0.0);
+            near[b] = nb ? 1.0 : 0.0;
+            nr += near[b];
+        }
         double q[ORC_MAX_IN], qmax = 0.0;
         for (int b = 0; b < B; ++b) {
-            q[b] = (1.0 - pr->mix) * st.p[b] + pr->mix / B;
+            const double rb = nr > 0.0 ? 0.75 * near[b] / nr + 0.25 / B : 1.0 / B;
+            q[b] = (1.0 - pr->mix) * st.p[b] + pr->mix * rb;
             if (q[b] > qmax) qmax = q[b];
         }
         if (qmax < pr->theta)
@@ -996,14 +1022,16 @@ int32_t orc_weight_histogram(const orc_model* m, const orc_params* p, int64_t n_
     return 0;
 }
 
-/* Cross-entropy of the target bins hist / sum(hist) against the proposal's
- * softmax, for rays whose target mass is at least min_mass; gradients of
- * scale * sum_r loss_r with respect to the proposal parameters. */
+/* Loss of a ray: the cross-entropy of the weight histogram against the
+ * proposal's softmax, weighted by the ray's weight mass,
+ * loss_r = -sum_b hist_b log p_b (rays with mass below min_mass skipped);
+ * gradients of scale * sum_r loss_r with respect to the proposal parameters
+ * (d loss / d logit_b = mass p_b - hist_b). */
 int32_t orc_proposal_backward(const orc_model* m, const orc_proposal* pr, int64_t n_rays,
                               const float* rays_o, const float* rays_d, const double* hist,
                               double min_mass, double scale, double* g_params, double* loss)
 {
-    const int B = pr->n_bins, W = pr->width, nin = 6 + B;
+    const int B = pr->n_bins, W = pr->width, nin = 7 + 2 * B;
     const double* W1 = pr->params;
     const double* b1 = W1 + W * nin;
     const double* W2 = b1 + W;
@@ -1027,9 +1055,8 @@ int32_t orc_proposal_backward(const orc_model* m, const orc_proposal* pr, int64_
         double dl[ORC_MAX_IN], dh2[ORC_MAX_W], dz2[ORC_MAX_W], dh1[ORC_MAX_W], dz1[ORC_MAX_W];
         double ce = 0.0;
         for (int b = 0; b < B; ++b) {
-            const double tgt = hist[r * B + b] / mass;
-            ce -= tgt * log(st.p[b]);
-            dl[b] = scale * (st.p[b] - tgt);
+            ce -= hist[r * B + b] * log(st.p[b]);
+            dl[b] = scale * (mass * st.p[b] - hist[r * B + b]);
         }
         if (loss) loss[r] = ce;
         for (int b = 0; b < B; ++b) {

@@ -13,7 +13,7 @@
 #define ORC_MAX_K 8
 #define ORC_MAX_L2 16
 #define ORC_MAX_W 64
-#define ORC_MAX_IN 40
+#define ORC_MAX_IN 48
 
 #define ORC_DIR_REFLECT 0
 #define ORC_DIR_VIEW 1
@@ -71,7 +71,8 @@ typedef struct orc_proposal {
     const double* occ;      /* [res_z][res_y][res_x] in {0, 1} */
     int32_t width;          /* hidden width */
     int32_t n_bins;         /* bins of [t_n, t_f] */
-    const double* params;   /* W1[W][6+B] b1[W] W2[W][W] b2[W] W3[B][W] b3[B] */
+    int32_t n_sub;          /* occupancy look-ups per bin */
+    const double* params;   /* W1[W][7+2B] b1[W] W2[W][W] b2[W] W3[B][W] b3[B] */
     double mix;             /* p' = (1 - mix) softmax + mix / B */
     double theta;           /* uniform fallback if max p' < theta */
 } orc_proposal;

@@ -23,7 +23,8 @@ __all__ = [
     "library", "grid_bytes", "mlp_param_count", "pack_grid", "unpack_grid", "BF16", "F16", "F32",
     "render_forward", "render_backward", "render", "device_status", "DIR_REFLECT", "DIR_VIEW",
     "ProposalDesc", "proposal_desc", "proposal_param_count", "occupancy_build",
-    "weight_histogram", "proposal_forward", "proposal_backward",
+    "weight_histogram", "proposal_forward", "proposal_backward", "adam_step", "Adam",
+    "occupancy_words", "occupancy_unpack",
 ]
 
 DIR_REFLECT = 0
@@ -62,7 +63,8 @@ class RenderParams(ctypes.Structure):
 
 class ProposalDesc(ctypes.Structure):
     _fields_ = [("occ_res", ctypes.c_int32 * 3), ("n_bins", ctypes.c_int32),
-                ("width", ctypes.c_int32), ("mix", ctypes.c_float), ("theta", ctypes.c_float)]
+                ("width", ctypes.c_int32), ("n_sub", ctypes.c_int32), ("mix", ctypes.c_float),
+                ("theta", ctypes.c_float)]
 
 
 _lock = threading.Lock()
@@ -104,7 +106,11 @@ def library() -> ctypes.CDLL:
                                              _P, _P, _P, _P, _P, _P, _P, _P]
         lib.psdf_render_occupancy.argtypes = [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_int32),
                                               ctypes.POINTER(ctypes.c_int32)]
+        lib.psdf_adam_step.argtypes = [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_float,
+                                       ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                       ctypes.c_int32, ctypes.c_int32, _P]
         lib.psdf_proposal_param_count.argtypes = [_P, ctypes.POINTER(ctypes.c_int64)]
+        lib.psdf_occupancy_words.argtypes = [_P, ctypes.POINTER(ctypes.c_int64)]
         lib.psdf_occupancy_build.argtypes = [_P, _P, ctypes.c_float, _P, _P]
         lib.psdf_weight_histogram.argtypes = [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32,
                                               _P, _P]
@@ -115,7 +121,8 @@ def library() -> ctypes.CDLL:
         for name in ("psdf_grid_bytes", "psdf_grid_create", "psdf_grid_pack", "psdf_grid_unpack",
                      "psdf_probes_create", "psdf_mlp_param_count", "psdf_mlp_create",
                      "psdf_render_forward", "psdf_render_backward", "psdf_render_occupancy",
-                     "psdf_proposal_param_count", "psdf_occupancy_build", "psdf_weight_histogram",
+                     "psdf_adam_step", "psdf_proposal_param_count", "psdf_occupancy_words",
+                     "psdf_occupancy_build", "psdf_weight_histogram",
                      "psdf_proposal_forward", "psdf_proposal_backward"):
             getattr(lib, name).restype = ctypes.c_int32
         _lib = lib
@@ -428,14 +435,47 @@ def render(scene: Scene, rays_o, rays_d, params: RenderParams, t_samples=None, m
 
 
 # ---------------------------------------------------------------------------
+# Optimiser (Adam, Sec. 3.4)
+# ---------------------------------------------------------------------------
+
+def adam_step(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, clear_grad=True):
+    """One in-place Adam update of a FP32 tensor (bias-corrected; `step` from 1)."""
+    _require_cuda(param, grad, m, v)
+    n = param.numel()
+    if grad.numel() != n or m.numel() != n or v.numel() != n:
+        raise LibraryError("adam_step: param, grad, m and v must have the same size")
+    _check(library().psdf_adam_step(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), n, float(lr),
+                                    float(beta1), float(beta2), float(eps), int(step),
+                                    int(bool(clear_grad)), _stream()), "psdf_adam_step")
+
+
+class Adam:
+    """Adam over a list of (param, grad, lr) FP32 device tensors; the moments
+    live beside them.  step() updates every parameter and clears its grad."""
+
+    def __init__(self, groups, beta1=0.9, beta2=0.999, eps=1e-8):
+        self.groups = [(p, g, float(lr), torch.zeros_like(p), torch.zeros_like(p))
+                       for p, g, lr in groups]
+        self.beta1, self.beta2, self.eps = beta1, beta2, eps
+        self.t = 0
+
+    def step(self):
+        self.t += 1
+        for p, g, lr, m, v in self.groups:
+            adam_step(p, g, m, v, self.t, lr, self.beta1, self.beta2, self.eps)
+
+
+# ---------------------------------------------------------------------------
 # Learned sample proposal (the paper marches its sparse grid instead)
 # ---------------------------------------------------------------------------
 
-def proposal_desc(occ_res=(32, 32, 32), n_bins=8, width=32, mix=0.1, theta=0.2) -> ProposalDesc:
+def proposal_desc(occ_res=(32, 32, 32), n_bins=8, width=32, mix=0.1, theta=0.2,
+                  n_sub=8) -> ProposalDesc:
     d = ProposalDesc()
     d.occ_res[:] = tuple(int(v) for v in occ_res)
     d.n_bins = int(n_bins)
     d.width = int(width)
+    d.n_sub = int(n_sub)
     d.mix = float(mix)
     d.theta = float(theta)
     return d
@@ -462,15 +502,31 @@ class _GridHandle:
         library().psdf_grid_destroy(self.h)
 
 
+def occupancy_words(occ_res) -> int:
+    res = (ctypes.c_int32 * 3)(*(int(v) for v in occ_res))
+    n = ctypes.c_int64()
+    _check(library().psdf_occupancy_words(res, ctypes.byref(n)), "psdf_occupancy_words")
+    return n.value
+
+
 def occupancy_build(scene: Scene, occ_res, threshold: float) -> torch.Tensor:
-    """[res_z, res_y, res_x] FP32 in {0, 1}: cells near the zero level set."""
-    rx, ry, rz = (int(v) for v in occ_res)
-    occ = torch.empty((rz, ry, rx), dtype=torch.float32, device=scene.grid.device)
-    res = (ctypes.c_int32 * 3)(rx, ry, rz)
+    """Occupancy bitmask (int32 words holding 32 cells each, cell
+    (z res_y + y) res_x + x at bit i & 31 of word i >> 5) of the cells near
+    the zero level set."""
+    occ = torch.empty(occupancy_words(occ_res), dtype=torch.int32, device=scene.grid.device)
+    res = (ctypes.c_int32 * 3)(*(int(v) for v in occ_res))
     with _GridHandle(scene) as g:
         _check(library().psdf_occupancy_build(g, res, float(threshold), _ptr(occ), _stream()),
                "psdf_occupancy_build")
     return occ
+
+
+def occupancy_unpack(occ_bits: torch.Tensor, occ_res) -> torch.Tensor:
+    """Bitmask -> [res_z, res_y, res_x] uint8 {0, 1} (host copy, for inspection)."""
+    rx, ry, rz = (int(v) for v in occ_res)
+    w = occ_bits.cpu().view(-1).to(torch.int64) & 0xFFFFFFFF
+    cells = torch.arange(rx * ry * rz)
+    return ((w[cells >> 5] >> (cells & 31)) & 1).to(torch.uint8).view(rz, ry, rx)
 
 
 def weight_histogram(scene: Scene, rays_o, rays_d, params: RenderParams, n_bins=8):
@@ -488,7 +544,8 @@ def weight_histogram(scene: Scene, rays_o, rays_d, params: RenderParams, n_bins=
 def proposal_forward(scene: Scene, desc: ProposalDesc, params, occ, rays_o, rays_d, n_out,
                      want_probs=True):
     """(t_samples [n, n_out + 1], mixed density p' [n, B] or None)."""
-    _require_cuda(params, occ, rays_o, rays_d)
+    _require_cuda(params, rays_o, rays_d)
+    _require_cuda(occ, dtypes=(torch.int32,))
     n = rays_o.shape[0]
     t = torch.empty((n, n_out + 1), dtype=torch.float32, device=rays_o.device)
     probs = (torch.empty((n, desc.n_bins), dtype=torch.float32, device=rays_o.device)
@@ -505,7 +562,8 @@ def proposal_backward(scene: Scene, desc: ProposalDesc, params, occ, rays_o, ray
                       min_mass=1e-3, scale=1.0, grad=None, want_loss=True):
     """(grad [param count] with the gradient of scale * sum(loss) ADDED,
     per-ray cross-entropy loss [n] or None)."""
-    _require_cuda(params, occ, rays_o, rays_d, hist, grad)
+    _require_cuda(params, rays_o, rays_d, hist, grad)
+    _require_cuda(occ, dtypes=(torch.int32,))
     n = rays_o.shape[0]
     if grad is None:
         grad = torch.zeros_like(params)

@@ -544,6 +544,26 @@ psdf_status psdf_render_occupancy(const psdf_grid* grid, const psdf_probes* prob
 
 
 // ---------------------------------------------------------------------------
+// Optimiser
+// ---------------------------------------------------------------------------
+
+psdf_status psdf_adam_step(float* param, float* grad, float* m, float* v, int64_t n, float lr,
+                           float beta1, float beta2, float eps, int32_t step, int32_t clear_grad,
+                           void* stream)
+{
+    if (n < 0 || step < 1) return PSDF_ERR_INVALID_ARG;
+    if (!(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) ||
+        !(eps > 0.0f))
+        return PSDF_ERR_INVALID_ARG;
+    if (n == 0) return PSDF_OK;
+    if (!param || !grad || !m || !v) return PSDF_ERR_INVALID_ARG;
+    if (!aligned16(param) || !aligned16(grad) || !aligned16(m) || !aligned16(v))
+        return PSDF_ERR_MISALIGNED;
+    return cuda_status(psdf::launch_adam(param, grad, m, v, n, lr, beta1, beta2, eps, step,
+                                         clear_grad, static_cast<cudaStream_t>(stream)));
+}
+
+// ---------------------------------------------------------------------------
 // Learned sample proposal
 // ---------------------------------------------------------------------------
 
@@ -553,8 +573,9 @@ psdf_status check_proposal_desc(const psdf_proposal_desc* d)
 {
     if (!d) return PSDF_ERR_INVALID_ARG;
     for (int a = 0; a < 3; ++a)
-        if (d->occ_res[a] < 2 || d->occ_res[a] > 1024) return PSDF_ERR_BAD_SHAPE;
-    if (d->n_bins != psdf::proposal_bins() || d->width != psdf::proposal_width())
+        if (d->occ_res[a] < 2 || d->occ_res[a] > 64) return PSDF_ERR_BAD_SHAPE;
+    if (d->n_sub < 1 || d->n_sub > 32) return PSDF_ERR_BAD_SHAPE;
+    if (!psdf::proposal_bins_supported(d->n_bins) || d->width != psdf::proposal_width())
         return PSDF_ERR_UNSUPPORTED;
     if (!(d->mix >= 0.0f && d->mix < 1.0f) || !(d->theta >= 0.0f)) return PSDF_ERR_INVALID_ARG;
     return PSDF_OK;
@@ -589,22 +610,33 @@ psdf_status psdf_proposal_param_count(const psdf_proposal_desc* desc, int64_t* c
     const psdf_status st = check_proposal_desc(desc);
     if (st != PSDF_OK) return st;
     if (!count) return PSDF_ERR_INVALID_ARG;
-    *count = psdf::proposal_param_count();
+    *count = psdf::proposal_param_count(desc->n_bins);
+    return PSDF_OK;
+}
+
+psdf_status psdf_occupancy_words(const int32_t occ_res[3], int64_t* words)
+{
+    if (!occ_res || !words) return PSDF_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (occ_res[a] < 2 || occ_res[a] > 64) return PSDF_ERR_BAD_SHAPE;
+    const int res[3] = {occ_res[0], occ_res[1], occ_res[2]};
+    *words = psdf::occupancy_words(res);
     return PSDF_OK;
 }
 
 psdf_status psdf_occupancy_build(const psdf_grid* grid, const int32_t occ_res[3],
-                                 float threshold, float* occ, void* stream)
+                                 float threshold, uint32_t* occ_bits, void* stream)
 {
     psdf::GridView g;
     psdf_status st = grid_view(grid, g);
     if (st != PSDF_OK) return st;
-    if (!occ_res || !occ) return PSDF_ERR_INVALID_ARG;
-    for (int a = 0; a < 3; ++a)
-        if (occ_res[a] < 1 || occ_res[a] > 1024) return PSDF_ERR_BAD_SHAPE;
-    if (!aligned16(occ)) return PSDF_ERR_MISALIGNED;
+    int64_t words = 0;
+    st = psdf_occupancy_words(occ_res, &words);
+    if (st != PSDF_OK) return st;
+    if (!occ_bits) return PSDF_ERR_INVALID_ARG;
+    if (!aligned16(occ_bits)) return PSDF_ERR_MISALIGNED;
     const int res[3] = {occ_res[0], occ_res[1], occ_res[2]};
-    return cuda_status(psdf::launch_occupancy(g, res, threshold, occ,
+    return cuda_status(psdf::launch_occupancy(g, res, threshold, occ_bits,
                                               static_cast<cudaStream_t>(stream)));
 }
 
@@ -635,7 +667,7 @@ psdf_status psdf_weight_histogram(const psdf_grid* grid, const psdf_render_param
 namespace {
 
 psdf_status proposal_launch(const psdf_grid* grid, const psdf_proposal_desc* desc,
-                            const float* params, const float* occ, const float* rays_o,
+                            const float* params, const uint32_t* occ, const float* rays_o,
                             const float* rays_d, int64_t n_rays, psdf::ProposalLaunch& L)
 {
     psdf_status st = check_proposal_desc(desc);
@@ -648,7 +680,9 @@ psdf_status proposal_launch(const psdf_grid* grid, const psdf_proposal_desc* des
     if (!aligned16(params) || !aligned16(occ) || !aligned16(rays_o) || !aligned16(rays_d))
         return PSDF_ERR_MISALIGNED;
     for (int a = 0; a < 3; ++a) L.occ_res[a] = desc->occ_res[a];
-    L.occ = occ;
+    L.n_bins = desc->n_bins;
+    L.n_sub = desc->n_sub;
+    L.occ_bits = occ;
     L.params = params;
     L.mix = desc->mix;
     L.theta = desc->theta;
@@ -661,12 +695,13 @@ psdf_status proposal_launch(const psdf_grid* grid, const psdf_proposal_desc* des
 }  // namespace
 
 psdf_status psdf_proposal_forward(const psdf_grid* grid, const psdf_proposal_desc* desc,
-                                  const float* params, const float* occ, const float* rays_o,
+                                  const float* params, const uint32_t* occ_bits,
+                                  const float* rays_o,
                                   const float* rays_d, int64_t n_rays, int32_t n_out,
                                   float* t_samples, float* probs, void* stream)
 {
     psdf::ProposalLaunch L;
-    psdf_status st = proposal_launch(grid, desc, params, occ, rays_o, rays_d, n_rays, L);
+    psdf_status st = proposal_launch(grid, desc, params, occ_bits, rays_o, rays_d, n_rays, L);
     if (st != PSDF_OK) return st;
     if (n_out < 1 || n_out > 4096) return PSDF_ERR_BAD_SHAPE;
     if (n_rays > 0 && !t_samples) return PSDF_ERR_INVALID_ARG;
@@ -679,13 +714,14 @@ psdf_status psdf_proposal_forward(const psdf_grid* grid, const psdf_proposal_des
 }
 
 psdf_status psdf_proposal_backward(const psdf_grid* grid, const psdf_proposal_desc* desc,
-                                   const float* params, const float* occ, const float* rays_o,
+                                   const float* params, const uint32_t* occ_bits,
+                                   const float* rays_o,
                                    const float* rays_d, int64_t n_rays, const float* hist,
                                    float min_mass, float scale, float* grad_params, float* loss,
                                    void* stream)
 {
     psdf::ProposalLaunch L;
-    psdf_status st = proposal_launch(grid, desc, params, occ, rays_o, rays_d, n_rays, L);
+    psdf_status st = proposal_launch(grid, desc, params, occ_bits, rays_o, rays_d, n_rays, L);
     if (st != PSDF_OK) return st;
     if (!grad_params || (n_rays > 0 && !hist)) return PSDF_ERR_INVALID_ARG;
     if (!aligned16(hist) || !aligned16(grad_params) || !aligned16(loss)) return PSDF_ERR_MISALIGNED;

@@ -44,6 +44,8 @@ int resident_ctas(const cudaFuncAttributes& fa, int threads, size_t dyn_smem, un
 cudaError_t forward_ctas_per_sm(const KernelShape& ks, int* n);
 cudaError_t backward_ctas_per_sm(const KernelShape& ks, int* n);
 
+cudaError_t launch_adam(float* p, float* g, float* m, float* v, int64_t n, float lr, float beta1,
+                        float beta2, float eps, int step, int clear_grad, cudaStream_t stream);
 cudaError_t launch_pack(const float* sdf, const float* feat, float4* packed, int64_t n_nodes,
                         cudaStream_t stream);
 cudaError_t launch_unpack(const float4* packed, float* sdf, float* feat, int64_t n_nodes,

@@ -3,16 +3,17 @@
 // box, and the samples are placed at the quantiles of that density, so that a
 // few samples land where uniform marching would need many.
 //
-//   occupancy_kernel      coarse occupancy grid from the SDF (|s| < threshold)
+//   occupancy_kernel      coarse occupancy bitmask from the SDF (|s| < threshold)
 //   histogram_kernel      per-bin sums of the uniform render's weights w_k
 //                         (SDF gathers only: the weights need no colour)
-//   proposal_fwd_kernel   [(o-c)/e, d, occupancy at bin centres] -> W -> W -> B
+//   proposal_fwd_kernel   [(o-c)/e, d, occupied fraction per bin] -> W -> W -> B
 //                         logits, softmax, mixed density, quantile placement
-//   proposal_bwd_kernel   cross-entropy to the normalised histogram and its
-//                         gradient with respect to the proposal MLP
+//   proposal_bwd_kernel   mass-weighted cross-entropy -sum_b hist_b log p_b and
+//                         its gradient with respect to the proposal MLP
 //
 // One thread per ray for the MLP parts (per-ray work, ~1.7 k FMA), one warp per
-// ray for the histogram march.
+// ray for the histogram march.  The proposal kernels keep the occupancy
+// bitmask (at most 64^3 bits = 32 KB) in shared memory.
 #include "internal.h"
 #include "proposal.h"
 #include "sample_eval.cuh"
@@ -21,38 +22,54 @@ namespace psdf {
 
 namespace {
 
-constexpr int kPB = 8;    // bins
-constexpr int kPW = 32;   // hidden width
-constexpr int kPIn = 6 + kPB;
-constexpr int kPParams = kPW * kPIn + kPW + kPW * kPW + kPW + kPB * kPW + kPB;
+constexpr int kPW = 32;  // hidden width
+
+// Compiled proposal shapes: B bins, inputs [o (3), d (3), first occupied
+// position (1), occupied fraction of each bin (B), share of each bin before
+// the first occupied point (B)].
+template <int B>
+struct PropShape {
+    static constexpr int kIn = 7 + 2 * B;
+    static constexpr int kParams = kPW * kIn + kPW + kPW * kPW + kPW + B * kPW + B;
+};
 
 __device__ __forceinline__ float grid_sdf_node(const GridView& g, int idx)
 {
     return g.sdf ? __ldg(g.sdf + idx) : __ldg(reinterpret_cast<const float*>(g.nodes + idx));
 }
 
+// One bit per cell (bit c & 31 of word c >> 5, c = (z res_y + y) res_x + x):
+// a warp builds one word with a ballot.
 __global__ void occupancy_kernel(GridView g, int rx, int ry, int rz, float threshold,
-                                 float* __restrict__ occ)
+                                 uint32_t* __restrict__ bits)
 {
     const int n = rx * ry * rz;
-    for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < n;
-         cell += gridDim.x * blockDim.x) {
-        const int c[3] = {cell % rx, (cell / rx) % ry, cell / (rx * ry)};
-        const int res[3] = {rx, ry, rz};
-        int lo[3], hi[3];
+    const int words = (n + 31) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int res[3] = {rx, ry, rz};
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < words;
+         w += (gridDim.x * blockDim.x) >> 5) {
+        const int cell = (w << 5) + lane;
+        bool occupied = false;
+        if (cell < n) {
+            const int c[3] = {cell % rx, (cell / rx) % ry, cell / (rx * ry)};
+            int lo[3], hi[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const long long span = g.R[a] - 1;
-            lo[a] = static_cast<int>((c[a] * span) / res[a]);
-            hi[a] = static_cast<int>(((c[a] + 1) * span + res[a] - 1) / res[a]);
-            hi[a] = min(hi[a], g.R[a] - 1);
+            for (int a = 0; a < 3; ++a) {
+                const long long span = g.R[a] - 1;
+                lo[a] = static_cast<int>((c[a] * span) / res[a]);
+                hi[a] = static_cast<int>(((c[a] + 1) * span + res[a] - 1) / res[a]);
+                hi[a] = min(hi[a], g.R[a] - 1);
+            }
+            float mn = INFINITY;
+            for (int iz = lo[2]; iz <= hi[2]; ++iz)
+                for (int iy = lo[1]; iy <= hi[1]; ++iy)
+                    for (int ix = lo[0]; ix <= hi[0]; ++ix)
+                        mn = fminf(mn, fabsf(grid_sdf_node(g, (iz * g.R[1] + iy) * g.R[0] + ix)));
+            occupied = mn < threshold;
         }
-        float mn = INFINITY;
-        for (int iz = lo[2]; iz <= hi[2]; ++iz)
-            for (int iy = lo[1]; iy <= hi[1]; ++iy)
-                for (int ix = lo[0]; ix <= hi[0]; ++ix)
-                    mn = fminf(mn, fabsf(grid_sdf_node(g, (iz * g.R[1] + iy) * g.R[0] + ix)));
-        occ[cell] = mn < threshold ? 1.0f : 0.0f;
+        const uint32_t word = __ballot_sync(0xffffffffu, occupied);
+        if (lane == 0) bits[w] = word;
     }
 }
 
@@ -125,7 +142,8 @@ __global__ void histogram_kernel(RenderArgs A, int n_bins, float* __restrict__ h
 struct PropArgs {
     GridView grid;
     int occ_res[3];
-    const float* __restrict__ occ;
+    int n_sub;
+    const uint32_t* __restrict__ occ_bits;
     const float* __restrict__ params;
     float mix, theta;
     const float* __restrict__ rays_o;
@@ -140,44 +158,66 @@ struct PropArgs {
     float* loss;
 };
 
-__device__ __forceinline__ float occ_sample(const PropArgs& P, const float x[3])
+// Occupancy features of a ray (x[6] = first occupied position, x[7 + b] =
+// occupied share of bin b, x[7 + B + b] = share of bin b before the first
+// occupied point): B n_sub points at the centres of equal
+// sub-intervals of [t_n, t_f], each looked up in the cell containing it.
+// Positions and cell indices use explicitly rounded FP32 operations (they
+// decide integers).
+template <int B>
+__device__ __forceinline__ void ray_occupancy(const PropArgs& P, const uint32_t* bits,
+                                              const float o[3], const float d[3], float tn,
+                                              float tf, float* x)
 {
-    int i[3];
-    float f[3];
+    const int S = P.n_sub;
+    const float seg = __fdiv_rn(__fsub_rn(tf, tn), static_cast<float>(B * S));
+    float inv[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const int r = P.occ_res[a];
-        float u = (x[a] - P.grid.bmin[a]) / (P.grid.bmax[a] - P.grid.bmin[a]) * r - 0.5f;
-        u = fminf(fmaxf(u, 0.0f), static_cast<float>(r - 1));
-        int fl = static_cast<int>(floorf(u));
-        fl = max(0, min(fl, r - 2));
-        i[a] = fl;
-        f[a] = r > 1 ? u - fl : 0.0f;
-    }
-    float v = 0.0f;
+    for (int a = 0; a < 3; ++a)
+        inv[a] = __fdiv_rn(static_cast<float>(P.occ_res[a]),
+                           __fsub_rn(P.grid.bmax[a], P.grid.bmin[a]));
+    int first = -1;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
-        const int jx = P.occ_res[0] > 1 ? i[0] + cx : 0;
-        const int jy = P.occ_res[1] > 1 ? i[1] + cy : 0;
-        const int jz = P.occ_res[2] > 1 ? i[2] + cz : 0;
-        const float w =
-            (cx ? f[0] : 1 - f[0]) * (cy ? f[1] : 1 - f[1]) * (cz ? f[2] : 1 - f[2]);
-        v = fmaf(w, __ldg(P.occ + (jz * P.occ_res[1] + jy) * P.occ_res[0] + jx), v);
+    for (int b = 0; b < B; ++b) {
+        int count = 0;
+        for (int j = 0; j < S; ++j) {
+            const int k = b * S + j;
+            const float t = __fmaf_rn(static_cast<float>(k) + 0.5f, seg, tn);
+            int c[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float xa = __fmaf_rn(t, d[a], o[a]);
+                float u = __fmul_rn(__fsub_rn(xa, P.grid.bmin[a]), inv[a]);
+                u = fminf(fmaxf(u, 0.0f), static_cast<float>(P.occ_res[a] - 1));
+                c[a] = static_cast<int>(floorf(u));
+            }
+            const int cell = (c[2] * P.occ_res[1] + c[1]) * P.occ_res[0] + c[0];
+            const uint32_t hit = (bits[cell >> 5] >> (cell & 31)) & 1u;
+            if (hit && first < 0) first = k;
+            count += hit;
+        }
+        x[7 + b] = static_cast<float>(count) / static_cast<float>(S);
     }
-    return v;
+    x[6] = first < 0 ? 1.0f
+                     : (static_cast<float>(first) + 0.5f) / static_cast<float>(B * S);
+#pragma unroll
+    for (int b = 0; b < B; ++b) x[7 + B + b] = fminf(fmaxf(B * x[6] - b, 0.0f), 1.0f);
 }
 
+template <int B>
 struct PropState {
     bool hit;
     float tn, tf;
-    float x[kPIn], h1[kPW], h2[kPW], p[kPB];
+    float x[PropShape<B>::kIn], h1[kPW], h2[kPW], p[B];
     uint32_t m1, m2;  // ReLU masks
 };
 
-__device__ __forceinline__ void proposal_eval(const PropArgs& P, const float* sw, int64_t ray,
-                                              PropState& S)
+template <int B>
+__device__ __forceinline__ void proposal_eval(const PropArgs& P, const float* sw,
+                                              const uint32_t* bits, int64_t ray,
+                                              PropState<B>& S)
 {
+    constexpr int kIn = PropShape<B>::kIn;
     float o[3], d[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -191,30 +231,28 @@ __device__ __forceinline__ void proposal_eval(const PropArgs& P, const float* sw
         S.x[a] = (o[a] - c) / (P.grid.bmax[a] - P.grid.bmin[a]);
         S.x[3 + a] = d[a];
     }
+    if (S.hit) {
+        ray_occupancy<B>(P, bits, o, d, S.tn, S.tf, S.x);
+    } else {
+        S.x[6] = 1.0f;
 #pragma unroll
-    for (int b = 0; b < kPB; ++b) {
-        float v = 0.0f;
-        if (S.hit) {
-            const float tb = S.tn + (b + 0.5f) * (S.tf - S.tn) / kPB;
-            float xw[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) xw[a] = fmaf(tb, d[a], o[a]);
-            v = occ_sample(P, xw);
+        for (int b = 0; b < B; ++b) {
+            S.x[7 + b] = 0.0f;
+            S.x[7 + B + b] = 1.0f;
         }
-        S.x[6 + b] = v;
     }
     const float* W1 = sw;
-    const float* b1 = W1 + kPW * kPIn;
+    const float* b1 = W1 + kPW * kIn;
     const float* W2 = b1 + kPW;
     const float* b2 = W2 + kPW * kPW;
     const float* W3 = b2 + kPW;
-    const float* b3 = W3 + kPB * kPW;
+    const float* b3 = W3 + B * kPW;
     S.m1 = S.m2 = 0;
 #pragma unroll
     for (int u = 0; u < kPW; ++u) {
         float z = b1[u];
 #pragma unroll
-        for (int i = 0; i < kPIn; ++i) z = fmaf(W1[u * kPIn + i], S.x[i], z);
+        for (int i = 0; i < kIn; ++i) z = fmaf(W1[u * kIn + i], S.x[i], z);
         S.m1 |= (z > 0.0f ? 1u : 0u) << u;
         S.h1[u] = fmaxf(z, 0.0f);
     }
@@ -226,9 +264,9 @@ __device__ __forceinline__ void proposal_eval(const PropArgs& P, const float* sw
         S.m2 |= (z > 0.0f ? 1u : 0u) << u;
         S.h2[u] = fmaxf(z, 0.0f);
     }
-    float mx = -INFINITY, l[kPB];
+    float mx = -INFINITY, l[B];
 #pragma unroll
-    for (int b = 0; b < kPB; ++b) {
+    for (int b = 0; b < B; ++b) {
         float z = b3[b];
 #pragma unroll
         for (int i = 0; i < kPW; ++i) z = fmaf(W3[b * kPW + i], S.h2[i], z);
@@ -237,58 +275,107 @@ __device__ __forceinline__ void proposal_eval(const PropArgs& P, const float* sw
     }
     float sum = 0.0f;
 #pragma unroll
-    for (int b = 0; b < kPB; ++b) {
+    for (int b = 0; b < B; ++b) {
         S.p[b] = expf(l[b] - mx);
         sum += S.p[b];
     }
-    const float inv = 1.0f / sum;
+    const float rsum = 1.0f / sum;
 #pragma unroll
-    for (int b = 0; b < kPB; ++b) S.p[b] *= inv;
+    for (int b = 0; b < B; ++b) S.p[b] *= rsum;
 }
 
+__device__ __forceinline__ int occ_words(const PropArgs& P)
+{
+    return (P.occ_res[0] * P.occ_res[1] * P.occ_res[2] + 31) >> 5;
+}
+
+// Parameters (and, for the adjoint, their accumulators) in static shared
+// memory, the occupancy bitmask in dynamic shared memory.
+template <int B>
 __global__ void proposal_fwd_kernel(PropArgs P)
 {
-    __shared__ float sw[kPParams];
-    for (int i = threadIdx.x; i < kPParams; i += blockDim.x) sw[i] = P.params[i];
+    constexpr int kParams = PropShape<B>::kParams;
+    constexpr unsigned FULL = 0xffffffffu;
+    __shared__ float sw[kParams];
+    extern __shared__ uint32_t sbits[];
+    for (int i = threadIdx.x; i < kParams; i += blockDim.x) sw[i] = P.params[i];
+    for (int i = threadIdx.x; i < occ_words(P); i += blockDim.x) sbits[i] = P.occ_bits[i];
     __syncthreads();
-    for (int64_t ray = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; ray < P.n_rays;
-         ray += int64_t(gridDim.x) * blockDim.x) {
-        PropState S;
-        proposal_eval(P, sw, ray, S);
-        float q[kPB], qmax = 0.0f;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    // whole warps iterate together: each lane evaluates one ray, then the warp
+    // writes the 32 rays' sample rows one after another, lane k writing
+    // samples k, k + 32, ... (coalesced stores)
+    for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < P.n_rays;
+         base += stride) {
+        const int64_t ray = base + lane;
+        const bool live = ray < P.n_rays;
+        PropState<B> S;
+        float q[B];
+        S.hit = false;
+        S.tn = S.tf = 0.0f;
 #pragma unroll
-        for (int b = 0; b < kPB; ++b) {
-            q[b] = (1.0f - P.mix) * S.p[b] + P.mix / kPB;
-            qmax = fmaxf(qmax, q[b]);
-        }
-        if (qmax < P.theta) {
+        for (int b = 0; b < B; ++b) q[b] = 1.0f / B;
+        if (live) {
+            proposal_eval<B>(P, sw, sbits, ray, S);
+            // mix share: a quarter on every bin, three quarters on the occupied
+            // bins and their neighbours (all of it uniformly when none is
+            // occupied)
+            float qmax = 0.0f;
+            int nr = 0;
+            uint32_t near = 0;
 #pragma unroll
-            for (int b = 0; b < kPB; ++b) q[b] = 1.0f / kPB;
-        }
-        if (P.probs) {
-#pragma unroll
-            for (int b = 0; b < kPB; ++b) P.probs[ray * kPB + b] = q[b];
-        }
-        float* t = P.t_samples + ray * (P.n_out + 1);
-        if (!S.hit) {
-            for (int k = 0; k <= P.n_out; ++k) t[k] = 0.0f;
-            continue;
-        }
-        // samples at the quantiles k / n_out of the piecewise-constant density
-        const float db = (S.tf - S.tn) / kPB;
-        int b = 0;
-        float c = 0.0f;
-        for (int k = 0; k <= P.n_out; ++k) {
-            const float u = static_cast<float>(k) / P.n_out;
-            while (b < kPB - 1 && c + q[b] <= u) {
-                c += q[b];
-                ++b;
+            for (int b = 0; b < B; ++b) {
+                const bool nb = S.x[7 + b] > 0.0f || (b > 0 && S.x[6 + b] > 0.0f) ||
+                                (b + 1 < B && S.x[8 + b] > 0.0f);
+                near |= (nb ? 1u : 0u) << b;
+                nr += nb;
             }
-            const float frac = fminf((u - c) / q[b], 1.0f);
-            t[k] = fmaf(b + frac, db, S.tn);
+            const float share = nr > 0 ? 0.75f * P.mix / nr : 0.0f;
+            const float floor_b = nr > 0 ? 0.25f * P.mix / B : P.mix / B;
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const float rb = floor_b + (((near >> b) & 1u) ? share : 0.0f);
+                q[b] = (1.0f - P.mix) * S.p[b] + rb;
+                qmax = fmaxf(qmax, q[b]);
+            }
+            if (qmax < P.theta) {
+#pragma unroll
+                for (int b = 0; b < B; ++b) q[b] = 1.0f / B;
+            }
+            if (P.probs) {
+#pragma unroll
+                for (int b = 0; b < B; ++b) P.probs[ray * B + b] = q[b];
+            }
         }
-        t[0] = S.tn;
-        t[P.n_out] = S.tf;
+        const int64_t left = P.n_rays - base;
+        const int rows = left < 32 ? static_cast<int>(left) : 32;
+        for (int r = 0; r < rows; ++r) {
+            float qr[B];
+#pragma unroll
+            for (int b = 0; b < B; ++b) qr[b] = __shfl_sync(FULL, q[b], r);
+            const float tn = __shfl_sync(FULL, S.tn, r);
+            const float tf = __shfl_sync(FULL, S.tf, r);
+            const bool hit = __shfl_sync(FULL, S.hit ? 1 : 0, r) != 0;
+            float* t = P.t_samples + (base + r) * (P.n_out + 1);
+            // samples at the quantiles k / n_out of the piecewise-constant density
+            const float db = (tf - tn) / B;
+            for (int k = lane; k <= P.n_out; k += 32) {
+                float v = 0.0f;
+                if (hit) {
+                    const float u = static_cast<float>(k) / P.n_out;
+                    int b = 0;
+                    float c = 0.0f;
+                    while (b < B - 1 && c + qr[b] <= u) {
+                        c += qr[b];
+                        ++b;
+                    }
+                    const float frac = fminf((u - c) / qr[b], 1.0f);
+                    v = k == 0 ? tn : (k == P.n_out ? tf : fmaf(b + frac, db, tn));
+                }
+                t[k] = v;
+            }
+        }
     }
 }
 
@@ -299,23 +386,28 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
+template <int B>
 __global__ void proposal_bwd_kernel(PropArgs P)
 {
-    __shared__ float sw[kPParams];
-    __shared__ float acc[kPParams];
-    for (int i = threadIdx.x; i < kPParams; i += blockDim.x) {
+    constexpr int kIn = PropShape<B>::kIn;
+    constexpr int kParams = PropShape<B>::kParams;
+    __shared__ float sw[kParams];
+    __shared__ float acc[kParams];
+    extern __shared__ uint32_t sbits[];
+    for (int i = threadIdx.x; i < kParams; i += blockDim.x) {
         sw[i] = P.params[i];
         acc[i] = 0.0f;
     }
+    for (int i = threadIdx.x; i < occ_words(P); i += blockDim.x) sbits[i] = P.occ_bits[i];
     __syncthreads();
-    const float* W2 = sw + kPW * kPIn + kPW;
+    const float* W2 = sw + kPW * kIn + kPW;
     const float* W3 = W2 + kPW * kPW + kPW;
     float* gW1 = acc;
-    float* gb1 = gW1 + kPW * kPIn;
+    float* gb1 = gW1 + kPW * kIn;
     float* gW2 = gb1 + kPW;
     float* gb2 = gW2 + kPW * kPW;
     float* gW3 = gb2 + kPW;
-    float* gb3 = gW3 + kPB * kPW;
+    float* gb3 = gW3 + B * kPW;
     const int lane = threadIdx.x & 31;
     // whole warps iterate together so that the per-parameter warp sums below
     // see every lane; lanes past the end contribute zeros
@@ -323,41 +415,41 @@ __global__ void proposal_bwd_kernel(PropArgs P)
     for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < P.n_rays;
          base += stride) {
         const int64_t ray = base + lane;
-        PropState S;
-        float dl[kPB];
+        PropState<B> S;
+        float dl[B];
         bool valid = false;
         if (ray < P.n_rays) {
             float mass = 0.0f;
 #pragma unroll
-            for (int b = 0; b < kPB; ++b) mass += __ldg(P.hist + ray * kPB + b);
+            for (int b = 0; b < B; ++b) mass += __ldg(P.hist + ray * B + b);
             valid = mass >= P.min_mass;
             float ce = 0.0f;
             if (valid) {
-                proposal_eval(P, sw, ray, S);
+                proposal_eval<B>(P, sw, sbits, ray, S);
 #pragma unroll
-                for (int b = 0; b < kPB; ++b) {
-                    const float tgt = __ldg(P.hist + ray * kPB + b) / mass;
-                    ce -= tgt * logf(S.p[b]);
-                    dl[b] = P.scale * (S.p[b] - tgt);
+                for (int b = 0; b < B; ++b) {
+                    const float h = __ldg(P.hist + ray * B + b);
+                    ce -= h * logf(S.p[b]);
+                    dl[b] = P.scale * (mass * S.p[b] - h);
                 }
             }
             if (P.loss) P.loss[ray] = ce;
         }
         if (!valid) {
 #pragma unroll
-            for (int b = 0; b < kPB; ++b) dl[b] = 0.0f;
+            for (int b = 0; b < B; ++b) dl[b] = 0.0f;
 #pragma unroll
             for (int i = 0; i < kPW; ++i) S.h1[i] = S.h2[i] = 0.0f;
 #pragma unroll
-            for (int i = 0; i < kPIn; ++i) S.x[i] = 0.0f;
+            for (int i = 0; i < kIn; ++i) S.x[i] = 0.0f;
             S.m1 = S.m2 = 0;
         }
         // layer 3
 #pragma unroll
-        for (int b = 0; b < kPB; ++b) {
+        for (int b = 0; b < B; ++b) {
             const float sb = warp_sum(dl[b]);
             if (lane == 0) atomicAdd(gb3 + b, sb);
-#pragma unroll
+#pragma unroll 4
             for (int i = 0; i < kPW; ++i) {
                 const float v = warp_sum(dl[b] * S.h2[i]);
                 if (lane == 0) atomicAdd(gW3 + b * kPW + i, v);
@@ -368,14 +460,14 @@ __global__ void proposal_bwd_kernel(PropArgs P)
         for (int i = 0; i < kPW; ++i) {
             float a = 0.0f;
 #pragma unroll
-            for (int b = 0; b < kPB; ++b) a = fmaf(W3[b * kPW + i], dl[b], a);
+            for (int b = 0; b < B; ++b) a = fmaf(W3[b * kPW + i], dl[b], a);
             dz2[i] = ((S.m2 >> i) & 1u) ? a : 0.0f;
         }
-#pragma unroll
+#pragma unroll 4
         for (int u = 0; u < kPW; ++u) {
             const float sb = warp_sum(dz2[u]);
             if (lane == 0) atomicAdd(gb2 + u, sb);
-#pragma unroll
+#pragma unroll 4
             for (int i = 0; i < kPW; ++i) {
                 const float v = warp_sum(dz2[u] * S.h1[i]);
                 if (lane == 0) atomicAdd(gW2 + u * kPW + i, v);
@@ -389,19 +481,19 @@ __global__ void proposal_bwd_kernel(PropArgs P)
             for (int u = 0; u < kPW; ++u) a = fmaf(W2[u * kPW + i], dz2[u], a);
             dz1[i] = ((S.m1 >> i) & 1u) ? a : 0.0f;
         }
-#pragma unroll
+#pragma unroll 4
         for (int u = 0; u < kPW; ++u) {
             const float sb = warp_sum(dz1[u]);
             if (lane == 0) atomicAdd(gb1 + u, sb);
 #pragma unroll
-            for (int i = 0; i < kPIn; ++i) {
+            for (int i = 0; i < kIn; ++i) {
                 const float v = warp_sum(dz1[u] * S.x[i]);
-                if (lane == 0) atomicAdd(gW1 + u * kPIn + i, v);
+                if (lane == 0) atomicAdd(gW1 + u * kIn + i, v);
             }
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kPParams; i += blockDim.x) red_add(P.grad + i, acc[i]);
+    for (int i = threadIdx.x; i < kParams; i += blockDim.x) red_add(P.grad + i, acc[i]);
 }
 
 int blocks_for(int64_t n, int threads, int cap)
@@ -420,16 +512,25 @@ int sm_count()
 
 }  // namespace
 
-int proposal_param_count() { return kPParams; }
-int proposal_bins() { return kPB; }
+int proposal_param_count(int n_bins)
+{
+    switch (n_bins) {
+        case 8: return PropShape<8>::kParams;
+        case 16: return PropShape<16>::kParams;
+        default: return 0;
+    }
+}
+bool proposal_bins_supported(int n_bins) { return n_bins == 8 || n_bins == 16; }
 int proposal_width() { return kPW; }
 
-cudaError_t launch_occupancy(const GridView& g, const int res[3], float threshold, float* occ,
-                             cudaStream_t stream)
+int occupancy_words(const int res[3]) { return (res[0] * res[1] * res[2] + 31) / 32; }
+
+cudaError_t launch_occupancy(const GridView& g, const int res[3], float threshold,
+                             uint32_t* bits, cudaStream_t stream)
 {
-    const int n = res[0] * res[1] * res[2];
-    occupancy_kernel<<<blocks_for(n, 128, 8 * sm_count()), 128, 0, stream>>>(
-        g, res[0], res[1], res[2], threshold, occ);
+    const int words = occupancy_words(res);
+    occupancy_kernel<<<blocks_for(int64_t(words) * 32, 128, 8 * sm_count()), 128, 0, stream>>>(
+        g, res[0], res[1], res[2], threshold, bits);
     return cudaGetLastError();
 }
 
@@ -441,12 +542,15 @@ cudaError_t launch_histogram(const RenderArgs& A, int n_bins, float* hist, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_proposal_forward(const ProposalLaunch& L, cudaStream_t stream)
+namespace {
+
+PropArgs prop_args(const ProposalLaunch& L)
 {
     PropArgs P;
     P.grid = L.grid;
     for (int a = 0; a < 3; ++a) P.occ_res[a] = L.occ_res[a];
-    P.occ = L.occ;
+    P.n_sub = L.n_sub;
+    P.occ_bits = L.occ_bits;
     P.params = L.params;
     P.mix = L.mix;
     P.theta = L.theta;
@@ -456,35 +560,55 @@ cudaError_t launch_proposal_forward(const ProposalLaunch& L, cudaStream_t stream
     P.n_out = L.n_out;
     P.t_samples = L.t_samples;
     P.probs = L.probs;
-    P.hist = nullptr;
-    P.grad = nullptr;
-    P.loss = nullptr;
-    proposal_fwd_kernel<<<blocks_for(L.n_rays, 128, 16 * sm_count()), 128, 0, stream>>>(P);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_proposal_backward(const ProposalLaunch& L, cudaStream_t stream)
-{
-    PropArgs P;
-    P.grid = L.grid;
-    for (int a = 0; a < 3; ++a) P.occ_res[a] = L.occ_res[a];
-    P.occ = L.occ;
-    P.params = L.params;
-    P.mix = L.mix;
-    P.theta = L.theta;
-    P.rays_o = L.rays_o;
-    P.rays_d = L.rays_d;
-    P.n_rays = L.n_rays;
-    P.n_out = 0;
-    P.t_samples = nullptr;
-    P.probs = nullptr;
     P.hist = L.hist;
     P.min_mass = L.min_mass;
     P.scale = L.scale;
     P.grad = L.grad;
     P.loss = L.loss;
-    proposal_bwd_kernel<<<blocks_for(L.n_rays, 128, 4 * sm_count()), 128, 0, stream>>>(P);
+    return P;
+}
+
+// Static parameter storage plus a bitmask of up to 32 KB can pass the 48 KB
+// default: opt in to the dynamic size the launch needs.
+template <class K>
+cudaError_t allow_smem(K kernel, size_t dynamic)
+{
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(dynamic));
+}
+
+template <int B>
+cudaError_t launch_fwd(const PropArgs& P, cudaStream_t stream)
+{
+    const size_t smem = sizeof(uint32_t) * occupancy_words(P.occ_res);
+    cudaError_t e = allow_smem(proposal_fwd_kernel<B>, smem);
+    if (e != cudaSuccess) return e;
+    proposal_fwd_kernel<B><<<blocks_for(P.n_rays, 128, 16 * sm_count()), 128, smem, stream>>>(P);
     return cudaGetLastError();
+}
+
+template <int B>
+cudaError_t launch_bwd(const PropArgs& P, cudaStream_t stream)
+{
+    const size_t smem = sizeof(uint32_t) * occupancy_words(P.occ_res);
+    cudaError_t e = allow_smem(proposal_bwd_kernel<B>, smem);
+    if (e != cudaSuccess) return e;
+    proposal_bwd_kernel<B><<<blocks_for(P.n_rays, 128, 4 * sm_count()), 128, smem, stream>>>(P);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_proposal_forward(const ProposalLaunch& L, cudaStream_t stream)
+{
+    const PropArgs P = prop_args(L);
+    return L.n_bins == 16 ? launch_fwd<16>(P, stream) : launch_fwd<8>(P, stream);
+}
+
+cudaError_t launch_proposal_backward(const ProposalLaunch& L, cudaStream_t stream)
+{
+    const PropArgs P = prop_args(L);
+    return L.n_bins == 16 ? launch_bwd<16>(P, stream) : launch_bwd<8>(P, stream);
 }
 
 }  // namespace psdf

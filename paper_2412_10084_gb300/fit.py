@@ -1,0 +1,141 @@
+"""Training loops on the library's kernels.
+
+fit_appearance: the scene's features, probes and MLP (optionally the SDF)
+are fitted to target colours with an L2 photometric loss, the render's
+forward and adjoint kernels and the library's Adam (Sec. 3.4; the paper's
+regularisers and coarse-to-fine schedule are left out: the loop exists to
+give synthetic scenes a non-trivial appearance).
+
+train_proposal: the learned sample proposal is trained on rays the method
+itself renders: its target is the per-bin histogram of the uniform march's
+weights w_k (Eqs. 8-10), its loss the cross-entropy against its softmax, its
+gradient the library's proposal adjoint, its optimiser the library's Adam.
+
+render_proposed: proposal placement followed by the render at those
+distances (inference).
+
+Torch supplies device memory, random batch indices and the loss's
+elementwise gradient; every render, adjoint, histogram and update step runs
+in the library.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import torch
+
+from . import (F32, Adam, LibraryError, RenderParams, Scene, occupancy_build, proposal_backward,
+               proposal_desc, proposal_forward, proposal_param_count, render_backward,
+               render_forward, render_params, weight_histogram)
+
+
+def _batch(gen, n_pool, batch, device):
+    return torch.randint(0, n_pool, (batch,), generator=gen, device=device)
+
+
+def fit_appearance(scene: Scene, rays_o, rays_d, target, params: RenderParams, steps=200,
+                   batch=1 << 14, lr_grid=1e-2, lr_probes=1e-2, lr_mlp=2e-3, train_sdf=False,
+                   seed=0, log_every=50):
+    """Fits an FP32-stored scene in place; returns [(step, mean L2 loss)]."""
+    if (scene.feat_dtype, scene.probe_dtype, scene.mlp_dtype) != (F32, F32, F32):
+        raise LibraryError("fit_appearance trains FP32 storage; convert afterwards")
+    dev = scene.grid.device
+    gg, gp, gm = scene.grad_buffers()
+    opt = Adam([(scene.grid.view(-1), gg.view(-1), lr_grid),
+                (scene.probes.view(-1), gp.view(-1), lr_probes),
+                (scene.mlp.view(-1), gm.view(-1), lr_mlp)])
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    n_pool = rays_o.shape[0]
+    log = []
+    for step in range(1, steps + 1):
+        idx = _batch(gen, n_pool, batch, dev)
+        o, d, tgt = rays_o[idx], rays_d[idx], target[idx]
+        rgb, _, _, logT = render_forward(scene, o, d, params)
+        diff = rgb - tgt
+        d_rgb = (2.0 / batch) * diff
+        render_backward(scene, o, d, params, d_rgb.contiguous(), logT, grads=(gg, gp, gm))
+        if not train_sdf:
+            gg[:, 0].zero_()
+        opt.step()
+        if step % log_every == 0 or step == steps:
+            log.append((step, float((diff * diff).sum(1).mean())))
+    return log
+
+
+@dataclasses.dataclass
+class Proposal:
+    """A learned sample proposal: its descriptor, FP32 parameters and the
+    coarse occupancy it reads."""
+    desc: object
+    params: torch.Tensor
+    occ: torch.Tensor
+
+    @classmethod
+    def create(cls, scene: Scene, init_params, occ_res=(32, 32, 32), voxels=2.0, mix=0.1,
+               theta=0.2, n_sub=8, n_bins=8):
+        """Occupancy from the scene's SDF with a threshold of `voxels` fine
+        voxel sizes; parameters copied from init_params (host or device)."""
+        desc = proposal_desc(occ_res, n_bins=n_bins, mix=mix, theta=theta, n_sub=n_sub)
+        n = proposal_param_count(desc)
+        p = torch.as_tensor(init_params, dtype=torch.float32).to(scene.grid.device).contiguous()
+        if p.numel() != n:
+            raise LibraryError(f"proposal parameters: expected {n}, got {p.numel()}")
+        vox = min((scene.box_max[a] - scene.box_min[a]) / (scene.dims[a] - 1) for a in range(3))
+        occ = occupancy_build(scene, occ_res, voxels * vox)
+        return cls(desc=desc, params=p, occ=occ)
+
+
+def train_proposal(scene: Scene, prop: Proposal, rays_o, rays_d, tau, n_uniform=256, steps=500,
+                   batch=1 << 14, lr=1e-2, lr_final=5e-4, min_mass=1e-3, seed=1, log_every=50):
+    """Trains prop.params in place on random batches of the ray pool (Adam,
+    cosine decay of the rate from lr to lr_final); returns [(step, mean of
+    the rays' normalised cross-entropy, mean over rays with mass)]."""
+    import math
+    dev = scene.grid.device
+    grad = torch.zeros_like(prop.params)
+    opt = Adam([(prop.params, grad, lr)])
+    params = render_params(tau, n_uniform)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    n_pool = rays_o.shape[0]
+    log = []
+    for step in range(1, steps + 1):
+        idx = _batch(gen, n_pool, batch, dev)
+        o, d = rays_o[idx], rays_d[idx]
+        hist = weight_histogram(scene, o, d, params, prop.desc.n_bins)
+        _, loss = proposal_backward(scene, prop.desc, prop.params, prop.occ, o, d, hist,
+                                    min_mass, 1.0 / batch, grad=grad,
+                                    want_loss=(step % log_every == 0 or step == steps))
+        rate = lr_final + 0.5 * (lr - lr_final) * (1.0 + math.cos(math.pi * (step - 1) / steps))
+        opt.groups[0] = opt.groups[0][:2] + (rate,) + opt.groups[0][3:]
+        opt.step()
+        if loss is not None:
+            mass = hist.sum(1)
+            valid = mass >= min_mass
+            ce = (loss[valid] / mass[valid]).mean() if bool(valid.any()) else torch.zeros(())
+            log.append((step, float(ce)))
+    return log
+
+
+def render_proposed(scene: Scene, prop: Proposal, rays_o, rays_d, n_out, params: RenderParams):
+    """(rgb, depth, wsum, logT) of the render at proposal-placed distances
+    (n_out colour samples per ray; params.n_samples is replaced by n_out)."""
+    t, _ = proposal_forward(scene, prop.desc, prop.params, prop.occ, rays_o, rays_d, n_out,
+                            want_probs=False)
+    p = render_params(params.tau, n_out, params.dir_mode, params.n_fresnel, tuple(params.bg))
+    return render_forward(scene, rays_o, rays_d, p, t)
+
+
+def reduced_copy(scene: Scene, feat_dtype, probe_dtype, mlp_dtype) -> Scene:
+    """The same parameters in reduced-precision storage (BF16 features,
+    FP16 probes, FP16 MLP arithmetic), converted once on the device."""
+    from . import grid_desc, pack_grid, unpack_grid
+    gd32 = grid_desc(scene.dims, scene.box_min, scene.box_max, scene.n_feat, scene.feat_dtype)
+    sdf, feat = unpack_grid(gd32, scene.grid)
+    gd = grid_desc(scene.dims, scene.box_min, scene.box_max, scene.n_feat, feat_dtype)
+    grid = pack_grid(gd, sdf, feat)
+    probes = scene.probes.half() if probe_dtype != F32 else scene.probes.float()
+    return dataclasses.replace(scene, grid=grid, probes=probes.contiguous(),
+                               mlp=scene.mlp.clone(), feat_dtype=feat_dtype,
+                               probe_dtype=probe_dtype, mlp_dtype=mlp_dtype)

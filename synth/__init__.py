@@ -153,28 +153,33 @@ def _torch_smin(a, b, k):
     return torch.minimum(a, b) - h * h * k * 0.25
 
 
+def _object_dist(P, shapes, k=0.05):
+    """Smooth-min union distance at points P [..., 3] (torch FP64)."""
+    import torch
+    acc = None
+    for kind, c, prm in shapes:
+        q = P - torch.as_tensor(c, dtype=torch.float64)
+        if kind == "sphere":
+            dist = q.norm(dim=-1) - prm
+        else:
+            radii, e, Rm = prm
+            ql = (q @ torch.as_tensor(Rm, dtype=torch.float64)) / torch.as_tensor(radii)
+            f = ql.abs().pow(e).sum(-1).pow(1.0 / e)
+            dist = (f - 1.0) * float(radii.min())
+        acc = dist if acc is None else _torch_smin(acc, dist, k)
+    return acc
+
+
 def object_sdf(dims, box_min, box_max, shapes, k=0.05, slab=16):
     """Smooth-min (polynomial, k) union of spheres and superquadrics.  The
     superquadric uses the usual implicit-function distance approximation.
     Evaluated with torch on the host (multithreaded), FP64, stored FP32."""
-    import torch
     Rx, Ry, Rz = dims
     out = np.empty((Rz, Ry, Rx), np.float32)
     for z0 in range(0, Rz, slab):
         z1 = min(Rz, z0 + slab)
         P = _torch_coords(dims, box_min, box_max, z0, z1)
-        acc = None
-        for kind, c, prm in shapes:
-            q = P - torch.as_tensor(c, dtype=torch.float64)
-            if kind == "sphere":
-                dist = q.norm(dim=-1) - prm
-            else:
-                radii, e, Rm = prm
-                ql = (q @ torch.as_tensor(Rm, dtype=torch.float64)) / torch.as_tensor(radii)
-                f = ql.abs().pow(e).sum(-1).pow(1.0 / e)
-                dist = (f - 1.0) * float(radii.min())
-            acc = dist if acc is None else _torch_smin(acc, dist, k)
-        out[z0:z1] = acc.numpy().astype(np.float32)
+        out[z0:z1] = _object_dist(P, shapes, k).numpy().astype(np.float32)
     return out
 
 
@@ -298,7 +303,8 @@ def image_rays(cam, width, height, fov_deg):
     dd = fwd + sx[..., None] * right + sy[..., None] * cup
     dd /= np.linalg.norm(dd, axis=-1, keepdims=True)
     o = np.broadcast_to(p, dd.shape)
-    return o.reshape(-1, 3).astype(np.float32), dd.reshape(-1, 3).astype(np.float32)
+    return (np.ascontiguousarray(o.reshape(-1, 3), dtype=np.float32),
+            np.ascontiguousarray(dd.reshape(-1, 3), dtype=np.float32))
 
 
 # ----------------------------------------------------------------------------
@@ -384,5 +390,103 @@ def random_unit_vectors(n, g):
 
 
 def proposal_params(g: np.random.Generator, width: int = 32, n_bins: int = 8) -> np.ndarray:
-    """Xavier-uniform initial parameters of the proposal MLP (6 + B -> W -> W -> B)."""
-    return mlp_params(6 + n_bins, width, g, n_out=n_bins)
+    """Xavier-uniform initial parameters of the proposal MLP (7 + 2B -> W -> W -> B)."""
+    return mlp_params(7 + 2 * n_bins, width, g, n_out=n_bins)
+
+
+# ----------------------------------------------------------------------------
+# Teacher images and novel views (appearance fitting and the inference test)
+# ----------------------------------------------------------------------------
+
+def workload_shapes(name: str):
+    """The procedural shapes of an object-style workload (the first draws of
+    its scene generator)."""
+    spec = WORKLOADS[name]
+    if name not in ("object256", "stress512"):
+        raise KeyError(f"{name} has no object shapes")
+    return object_shapes(rng(spec["seed"]), 32)
+
+
+_ALBEDO_FREQ = np.array([[3.1, -1.7, 2.3], [-2.2, 2.9, 1.3], [1.4, 2.1, -3.3]])
+_ALBEDO_PHASE = np.array([0.3, 1.9, 4.1])
+_LIGHT = np.array([0.48, 0.36, 0.8]) / np.linalg.norm([0.48, 0.36, 0.8])
+
+
+def teacher_colors(name: str, rays_o, rays_d, max_iter=160, chunk=1 << 16):
+    """Teacher RGB of each ray: the first hit of the workload's analytic SDF
+    (sphere tracing at 0.8 of the distance, inside the box), shaded by a
+    procedural 3D albedo x (ambient + Lambert) plus a white Phong lobe; rays
+    that miss get 0 (the render's black background).  FP64 on the host."""
+    import torch
+    spec = WORKLOADS[name]
+    shapes = workload_shapes(name)
+    bmin = np.array(spec["box"][0], float)
+    bmax = np.array(spec["box"][1], float)
+    o_all = np.asarray(rays_o, np.float64).reshape(-1, 3)
+    d_all = np.asarray(rays_d, np.float64).reshape(-1, 3)
+    out = np.zeros((o_all.shape[0], 3))
+    for c0 in range(0, o_all.shape[0], chunk):
+        o = o_all[c0:c0 + chunk]
+        d = d_all[c0:c0 + chunk]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            inv = 1.0 / d
+            t0 = (bmin - o) * inv
+            t1 = (bmax - o) * inv
+        tn = np.maximum(np.nanmax(np.minimum(t0, t1), axis=1), 0.0)
+        tf = np.nanmin(np.maximum(t0, t1), axis=1)
+        t = tn.copy()
+        active = tf > tn
+        hit = np.zeros(o.shape[0], bool)
+        for _ in range(max_iter):
+            idx = np.nonzero(active)[0]
+            if idx.size == 0:
+                break
+            P = torch.as_tensor(o[idx] + t[idx, None] * d[idx])
+            s = _object_dist(P, shapes).numpy()
+            done = s < 1e-5
+            hit[idx[done]] = True
+            t[idx] += np.where(done, 0.0, 0.8 * np.maximum(s, 1e-5))
+            active[idx[done]] = False
+            active[idx[t[idx] > tf[idx]]] = False
+        idx = np.nonzero(hit)[0]
+        if idx.size == 0:
+            continue
+        x = o[idx] + t[idx, None] * d[idx]
+        h = 1e-5
+        n = np.zeros_like(x)
+        for a in range(3):
+            e = np.zeros(3)
+            e[a] = h
+            n[:, a] = (_object_dist(torch.as_tensor(x + e), shapes).numpy() -
+                       _object_dist(torch.as_tensor(x - e), shapes).numpy())
+        n /= np.maximum(np.linalg.norm(n, axis=1, keepdims=True), 1e-12)
+        albedo = 0.5 + 0.4 * np.sin(2 * math.pi * x @ _ALBEDO_FREQ.T + _ALBEDO_PHASE)
+        lam = np.maximum(n @ _LIGHT, 0.0)
+        v = -d[idx]
+        r = 2 * np.sum(n * v, 1, keepdims=True) * n - v
+        spec_ = 0.25 * np.maximum(r @ _LIGHT, 0.0) ** 16
+        out[c0 + idx] = np.clip(albedo * (0.25 + 0.75 * lam[:, None]) + spec_[:, None], 0.0, 1.0)
+    return out.astype(np.float32)
+
+
+def novel_cameras(name: str, n_views: int = 8):
+    """Views off the training rig: a ring at 30 degrees elevation, radius
+    1.15x the training radius, rotated half a step from the training
+    azimuths."""
+    spec = WORKLOADS[name]
+    bmin = np.array(spec["box"][0], float)
+    bmax = np.array(spec["box"][1], float)
+    center = 0.5 * (bmin + bmax)
+    r = 1.15 * spec["cam_r"]
+    el = math.radians(30.0)
+    az = 2 * math.pi * (np.arange(n_views) + 0.37) / n_views
+    pos = center + r * np.stack([math.cos(el) * np.cos(az), math.cos(el) * np.sin(az),
+                                 np.full(n_views, math.sin(el))], -1)
+    return look_at_cameras(pos, center)
+
+
+def training_pool(name: str, n_rays: int, seed_offset: int = 0):
+    """Random pixel rays of the workload's training cameras with their
+    teacher colours (Rays with target = teacher RGB)."""
+    r = make_rays(name, n_rays=n_rays, seed_offset=seed_offset)
+    return Rays(o=r.o, d=r.d, target=teacher_colors(name, r.o, r.d))

@@ -535,10 +535,12 @@ def _proposal_fixture(seed=81, logit_scale=1.0):
     return sc, m, occ, params
 
 
-def test_proposal_uniform_density_gives_uniform_quantiles():
+@pytest.mark.parametrize("occ_fill", [0.0, 1.0])
+def test_proposal_uniform_density_gives_uniform_quantiles(occ_fill):
     sc, m, occ, params = _proposal_fixture()
     params[-8 - 8 * 32:] = 0.0  # W3 = 0, b3 = 0: every logit 0
-    prop = oracle.Proposal(occ, params, mix=0.1, theta=0.0)
+    # no bin occupied, or every bin: the mix share is uniform as well
+    prop = oracle.Proposal(np.full_like(occ, occ_fill), params, mix=0.1, theta=0.0)
     o, d = rays_into_box(40, 82)
     out = oracle.proposal_forward(m, prop, o, d, 24)
     np.testing.assert_allclose(out["probs"], 1.0 / 8, atol=1e-15)
@@ -569,7 +571,7 @@ def test_proposal_quantile_placement_follows_density():
         # the piecewise-linear CDF of the bin density reaches k / n_out at t_k
         cdf = np.interp(t, edges, np.concatenate([[0.0], np.cumsum(out["probs"][i])]))
         np.testing.assert_allclose(cdf, np.arange(n_out + 1) / n_out, atol=1e-6)
-        assert abs(out["probs"][i].sum() - 1) < 1e-12 and out["probs"][i].min() >= 0.1 / 8 - 1e-15
+        assert abs(out["probs"][i].sum() - 1) < 1e-12 and out["probs"][i].min() >= 0.1 / 32 - 1e-15
 
 
 def test_weight_histogram_sums_to_wsum():
@@ -620,3 +622,57 @@ def test_proposal_gradient_central_differences():
         flat[i] = old
         fd = 0.5 * (lp - lm) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * np.abs(g).max() + 1e-9, (i, fd, g[i])
+
+
+def _passthrough_params(B, pick):
+    """Proposal weights whose logits equal its occupancy inputs (all >= 0, so
+    the ReLUs pass them): the bin fractions (pick "frac"), the step inputs
+    ("step"), or the first-position input in logit 0 ("first")."""
+    W, nin = 32, 7 + 2 * B
+    W1 = np.zeros((W, nin))
+    first_col = {"frac": 7, "step": 7 + B, "first": 6}[pick]
+    for u in range(B if pick != "first" else 1):
+        W1[u, first_col + u] = 1.0
+    W2 = np.eye(W)
+    W3 = np.zeros((B, W))
+    for b in range(B if pick != "first" else 1):
+        W3[b, b] = 1.0
+    return np.concatenate([W1.ravel(), np.zeros(W), W2.ravel(), np.zeros(W), W3.ravel(),
+                           np.zeros(B)])
+
+
+@pytest.mark.parametrize("B,n_sub,res", [(8, 3, (4, 5, 3)), (16, 2, (7, 7, 7))])
+def test_proposal_occupancy_inputs_brute_force(B, n_sub, res):
+    sc = tiny_scene(R=(16, 16, 16), P=(4, 4, 4))
+    m = oracle.Model.from_scene(sc)
+    g = synth.rng(88 + B)
+    occ = (g.uniform(size=res[::-1]) < 0.3).astype(np.float64)
+    o, d = rays_into_box(60, 89 + B)
+    fr, fi, fs = (oracle.proposal_forward(m, oracle.Proposal(occ, _passthrough_params(B, k),
+                                                             n_bins=B, n_sub=n_sub), o, d, 4)
+                  for k in ("frac", "first", "step"))
+    bmin = np.asarray(sc.box_min, np.float64)
+    ext = np.asarray(sc.box_max, np.float64) - bmin
+    checked = 0
+    for i in range(60):
+        tn, tf = fr["t"][i, 0], fr["t"][i, -1]
+        if not tf > tn:
+            continue
+        k = np.arange(B * n_sub)
+        t = tn + (k + 0.5) * (tf - tn) / (B * n_sub)
+        u = (o[i].astype(np.float64) + t[:, None] * d[i].astype(np.float64) - bmin) / ext * res
+        r = np.round(u)
+        inner = (r >= 1) & (r <= np.array(res) - 1)  # the faces between two cells
+        if np.any(inner & (np.abs(u - r) < 1e-4)):
+            continue  # a point on a cell face: its cell is decided by FP32 rounding
+        c = np.floor(np.clip(u, 0, np.array(res) - 1)).astype(int)
+        hit = occ[c[:, 2], c[:, 1], c[:, 0]] > 0.5
+        frac = hit.reshape(B, n_sub).mean(1)
+        first = (np.argmax(hit) + 0.5) / (B * n_sub) if hit.any() else 1.0
+        np.testing.assert_allclose(fr["logits"][i], frac, atol=1e-12)
+        assert abs(fi["logits"][i, 0] - first) < 1e-12
+        # share of each bin before the first occupied point
+        before = np.array([np.clip(first * B - b, 0.0, 1.0) for b in range(B)])
+        np.testing.assert_allclose(fs["logits"][i], before, atol=1e-12)
+        checked += 1
+    assert checked > 20
