@@ -37,6 +37,8 @@ struct BwdLayout {
     static constexpr int kDZ = 128 * DZC * 2;
     static constexpr uint32_t kSboXH = (XHC / 8) * 128;
     static constexpr uint32_t kSboDZ = (DZC / 8) * 128;
+    static constexpr int kDZWarp = 4 * kSboDZ;  // bytes of a warp's 32 rows of a DZ tile
+    static_assert(32 * C::W * 4 <= kDZWarp, "h2 staging fits the warp's rows of the DZ tile");
     static constexpr int PST = ((8 + C::L2 + C::NA + 1) + 3) & ~3;  // probe staging row (floats)
     static constexpr int kParamsPad = (C::kParams + 3) & ~3;
     static constexpr int oW = 0;
@@ -56,23 +58,6 @@ __device__ __forceinline__ float warp_max(float v)
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
     return v;
-}
-
-// Reduce-scatter of 16 elements over the warp: on return lane l holds the
-// warp sum of element (l % 16).
-__device__ __forceinline__ float reduce_scatter16(float* v, int lane)
-{
-#pragma unroll
-    for (int m = 8, half = 8; m > 0; m >>= 1, half >>= 1) {
-        const bool upper = (lane & m) != 0;
-#pragma unroll
-        for (int j = 0; j < half; ++j) {
-            const float send = upper ? v[j] : v[j + half];
-            const float keep = upper ? v[j + half] : v[j];
-            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, m);
-        }
-    }
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
 }
 
 // Probe-coefficient gradient (Eqs. 6-7): dL/db_ijc = sum_k w_i(k) Y_j(k) dF_a,c(k).
@@ -97,14 +82,26 @@ __device__ __forceinline__ void scatter_probe_grad(const RenderArgs& A, const fl
 #pragma unroll
         for (int j = 0; j < L2; ++j) acc[m][j] = 0.f;
     }
+    static_assert(PST % 4 == 0, "rows of whole 16-byte vectors");
+    constexpr int L2V = (L2 + 3) / 4;  // Y_j starts at float 8: 16-byte aligned
+    static_assert(8 + 4 * L2V <= PST, "vector reads stay inside the row");
+    int cell = nact > 0 ? __float_as_int(pst[8 + L2 + NA]) : -1;
     for (int s = 0; s < nact; ++s) {
         const float* row = pst + s * PST;
-        const int cell = __float_as_int(row[8 + L2 + NA]);
+        float Y[4 * L2V];
+#pragma unroll
+        for (int v = 0; v < L2V; ++v) {
+            const float4 y4 = *reinterpret_cast<const float4*>(row + 8 + 4 * v);
+            Y[4 * v + 0] = y4.x;
+            Y[4 * v + 1] = y4.y;
+            Y[4 * v + 2] = y4.z;
+            Y[4 * v + 3] = y4.w;
+        }
 #pragma unroll
         for (int m = 0; m < CPL; ++m) {
             const float coef = row[q[m]] * row[8 + L2 + ch[m]];
 #pragma unroll
-            for (int j = 0; j < L2; ++j) acc[m][j] = fmaf(coef, row[8 + j], acc[m][j]);
+            for (int j = 0; j < L2; ++j) acc[m][j] = fmaf(coef, Y[j], acc[m][j]);
         }
         const int next = s + 1 < nact ? __float_as_int(pst[(s + 1) * PST + 8 + L2 + NA]) : -1;
         if (next != cell) {
@@ -118,6 +115,7 @@ __device__ __forceinline__ void scatter_probe_grad(const RenderArgs& A, const fl
                 }
             }
         }
+        cell = next;
     }
 }
 
@@ -371,18 +369,47 @@ render_backward_kernel(RenderArgs A)
             float dz3[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) dz3[c] = w * drgb[c] * col[c] * (1.0f - col[c]);
-            // dW3 and db3 on the CUDA cores: warp reduce-scatter of dz3 (x) h2 in
-            // 16-column slices; lane l accumulates column 16 * (l / 16) + l % 16
+            // dW3 and db3 on the CUDA cores.  The warp's rows of the DZ tiles
+            // are free until its dz2 row is stored below: h2 goes there
+            // transposed (16-byte groups XOR-swizzled by row, so that both the
+            // row writes and the column reads are free of bank conflicts) and
+            // lane l sums column l of dz3 (x) h2 over the warp's 32 samples.
+            {
+                float* h2s = reinterpret_cast<float*>(dzh + warp * L::kDZWarp);
+#pragma unroll
+                for (int v = 0; v < W / 4; ++v)
+                    *reinterpret_cast<float4*>(h2s + lane * W + 4 * (v ^ (lane & (W / 4 - 1)))) =
+                        make_float4(h2[4 * v], h2[4 * v + 1], h2[4 * v + 2], h2[4 * v + 3]);
+                float* d3s = nullptr;
+                if constexpr (M::kSplit == 2) {
+                    d3s = reinterpret_cast<float*>(dzl + warp * L::kDZWarp);
+                    *reinterpret_cast<float4*>(d3s + 4 * lane) =
+                        make_float4(dz3[0], dz3[1], dz3[2], 0.0f);
+                }
+                __syncwarp();
+                const int col_l = lane & (W - 1);
+#pragma unroll 8
+                for (int r = 0; r < 32; ++r) {
+                    const float h = h2s[r * W + 4 * ((col_l >> 2) ^ (r & (W / 4 - 1))) + (col_l & 3)];
+                    float e0, e1, e2;
+                    if constexpr (M::kSplit == 2) {
+                        const float4 e = *reinterpret_cast<const float4*>(d3s + 4 * r);
+                        e0 = e.x;
+                        e1 = e.y;
+                        e2 = e.z;
+                    } else {
+                        e0 = __shfl_sync(FULL, dz3[0], r);
+                        e1 = __shfl_sync(FULL, dz3[1], r);
+                        e2 = __shfl_sync(FULL, dz3[2], r);
+                    }
+                    acc3[0] = fmaf(e0, h, acc3[0]);
+                    acc3[1] = fmaf(e1, h, acc3[1]);
+                    acc3[2] = fmaf(e2, h, acc3[2]);
+                }
+                __syncwarp();
+            }
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-#pragma unroll
-                for (int hs = 0; hs < W / 16; ++hs) {
-                    float v[16];
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] = dz3[c] * h2[16 * hs + i];
-                    const float r = reduce_scatter16(v, lane);
-                    if ((lane >> 4) == hs) acc3[c] += r;
-                }
                 float sb = dz3[c];
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) sb += __shfl_xor_sync(FULL, sb, off);
@@ -582,7 +609,7 @@ done:
                 gacc[C::gB2 + (r - W)] += v[NIN] * inv_s2;
             }
         }
-        if (lane < W) {  // lane l holds column l (16-column slices, see P2)
+        if (lane < W) {  // lane l holds column l (see P2)
 #pragma unroll
             for (int c = 0; c < 3; ++c) atomicAdd(gacc + C::gW3 + c * W + lane, acc3[c]);
         }
