@@ -340,7 +340,7 @@ def run_ours(args, world, rank, local):
         if record:
             e0 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-        rgb, depth, wsum, logT = ps.render_forward(scene, o, d, params)
+        rgb, depth, wsum, logT, live = ps.render_forward(scene, o, d, params, want_live=True)
         if record:
             e1 = torch.cuda.Event(enable_timing=True)
             e1.record(stream)
@@ -348,7 +348,7 @@ def run_ours(args, world, rank, local):
         if record:
             e2 = torch.cuda.Event(enable_timing=True)
             e2.record(stream)
-        ps.render_backward(scene, o, d, params, d_rgb, logT, grads=(gg, gp, gm))
+        ps.render_backward(scene, o, d, params, d_rgb, logT, grads=(gg, gp, gm), n_live=live)
         if record:
             e3 = torch.cuda.Event(enable_timing=True)
             e3.record(stream)

@@ -168,13 +168,18 @@ void psdf_mlp_destroy(psdf_mlp* mlp);
  *   depth          : device FP32 [n_rays]    = sum_k w_k t_k
  *   wsum           : device FP32 [n_rays]    = sum_k w_k
  *   logT_final     : device FP32 [n_rays]    = log T_N, needed by the backward
+ *   n_live         : device int32 [n_rays] or NULL: 1 + the index of the ray's
+ *                    last sample with a nonzero opacity alpha_k (0 when none
+ *                    is, or the ray misses); lets the backward skip the
+ *                    samples after it, whose adjoint terms are all zero
  * Rays that miss the box give rgb = bg and zeros elsewhere.  n_rays = 0 is a
  * valid no-op. */
 psdf_status psdf_render_forward(const psdf_grid* grid, const psdf_probes* probes,
                                 const psdf_mlp* mlp, const psdf_render_params* params,
                                 const float* rays_o, const float* rays_d,
                                 const float* t_samples, int64_t n_rays, float* rgb,
-                                float* depth, float* wsum, float* logT_final, void* stream);
+                                float* depth, float* wsum, float* logT_final, int32_t* n_live,
+                                void* stream);
 
 /* Adjoint of psdf_render_forward (Sec. 3.3-3.4: gradients for the SDF
  * values, spatial features, probe coefficients and MLP weights).  The
@@ -182,6 +187,8 @@ psdf_status psdf_render_forward(const psdf_grid* grid, const psdf_probes* probes
  *   d_rgb          : device FP32 [n_rays][3] (required)
  *   d_depth, d_wsum: device FP32 [n_rays] or NULL (= zero)
  *   logT_final     : the forward's output for the same inputs
+ *   n_live         : the forward's n_live for the same inputs, or NULL (every
+ *                    sample of every ray is visited)
  *   grad_grid      : device FP32, grad_bytes of psdf_grid_bytes, {dsdf, df0..2} per node
  *   grad_probes    : device FP32 [Pz][Py][Px][l*l][n_a] (FP32 whatever the storage)
  *   grad_mlp       : device FP32 [psdf_mlp_param_count]
@@ -193,8 +200,9 @@ psdf_status psdf_render_backward(const psdf_grid* grid, const psdf_probes* probe
                                  const float* rays_o, const float* rays_d,
                                  const float* t_samples, int64_t n_rays, const float* d_rgb,
                                  const float* d_depth, const float* d_wsum,
-                                 const float* logT_final, float* grad_grid,
-                                 float* grad_probes, float* grad_mlp, void* stream);
+                                 const float* logT_final, const int32_t* n_live,
+                                 float* grad_grid, float* grad_probes, float* grad_mlp,
+                                 void* stream);
 
 /* Resident CTAs per SM that psdf_render_forward / psdf_render_backward launch
  * with for these objects (each CTA renders 4 rays at a time).  Host query,

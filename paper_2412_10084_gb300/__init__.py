@@ -101,9 +101,9 @@ def library() -> ctypes.CDLL:
         lib.psdf_mlp_destroy.argtypes = [_P]
         lib.psdf_mlp_destroy.restype = None
         lib.psdf_render_forward.argtypes = [_P, _P, _P, _P, _P, _P, _P, ctypes.c_int64,
-                                            _P, _P, _P, _P, _P]
+                                            _P, _P, _P, _P, _P, _P]
         lib.psdf_render_backward.argtypes = [_P, _P, _P, _P, _P, _P, _P, ctypes.c_int64,
-                                             _P, _P, _P, _P, _P, _P, _P, _P]
+                                             _P, _P, _P, _P, _P, _P, _P, _P, _P]
         lib.psdf_render_occupancy.argtypes = [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_int32),
                                               ctypes.POINTER(ctypes.c_int32)]
         lib.psdf_adam_step.argtypes = [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_float,
@@ -321,8 +321,10 @@ class _Handles:
 
 
 def render_forward(scene: Scene, rays_o, rays_d, params: RenderParams, t_samples=None,
-                   grid=None, probes=None, mlp=None):
-    """-> rgb [n,3], depth [n], wsum [n], logT_final [n] (device FP32)."""
+                   grid=None, probes=None, mlp=None, want_live=False):
+    """-> rgb [n,3], depth [n], wsum [n], logT_final [n] (device FP32), and
+    with want_live n_live [n] (int32: 1 + the last sample with a nonzero
+    opacity), which lets render_backward skip the samples after it."""
     grid = scene.grid if grid is None else grid
     probes = scene.probes if probes is None else probes
     mlp = scene.mlp if mlp is None else mlp
@@ -334,27 +336,33 @@ def render_forward(scene: Scene, rays_o, rays_d, params: RenderParams, t_samples
     depth = torch.empty(n, dtype=torch.float32, device=dev)
     wsum = torch.empty(n, dtype=torch.float32, device=dev)
     logT = torch.empty(n, dtype=torch.float32, device=dev)
+    live = torch.empty(n, dtype=torch.int32, device=dev) if want_live else None
     gd, pd, md = scene.descs(params.n_fresnel)
     h = _Handles(grid, probes, mlp, gd, pd, md)
     try:
         _check(library().psdf_render_forward(h.g, h.p, h.m, ctypes.byref(params), _ptr(rays_o),
                                              _ptr(rays_d), _ptr(t_samples), n, _ptr(rgb),
-                                             _ptr(depth), _ptr(wsum), _ptr(logT), _stream()),
+                                             _ptr(depth), _ptr(wsum), _ptr(logT), _ptr(live),
+                                             _stream()),
                "psdf_render_forward")
     finally:
         h.close()
+    if want_live:
+        return rgb, depth, wsum, logT, live
     return rgb, depth, wsum, logT
 
 
 def render_backward(scene: Scene, rays_o, rays_d, params: RenderParams, d_rgb, logT,
                     d_depth=None, d_wsum=None, t_samples=None, grads=None, grid=None,
-                    probes=None, mlp=None):
-    """Accumulates into (and returns) grad_grid [R^3,4], grad_probes, grad_mlp."""
+                    probes=None, mlp=None, n_live=None):
+    """Accumulates into (and returns) grad_grid [R^3,4], grad_probes, grad_mlp.
+    n_live: the forward's per-ray live extent (optional)."""
     grid = scene.grid if grid is None else grid
     probes = scene.probes if probes is None else probes
     mlp = scene.mlp if mlp is None else mlp
     _require_cuda(grid, probes, mlp, dtypes=(torch.float32, torch.float16, torch.uint8))
     _require_cuda(rays_o, rays_d, t_samples, d_rgb, d_depth, d_wsum, logT)
+    _require_cuda(n_live, dtypes=(torch.int32,))
     if grads is None:
         grads = scene.grad_buffers()
     _require_cuda(*grads)
@@ -364,8 +372,8 @@ def render_backward(scene: Scene, rays_o, rays_d, params: RenderParams, d_rgb, l
     try:
         _check(library().psdf_render_backward(
             h.g, h.p, h.m, ctypes.byref(params), _ptr(rays_o), _ptr(rays_d), _ptr(t_samples),
-            rays_o.shape[0], _ptr(d_rgb), _ptr(d_depth), _ptr(d_wsum), _ptr(logT), _ptr(gg),
-            _ptr(gp), _ptr(gm), _stream()), "psdf_render_backward")
+            rays_o.shape[0], _ptr(d_rgb), _ptr(d_depth), _ptr(d_wsum), _ptr(logT), _ptr(n_live),
+            _ptr(gg), _ptr(gp), _ptr(gm), _stream()), "psdf_render_backward")
     finally:
         h.close()
     return gg, gp, gm
@@ -393,26 +401,27 @@ class RenderFunction(torch.autograd.Function):
     records and [Pz,Py,Px,l*l,n_a]) when the scene stores BF16 features or
     FP16 probes; the kernels read the scene's storage either way.  The
     backward recomputes per-sample activations in the library's adjoint
-    kernel; only log T_N per ray is saved."""
+    kernel; only log T_N and the live extent per ray are saved."""
 
     @staticmethod
     def forward(ctx, grid_p, probes_p, mlp, rays_o, rays_d, t_samples, scene, params):
         grid = grid_p if scene.feat_dtype == F32 else scene.grid
         probes = probes_p if scene.probe_dtype == F32 else scene.probes
-        rgb, depth, wsum, logT = render_forward(scene, rays_o, rays_d, params, t_samples,
-                                                grid=grid, probes=probes, mlp=mlp)
-        ctx.save_for_backward(mlp, rays_o, rays_d, logT,
+        rgb, depth, wsum, logT, live = render_forward(scene, rays_o, rays_d, params, t_samples,
+                                                      grid=grid, probes=probes, mlp=mlp,
+                                                      want_live=True)
+        ctx.save_for_backward(mlp, rays_o, rays_d, logT, live,
                               t_samples if t_samples is not None else torch.empty(0))
         ctx.storage = (grid, probes)
         ctx.has_t = t_samples is not None
         ctx.scene = scene
         ctx.params = params
-        ctx.mark_non_differentiable(logT)
+        ctx.mark_non_differentiable(logT, live)
         return rgb, depth, wsum
 
     @staticmethod
     def backward(ctx, d_rgb, d_depth, d_wsum):
-        mlp, rays_o, rays_d, logT, t_samples = ctx.saved_tensors
+        mlp, rays_o, rays_d, logT, live, t_samples = ctx.saved_tensors
         grid, probes = ctx.storage
         t_samples = t_samples if ctx.has_t else None
         d_rgb = torch.zeros((rays_o.shape[0], 3), dtype=torch.float32, device=rays_o.device) \
@@ -421,7 +430,7 @@ class RenderFunction(torch.autograd.Function):
         d_wsum = None if d_wsum is None else d_wsum.contiguous()
         gg, gp, gm = render_backward(ctx.scene, rays_o, rays_d, ctx.params, d_rgb, logT,
                                      d_depth=d_depth, d_wsum=d_wsum, t_samples=t_samples,
-                                     grid=grid, probes=probes, mlp=mlp)
+                                     grid=grid, probes=probes, mlp=mlp, n_live=live)
         return gg, gp, gm, None, None, None, None, None
 
 

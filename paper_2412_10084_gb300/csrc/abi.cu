@@ -470,19 +470,22 @@ psdf_status psdf_render_forward(const psdf_grid* grid, const psdf_probes* probes
                                 const psdf_mlp* mlp, const psdf_render_params* params,
                                 const float* rays_o, const float* rays_d,
                                 const float* t_samples, int64_t n_rays, float* rgb,
-                                float* depth, float* wsum, float* logT_final, void* stream)
+                                float* depth, float* wsum, float* logT_final, int32_t* n_live,
+                                void* stream)
 {
     Resolved r;
     psdf_status st = resolve(grid, probes, mlp, params, rays_o, rays_d, t_samples, n_rays, r);
     if (st != PSDF_OK) return st;
     if (n_rays > 0 && (!rgb || !depth || !wsum || !logT_final)) return PSDF_ERR_INVALID_ARG;
-    if (!aligned16(rgb) || !aligned16(depth) || !aligned16(wsum) || !aligned16(logT_final))
+    if (!aligned16(rgb) || !aligned16(depth) || !aligned16(wsum) || !aligned16(logT_final) ||
+        !aligned16(n_live))
         return PSDF_ERR_MISALIGNED;
     if (n_rays == 0) return PSDF_OK;
     r.args.rgb = rgb;
     r.args.depth = depth;
     r.args.wsum = wsum;
     r.args.logT = logT_final;
+    r.args.n_live = n_live;
     int per_sm = 0;
     st = cuda_status(psdf::forward_ctas_per_sm(r.shape, &per_sm));
     if (st != PSDF_OK) return st;
@@ -496,8 +499,9 @@ psdf_status psdf_render_backward(const psdf_grid* grid, const psdf_probes* probe
                                  const float* rays_o, const float* rays_d,
                                  const float* t_samples, int64_t n_rays, const float* d_rgb,
                                  const float* d_depth, const float* d_wsum,
-                                 const float* logT_final, float* grad_grid,
-                                 float* grad_probes, float* grad_mlp, void* stream)
+                                 const float* logT_final, const int32_t* n_live,
+                                 float* grad_grid, float* grad_probes, float* grad_mlp,
+                                 void* stream)
 {
     Resolved r;
     psdf_status st = resolve(grid, probes, mlp, params, rays_o, rays_d, t_samples, n_rays, r);
@@ -505,11 +509,12 @@ psdf_status psdf_render_backward(const psdf_grid* grid, const psdf_probes* probe
     if (!grad_grid || !grad_probes || !grad_mlp) return PSDF_ERR_INVALID_ARG;
     if (n_rays > 0 && (!d_rgb || !logT_final)) return PSDF_ERR_INVALID_ARG;
     if (!aligned16(d_rgb) || !aligned16(d_depth) || !aligned16(d_wsum) ||
-        !aligned16(logT_final) || !aligned16(grad_grid) || !aligned16(grad_probes) ||
-        !aligned16(grad_mlp))
+        !aligned16(logT_final) || !aligned16(n_live) || !aligned16(grad_grid) ||
+        !aligned16(grad_probes) || !aligned16(grad_mlp))
         return PSDF_ERR_MISALIGNED;
     if (n_rays == 0) return PSDF_OK;
     r.args.logT = const_cast<float*>(logT_final);
+    r.args.n_live = const_cast<int32_t*>(n_live);
     r.args.d_rgb = d_rgb;
     r.args.d_depth = d_depth;
     r.args.d_wsum = d_wsum;

@@ -62,14 +62,18 @@ __device__ __forceinline__ float warp_max(float v)
 
 // Probe-coefficient gradient (Eqs. 6-7): dL/db_ijc = sum_k w_i(k) Y_j(k) dF_a,c(k).
 // Samples of a chunk that share a probe cell are consecutive; lane (corner i,
-// channel c) sums each run and issues one reduction per coefficient.
+// channel c) sums each run over the rows in `live` and issues one reduction
+// per coefficient.
 template <class C, int PST>
-__device__ __forceinline__ void scatter_probe_grad(const RenderArgs& A, const float* pst, int nact,
-                                                   int lane)
+__device__ __forceinline__ void scatter_probe_grad(const RenderArgs& A, const float* pst,
+                                                   uint32_t live, int lane)
 {
     constexpr int L2 = C::L2, NA = C::NA;
     constexpr int CPL = (8 * NA) / 32;
     static_assert((8 * NA) % 32 == 0, "8 corners x channels must fill whole warps");
+    static_assert(PST % 4 == 0, "rows of whole 16-byte vectors");
+    constexpr int L2V = (L2 + 3) / 4;  // Y_j starts at float 8: 16-byte aligned
+    static_assert(8 + 4 * L2V <= PST, "vector reads stay inside the row");
     const int Px = A.probes.P[0], Pxy = A.probes.P[0] * A.probes.P[1];
     int q[CPL], ch[CPL], qoff[CPL];
     float acc[CPL][L2];
@@ -82,12 +86,13 @@ __device__ __forceinline__ void scatter_probe_grad(const RenderArgs& A, const fl
 #pragma unroll
         for (int j = 0; j < L2; ++j) acc[m][j] = 0.f;
     }
-    static_assert(PST % 4 == 0, "rows of whole 16-byte vectors");
-    constexpr int L2V = (L2 + 3) / 4;  // Y_j starts at float 8: 16-byte aligned
-    static_assert(8 + 4 * L2V <= PST, "vector reads stay inside the row");
-    int cell = nact > 0 ? __float_as_int(pst[8 + L2 + NA]) : -1;
-    for (int s = 0; s < nact; ++s) {
+    // only rows of samples with a nonzero opacity carry a gradient (dx = 0
+    // elsewhere); a run of rows in one probe cell is summed, then flushed
+    while (live) {
+        const int s = __ffs(live) - 1;
+        live &= live - 1;
         const float* row = pst + s * PST;
+        const int cell = __float_as_int(row[8 + L2 + NA]);
         float Y[4 * L2V];
 #pragma unroll
         for (int v = 0; v < L2V; ++v) {
@@ -103,7 +108,8 @@ __device__ __forceinline__ void scatter_probe_grad(const RenderArgs& A, const fl
 #pragma unroll
             for (int j = 0; j < L2; ++j) acc[m][j] = fmaf(coef, Y[j], acc[m][j]);
         }
-        const int next = s + 1 < nact ? __float_as_int(pst[(s + 1) * PST + 8 + L2 + NA]) : -1;
+        const int next =
+            live ? __float_as_int(pst[(__ffs(live) - 1) * PST + 8 + L2 + NA]) : -1;
         if (next != cell) {
 #pragma unroll
             for (int m = 0; m < CPL; ++m) {
@@ -115,7 +121,6 @@ __device__ __forceinline__ void scatter_probe_grad(const RenderArgs& A, const fl
                 }
             }
         }
-        cell = next;
     }
 }
 
@@ -204,36 +209,49 @@ render_backward_kernel(RenderArgs A)
     bool bad = false, any_chunk = false, dw_started = false;
     float acc3[3] = {0.f, 0.f, 0.f}, accb3 = 0.0f;  // dW3 column (lane % W) and db3 (lane < 3)
 
+    // Per-warp work cursor: the warp's current ray and chunk.  Each CTA step
+    // every warp renders one chunk (or an empty tile slice), so the barriers
+    // below stay CTA-uniform while rays take different numbers of chunks.
+    // A ray starts at the chunk that holds sample n_live: every later sample
+    // has alpha = 0 and a zero adjoint, and lam = 0 there leaves log T and the
+    // suffix term of Eq. 10 at their end-of-ray values.
+    RayIn R;
+    RaySpan sp;
+    bool have = false;
+    int ch = -1;
+    float drgb[3] = {0.f, 0.f, 0.f}, ddepth = 0.f, dwsum = 0.f, logT_end = 0.f, s_carry = 0.f;
+    const int nch = (N + 31) >> 5;
     for (;;) {
-        RayIn R;
-        RaySpan sp;
-        bool have = false;
-        while (ray < A.n_rays) {
-            R = load_ray(A, ray);
-            sp = ray_span(A, R, ray);
-            if (sp.hit) {
-                have = true;
-                break;
+        if (ch < 0) {
+            if (have) ray += stride;
+            have = false;
+            while (ray < A.n_rays) {
+                R = load_ray(A, ray);
+                sp = ray_span(A, R, ray);
+                const int live = A.n_live ? __ldg(A.n_live + ray) : N;
+                if (sp.hit && live > 0) {
+                    have = true;
+                    ch = min(nch - 1, live >> 5);
+                    break;
+                }
+                ray += stride;
             }
-            ray += stride;
+            drgb[0] = drgb[1] = drgb[2] = 0.f;
+            ddepth = dwsum = logT_end = 0.f;
+            if (have) {
+                drgb[0] = __ldg(A.d_rgb + 3 * ray);
+                drgb[1] = __ldg(A.d_rgb + 3 * ray + 1);
+                drgb[2] = __ldg(A.d_rgb + 3 * ray + 2);
+                ddepth = A.d_depth ? __ldg(A.d_depth + ray) : 0.0f;
+                dwsum = A.d_wsum ? __ldg(A.d_wsum + ray) : 0.0f;
+                logT_end = __ldg(A.logT + ray);
+            }
+            s_carry = drgb[0] * A.bg[0] + drgb[1] * A.bg[1] + drgb[2] * A.bg[2];
         }
         if (!__syncthreads_or(have)) break;
         any_chunk = true;
-
-        float drgb[3] = {0.f, 0.f, 0.f}, ddepth = 0.f, dwsum = 0.f, logT_end = 0.f;
-        if (have) {
-            drgb[0] = __ldg(A.d_rgb + 3 * ray);
-            drgb[1] = __ldg(A.d_rgb + 3 * ray + 1);
-            drgb[2] = __ldg(A.d_rgb + 3 * ray + 2);
-            ddepth = A.d_depth ? __ldg(A.d_depth + ray) : 0.0f;
-            dwsum = A.d_wsum ? __ldg(A.d_wsum + ray) : 0.0f;
-            logT_end = __ldg(A.logT + ray);
-        }
-        float s_carry = drgb[0] * A.bg[0] + drgb[1] * A.bg[1] + drgb[2] * A.bg[2];
-        const int nch = (N + 31) >> 5;
-
-        for (int ch = nch - 1; ch >= 0; --ch) {
-            const int base = ch * 32;
+        {
+            const int base = (have ? ch : 0) * 32;
             const int k = base + lane;
             const bool active = have && k < N;
             const int nact = have ? min(32, N - base) : 0;
@@ -248,11 +266,7 @@ render_backward_kernel(RenderArgs A)
             c1.f[0] = c1.f[1] = c1.f[2] = 0.0f;
             if (have) {
                 t = span_t(sp, k < N ? k : N - 1);
-                eval_geometry<C>(A, R.o, R.d, t, S);
-                float xin[K1];
-#pragma unroll
-                for (int i = 0; i < K1; ++i) xin[i] = i < NIN ? S.x[i] : (i == NIN ? 1.0f : 0.0f);
-                store_row<K1, M::kSplit>(xhh, xhl, tid, 0, L::XHC, xin);
+                eval_sdf<C>(A, R.o, R.d, t, S);
                 s_next = __shfl_down_sync(FULL, S.s, 1);
                 if (extra) {
                     float xw[3];
@@ -265,6 +279,17 @@ render_backward_kernel(RenderArgs A)
                     unclipped = diff < 0.0f;
                     lam = unclipped ? diff : 0.0f;
                 }
+                // alpha = 0 where the opacity is clipped: the sample's weight,
+                // colour terms, dz rows and so dF (dx) are exactly zero, and its
+                // appearance is not needed (see P5)
+                if (unclipped)
+                    eval_appearance<C>(A, R.o, R.d, t, S);
+                else
+                    zero_appearance<C>(S);
+                float xin[K1];
+#pragma unroll
+                for (int i = 0; i < K1; ++i) xin[i] = i < NIN ? S.x[i] : (i == NIN ? 1.0f : 0.0f);
+                store_row<K1, M::kSplit>(xhh, xhl, tid, 0, L::XHC, xin);
             } else {
                 zero_row<K1, M::kSplit>(xhh, xhl, tid, 0, L::XHC);
                 S.s = 0.0f;
@@ -483,70 +508,76 @@ render_backward_kernel(RenderArgs A)
             __syncthreads();  // tiles are free from here on
 
             // ---- P5: angular / Fresnel / normal adjoints and grid reductions ----
+            // Samples with a clipped opacity have dx = 0 exactly: no angular,
+            // Fresnel or normal adjoint, and only the SDF-value gradient of the
+            // transmittance term (ds_own), skipped when that is zero too.
             float* pst = reinterpret_cast<float*>(dzh) + warp * 32 * L::PST;
             if (have) {
-                float wq[8];
-                corner_weights(S.pcell.f, wq);
-                int pidx[8];
-                probe_corner_index(A.probes, S.pcell, pidx);
-                float dY[L2];
+                float gxs = 0.0f, gys = 0.0f, gzs = 0.0f;
+                if (unclipped) {
+                    float wq[8];
+                    corner_weights(S.pcell.f, wq);
+                    int pidx[8];
+                    probe_corner_index(A.probes, S.pcell, pidx);
+                    float dY[L2];
 #pragma unroll
-                for (int j = 0; j < L2; ++j) dY[j] = 0.0f;
+                    for (int j = 0; j < L2; ++j) dY[j] = 0.0f;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
+                    for (int q = 0; q < 8; ++q) {
 #pragma unroll
-                    for (int j = 0; j < L2; ++j) {
-                        float acc = 0.0f;
+                        for (int j = 0; j < L2; ++j) {
+                            float acc = 0.0f;
 #pragma unroll
-                        for (int cg = 0; cg < C::NA4; ++cg) {
-                            const float4 bb = probe_coeffs<C>(A.probes, pidx[q], j, cg);
-                            acc = fmaf(bb.x, dx[3 + 4 * cg + 0], acc);
-                            acc = fmaf(bb.y, dx[3 + 4 * cg + 1], acc);
-                            acc = fmaf(bb.z, dx[3 + 4 * cg + 2], acc);
-                            acc = fmaf(bb.w, dx[3 + 4 * cg + 3], acc);
+                            for (int cg = 0; cg < C::NA4; ++cg) {
+                                const float4 bb = probe_coeffs<C>(A.probes, pidx[q], j, cg);
+                                acc = fmaf(bb.x, dx[3 + 4 * cg + 0], acc);
+                                acc = fmaf(bb.y, dx[3 + 4 * cg + 1], acc);
+                                acc = fmaf(bb.z, dx[3 + 4 * cg + 2], acc);
+                                acc = fmaf(bb.w, dx[3 + 4 * cg + 3], acc);
+                            }
+                            dY[j] = fmaf(wq[q], acc, dY[j]);
                         }
-                        dY[j] = fmaf(wq[q], acc, dY[j]);
                     }
-                }
-                {
-                    float Y[L2];
-                    sh_basis<L2>(S.r, Y);
-                    float* row = pst + lane * L::PST;
+                    {
+                        float Y[L2];
+                        sh_basis<L2>(S.r, Y);
+                        float* row = pst + lane * L::PST;
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) row[q] = wq[q];
+                        for (int q = 0; q < 8; ++q) row[q] = wq[q];
 #pragma unroll
-                    for (int j = 0; j < L2; ++j) row[8 + j] = Y[j];
+                        for (int j = 0; j < L2; ++j) row[8 + j] = Y[j];
 #pragma unroll
-                    for (int c = 0; c < NA; ++c) row[8 + L2 + c] = active ? dx[3 + c] : 0.0f;
-                    row[8 + L2 + NA] = __int_as_float(S.pcell.base);
-                }
-                float dr[3];
-                sh_basis_vjp<L2>(S.r, dY, dr);
-                const float v[3] = {-R.d[0], -R.d[1], -R.d[2]};
-                float dn[3] = {0.f, 0.f, 0.f};
-                if (A.dir_mode != 1) {
-                    const float drn = dr[0] * S.n[0] + dr[1] * S.n[1] + dr[2] * S.n[2];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) dn[a] = 2.0f * drn * v[a] + 2.0f * S.ndv * dr[a];
-                }
-                {
-                    const float om = 1.0f - S.ndv;
-                    float dndv = 0.0f, pw = 1.0f;
-#pragma unroll
-                    for (int kk = 1; kk <= C::K; ++kk) {
-                        dndv -= dx[3 + NA + kk - 1] * static_cast<float>(kk) * pw;
-                        pw *= om;
+                        for (int c = 0; c < NA; ++c) row[8 + L2 + c] = dx[3 + c];
+                        row[8 + L2 + NA] = __int_as_float(S.pcell.base);
                     }
+                    float dr[3];
+                    sh_basis_vjp<L2>(S.r, dY, dr);
+                    const float v[3] = {-R.d[0], -R.d[1], -R.d[2]};
+                    float dn[3] = {0.f, 0.f, 0.f};
+                    if (A.dir_mode != 1) {
+                        const float drn = dr[0] * S.n[0] + dr[1] * S.n[1] + dr[2] * S.n[2];
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) dn[a] = fmaf(dndv, v[a], dn[a]);
+                        for (int a = 0; a < 3; ++a) dn[a] = 2.0f * drn * v[a] + 2.0f * S.ndv * dr[a];
+                    }
+                    {
+                        const float om = 1.0f - S.ndv;
+                        float dndv = 0.0f, pw = 1.0f;
+#pragma unroll
+                        for (int kk = 1; kk <= C::K; ++kk) {
+                            dndv -= dx[3 + NA + kk - 1] * static_cast<float>(kk) * pw;
+                            pw *= om;
+                        }
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) dn[a] = fmaf(dndv, v[a], dn[a]);
+                    }
+                    const float ndn = S.n[0] * dn[0] + S.n[1] * dn[1] + S.n[2] * dn[2];
+                    const float irho = 1.0f / S.rho;
+                    gxs = (dn[0] - S.n[0] * ndn) * irho * A.grid.sc[0];
+                    gys = (dn[1] - S.n[1] * ndn) * irho * A.grid.sc[1];
+                    gzs = (dn[2] - S.n[2] * ndn) * irho * A.grid.sc[2];
                 }
-                const float ndn = S.n[0] * dn[0] + S.n[1] * dn[1] + S.n[2] * dn[2];
-                const float irho = 1.0f / S.rho;
-                const float gxs = (dn[0] - S.n[0] * ndn) * irho * A.grid.sc[0];
-                const float gys = (dn[1] - S.n[1] * ndn) * irho * A.grid.sc[1];
-                const float gzs = (dn[2] - S.n[2] * ndn) * irho * A.grid.sc[2];
                 const int sy = A.grid.R[0], sz = A.grid.R[0] * A.grid.R[1];
-                if (active) {
+                if (unclipped) {
                     const float fx = S.cell.f[0], fy = S.cell.f[1], fz = S.cell.f[2];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
@@ -561,25 +592,37 @@ render_backward_kernel(RenderArgs A)
                             A.grad_grid + 4 * (size_t)(S.cell.base + cx + cy * sy + cz * sz);
                         red_add_v4(dst, dsdf, wc * dx[0], wc * dx[1], wc * dx[2]);
                     }
-                }
-                if (extra) {
-                    const float ds1 = dlam * dlog_phi(tau, s_next);
-                    float w1[8];
-                    corner_weights(c1.f, w1);
+                } else if (active && ds_own != 0.0f) {
+                    float w8[8];
+                    corner_weights(S.cell.f, w8);
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         const int cx = q & 1, cy = (q >> 1) & 1, cz = (q >> 2) & 1;
-                        red_add(A.grad_grid + 4 * (size_t)(c1.base + cx + cy * sy + cz * sz),
-                                ds1 * w1[q]);
+                        red_add(A.grad_grid + 4 * (size_t)(S.cell.base + cx + cy * sy + cz * sz),
+                                ds_own * w8[q]);
                     }
                 }
+                if (extra) {
+                    const float ds1 = dlam * dlog_phi(tau, s_next);
+                    if (ds1 != 0.0f) {
+                        float w1[8];
+                        corner_weights(c1.f, w1);
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const int cx = q & 1, cy = (q >> 1) & 1, cz = (q >> 2) & 1;
+                            red_add(A.grad_grid + 4 * (size_t)(c1.base + cx + cy * sy + cz * sz),
+                                    ds1 * w1[q]);
+                        }
+                    }
+                }
+                const uint32_t live = __ballot_sync(FULL, unclipped);
                 __syncwarp();
-                scatter_probe_grad<C, L::PST>(A, pst, nact, lane);
+                scatter_probe_grad<C, L::PST>(A, pst, live, lane);
                 logT_end = __shfl_sync(FULL, logTk, 0);
                 s_carry = next_carry;
             }
         }
-        if (have) ray += stride;
+        if (have) --ch;
     }
 done:
     // every thread reaches this point together (the loop exits and the jump

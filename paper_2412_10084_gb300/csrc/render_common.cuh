@@ -50,6 +50,9 @@ struct RenderArgs {
     float* depth;
     float* wsum;
     float* logT;
+    // forward output / backward input (nullable): 1 + index of the ray's last
+    // sample with a nonzero opacity (0 when none is)
+    int* n_live;
     // backward
     const float* __restrict__ d_rgb;
     const float* __restrict__ d_depth;

@@ -4,9 +4,11 @@
 // (misses are written out at once) and walks its ray in chunks of 32 samples,
 // lane = sample.  The 4 warps advance chunk by chunk in lockstep so that their
 // 128 samples form one M = 128 tile for the tensor-core MLP:
-//   P0  trilinear gather of 8 packed 16-byte node records per sample, normal,
-//       SH of the lookup direction, probe blend, Fresnel powers -> MLP input
-//       row (split FP16) in shared memory;
+//   P0  trilinear gather of 8 packed 16-byte node records per sample and the
+//       sample's opacity; where it is nonzero, normal, SH of the lookup
+//       direction, probe blend, Fresnel powers -> MLP input row (split FP16)
+//       in shared memory (a sample with alpha = 0 has weight 0, so its
+//       appearance is never evaluated);
 //   P1  layer 1 on the tensor cores; meanwhile the warp scan of the clipped
 //       log-opacities gives every sample's transmittance (Eq. 8);
 //   P2  ReLU epilogue -> layer 2 on the tensor cores -> layer 3 and sigmoid on
@@ -86,6 +88,7 @@ render_forward_kernel(RenderArgs A)
                 A.depth[ray] = 0.0f;
                 A.wsum[ray] = 0.0f;
                 A.logT[ray] = 0.0f;
+                if (A.n_live) A.n_live[ray] = 0;
             }
             ray += stride;
         }
@@ -93,6 +96,7 @@ render_forward_kernel(RenderArgs A)
 
         float acc_r = 0.f, acc_g = 0.f, acc_b = 0.f, acc_d = 0.f, acc_w = 0.f;
         float carry = 0.f, comp = 0.f;  // Kahan sum of log T over chunks
+        int n_live = 0;                 // 1 + last sample with lam < 0
         for (int base = 0; base < N; base += 32) {
             const int k = base + lane;
             const bool active = have && k < N;
@@ -101,21 +105,29 @@ render_forward_kernel(RenderArgs A)
             if (have) {
                 t = span_t(sp, k < N ? k : N - 1);
                 SampleGeom<C> S;
-                eval_geometry<C>(A, R.o, R.d, t, S);
-                float xin[M::K1];
-#pragma unroll
-                for (int i = 0; i < M::K1; ++i) xin[i] = i < C::NIN ? S.x[i] : 0.0f;
-                store_row<M::K1, M::kSplit>(xh, xl, tid, 0, M::K1, xin);
+                eval_sdf<C>(A, R.o, R.d, t, S);
                 float s_next = __shfl_down_sync(FULL, S.s, 1);
                 if (active && (lane == 31 || k + 1 >= N)) {
                     float xw[3];
                     point_at(R.o, R.d, span_t(sp, k + 1), xw);
                     s_next = sdf_value(A.grid, locate(xw, A.grid.bmin, A.grid.sc, A.grid.R));
                 }
+                bool opaque = false;
                 if (active) {
                     const float diff = log_transmittance(A.tau, S.s, s_next);
-                    lam = diff < 0.0f ? diff : 0.0f;
+                    opaque = diff < 0.0f;
+                    lam = opaque ? diff : 0.0f;
                 }
+                // a clipped opacity (alpha = 0) gives the sample weight 0: its
+                // colour, and so its appearance inputs, never reach an output
+                if (opaque)
+                    eval_appearance<C>(A, R.o, R.d, t, S);
+                else
+                    zero_appearance<C>(S);
+                float xin[M::K1];
+#pragma unroll
+                for (int i = 0; i < M::K1; ++i) xin[i] = i < C::NIN ? S.x[i] : 0.0f;
+                store_row<M::K1, M::kSplit>(xh, xl, tid, 0, M::K1, xin);
             } else {
                 zero_row<M::K1, M::kSplit>(xh, xl, tid, 0, M::K1);
             }
@@ -128,6 +140,10 @@ render_forward_kernel(RenderArgs A)
                 mma_k<M::kSplit>(tmem + 0, xh, xl, M::w1h(wt), M::w1l(wt), 128,
                                  (M::K1 / 8) * 128, 128, (M::K1 / 8) * 128, M::kIdescL, false);
                 tc::commit(mbar);
+            }
+            {
+                const uint32_t opaque = __ballot_sync(FULL, lam < 0.0f);
+                if (opaque) n_live = base + 32 - __clz(opaque);
             }
             // transmittance of the chunk (Eq. 8): exclusive warp scan of lam
             float incl = lam;
@@ -207,6 +223,7 @@ render_forward_kernel(RenderArgs A)
                 A.depth[ray] = acc_d;
                 A.wsum[ray] = acc_w;
                 A.logT[ray] = logT;
+                if (A.n_live) A.n_live[ray] = n_live;
             }
             ray += stride;
         }

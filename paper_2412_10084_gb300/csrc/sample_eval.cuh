@@ -92,9 +92,11 @@ __device__ __forceinline__ void probe_corner_index(const ProbeView& p, const Cel
     idx[7] = pc.base + sz + sy + sx;
 }
 
+// SDF part of a sample: cell, trilinear SDF value and gradient, spatial
+// features (MLP input columns 0..2).
 template <class C>
-__device__ __forceinline__ void eval_geometry(const RenderArgs& A, const float o[3],
-                                              const float d[3], float t, SampleGeom<C>& S)
+__device__ __forceinline__ void eval_sdf(const RenderArgs& A, const float o[3], const float d[3],
+                                         float t, SampleGeom<C>& S)
 {
     float xw[3];
     point_at(o, d, t, xw);
@@ -103,7 +105,18 @@ __device__ __forceinline__ void eval_geometry(const RenderArgs& A, const float o
     gather_corners_t<C>(A.grid, S.cell, k);
     float fs[3];
     sdf_full(A.grid, S.cell, k, S.s, S.g, fs);
+    S.x[0] = fs[0];
+    S.x[1] = fs[1];
+    S.x[2] = fs[2];
+}
 
+// Appearance part: normal (Eq. 13), SH lookup direction and basis, probe-
+// blended angular features (Eqs. 6-7) and Fresnel inputs (Eq. 4), the MLP
+// input columns 3.. .  Needed only where the sample's opacity is nonzero.
+template <class C>
+__device__ __forceinline__ void eval_appearance(const RenderArgs& A, const float o[3],
+                                                const float d[3], float t, SampleGeom<C>& S)
+{
     const float gg = S.g[0] * S.g[0] + S.g[1] * S.g[1] + S.g[2] * S.g[2];
     S.rho = sqrtf(gg + kNormalEps * kNormalEps);
     const float inv = 1.0f / S.rho;
@@ -120,6 +133,8 @@ __device__ __forceinline__ void eval_geometry(const RenderArgs& A, const float o
     sh_basis<C::L2>(S.r, S.Y);
 
     // Angular features (Eqs. 6-7): F_a = sum_i w_i sum_j b_ij Y_j(r).
+    float xw[3];
+    point_at(o, d, t, xw);
     S.pcell = locate(xw, A.grid.bmin, A.probes.sc, A.probes.P);
     float wq[8];
     corner_weights(S.pcell.f, wq);
@@ -147,10 +162,6 @@ __device__ __forceinline__ void eval_geometry(const RenderArgs& A, const float o
 #pragma unroll
         for (int c = 0; c < C::NA; ++c) fa[c] = fmaf(wq[q], part[c], fa[c]);
     }
-
-    S.x[0] = fs[0];
-    S.x[1] = fs[1];
-    S.x[2] = fs[2];
 #pragma unroll
     for (int c = 0; c < C::NA; ++c) S.x[3 + c] = fa[c];
     // Fresnel inputs (Eq. 4): (1 - n.v)^k, k = 1..K
@@ -163,6 +174,24 @@ __device__ __forceinline__ void eval_geometry(const RenderArgs& A, const float o
     }
 #pragma unroll
     for (int i = C::NIN; i < C::NINP; ++i) S.x[i] = 0.0f;
+}
+
+// MLP input of a sample whose opacity is zero: its colour is never used
+// (every term it enters is multiplied by alpha = 0), so the appearance
+// columns are left at zero.
+template <class C>
+__device__ __forceinline__ void zero_appearance(SampleGeom<C>& S)
+{
+#pragma unroll
+    for (int i = 3; i < C::NINP; ++i) S.x[i] = 0.0f;
+}
+
+template <class C>
+__device__ __forceinline__ void eval_geometry(const RenderArgs& A, const float o[3],
+                                              const float d[3], float t, SampleGeom<C>& S)
+{
+    eval_sdf<C>(A, o, d, t, S);
+    eval_appearance<C>(A, o, d, t, S);
 }
 
 // Ray record (broadcast by every lane of the warp).

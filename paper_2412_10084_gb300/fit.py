@@ -51,10 +51,11 @@ def fit_appearance(scene: Scene, rays_o, rays_d, target, params: RenderParams, s
     for step in range(1, steps + 1):
         idx = _batch(gen, n_pool, batch, dev)
         o, d, tgt = rays_o[idx], rays_d[idx], target[idx]
-        rgb, _, _, logT = render_forward(scene, o, d, params)
+        rgb, _, _, logT, live = render_forward(scene, o, d, params, want_live=True)
         diff = rgb - tgt
         d_rgb = (2.0 / batch) * diff
-        render_backward(scene, o, d, params, d_rgb.contiguous(), logT, grads=(gg, gp, gm))
+        render_backward(scene, o, d, params, d_rgb.contiguous(), logT, grads=(gg, gp, gm),
+                        n_live=live)
         if not train_sdf:
             gg[:, 0].zero_()
         opt.step()

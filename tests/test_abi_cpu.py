@@ -68,9 +68,9 @@ def test_host_validation_without_gpu(lib):
     assert lib.psdf_grid_create(ctypes.byref(gd), ctypes.c_void_p(0x1008), ctypes.byref(h)) == -4
     assert lib.psdf_grid_create(ctypes.byref(gd), None, ctypes.byref(h)) == -1
     lib.psdf_render_forward.argtypes = [ctypes.c_void_p] * 7 + [ctypes.c_int64] + \
-        [ctypes.c_void_p] * 5
+        [ctypes.c_void_p] * 6
     assert lib.psdf_render_forward(None, None, None, None, None, None, None, 0,
-                                   None, None, None, None, None) == -1
+                                   None, None, None, None, None, None) == -1
 
 
 def test_kernel_sh_constants_match_closed_form():

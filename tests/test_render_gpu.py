@@ -10,6 +10,7 @@ import torch
 import copy
 import os
 
+import oracle
 import synth
 from helpers import (GRAD_RTOL, RGB_DEPTH_RTOL, box_interval, clean_rays, log_errors,
                      oracle_backward, oracle_forward, rel_err_elementwise, rel_err_tensor, worst)
@@ -32,13 +33,15 @@ def gpu_forward(scene, o, d, params, t_samples=None):
             for k, v in (("rgb", rgb), ("depth", depth), ("wsum", wsum), ("logT", logT))}
 
 
-def gpu_backward(scene, o, d, params, drgb, ddepth=None, dwsum=None, t_samples=None):
+def gpu_backward(scene, o, d, params, drgb, ddepth=None, dwsum=None, t_samples=None,
+                 use_live=True):
     o_, d_ = dev(o), dev(d)
     ts = None if t_samples is None else dev(t_samples)
-    _, _, _, logT = ps.render_forward(scene, o_, d_, params, ts)
+    _, _, _, logT, live = ps.render_forward(scene, o_, d_, params, ts, want_live=True)
     gg, gp, gm = ps.render_backward(scene, o_, d_, params, dev(drgb), logT,
                                     d_depth=None if ddepth is None else dev(ddepth),
-                                    d_wsum=None if dwsum is None else dev(dwsum), t_samples=ts)
+                                    d_wsum=None if dwsum is None else dev(dwsum), t_samples=ts,
+                                    n_live=live if use_live else None)
     gd, _, _ = scene.descs(params.n_fresnel)
     gsdf, gfeat = ps.unpack_grid(gd, gg)
     assert ps.device_status() == 0
@@ -424,3 +427,30 @@ def test_gpu_central_differences():
     fds, ans = np.array(fds), np.array(ans)
     assert fds.size == 64
     assert np.linalg.norm(fds - ans) <= 2.5e-2 * np.linalg.norm(ans)
+
+
+def test_live_extent_matches_oracle_and_skipping_is_exact(sphere64):
+    """n_live (1 + the last sample with a nonzero opacity) equals the oracle's
+    on rays away from the clip kink, and the adjoint that skips the samples
+    after it gives the gradients of the one that visits every sample."""
+    sc, rays = sphere64
+    o, d = rays.o[:600], rays.d[:600]
+    tau, N = 64.0, 128
+    scene = ps.Scene.from_host(sc)
+    params = ps.render_params(tau, N, n_fresnel=sc.n_fresnel)
+    out = ps.render_forward(scene, dev(o), dev(d), params, want_live=True)
+    live = out[4].cpu().numpy()
+    keep = clean_rays(sc, o, d, tau, N)
+    m = oracle.Model.from_scene(sc)
+    for i in keep[:120]:
+        tr = oracle.render_trace(m, o[i], d[i], tau, N)
+        ref = 0 if not tr["hit"] else int(np.nonzero(tr["w"] > 0)[0].max() + 1) \
+            if np.any(tr["w"] > 0) else 0
+        assert live[i] == ref, (i, live[i], ref)
+    assert 0 < np.mean(live[live > 0]) < N  # samples are actually skipped
+    g = synth.rng(17)
+    drgb = (g.normal(size=(600, 3)) / 600).astype(np.float32)
+    a = gpu_backward(scene, o, d, params, drgb, use_live=True)
+    b = gpu_backward(scene, o, d, params, drgb, use_live=False)
+    for k in a:
+        assert rel_err_tensor(a[k], b[k]) <= 1e-6, (k, rel_err_tensor(a[k], b[k]))
