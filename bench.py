@@ -89,6 +89,25 @@ def parse():
     return ap.parse_args()
 
 
+def captured_traffic(workload, kernel, rays):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, if it
+    was taken on these kernel sources at this size (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        sys.path.insert(0, os.path.join(ROOT, "paper_2412_10084_gb300"))
+        import build as _b
+        if rec.get("source_digest") != _b.source_digest():
+            return None
+        w = rec.get(workload)
+        if not w or w.get("rays") != rays or kernel not in w:
+            return None
+        return int(w[kernel]["read"] + w[kernel]["write"])
+    except (OSError, ValueError, KeyError, ImportError):
+        return None
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -431,12 +450,15 @@ def run_ours(args, world, rank, local):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": "render_backward_kernel",
                      "achieved": bwd_gbs, "peak": peak, "unit": "GB/s",
-                     "frac": bwd_gbs / peak, "traffic": None,
+                     "frac": bwd_gbs / peak,
+                     "traffic": captured_traffic(args.workload, "render_backward_kernel", n),
                      "bytes_per_sample": BYTES_BWD, "peak_kind": peak_kind,
                      "launch_ms": bwd_ms},
         "roofline_forward": {"bound": "hbm", "kernel": "render_forward_kernel",
                              "achieved": fwd_gbs, "peak": peak, "unit": "GB/s",
                              "frac": fwd_gbs / peak, "bytes_per_sample": BYTES_FWD,
+                             "traffic": captured_traffic(args.workload, "render_forward_kernel",
+                                                         n),
                              "launch_ms": fwd_ms},
         "roofline_step": {"achieved": step_gbs, "peak": peak, "unit": "GB/s",
                           "frac": step_gbs / peak, "bytes_per_sample": BYTES_STEP},

@@ -42,14 +42,25 @@ def _inputs_digest(flags):
                 h.update(f.encode())
                 with open(p, "rb") as fh:
                     h.update(fh.read())
-    h.update(" ".join(flags).encode())
+    # the flags enter without machine paths, so a digest names the same build everywhere
+    h.update(" ".join(f.replace(INCLUDE, "<include>").replace(CSRC, "<csrc>")
+                      for f in flags).encode())
     return h.hexdigest()
+
+
+def base_flags():
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+                   "-I", INCLUDE, "-I", CSRC]
+
+
+def source_digest() -> str:
+    """Digest of the kernel sources, headers and default flags (the build stamp)."""
+    return _inputs_digest(base_flags())
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                    "-I", INCLUDE, "-I", CSRC]
+    flags = base_flags()
     if verbose:
         flags += ["-Xptxas", "-v"]
     digest = _inputs_digest(flags)
