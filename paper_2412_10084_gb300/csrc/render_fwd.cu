@@ -35,7 +35,7 @@ struct FwdLayout {
 };
 
 template <class C>
-__global__ void __launch_bounds__(kFwdThreads)
+__global__ void __launch_bounds__(kFwdThreads, 6)
 render_forward_kernel(RenderArgs A)
 {
     using M = MlpTC<C>;
