@@ -580,14 +580,15 @@ def run_inference(args, world, rank, local):
     matched = [k for k in sorted(forms) if forms[k]["psnr_db"] >= psnr_u - 0.1]
     chosen = matched[0] if matched else max(forms, key=lambda k: forms[k]["psnr_db"])
     pn = ps.render_params(tau, chosen, n_fresnel=sc.n_fresnel)
+    pnb = ps.render_params(tau, chosen, n_fresnel=sc.n_fresnel, n_bins=prop.desc.n_bins)
     ev = []
     for _ in range(args.steps):
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
-        t, _ = ps.proposal_forward(fast_scene, prop.desc, prop.params, prop.occ, o, d, chosen,
-                                   want_probs=False)
+        _, q = ps.proposal_forward(fast_scene, prop.desc, prop.params, prop.occ, o, d, chosen,
+                                   want_t=False)
         e1.record(stream)
-        ps.render_forward(fast_scene, o, d, pn, t)
+        ps.render_forward(fast_scene, o, d, pnb, q)
         e2.record(stream)
         ev.append((e0, e1, e2))
     torch.cuda.synchronize(device)
@@ -634,7 +635,7 @@ def run_inference(args, world, rank, local):
         "speedup_vs_uniform256": (ms_u / n_views) / fast_ms,
         "silhouette_pixels": int(mask.sum()),
         "kernels_ms": {"proposal_forward": prop_ms, "render_forward": rend_ms},
-        "roofline": {"bound": "hbm", "kernel": "render_forward_kernel (BF16/FP16, explicit t)",
+        "roofline": {"bound": "hbm", "kernel": "render_forward_kernel (BF16/FP16, bin densities)",
                      "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                      "traffic": None, "bytes_per_sample": bfwd, "peak_kind": peak_kind,
                      "launch_ms": rend_ms},

@@ -100,6 +100,8 @@ typedef struct psdf_render_params {
     int32_t dir_mode;    /* PSDF_DIR_REFLECT or PSDF_DIR_VIEW */
     int32_t n_fresnel;   /* K: inputs (1 - n.v)^1..K (Eq. 4 uses powers of 1 - n.v); 3 compiled in */
     float bg[3];         /* background colour added with the final transmittance */
+    int32_t n_bins;      /* 0: t_samples (if given) are sample distances; B in [1, 32]:
+                            t_samples are per-bin densities (see psdf_render_forward) */
 } psdf_render_params;
 
 typedef struct psdf_grid psdf_grid;
@@ -163,7 +165,15 @@ void psdf_mlp_destroy(psdf_mlp* mlp);
  *   t_samples      : NULL for N evenly spaced samples over the ray's segment
  *                    inside the box (slab test, t >= 0), or device FP32
  *                    [n_rays][N+1] of increasing sample distances (a ray with
- *                    t[N] <= t[0] is treated as a miss).
+ *                    t[N] <= t[0] is treated as a miss), or, when
+ *                    params->n_bins = B > 0, device FP32 [n_rays][B] densities
+ *                    q_b of B equal bins of the box segment [t_n, t_f] (as
+ *                    psdf_proposal_forward returns in `probs`, summing to 1,
+ *                    each > 0): sample k sits at the quantile k / N,
+ *                    t_k = t_n + (b + (k/N - c_b) / q_b) (t_f - t_n) / B with
+ *                    c_b = q_0 + .. + q_{b-1} and b the last bin with c_b <= k/N
+ *                    (t_0 = t_n, t_N = t_f) -- the distances
+ *                    psdf_proposal_forward writes to its t_samples.
  *   rgb            : device FP32 [n_rays][3] = sum_k w_k C_k + T_N bg
  *   depth          : device FP32 [n_rays]    = sum_k w_k t_k
  *   wsum           : device FP32 [n_rays]    = sum_k w_k
@@ -280,8 +290,10 @@ psdf_status psdf_weight_histogram(const psdf_grid* grid, const psdf_render_param
 /* Proposal forward and sample placement:
  *   params    : device FP32 [psdf_proposal_param_count]
  *   occ_bits  : device occupancy bitmask of psdf_occupancy_build for desc->occ_res
- *   t_samples : device FP32 [n_rays][n_out + 1] (rays missing the box get zeros)
- *   probs     : device FP32 [n_rays][B] mixed density p', or NULL */
+ *   t_samples : device FP32 [n_rays][n_out + 1] (rays missing the box get
+ *               zeros), or NULL: the densities alone (render them with
+ *               psdf_render_params.n_bins = B)
+ *   probs     : device FP32 [n_rays][B] mixed density p', or NULL (not both) */
 psdf_status psdf_proposal_forward(const psdf_grid* grid, const psdf_proposal_desc* desc,
                                   const float* params, const uint32_t* occ_bits,
                                   const float* rays_o,

@@ -109,6 +109,9 @@ def _load():
             lib.orc_proposal_forward.argtypes = [P, P, ctypes.c_int64, P, P, ctypes.c_int32, P,
                                                  P, P, P]
             lib.orc_proposal_forward.restype = ctypes.c_int32
+            lib.orc_place_samples.argtypes = [P, ctypes.c_int64, P, P, P, ctypes.c_int32,
+                                              ctypes.c_int32, P]
+            lib.orc_place_samples.restype = ctypes.c_int32
             lib.orc_weight_histogram.argtypes = [P, P, ctypes.c_int64, P, P, ctypes.c_int32, P,
                                                  ctypes.c_int32]
             lib.orc_weight_histogram.restype = ctypes.c_int32
@@ -340,6 +343,21 @@ def proposal_forward(model: Model, prop: Proposal, rays_o, rays_d, n_out):
     if st != 0:
         raise ValueError("oracle proposal_forward rejected its arguments")
     return {"logits": logits, "probs": probs, "t": t, "margin": mg}
+
+
+def place_samples(model: Model, rays_o, rays_d, q, n_out):
+    """[n, n_out + 1] distances at the quantiles of the per-bin densities q [n, B]
+    over each ray's box segment (zeros for misses)."""
+    lib = _load()
+    o, d = _f32(rays_o).reshape(-1, 3), _f32(rays_d).reshape(-1, 3)
+    n = o.shape[0]
+    qq = _f64(q).reshape(n, -1)
+    t = np.zeros((n, n_out + 1))
+    st = lib.orc_place_samples(ctypes.byref(model._s), n, _ptr(o), _ptr(d), _ptr(qq),
+                               qq.shape[1], int(n_out), _ptr(t))
+    if st != 0:
+        raise ValueError("oracle place_samples rejected its arguments")
+    return t
 
 
 def weight_histogram(model: Model, rays_o, rays_d, tau, n_samples, n_bins):

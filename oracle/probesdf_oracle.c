@@ -928,6 +928,29 @@ static void proposal_eval(const orc_model* m, const orc_proposal* pr, const floa
     for (int b = 0; b < B; ++b) st->p[b] /= sum;
 }
 
+/* Samples at the quantiles k / n_out, k = 0..n_out, of the piecewise-constant
+ * density q over B equal bins of [t_n, t_f]: the sample's bin is where the
+ * running sum of q first passes k / n_out, and it sits at the matching
+ * fraction of that bin. */
+static void place_quantiles(double tn, double tf, const double* q, int B, int n_out, double* t)
+{
+    const double db = (tf - tn) / B;
+    for (int k = 0; k <= n_out; ++k) {
+        const double u = (double)k / n_out;
+        double c = 0.0;
+        int b = 0;
+        while (b < B - 1 && c + q[b] <= u) {
+            c += q[b];
+            ++b;
+        }
+        double frac = (u - c) / q[b];
+        if (frac > 1.0) frac = 1.0;
+        t[k] = tn + (b + frac) * db;
+    }
+    t[0] = tn;
+    t[n_out] = tf;
+}
+
 int32_t orc_proposal_forward(const orc_model* m, const orc_proposal* pr, int64_t n_rays,
                              const float* rays_o, const float* rays_d, int32_t n_out,
                              double* logits, double* probs, double* t_samples, double* margin)
@@ -978,22 +1001,24 @@ int32_t orc_proposal_forward(const orc_model* m, const orc_proposal* pr, int64_t
             for (int k = 0; k <= n_out; ++k) t[k] = 0.0;
             continue;
         }
-        /* samples at the quantiles k / n_out of the piecewise-constant density */
-        const double tn = st.tn, tf = st.tf, db = (tf - tn) / B;
-        for (int k = 0; k <= n_out; ++k) {
-            const double u = (double)k / n_out;
-            double c = 0.0;
-            int b = 0;
-            while (b < B - 1 && c + q[b] <= u) {
-                c += q[b];
-                ++b;
-            }
-            double frac = (u - c) / q[b];
-            if (frac > 1.0) frac = 1.0;
-            t[k] = tn + (b + frac) * db;
+        place_quantiles(st.tn, st.tf, q, B, n_out, t);
+    }
+    return 0;
+}
+
+int32_t orc_place_samples(const orc_model* m, int64_t n_rays, const float* rays_o,
+                          const float* rays_d, const double* q, int32_t n_bins, int32_t n_out,
+                          double* t_samples)
+{
+    if (n_bins < 1 || n_out < 1) return -2;
+    for (int64_t r = 0; r < n_rays; ++r) {
+        float tn, tf;
+        double* t = t_samples + r * (n_out + 1);
+        if (!ray_box_f32(rays_o + 3 * r, rays_d + 3 * r, m->bmin, m->bmax, &tn, &tf)) {
+            for (int k = 0; k <= n_out; ++k) t[k] = 0.0;
+            continue;
         }
-        t[0] = tn;
-        t[n_out] = tf;
+        place_quantiles(tn, tf, q + r * n_bins, n_bins, n_out, t);
     }
     return 0;
 }

@@ -81,6 +81,9 @@ int32_t orc_occupancy(const orc_model* m, const int32_t res[3], double threshold
 int32_t orc_proposal_forward(const orc_model* m, const orc_proposal* pr, int64_t n_rays,
                              const float* rays_o, const float* rays_d, int32_t n_out,
                              double* logits, double* probs, double* t_samples, double* margin);
+int32_t orc_place_samples(const orc_model* m, int64_t n_rays, const float* rays_o,
+                          const float* rays_d, const double* q, int32_t n_bins, int32_t n_out,
+                          double* t_samples);
 int32_t orc_weight_histogram(const orc_model* m, const orc_params* p, int64_t n_rays,
                              const float* rays_o, const float* rays_d, int32_t n_bins,
                              double* hist, int32_t n_threads);

@@ -58,7 +58,7 @@ class MlpDesc(ctypes.Structure):
 class RenderParams(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_float), ("n_samples", ctypes.c_int32),
                 ("dir_mode", ctypes.c_int32), ("n_fresnel", ctypes.c_int32),
-                ("bg", ctypes.c_float * 3)]
+                ("bg", ctypes.c_float * 3), ("n_bins", ctypes.c_int32)]
 
 
 class ProposalDesc(ctypes.Structure):
@@ -290,8 +290,11 @@ class Scene:
 
 
 def render_params(tau=64.0, n_samples=128, dir_mode=DIR_REFLECT, n_fresnel=3,
-                  bg=(0.0, 0.0, 0.0)) -> RenderParams:
+                  bg=(0.0, 0.0, 0.0), n_bins=0) -> RenderParams:
+    """n_bins > 0: the render's t_samples argument holds [n, n_bins] bin
+    densities (samples at their quantiles) instead of distances."""
     p = RenderParams()
+    p.n_bins = int(n_bins)
     p.tau = float(tau)
     p.n_samples = int(n_samples)
     p.dir_mode = int(dir_mode)
@@ -551,12 +554,13 @@ def weight_histogram(scene: Scene, rays_o, rays_d, params: RenderParams, n_bins=
 
 
 def proposal_forward(scene: Scene, desc: ProposalDesc, params, occ, rays_o, rays_d, n_out,
-                     want_probs=True):
-    """(t_samples [n, n_out + 1], mixed density p' [n, B] or None)."""
+                     want_probs=True, want_t=True):
+    """(t_samples [n, n_out + 1] or None, mixed density p' [n, B] or None)."""
     _require_cuda(params, rays_o, rays_d)
     _require_cuda(occ, dtypes=(torch.int32,))
     n = rays_o.shape[0]
-    t = torch.empty((n, n_out + 1), dtype=torch.float32, device=rays_o.device)
+    t = torch.empty((n, n_out + 1), dtype=torch.float32, device=rays_o.device) \
+        if want_t else None
     probs = (torch.empty((n, desc.n_bins), dtype=torch.float32, device=rays_o.device)
              if want_probs else None)
     with _GridHandle(scene) as g:

@@ -125,6 +125,8 @@ psdf_status resolve(const psdf_grid* grid, const psdf_probes* probes, const psdf
     if (p->dir_mode != PSDF_DIR_REFLECT && p->dir_mode != PSDF_DIR_VIEW)
         return PSDF_ERR_INVALID_ARG;
     if (p->n_fresnel < 0 || p->n_fresnel > 8) return PSDF_ERR_BAD_SHAPE;
+    if (p->n_bins < 0 || p->n_bins > 32) return PSDF_ERR_BAD_SHAPE;
+    if (p->n_bins > 0 && n_rays > 0 && !t_samples) return PSDF_ERR_INVALID_ARG;
     const psdf_grid_desc& gd = grid->desc;
     const psdf_probe_desc& pd = probes->desc;
     const psdf_mlp_desc& md = mlp->desc;
@@ -179,6 +181,7 @@ psdf_status resolve(const psdf_grid* grid, const psdf_probes* probes, const psdf
     A.rays_o = rays_o;
     A.rays_d = rays_d;
     A.t_samples = t_samples;
+    A.n_bins = t_samples ? p->n_bins : 0;
     A.n_rays = n_rays;
     A.status = device_status_ptr();
     if (!A.status) return cuda_status(cudaErrorInvalidDevice);
@@ -709,7 +712,7 @@ psdf_status psdf_proposal_forward(const psdf_grid* grid, const psdf_proposal_des
     psdf_status st = proposal_launch(grid, desc, params, occ_bits, rays_o, rays_d, n_rays, L);
     if (st != PSDF_OK) return st;
     if (n_out < 1 || n_out > 4096) return PSDF_ERR_BAD_SHAPE;
-    if (n_rays > 0 && !t_samples) return PSDF_ERR_INVALID_ARG;
+    if (n_rays > 0 && !t_samples && !probs) return PSDF_ERR_INVALID_ARG;
     if (!aligned16(t_samples) || !aligned16(probs)) return PSDF_ERR_MISALIGNED;
     if (n_rays == 0) return PSDF_OK;
     L.n_out = n_out;

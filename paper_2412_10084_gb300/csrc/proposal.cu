@@ -295,8 +295,9 @@ template <int B>
 __global__ void proposal_fwd_kernel(PropArgs P)
 {
     constexpr int kParams = PropShape<B>::kParams;
-    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int kRow = 2 * B + 4;  // per ray: c_0..c_B, 1/q_0..1/q_{B-1}, hit, t_n, t_f
     __shared__ float sw[kParams];
+    __shared__ float srow[4 * 32 * kRow];
     extern __shared__ uint32_t sbits[];
     for (int i = threadIdx.x; i < kParams; i += blockDim.x) sw[i] = P.params[i];
     for (int i = threadIdx.x; i < occ_words(P); i += blockDim.x) sbits[i] = P.occ_bits[i];
@@ -348,34 +349,53 @@ __global__ void proposal_fwd_kernel(PropArgs P)
                 for (int b = 0; b < B; ++b) P.probs[ray * B + b] = q[b];
             }
         }
+        if (!P.t_samples) continue;  // densities only (the render places the samples)
+        // each lane stages its ray's density q_b and running sums c_b (summed in
+        // bin order, as the inverse CDF below defines them) for the row writes
+        float* cq = srow + (threadIdx.x >> 5) * 32 * kRow + lane * kRow;
+        {
+            float c = 0.0f;
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                cq[b] = c;
+                cq[B + 1 + b] = 1.0f / q[b];
+                c += q[b];
+            }
+            cq[B] = c;
+            cq[2 * B + 1] = __int_as_float(S.hit ? 1 : 0);
+            cq[2 * B + 2] = S.tn;
+            cq[2 * B + 3] = S.tf;
+        }
+        __syncwarp();
         const int64_t left = P.n_rays - base;
         const int rows = left < 32 ? static_cast<int>(left) : 32;
         for (int r = 0; r < rows; ++r) {
-            float qr[B];
-#pragma unroll
-            for (int b = 0; b < B; ++b) qr[b] = __shfl_sync(FULL, q[b], r);
-            const float tn = __shfl_sync(FULL, S.tn, r);
-            const float tf = __shfl_sync(FULL, S.tf, r);
-            const bool hit = __shfl_sync(FULL, S.hit ? 1 : 0, r) != 0;
+            const float* row = srow + (threadIdx.x >> 5) * 32 * kRow + r * kRow;
+            const bool hit = __float_as_int(row[2 * B + 1]) != 0;
+            const float tn = row[2 * B + 2], tf = row[2 * B + 3];
             float* t = P.t_samples + (base + r) * (P.n_out + 1);
-            // samples at the quantiles k / n_out of the piecewise-constant density
+            // samples at the quantiles k / n_out of the piecewise-constant
+            // density: bin b = the last with c_b <= u (binary search), which is
+            // where the walk "advance while c_b + q_b <= u" stops; the
+            // reciprocals 1 / n_out and 1 / q_b are rounded once (the render's
+            // bin-density placement uses the same expressions)
             const float db = (tf - tn) / B;
+            const float inv_n = 1.0f / P.n_out;
             for (int k = lane; k <= P.n_out; k += 32) {
                 float v = 0.0f;
                 if (hit) {
-                    const float u = static_cast<float>(k) / P.n_out;
+                    const float u = static_cast<float>(k) * inv_n;
                     int b = 0;
-                    float c = 0.0f;
-                    while (b < B - 1 && c + qr[b] <= u) {
-                        c += qr[b];
-                        ++b;
-                    }
-                    const float frac = fminf((u - c) / qr[b], 1.0f);
+#pragma unroll
+                    for (int step = B / 2; step > 0; step >>= 1)
+                        if (b + step < B && row[b + step] <= u) b += step;
+                    const float frac = fminf((u - row[b]) * row[B + 1 + b], 1.0f);
                     v = k == 0 ? tn : (k == P.n_out ? tf : fmaf(b + frac, db, tn));
                 }
                 t[k] = v;
             }
         }
+        __syncwarp();
     }
 }
 

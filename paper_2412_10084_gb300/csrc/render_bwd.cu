@@ -46,7 +46,8 @@ struct BwdLayout {
     static constexpr int oXH = (oF32 + 4 * M::kF32 + 127) & ~127;
     static constexpr int oDZ = oXH + M::kSplit * kXH;
     static constexpr int oG = oDZ + M::kSplit * kDZ;
-    static constexpr int oMisc = oG + 4 * kParamsPad;
+    static constexpr int oTab = oG + 4 * kParamsPad;  // per warp: 64-float placement table
+    static constexpr int oMisc = oTab + 4 * 64 * 4;
     static constexpr int kBytes = oMisc + 64;
     static constexpr uint32_t kTmemCols = 128;  // z1/dh1 at 0, z2/dx at 32, dW at 64
     static_assert(128 * PST * 4 <= M::kSplit * kDZ, "probe staging aliases the DZ tiles");
@@ -143,6 +144,7 @@ render_backward_kernel(RenderArgs A)
     uint8_t* dzh = smem + L::oDZ;
     uint8_t* dzl = dzh + L::kDZ;
     float* gacc = reinterpret_cast<float*>(smem + L::oG);
+    float* stab = reinterpret_cast<float*>(smem + L::oTab);
     float* red = reinterpret_cast<float*>(smem + L::oMisc);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::oMisc + 32);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::oMisc + 40);
@@ -227,7 +229,7 @@ render_backward_kernel(RenderArgs A)
             have = false;
             while (ray < A.n_rays) {
                 R = load_ray(A, ray);
-                sp = ray_span(A, R, ray);
+                sp = ray_span(A, R, ray, stab + 64 * warp);
                 const int live = A.n_live ? __ldg(A.n_live + ray) : N;
                 if (sp.hit && live > 0) {
                     have = true;

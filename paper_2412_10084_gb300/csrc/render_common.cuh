@@ -43,7 +43,8 @@ struct RenderArgs {
     float bg[3];
     const float* __restrict__ rays_o;
     const float* __restrict__ rays_d;
-    const float* __restrict__ t_samples;  // nullable [n_rays][N+1]
+    const float* __restrict__ t_samples;  // nullable [n_rays][N+1], or [n_rays][n_bins]
+    int n_bins;                           // > 0: t_samples holds bin densities
     int64_t n_rays;
     // forward outputs / backward inputs
     float* rgb;

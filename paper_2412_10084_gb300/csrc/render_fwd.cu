@@ -29,7 +29,8 @@ struct FwdLayout {
     static constexpr int oF32 = oW + M::kWeightBytes;
     static constexpr int oX = (oF32 + 4 * M::kF32 + 127) & ~127;
     static constexpr int oH = oX + M::kSplit * kXT;
-    static constexpr int oBar = oH + M::kSplit * kHT;
+    static constexpr int oTab = oH + M::kSplit * kHT;  // per warp: 64-float placement table
+    static constexpr int oBar = oTab + 4 * 64 * 4;
     static constexpr int kBytes = oBar + 16;
     static constexpr uint32_t kTmemCols = 64;  // layer 1 at column 0, layer 2 at 32
 };
@@ -48,6 +49,7 @@ render_forward_kernel(RenderArgs A)
     uint8_t* xl = xh + L::kXT;
     uint8_t* hh = smem + L::oH;
     uint8_t* hl = hh + L::kHT;
+    float* stab = reinterpret_cast<float*>(smem + L::oTab);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::oBar);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::oBar + 8);
 
@@ -76,7 +78,7 @@ render_forward_kernel(RenderArgs A)
         bool have = false;
         while (ray < A.n_rays) {
             R = load_ray(A, ray);
-            sp = ray_span(A, R, ray);
+            sp = ray_span(A, R, ray, stab + 64 * warp);
             if (sp.hit) {
                 have = true;
                 break;

@@ -215,14 +215,48 @@ struct RaySpan {
     bool hit;
     float tn, dt;
     const float* tk;  // given distances or nullptr
+    // placement at the quantiles k / N of per-bin densities (n_bins > 0): the
+    // warp's shared-memory table holds the running sums c_b = q_0 + .. + q_{b-1}
+    // at [0, 32) and 1 / q_b at [32, 64); dt is then the bin width
+    int n_bins, n;
+    float tf, inv_n;
+    const float* tab;
 };
 
-__device__ __forceinline__ RaySpan ray_span(const RenderArgs& A, const RayIn& R, int64_t ray)
+// tab: this warp's 64-float shared-memory table (used in the bin-density
+// mode).  Warp-uniform: every lane of the warp calls it for the warp's ray.
+__device__ __forceinline__ RaySpan ray_span(const RenderArgs& A, const RayIn& R, int64_t ray,
+                                            float* tab)
 {
     RaySpan sp;
     sp.tk = nullptr;
     sp.tn = 0.0f;
+    sp.tf = 0.0f;
     sp.dt = 0.0f;
+    sp.n_bins = 0;
+    sp.n = A.n_samples;
+    sp.inv_n = 0.0f;
+    sp.tab = tab;
+    if (A.t_samples && A.n_bins > 0) {
+        const int lane = threadIdx.x & 31;
+        float tf;
+        sp.hit = ray_box(R.o, R.d, A.grid, sp.tn, tf);
+        sp.tf = tf;
+        sp.n_bins = A.n_bins;
+        const float q = lane < A.n_bins ? __ldg(A.t_samples + ray * (int64_t)A.n_bins + lane) : 0.0f;
+        float c = 0.0f;
+        for (int i = 0; i < A.n_bins; ++i) {  // running sums in bin order
+            const float qi = __shfl_sync(0xffffffffu, q, i);
+            if (i < lane) c += qi;
+        }
+        __syncwarp();  // the previous ray's readers are done with the table
+        tab[lane] = c;
+        tab[32 + lane] = lane < A.n_bins ? 1.0f / q : 0.0f;
+        __syncwarp();
+        sp.dt = (tf - sp.tn) / A.n_bins;
+        sp.inv_n = 1.0f / A.n_samples;
+        return sp;
+    }
     if (A.t_samples) {
         sp.tk = A.t_samples + ray * (int64_t)(A.n_samples + 1);
         sp.hit = __ldg(sp.tk + A.n_samples) > __ldg(sp.tk);
@@ -234,8 +268,24 @@ __device__ __forceinline__ RaySpan ray_span(const RenderArgs& A, const RayIn& R,
     return sp;
 }
 
+// Distance of sample k (0..N).
 __device__ __forceinline__ float span_t(const RaySpan& sp, int k)
 {
+    if (sp.n_bins > 0) {
+        // the sample's bin is the last with c_b <= u (binary search over the
+        // running sums), then t = t_n + (b + (u - c_b) / q_b) width, with the
+        // reciprocals rounded once per ray (the proposal kernel uses the same
+        // expressions, so both place samples at the same FP32 distances)
+        const float u = static_cast<float>(k) * sp.inv_n;
+        int b = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int j = b + step;
+            if (j < sp.n_bins && sp.tab[j] <= u) b = j;
+        }
+        const float frac = fminf((u - sp.tab[b]) * sp.tab[32 + b], 1.0f);
+        return k == 0 ? sp.tn : (k == sp.n ? sp.tf : fmaf(b + frac, sp.dt, sp.tn));
+    }
     return sp.tk ? __ldg(sp.tk + k) : sample_t(k, sp.dt, sp.tn);
 }
 

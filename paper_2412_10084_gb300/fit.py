@@ -121,11 +121,14 @@ def train_proposal(scene: Scene, prop: Proposal, rays_o, rays_d, tau, n_uniform=
 
 def render_proposed(scene: Scene, prop: Proposal, rays_o, rays_d, n_out, params: RenderParams):
     """(rgb, depth, wsum, logT) of the render at proposal-placed distances
-    (n_out colour samples per ray; params.n_samples is replaced by n_out)."""
-    t, _ = proposal_forward(scene, prop.desc, prop.params, prop.occ, rays_o, rays_d, n_out,
-                            want_probs=False)
-    p = render_params(params.tau, n_out, params.dir_mode, params.n_fresnel, tuple(params.bg))
-    return render_forward(scene, rays_o, rays_d, p, t)
+    (n_out colour samples per ray; params.n_samples is replaced by n_out).
+    The proposal returns its per-bin densities and the render places the
+    samples at their quantiles itself."""
+    _, q = proposal_forward(scene, prop.desc, prop.params, prop.occ, rays_o, rays_d, n_out,
+                            want_probs=True, want_t=False)
+    p = render_params(params.tau, n_out, params.dir_mode, params.n_fresnel, tuple(params.bg),
+                      n_bins=prop.desc.n_bins)
+    return render_forward(scene, rays_o, rays_d, p, q)
 
 
 def reduced_copy(scene: Scene, feat_dtype, probe_dtype, mlp_dtype) -> Scene:

@@ -229,3 +229,46 @@ def test_proposal_host_validation():
     t, _ = ps.proposal_forward(scene, ps.proposal_desc((8, 8, 8)), prm, occ, dev(o[:0]),
                                dev(d[:0]), 8)
     assert t.shape == (0, 9)
+
+
+@pytest.mark.parametrize("B", [8, 16])
+def test_bin_density_render_equals_explicit_distances(B):
+    """The render placing samples from the proposal's bin densities uses the
+    very distances the proposal writes: forward outputs are bit-identical and
+    the adjoints agree to summation order."""
+    sc, o, d = scene_and_rays(n_rays=700, seed_offset=30 + B)
+    scene = ps.Scene.from_host(sc)
+    res = (16, 16, 16)
+    occ = ps.occupancy_build(scene, res, threshold_f32(sc))
+    desc = ps.proposal_desc(res, n_bins=B, mix=0.3, theta=0.0)
+    o_, d_ = dev(o), dev(d)
+    n_out = 45
+    t, q = ps.proposal_forward(scene, desc, dev(proposal_params(B=B)), occ, o_, d_, n_out)
+    pe = ps.render_params(64.0, n_out, n_fresnel=sc.n_fresnel)
+    pb = ps.render_params(64.0, n_out, n_fresnel=sc.n_fresnel, n_bins=B)
+    a = ps.render_forward(scene, o_, d_, pe, t, want_live=True)
+    b = ps.render_forward(scene, o_, d_, pb, q, want_live=True)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    drgb = dev(synth.rng(5).normal(size=(700, 3)) / 700)
+    ga = ps.render_backward(scene, o_, d_, pe, drgb, a[3], t_samples=t, n_live=a[4])
+    gb = ps.render_backward(scene, o_, d_, pb, drgb, b[3], t_samples=q, n_live=b[4])
+    for x, y in zip(ga, gb):
+        assert rel_err_tensor(x.cpu().numpy(), y.cpu().numpy()) <= 1e-6
+
+
+def test_bin_density_render_parity_with_oracle():
+    sc, o, d = scene_and_rays(n_rays=500, seed_offset=77)
+    B, n_out = 16, 40
+    g = synth.rng(12)
+    q = g.uniform(0.2, 1.0, size=(500, B)) ** 3
+    q = (q / q.sum(1, keepdims=True)).astype(np.float32)  # the same FP32 densities both sides
+    scene = ps.Scene.from_host(sc)
+    params = ps.render_params(64.0, n_out, n_fresnel=sc.n_fresnel, n_bins=B)
+    rgb, depth, wsum, _ = ps.render_forward(scene, dev(o), dev(d), params, dev(q))
+    m = oracle.Model.from_scene(sc)
+    t_ref = oracle.place_samples(m, o, d, q.astype(np.float64), n_out)
+    ref = oracle.render_forward(m, o, d, 64.0, n_out, t_samples=t_ref)
+    for name, x in (("rgb", rgb), ("depth", depth), ("wsum", wsum)):
+        err = np.max(np.abs(x.cpu().numpy() - ref[name]) / np.maximum(np.abs(ref[name]), 1e-2))
+        assert err <= 1e-5, (name, err)
