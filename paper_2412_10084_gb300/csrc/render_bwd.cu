@@ -49,7 +49,13 @@ struct BwdLayout {
     static constexpr int oTab = oG + 4 * kParamsPad;  // per warp: 64-float placement table
     static constexpr int oMisc = oTab + 4 * 64 * 4;
     static constexpr int kBytes = oMisc + 64;
-    static constexpr uint32_t kTmemCols = 128;  // z1/dh1 at 0, z2/dx at 32, dW at 64
+    static constexpr uint32_t kTmemCols = 128;  // z1/dh1 at 0, z2/dx at 32, dW at 64..111
+    // blended probe coefficients of each sample (Bc, L2 x NA floats), kept from
+    // P0 to P5 in columns 112..127 and a second 32-column allocation
+    static constexpr int kBc = C::L2 * C::NA;
+    static constexpr bool kKeepBc = kBc <= 48 && kBc % 4 == 0;
+    static constexpr uint32_t kTmemCols2 = kKeepBc ? 32 : 0;
+    static constexpr uint32_t kBcCol = 112;
     static_assert(128 * PST * 4 <= M::kSplit * kDZ, "probe staging aliases the DZ tiles");
     static_assert(XHC <= 64, "dW accumulator fits columns 64..127");
 };
@@ -125,6 +131,38 @@ __device__ __forceinline__ void scatter_probe_grad(const RenderArgs& A, const fl
     }
 }
 
+// The blended probe coefficients of the warp's 32 samples into / out of their
+// tensor-memory columns (warp-collective): the first 16 in columns 112..127 of
+// the main allocation, the rest from column 0 of the second.
+template <class L>
+__device__ __forceinline__ void bc_store(uint32_t t_row, uint32_t t_row2, const float* Bc)
+{
+    tc::tmem_st16(t_row + L::kBcCol, Bc);
+#pragma unroll
+    for (int i = 16; i < L::kBc; i += 16) {
+        if (i + 16 <= L::kBc)
+            tc::tmem_st16(t_row2 + (i - 16), Bc + i);
+        else
+#pragma unroll
+            for (int r = i; r < L::kBc; r += 4) tc::tmem_st4(t_row2 + (r - 16), Bc + r);
+    }
+    tc::tmem_st_wait();
+}
+
+template <class L>
+__device__ __forceinline__ void bc_load(uint32_t t_row, uint32_t t_row2, float* Bc)
+{
+    tc::tmem_ld16(t_row + L::kBcCol, Bc);
+#pragma unroll
+    for (int i = 16; i < L::kBc; i += 16) {
+        if (i + 16 <= L::kBc)
+            tc::tmem_ld16(t_row2 + (i - 16), Bc + i);
+        else
+#pragma unroll
+            for (int r = i; r < L::kBc; r += 4) tc::tmem_ld4(t_row2 + (r - 16), Bc + r);
+    }
+}
+
 template <class C>
 __global__ void __launch_bounds__(kBwdThreads, 3)
 render_backward_kernel(RenderArgs A)
@@ -148,6 +186,7 @@ render_backward_kernel(RenderArgs A)
     float* red = reinterpret_cast<float*>(smem + L::oMisc);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::oMisc + 32);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::oMisc + 40);
+    uint32_t* tslot2 = reinterpret_cast<uint32_t*>(smem + L::oMisc + 44);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const unsigned FULL = 0xffffffffu;
@@ -158,7 +197,10 @@ render_backward_kernel(RenderArgs A)
 
     load_mlp_tc<C>(A.mlp, wt, f32);
     for (int i = tid; i < L::kParamsPad; i += blockDim.x) gacc[i] = 0.0f;
-    if (warp == 0) tc::tmem_alloc(tslot, L::kTmemCols);
+    if (warp == 0) {
+        tc::tmem_alloc(tslot, L::kTmemCols, !L::kKeepBc);
+        if constexpr (L::kKeepBc) tc::tmem_alloc(tslot2, L::kTmemCols2, true);
+    }
     if (tid == 0) tc::mbar_init(mbar, 1);
     {
         // gradient scale: the largest |dL/drgb| over the rays this CTA renders
@@ -176,6 +218,7 @@ render_backward_kernel(RenderArgs A)
     tc::fence_after();
     const uint32_t tmem = *tslot;
     const uint32_t t_row = tmem + (static_cast<uint32_t>(32 * warp) << 16);
+    const uint32_t t_row2 = L::kKeepBc ? *tslot2 + (static_cast<uint32_t>(32 * warp) << 16) : 0u;
     // Power-of-two scales of the dz2 and dz1 tiles.  With |w| <= 1 and
     // sigmoid' <= 1/4: |dz3| <= M/4 (M = largest |dL/drgb| of the CTA),
     // |dz2_i| <= B2 = M/4 * sum_c |W3[c][i]|, |dz1_i| <= B1 = max_i sum_o |W2[o][i]| * B2.
@@ -284,10 +327,21 @@ render_backward_kernel(RenderArgs A)
                 // alpha = 0 where the opacity is clipped: the sample's weight,
                 // colour terms, dz rows and so dF (dx) are exactly zero, and its
                 // appearance is not needed (see P5)
-                if (unclipped)
+                if constexpr (L::kKeepBc) {
+                    float Bc[L::kBc];
+                    if (unclipped) {
+                        eval_appearance_blend<C>(A, R.o, R.d, t, S, Bc);
+                    } else {
+                        zero_appearance<C>(S);
+#pragma unroll
+                        for (int i = 0; i < L::kBc; ++i) Bc[i] = 0.0f;
+                    }
+                    bc_store<L>(t_row, t_row2, Bc);
+                } else if (unclipped) {
                     eval_appearance<C>(A, R.o, R.d, t, S);
-                else
+                } else {
                     zero_appearance<C>(S);
+                }
                 float xin[K1];
 #pragma unroll
                 for (int i = 0; i < K1; ++i) xin[i] = i < NIN ? S.x[i] : (i == NIN ? 1.0f : 0.0f);
@@ -295,6 +349,12 @@ render_backward_kernel(RenderArgs A)
             } else {
                 zero_row<K1, M::kSplit>(xhh, xhl, tid, 0, L::XHC);
                 S.s = 0.0f;
+                if constexpr (L::kKeepBc) {  // warp-collective store: keep every warp in step
+                    float Bc[L::kBc];
+#pragma unroll
+                    for (int i = 0; i < L::kBc; ++i) Bc[i] = 0.0f;
+                    bc_store<L>(t_row, t_row2, Bc);
+                }
             }
             tc::fence_smem_to_async();
             tc::fence_before();
@@ -516,14 +576,24 @@ render_backward_kernel(RenderArgs A)
             float* pst = reinterpret_cast<float*>(dzh) + warp * 32 * L::PST;
             if (have) {
                 float gxs = 0.0f, gys = 0.0f, gzs = 0.0f;
+                float Bc[L::kKeepBc ? L::kBc : 1];
+                if constexpr (L::kKeepBc) bc_load<L>(t_row, t_row2, Bc);  // warp-collective
                 if (unclipped) {
                     float wq[8];
                     corner_weights(S.pcell.f, wq);
-                    int pidx[8];
-                    probe_corner_index(A.probes, S.pcell, pidx);
                     float dY[L2];
 #pragma unroll
                     for (int j = 0; j < L2; ++j) dY[j] = 0.0f;
+                    if constexpr (L::kKeepBc) {
+                        // dF_a,c / dY_j = Bc_jc (Eq. 7)
+#pragma unroll
+                        for (int j = 0; j < L2; ++j)
+#pragma unroll
+                            for (int c = 0; c < NA; ++c)
+                                dY[j] = fmaf(Bc[j * NA + c], dx[3 + c], dY[j]);
+                    } else {
+                    int pidx[8];
+                    probe_corner_index(A.probes, S.pcell, pidx);
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
 #pragma unroll
@@ -539,6 +609,7 @@ render_backward_kernel(RenderArgs A)
                             }
                             dY[j] = fmaf(wq[q], acc, dY[j]);
                         }
+                    }
                     }
                     {
                         float Y[L2];
@@ -662,7 +733,10 @@ done:
     }
     tc::fence_before();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, L::kTmemCols);
+    if (warp == 0) {
+        tc::tmem_dealloc(tmem, L::kTmemCols);
+        if constexpr (L::kKeepBc) tc::tmem_dealloc(*tslot2, L::kTmemCols2);
+    }
     if (any_chunk)
         for (int i = tid; i < C::kParams; i += blockDim.x) red_add(A.grad_mlp + i, gacc[i]);
 }
@@ -699,7 +773,7 @@ cudaError_t backward_occupancy_t(int* n)
     cudaFuncAttributes fa;
     e = cudaFuncGetAttributes(&fa, render_backward_kernel<C>);
     if (e != cudaSuccess) return e;
-    *n = resident_ctas(fa, kBwdThreads, L::kBytes, L::kTmemCols);
+    *n = resident_ctas(fa, kBwdThreads, L::kBytes, L::kTmemCols + L::kTmemCols2);
     return *n > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
 }
 

@@ -176,6 +176,71 @@ __device__ __forceinline__ void eval_appearance(const RenderArgs& A, const float
     for (int i = C::NIN; i < C::NINP; ++i) S.x[i] = 0.0f;
 }
 
+// eval_appearance that also returns the blended probe coefficients
+// Bc[j NA + c] = sum_i w_i b_ijc (Eq. 7 before the SH contraction), which the
+// adjoint reuses for dF_a / dY_j = Bc_j . dF_a.
+template <class C>
+__device__ __forceinline__ void eval_appearance_blend(const RenderArgs& A, const float o[3],
+                                                      const float d[3], float t,
+                                                      SampleGeom<C>& S, float* Bc)
+{
+    const float gg = S.g[0] * S.g[0] + S.g[1] * S.g[1] + S.g[2] * S.g[2];
+    S.rho = sqrtf(gg + kNormalEps * kNormalEps);
+    const float inv = 1.0f / S.rho;
+    float v[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        S.n[a] = S.g[a] * inv;
+        v[a] = -d[a];
+    }
+    S.ndv = S.n[0] * v[0] + S.n[1] * v[1] + S.n[2] * v[2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        S.r[a] = A.dir_mode == 1 ? v[a] : 2.0f * S.ndv * S.n[a] - v[a];
+    sh_basis<C::L2>(S.r, S.Y);
+
+    float xw[3];
+    point_at(o, d, t, xw);
+    S.pcell = locate(xw, A.grid.bmin, A.probes.sc, A.probes.P);
+    float wq[8];
+    corner_weights(S.pcell.f, wq);
+    int pidx[8];
+    probe_corner_index(A.probes, S.pcell, pidx);
+#pragma unroll
+    for (int i = 0; i < C::L2 * C::NA; ++i) Bc[i] = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+#pragma unroll
+        for (int j = 0; j < C::L2; ++j) {
+#pragma unroll
+            for (int cg = 0; cg < C::NA4; ++cg) {
+                const float4 bb = probe_coeffs<C>(A.probes, pidx[q], j, cg);
+                float* b4 = Bc + j * C::NA + 4 * cg;
+                b4[0] = fmaf(wq[q], bb.x, b4[0]);
+                b4[1] = fmaf(wq[q], bb.y, b4[1]);
+                b4[2] = fmaf(wq[q], bb.z, b4[2]);
+                b4[3] = fmaf(wq[q], bb.w, b4[3]);
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < C::NA; ++c) {
+        float fa = 0.0f;
+#pragma unroll
+        for (int j = 0; j < C::L2; ++j) fa = fmaf(S.Y[j], Bc[j * C::NA + c], fa);
+        S.x[3 + c] = fa;
+    }
+    const float om = 1.0f - S.ndv;
+    float pw = 1.0f;
+#pragma unroll
+    for (int kk = 0; kk < C::K; ++kk) {
+        pw *= om;
+        S.x[3 + C::NA + kk] = pw;
+    }
+#pragma unroll
+    for (int i = C::NIN; i < C::NINP; ++i) S.x[i] = 0.0f;
+}
+
 // MLP input of a sample whose opacity is zero: its colour is never used
 // (every term it enters is multiplied by alpha = 0), so the appearance
 // columns are left at zero.
