@@ -61,7 +61,18 @@ class _Model(ctypes.Structure):
         ("width", ctypes.c_int32),
         ("n_fresnel", ctypes.c_int32),
         ("mlp", ctypes.c_void_p),
+        ("feat_layout", ctypes.c_int32),
+        ("planes", ctypes.c_void_p),
     ]
+
+
+FEAT_NODES = 0
+FEAT_TRIPLANE = 1
+TILE = 16
+
+
+def n_tiles(R):
+    return (int(R) - 1 + TILE - 1) // TILE
 
 
 class _Params(ctypes.Structure):
@@ -141,9 +152,11 @@ class Model:
     (W1[W][n_in] b1 W2[W][W] b2 W3[3][W] b3), box in FP32.
     """
 
-    def __init__(self, sdf, feat, probes, mlp, box_min, box_max, sh_l, width, n_fresnel):
+    def __init__(self, sdf, feat, probes, mlp, box_min, box_max, sh_l, width, n_fresnel,
+                 planes=None):
         self.sdf = _f64(sdf)
         self.feat = _f64(feat)
+        self.planes = None if planes is None else _f64(planes)
         self.probes = _f64(probes)
         self.mlp = _f64(mlp).ravel()
         self.box_min = _f32(box_min)
@@ -152,7 +165,10 @@ class Model:
         self.width = int(width)
         self.n_fresnel = int(n_fresnel)
         Rz, Ry, Rx = self.sdf.shape
-        self.n_s = self.feat.shape[-1]
+        self.n_s = self.feat.shape[-1] if self.planes is None else self.planes.shape[-1]
+        if self.planes is not None:
+            assert self.planes.shape == (n_tiles(Rz), n_tiles(Ry), n_tiles(Rx), 3, TILE, TILE,
+                                         self.n_s), "planes [tz][ty][tx][3][16][16][n_s]"
         Pz, Py, Px, L2, na = self.probes.shape
         assert L2 == self.sh_l ** 2
         self.n_a = na
@@ -173,12 +189,14 @@ class Model:
         s.width = W
         s.n_fresnel = self.n_fresnel
         s.mlp = self.mlp.ctypes.data
+        s.feat_layout = FEAT_NODES if self.planes is None else FEAT_TRIPLANE
+        s.planes = None if self.planes is None else self.planes.ctypes.data
         self._s = s
 
     @classmethod
     def from_scene(cls, sc):
         return cls(sc.sdf, sc.feat, sc.probes, sc.mlp, sc.box_min, sc.box_max, sc.sh_l,
-                   sc.width, sc.n_fresnel)
+                   sc.width, sc.n_fresnel, planes=getattr(sc, "planes", None))
 
 
 def _params(tau, n_samples, dir_mode=DIR_REFLECT, bg=(0.0, 0.0, 0.0)):
@@ -217,7 +235,8 @@ def render_backward(model: Model, rays_o, rays_d, d_rgb, tau, n_samples, d_depth
                     d_wsum=None, dir_mode=DIR_REFLECT, bg=(0.0, 0.0, 0.0), t_samples=None,
                     n_threads=1):
     """Gradients of sum(d_rgb*rgb + d_depth*depth + d_wsum*wsum) w.r.t. the
-    SDF nodes, node features, probe coefficients and MLP parameters."""
+    SDF nodes, node features (or tile planes), probe coefficients and MLP
+    parameters."""
     lib = _load()
     o, d = _f32(rays_o).reshape(-1, 3), _f32(rays_d).reshape(-1, 3)
     n = o.shape[0]
@@ -226,7 +245,7 @@ def render_backward(model: Model, rays_o, rays_d, d_rgb, tau, n_samples, d_depth
     dd = None if d_depth is None else _f64(d_depth).reshape(n)
     dw = None if d_wsum is None else _f64(d_wsum).reshape(n)
     g_sdf = np.zeros_like(model.sdf)
-    g_feat = np.zeros_like(model.feat)
+    g_feat = np.zeros_like(model.feat if model.planes is None else model.planes)
     g_probe = np.zeros_like(model.probes)
     g_mlp = np.zeros_like(model.mlp)
     p = _params(tau, n_samples, dir_mode, bg)

@@ -224,6 +224,80 @@ static inline double log_phi(double tau, double s)
 
 static int mlp_n_in(const orc_model* m) { return m->n_s + m->n_a + m->n_fresnel; }
 
+/* Tile tri-plane spatial features (Sec. 3.1, Sec. 4): the grid's cells are cut
+ * into tiles of 16^3; each tile holds three 16 x 16 planes of n_s channels,
+ * orthogonal to x, y and z, and F_s = F_x (.) F_y (.) F_z, each factor a
+ * bilinear lookup in its plane at the point's two in-plane coordinates.  A
+ * plane's 16 texels per axis sit at the centres of the tile's 16 cells; a
+ * point's texel coordinate is clamped to the tile's texels.  The tile and
+ * texel of a coordinate are exact functions of the FP32 grid coordinate u
+ * (u / 16 and u - 16 t are exact). */
+typedef struct {
+    size_t plane0;     /* offset of the tile's first plane (in values) */
+    int i[3];          /* texel index along x, y, z (0..14) */
+    double f[3];       /* fraction to the next texel */
+    double b[3][ORC_MAX_NS];  /* the three bilinear lookups per channel */
+} tri_at;
+
+static int n_tiles(int32_t R) { return (R - 1 + ORC_TILE - 1) / ORC_TILE; }
+
+static size_t texel(int plane, int r, int c, int ns)
+{
+    return (((size_t)plane * ORC_TILE + (size_t)r) * ORC_TILE + (size_t)c) * (size_t)ns;
+}
+
+static void triplane_locate(const orc_model* m, const int ci[3], const double cf[3], tri_at* T)
+{
+    int t[3];
+    for (int a = 0; a < 3; ++a) {
+        const double u = (double)ci[a] + cf[a];
+        const int nt = n_tiles(m->R[a]);
+        int ta = (int)floor(u / ORC_TILE);
+        if (ta > nt - 1) ta = nt - 1;
+        if (ta < 0) ta = 0;
+        double tau = u - (double)ORC_TILE * ta - 0.5;
+        if (tau < 0.0) tau = 0.0;
+        if (tau > ORC_TILE - 1) tau = ORC_TILE - 1;
+        int i = (int)floor(tau);
+        if (i > ORC_TILE - 2) i = ORC_TILE - 2;
+        t[a] = ta;
+        T->i[a] = i;
+        T->f[a] = tau - i;
+    }
+    const size_t tile = ((size_t)t[2] * n_tiles(m->R[1]) + t[1]) * n_tiles(m->R[0]) + t[0];
+    T->plane0 = tile * 3 * ORC_TILE * ORC_TILE * (size_t)m->n_s;
+}
+
+/* Bilinear weights of a plane lookup at (row axis, column axis). */
+static void bilerp_w(const tri_at* T, int ra, int ca, double w[4])
+{
+    const double fr = T->f[ra], fc = T->f[ca];
+    w[0] = (1 - fr) * (1 - fc);
+    w[1] = (1 - fr) * fc;
+    w[2] = fr * (1 - fc);
+    w[3] = fr * fc;
+}
+
+/* plane p: 0 is [z][y], 1 is [z][x], 2 is [y][x] */
+static const int kPlaneRow[3] = {2, 2, 1}, kPlaneCol[3] = {1, 0, 0};
+
+static void triplane_features(const orc_model* m, tri_at* T, double* fs)
+{
+    const int ns = m->n_s;
+    for (int p = 0; p < 3; ++p) {
+        const int ra = kPlaneRow[p], ca = kPlaneCol[p];
+        double w[4];
+        bilerp_w(T, ra, ca, w);
+        const int r = T->i[ra], c = T->i[ca];
+        const double* P = m->planes + T->plane0;
+        for (int q = 0; q < ns; ++q)
+            T->b[p][q] = w[0] * P[texel(p, r, c, ns) + q] + w[1] * P[texel(p, r, c + 1, ns) + q] +
+                         w[2] * P[texel(p, r + 1, c, ns) + q] +
+                         w[3] * P[texel(p, r + 1, c + 1, ns) + q];
+    }
+    for (int q = 0; q < ns; ++q) fs[q] = T->b[0][q] * T->b[1][q] * T->b[2][q];
+}
+
 /* Point geometry (positions, cells, SDF value and gradient, spatial
  * features).  `color` also asks for the rest of the colour inputs. */
 static void eval_point(const orc_model* m, const orc_params* p, const float o[3],
@@ -248,10 +322,15 @@ static void eval_point(const orc_model* m, const orc_params* p, const float o[3]
         const double sv = m->sdf[nd];
         S->s += w * sv;
         for (int a = 0; a < 3; ++a) S->g[a] += sv * dw[a] * (double)sc[a];
-        if (color)
+        if (color && m->feat_layout == ORC_FEAT_NODES)
             for (int q = 0; q < ns; ++q) S->x[q] += w * m->feat[nd * (size_t)ns + q];
     }
     if (!color) return;
+    if (m->feat_layout == ORC_FEAT_TRIPLANE) {
+        tri_at T;
+        triplane_locate(m, S->ci, S->cf, &T);
+        triplane_features(m, &T, S->x);
+    }
 
     /* Normal (Eq. 13) with a guard against 0/0, view and reflected vectors. */
     const double gg = S->g[0] * S->g[0] + S->g[1] * S->g[1] + S->g[2] * S->g[2];
@@ -551,9 +630,33 @@ static void backward_ray(const orc_model* m, const orc_params* p, const float* d
             if (k < N)
                 for (int a = 0; a < 3; ++a) gsdf += dg[a] * dw[a] * (double)sc[a];
             add_f64(&gs->g_sdf[nd], gsdf, gs->atomic);
-            if (k < N)
+            if (k < N && m->feat_layout == ORC_FEAT_NODES)
                 for (int q = 0; q < ns; ++q)
                     add_f64(&gs->g_feat[nd * (size_t)ns + q], w * dx[q], gs->atomic);
+        }
+        if (k < N && m->feat_layout == ORC_FEAT_TRIPLANE) {
+            /* F_s = b0 b1 b2 per channel: each plane's lookup gets dF_s times the
+             * other two, spread over its 4 texels by the bilinear weights */
+            tri_at T;
+            triplane_locate(m, S->ci, S->cf, &T);
+            double fs[ORC_MAX_NS];
+            triplane_features(m, &T, fs);
+            for (int p2 = 0; p2 < 3; ++p2) {
+                const int ra = kPlaneRow[p2], ca = kPlaneCol[p2];
+                double w4[4];
+                bilerp_w(&T, ra, ca, w4);
+                const int r = T.i[ra], c = T.i[ca];
+                const size_t o4[4] = {texel(p2, r, c, ns), texel(p2, r, c + 1, ns),
+                                      texel(p2, r + 1, c, ns), texel(p2, r + 1, c + 1, ns)};
+                for (int q = 0; q < ns; ++q) {
+                    double other = 1.0;
+                    for (int p3 = 0; p3 < 3; ++p3)
+                        if (p3 != p2) other *= T.b[p3][q];
+                    for (int e = 0; e < 4; ++e)
+                        add_f64(&gs->g_feat[T.plane0 + o4[e] + q], w4[e] * other * dx[q],
+                                gs->atomic);
+                }
+            }
         }
     }
     free(G);
@@ -692,6 +795,10 @@ static int check_model(const orc_model* m, const orc_params* p)
     for (int a = 0; a < 3; ++a)
         if (m->R[a] < 2 || m->P[a] < 2 || !(m->bmax[a] > m->bmin[a])) return -2;
     if (p->n_samples < 1) return -2;
+    if (m->feat_layout == ORC_FEAT_TRIPLANE ? !m->planes
+                                            : (m->feat_layout != ORC_FEAT_NODES ||
+                                               (m->n_s > 0 && !m->feat)))
+        return -2;
     return 0;
 }
 

@@ -32,7 +32,14 @@ typedef struct orc_model {
     int32_t width;         /* MLP hidden width W */
     int32_t n_fresnel;     /* K: Fresnel powers 1..K */
     const double* mlp;     /* W1[W][n_in] b1[W] W2[W][W] b2[W] W3[3][W] b3[3] */
+    int32_t feat_layout;   /* ORC_FEAT_NODES: feat per node; ORC_FEAT_TRIPLANE: planes */
+    const double* planes;  /* [tz][ty][tx][3][16][16][n_s]: per 16^3 tile, the planes
+                              orthogonal to x ([z][y]), y ([z][x]) and z ([y][x]) */
 } orc_model;
+
+#define ORC_FEAT_NODES 0
+#define ORC_FEAT_TRIPLANE 1
+#define ORC_TILE 16
 
 typedef struct orc_params {
     double tau;            /* NeuS logistic scale */

@@ -46,6 +46,7 @@ class Scene:
     sh_l: int
     width: int
     n_fresnel: int
+    planes: np.ndarray | None = None  # float32 [tz][ty][tx][3][16][16][n_s] (tile tri-planes)
 
     @property
     def dims(self):
@@ -59,7 +60,7 @@ class Scene:
 
     @property
     def n_s(self):
-        return self.feat.shape[-1]
+        return self.feat.shape[-1] if self.planes is None else self.planes.shape[-1]
 
     @property
     def n_a(self):
@@ -490,3 +491,20 @@ def training_pool(name: str, n_rays: int, seed_offset: int = 0):
     teacher colours (Rays with target = teacher RGB)."""
     r = make_rays(name, n_rays=n_rays, seed_offset=seed_offset)
     return Rays(o=r.o, d=r.d, target=teacher_colors(name, r.o, r.d))
+
+
+TILE = 16
+
+
+def tile_planes(dims, n_s, g: np.random.Generator, mean=1.0, std=0.3) -> np.ndarray:
+    """Seeded tile tri-planes [tz][ty][tx][3][16][16][n_s] for a grid of `dims`
+    nodes (16^3-cell tiles): N(mean, std) texels, so that the product of the
+    three lookups stays of order one."""
+    nt = [(int(r) - 1 + TILE - 1) // TILE for r in dims]
+    return g.normal(mean, std, size=(nt[2], nt[1], nt[0], 3, TILE, TILE, n_s)).astype(np.float32)
+
+
+def with_triplanes(sc: Scene, seed: int, **kw) -> Scene:
+    """The scene with tile tri-plane spatial features instead of node features."""
+    return dataclasses.replace(sc, planes=tile_planes(sc.dims, sc.feat.shape[-1], rng(seed), **kw),
+                               feat=np.zeros(sc.feat.shape[:-1] + (0,), np.float32))

@@ -676,3 +676,112 @@ def test_proposal_occupancy_inputs_brute_force(B, n_sub, res):
         np.testing.assert_allclose(fs["logits"][i], before, atol=1e-12)
         checked += 1
     assert checked > 20
+
+
+# ----------------------------------------------------------------------------
+# Tile tri-plane spatial features (Sec. 3.1, Sec. 4)
+# ----------------------------------------------------------------------------
+
+def _triplane_scene(R=(20, 35, 18), seed=5, planes=None):
+    sc = tiny_scene(R=R, P=(4, 4, 4), seed=seed)
+    sc = synth.with_triplanes(sc, seed + 1)
+    if planes is not None:
+        sc.planes[...] = planes
+    return sc
+
+
+def _fs_at(m, sc, pts):
+    """F_s (the first n_s MLP inputs) at world points, looked up along +x rays."""
+    out = []
+    for x in pts:
+        o = np.asarray(x, np.float32) - np.float32([1.0, 0.0, 0.0])
+        d = np.float32([1.0, 0.0, 0.0])
+        r = oracle.point_eval(m, o, d, 1.0)
+        out.append(r["x"][:sc.n_s])
+    return np.array(out)
+
+
+def test_triplane_constant_planes_give_the_product():
+    sc = _triplane_scene()
+    c = np.array([1.5, -0.7, 2.0])  # plane p holds c[p] in every texel and channel
+    sc.planes[...] = c[None, None, None, :, None, None, None]
+    m = oracle.Model.from_scene(sc)
+    pts = synth.rng(7).uniform(0.02, 0.98, size=(40, 3))
+    want = np.prod(c.astype(np.float32).astype(np.float64))  # the planes are stored in FP32
+    np.testing.assert_allclose(_fs_at(m, sc, pts), want, rtol=1e-14)
+
+
+def test_triplane_affine_planes_are_reproduced_inside_a_tile():
+    """Texels affine in their in-plane coordinates: the bilinear lookups are
+    exact, so F_s is the product of the affine functions of the point's local
+    coordinates (texel i sits at local coordinate i + 1/2)."""
+    R = (33, 33, 33)  # two tiles per axis, spacing 1/32
+    sc = _triplane_scene(R=R)
+    i = np.arange(16) + 0.5
+    a = [(0.3, 1.0), (-0.2, 4.0), (0.05, 0.5)]  # per plane: slope in its column coordinate
+    b = [(0.1,), (0.0,), (0.2,)]                 # and in its row coordinate
+    for p in range(3):
+        for ch in range(sc.n_s):
+            val = a[p][0] * i[None, :] + a[p][1] + b[p][0] * i[:, None] + 0.1 * ch
+            sc.planes[:, :, :, p, :, :, ch] = val
+    m = oracle.Model.from_scene(sc)
+    g = synth.rng(8)
+    tile = g.integers(0, 2, size=(60, 3))
+    local = g.uniform(0.6, 15.4, size=(60, 3))  # away from the clamped edge texels
+    u = tile * 16 + local
+    pts = u / 32.0
+    fs = _fs_at(m, sc, pts)
+    lx, ly, lz = local[:, 0], local[:, 1], local[:, 2]
+    for ch in range(sc.n_s):
+        f0 = a[0][0] * ly + a[0][1] + b[0][0] * lz + 0.1 * ch   # plane [z][y]
+        f1 = a[1][0] * lx + a[1][1] + b[1][0] * lz + 0.1 * ch   # plane [z][x]
+        f2 = a[2][0] * lx + a[2][1] + b[2][0] * ly + 0.1 * ch   # plane [y][x]
+        np.testing.assert_allclose(fs[:, ch], f0 * f1 * f2, rtol=2e-6)
+
+
+def test_triplane_tile_of_a_point():
+    """A point reads the planes of the tile holding its cell; the far face of
+    the last tile belongs to the last tile."""
+    R = (40, 17, 17)  # x: 39 cells -> tiles of 16, 16, 7
+    sc = _triplane_scene(R=R)
+    sc.planes[...] = 1.0
+    sc.planes[:, :, 1, 0] = 2.0   # tile x = 1: plane 0 doubled
+    sc.planes[:, :, 2, 1] = 3.0   # tile x = 2: plane 1 tripled
+    m = oracle.Model.from_scene(sc)
+    h = 1.0 / 39
+    for ux, want in ((15.5, 1.0), (16.5, 2.0), (31.9, 2.0), (32.1, 3.0), (38.999, 3.0)):
+        fs = _fs_at(m, sc, [(ux * h, 0.5, 0.5)])[0]
+        np.testing.assert_allclose(fs, want, rtol=1e-12)
+
+
+@pytest.mark.parametrize("dir_mode", [oracle.DIR_REFLECT])
+def test_triplane_adjoint_matches_central_differences(dir_mode):
+    sc = _triplane_scene(R=(20, 18, 19), seed=9)
+    sc.planes[...] = synth.rng(10).normal(1.0, 0.3, size=sc.planes.shape)
+    m = oracle.Model.from_scene(sc)
+    tau, N = 8.0, 16
+    o, d = rays_into_box(48, 53)
+    fw = oracle.render_forward(m, o, d, tau, N, margin=True)
+    keep = (fw["margin"] > 2e-3) & (fw["wsum"] > 0)
+    o, d = o[keep][:16], d[keep][:16]
+    assert o.shape[0] >= 8
+    g = synth.rng(54)
+    drgb = g.normal(size=(o.shape[0], 3))
+    grads = oracle.render_backward(m, o, d, drgb, tau, N)
+    gp = grads["feat"]
+    assert gp.shape == m.planes.shape and np.abs(gp).max() > 0
+    flat, gflat = m.planes.reshape(-1), gp.reshape(-1)
+    nz = np.nonzero(gflat)[0]
+    idx = np.concatenate([g.choice(nz, min(300, nz.size), replace=False),
+                          g.choice(flat.size, 100, replace=False)])
+    scale = np.abs(gflat).max()
+    h = 1e-6
+    for i in idx:
+        old = flat[i]
+        flat[i] = old + h
+        lp = _loss(m, o, d, drgb, 0, 0, tau, N, dir_mode, (0, 0, 0))
+        flat[i] = old - h
+        lm = _loss(m, o, d, drgb, 0, 0, tau, N, dir_mode, (0, 0, 0))
+        flat[i] = old
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - gflat[i]) <= 1e-6 * scale + 1e-9, (i, fd, gflat[i])
