@@ -66,6 +66,11 @@ typedef int32_t psdf_status;
 #define PSDF_GRID_VALUES 0
 #define PSDF_GRID_GRAD 1
 
+#define PSDF_FEAT_NODES 0     /* n_feat features stored at every grid node */
+#define PSDF_FEAT_TRIPLANE 1  /* tile tri-planes (Sec. 3.1): per 16^3-cell tile, three
+                                 16 x 16 planes; F_s = F_x * F_y * F_z per channel */
+#define PSDF_TILE 16
+
 /* SDF + spatial-feature grid (Sec. 3, "explicit SDF grid"; Sec. 3.1 F_s). */
 typedef struct psdf_grid_desc {
     int32_t dims[3];     /* nodes along x, y, z; each in [2, 4096], product < 2^31 */
@@ -73,6 +78,14 @@ typedef struct psdf_grid_desc {
     float box_max[3];    /* box_max > box_min on every axis */
     int32_t n_feat;      /* spatial features per node (n_s); 3 is compiled in */
     int32_t feat_dtype;  /* PSDF_F32 or PSDF_BF16 (storage of the features; SDF stays FP32) */
+    int32_t feat_layout; /* PSDF_FEAT_NODES, or PSDF_FEAT_TRIPLANE (FP32 features only):
+                            the cells form tiles of 16^3 (tiles_a = ceil((dims_a - 1) / 16));
+                            a tile holds three planes of 16 x 16 texels, orthogonal to x
+                            (indexed [z][y]), y ([z][x]) and z ([y][x]), texel (r, c) at the
+                            centre of the tile's cell row r, column c; a point's spatial
+                            feature c is the product of the three planes' bilinear lookups
+                            at its in-plane coordinates (texel coordinate clamped to the
+                            tile) */
 } psdf_grid_desc;
 
 /* Light-field probe grid (Sec. 3.2): l*l SH coefficients of n_a channels. */
@@ -130,6 +143,9 @@ psdf_status psdf_device_status(void* stream, int32_t* flags);
  * Values, PSDF_BF16 features: an FP32 SDF array, then (at the next 16-byte
  * boundary) one 8-byte record {f0, f1, f2, 0} of BF16 per node.
  * Gradient (either case): one FP32 record {dsdf, df0, df1, df2} per node.
+ * PSDF_FEAT_TRIPLANE, values and gradient alike: an FP32 SDF array, then (at the
+ * next 16-byte boundary) the planes: [tz][ty][tx][3][16][16] texels of 16 bytes
+ * {f0, f1, f2, 0}.
  * Node order is x fastest. */
 psdf_status psdf_grid_bytes(const psdf_grid_desc* desc, size_t* values_bytes, size_t* grad_bytes);
 
@@ -139,8 +155,9 @@ void psdf_grid_destroy(psdf_grid* grid);
 
 /* Dense <-> packed conversion on `stream`.
  * pack:   sdf (device, FP32 [Rz][Ry][Rx]) and feat (device, FP32
- *         [Rz][Ry][Rx][n_feat]) -> packed values (device, values_bytes);
- *         BF16 features are rounded to nearest even.
+ *         [Rz][Ry][Rx][n_feat], or for tri-planes [tz][ty][tx][3][16][16][n_feat])
+ *         -> packed values (device, values_bytes); BF16 features are rounded to
+ *         nearest even.
  * unpack: packed values (which = PSDF_GRID_VALUES) or a gradient buffer
  *         (PSDF_GRID_GRAD) -> the dense arrays (either may be NULL). */
 psdf_status psdf_grid_pack(const psdf_grid_desc* desc, const float* sdf, const float* feat,

@@ -21,6 +21,7 @@ from . import build as _build
 __all__ = [
     "GridDesc", "ProbeDesc", "MlpDesc", "RenderParams", "Scene", "LibraryError",
     "library", "grid_bytes", "mlp_param_count", "pack_grid", "unpack_grid", "BF16", "F16", "F32",
+    "FEAT_NODES", "FEAT_TRIPLANE", "tri_tiles",
     "render_forward", "render_backward", "render", "device_status", "DIR_REFLECT", "DIR_VIEW",
     "ProposalDesc", "proposal_desc", "proposal_param_count", "occupancy_build",
     "weight_histogram", "proposal_forward", "proposal_backward", "adam_step", "Adam",
@@ -34,6 +35,14 @@ BF16 = 1
 F16 = 2
 GRID_VALUES = 0
 GRID_GRAD = 1
+FEAT_NODES = 0
+FEAT_TRIPLANE = 1
+TILE = 16
+
+
+def tri_tiles(dims):
+    """Tiles of 16 cells along x, y, z of a grid with `dims` nodes."""
+    return tuple((int(r) - 1 + TILE - 1) // TILE for r in dims)
 
 
 class LibraryError(RuntimeError):
@@ -43,7 +52,7 @@ class LibraryError(RuntimeError):
 class GridDesc(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int32 * 3), ("box_min", ctypes.c_float * 3),
                 ("box_max", ctypes.c_float * 3), ("n_feat", ctypes.c_int32),
-                ("feat_dtype", ctypes.c_int32)]
+                ("feat_dtype", ctypes.c_int32), ("feat_layout", ctypes.c_int32)]
 
 
 class ProbeDesc(ctypes.Structure):
@@ -168,8 +177,10 @@ def _require_cuda(*tensors, dtypes=(torch.float32,)):
                 raise LibraryError("tensors must be contiguous")
 
 
-def grid_desc(dims, box_min, box_max, n_feat=3, feat_dtype=F32) -> GridDesc:
+def grid_desc(dims, box_min, box_max, n_feat=3, feat_dtype=F32,
+              feat_layout=FEAT_NODES) -> GridDesc:
     d = GridDesc()
+    d.feat_layout = int(feat_layout)
     d.dims[:] = tuple(int(v) for v in dims)
     d.box_min[:] = tuple(float(v) for v in box_min)
     d.box_max[:] = tuple(float(v) for v in box_max)
@@ -195,11 +206,14 @@ def mlp_param_count(n_in: int, width: int) -> int:
 
 
 def pack_grid(desc: GridDesc, sdf: torch.Tensor, feat: torch.Tensor) -> torch.Tensor:
-    """Dense sdf [Rz,Ry,Rx] + feat [Rz,Ry,Rx,3] (device FP32) -> packed values:
-    float32 [R^3, 4] for FP32 features, a uint8 buffer for BF16 features."""
+    """Dense sdf [Rz,Ry,Rx] + feat [Rz,Ry,Rx,3] (or tile planes
+    [tz,ty,tx,3,16,16,3]) (device FP32) -> packed values: float32 [R^3, 4] for
+    FP32 node features, [bytes/16, 4] for tri-planes, a uint8 buffer for BF16."""
     _require_cuda(sdf, feat)
     nbytes, _ = grid_bytes(desc)
-    if desc.feat_dtype == F32:
+    if desc.feat_layout == FEAT_TRIPLANE:
+        out = torch.empty(nbytes // 4, dtype=torch.float32, device=sdf.device).view(-1, 4)
+    elif desc.feat_dtype == F32:
         out = torch.empty(nbytes // 4, dtype=torch.float32, device=sdf.device).view(-1, 4)
     else:
         out = torch.empty(nbytes, dtype=torch.uint8, device=sdf.device)
@@ -218,7 +232,12 @@ def unpack_grid(desc: GridDesc, packed: torch.Tensor, which: int = None):
             else GRID_GRAD
     Rx, Ry, Rz = desc.dims
     sdf = torch.empty((Rz, Ry, Rx), dtype=torch.float32, device=packed.device)
-    feat = torch.empty((Rz, Ry, Rx, desc.n_feat), dtype=torch.float32, device=packed.device)
+    if desc.feat_layout == FEAT_TRIPLANE:
+        tx, ty, tz = tri_tiles(desc.dims)
+        feat = torch.empty((tz, ty, tx, 3, TILE, TILE, desc.n_feat), dtype=torch.float32,
+                           device=packed.device)
+    else:
+        feat = torch.empty((Rz, Ry, Rx, desc.n_feat), dtype=torch.float32, device=packed.device)
     _check(library().psdf_grid_unpack(ctypes.byref(desc), int(which), _ptr(packed), _ptr(sdf),
                                       _ptr(feat), _stream()), "psdf_grid_unpack")
     return sdf, feat
@@ -238,6 +257,7 @@ class Scene:
     width: int
     n_feat: int = 3
     feat_dtype: int = F32    # storage of the spatial features (F32 or BF16)
+    feat_layout: int = FEAT_NODES  # node features or tile tri-planes
     probe_dtype: int = F32   # storage of the probe coefficients (F32 or F16)
     mlp_dtype: int = F32     # MLP arithmetic (F32-equivalent or F16)
 
@@ -251,7 +271,8 @@ class Scene:
         return self.probes.shape[-1]
 
     def descs(self, n_fresnel):
-        gd = grid_desc(self.dims, self.box_min, self.box_max, self.n_feat, self.feat_dtype)
+        gd = grid_desc(self.dims, self.box_min, self.box_max, self.n_feat, self.feat_dtype,
+                       self.feat_layout)
         pd = ProbeDesc()
         pd.dims[:] = self.probe_dims
         pd.sh_l = self.sh_l
@@ -275,8 +296,12 @@ class Scene:
         the requested storage precision."""
         dev = torch.device(device)
         sdf = torch.as_tensor(sc.sdf, dtype=torch.float32, device=dev).contiguous()
-        feat = torch.as_tensor(sc.feat, dtype=torch.float32, device=dev).contiguous()
-        gd = grid_desc(sc.dims, sc.box_min, sc.box_max, sc.feat.shape[-1], feat_dtype)
+        planes = getattr(sc, "planes", None)
+        layout = FEAT_NODES if planes is None else FEAT_TRIPLANE
+        feat = torch.as_tensor(sc.feat if planes is None else planes, dtype=torch.float32,
+                               device=dev).contiguous()
+        n_feat = int(feat.shape[-1])
+        gd = grid_desc(sc.dims, sc.box_min, sc.box_max, n_feat, feat_dtype, layout)
         grid = pack_grid(gd, sdf, feat)
         probes = torch.as_tensor(sc.probes, dtype=torch.float32, device=dev)
         if probe_dtype == F16:
@@ -285,8 +310,8 @@ class Scene:
         return cls(grid=grid, probes=probes.contiguous(), mlp=mlp, dims=tuple(sc.dims),
                    box_min=tuple(float(v) for v in sc.box_min),
                    box_max=tuple(float(v) for v in sc.box_max), sh_l=int(sc.sh_l),
-                   width=int(sc.width), n_feat=int(sc.feat.shape[-1]), feat_dtype=feat_dtype,
-                   probe_dtype=probe_dtype, mlp_dtype=mlp_dtype)
+                   width=int(sc.width), n_feat=n_feat, feat_dtype=feat_dtype,
+                   probe_dtype=probe_dtype, mlp_dtype=mlp_dtype, feat_layout=layout)
 
 
 def render_params(tau=64.0, n_samples=128, dir_mode=DIR_REFLECT, n_fresnel=3,

@@ -66,7 +66,19 @@ psdf_status check_grid_desc(const psdf_grid_desc* d)
     if (n >= (int64_t(1) << 31)) return PSDF_ERR_BAD_SHAPE;
     if (d->feat_dtype != PSDF_F32 && d->feat_dtype != PSDF_BF16) return PSDF_ERR_BAD_DTYPE;
     if (d->n_feat != 3) return PSDF_ERR_UNSUPPORTED;
+    if (d->feat_layout != PSDF_FEAT_NODES && d->feat_layout != PSDF_FEAT_TRIPLANE)
+        return PSDF_ERR_INVALID_ARG;
+    if (d->feat_layout == PSDF_FEAT_TRIPLANE && d->feat_dtype != PSDF_F32)
+        return PSDF_ERR_UNSUPPORTED;
     return PSDF_OK;
+}
+
+int tri_tiles(int32_t dims) { return (dims - 1 + PSDF_TILE - 1) / PSDF_TILE; }
+
+int64_t tri_texels(const psdf_grid_desc* d)
+{
+    return int64_t(tri_tiles(d->dims[0])) * tri_tiles(d->dims[1]) * tri_tiles(d->dims[2]) * 3 *
+           PSDF_TILE * PSDF_TILE;
 }
 
 int64_t grid_nodes(const psdf_grid_desc* d)
@@ -78,6 +90,23 @@ int64_t grid_nodes(const psdf_grid_desc* d)
 size_t bf16_feat_offset(const psdf_grid_desc* d)
 {
     return (static_cast<size_t>(grid_nodes(d)) * 4 + 15) & ~size_t(15);
+}
+
+// Device pointers of a grid's packed values (the layouts of psdf_grid_bytes).
+void set_grid_view(const psdf_grid_desc& gd, const void* values, psdf::GridView& g)
+{
+    const uint8_t* base = static_cast<const uint8_t*>(values);
+    if (gd.feat_layout == PSDF_FEAT_TRIPLANE) {
+        g.sdf = reinterpret_cast<const float*>(base);
+        g.planes = reinterpret_cast<const float4*>(base + bf16_feat_offset(&gd));
+        g.plane_off = static_cast<int64_t>(bf16_feat_offset(&gd) / 4);
+        for (int a = 0; a < 3; ++a) g.tiles[a] = tri_tiles(gd.dims[a]);
+    } else if (gd.feat_dtype == PSDF_BF16) {
+        g.sdf = reinterpret_cast<const float*>(base);
+        g.feat16 = reinterpret_cast<const uint2*>(base + bf16_feat_offset(&gd));
+    } else {
+        g.nodes = static_cast<const float4*>(values);
+    }
 }
 
 psdf_status check_probe_desc(const psdf_probe_desc* d)
@@ -140,7 +169,7 @@ psdf_status resolve(const psdf_grid* grid, const psdf_probes* probes, const psdf
     r.shape.l2 = pd.sh_l * pd.sh_l;
     r.shape.width = md.width;
     r.shape.k = p->n_fresnel;
-    r.shape.fb = gd.feat_dtype == PSDF_BF16;
+    r.shape.fb = gd.feat_layout == PSDF_FEAT_TRIPLANE ? 2 : (gd.feat_dtype == PSDF_BF16 ? 1 : 0);
     r.shape.ph = pd.dtype == PSDF_F16;
     r.shape.mh = md.dtype == PSDF_F16;
     bool known = false;
@@ -152,13 +181,7 @@ psdf_status resolve(const psdf_grid* grid, const psdf_probes* probes, const psdf
 
     psdf::RenderArgs& A = r.args;
     std::memset(&A, 0, sizeof(A));
-    if (r.shape.fb) {
-        const uint8_t* base = static_cast<const uint8_t*>(grid->values);
-        A.grid.sdf = reinterpret_cast<const float*>(base);
-        A.grid.feat16 = reinterpret_cast<const uint2*>(base + bf16_feat_offset(&gd));
-    } else {
-        A.grid.nodes = static_cast<const float4*>(grid->values);
-    }
+    set_grid_view(gd, grid->values, A.grid);
     for (int a = 0; a < 3; ++a) {
         A.grid.R[a] = gd.dims[a];
         A.grid.bmin[a] = gd.box_min[a];
@@ -220,6 +243,33 @@ __global__ void unpack_kernel(const float4* __restrict__ in, float* __restrict__
             feat[3 * i] = v.y;
             feat[3 * i + 1] = v.z;
             feat[3 * i + 2] = v.w;
+        }
+    }
+}
+
+// Tri-plane layout: dense SDF and planes [..][3] <-> the packed SDF array and
+// 16-byte texels (either dense pointer may be null).
+__global__ void tri_copy_kernel(float* __restrict__ sdf, float* __restrict__ planes,
+                                float* __restrict__ out_sdf, float4* __restrict__ out_tex,
+                                int64_t n_nodes, int64_t n_texels, bool pack)
+{
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+         i < (n_nodes > n_texels ? n_nodes : n_texels); i += int64_t(gridDim.x) * blockDim.x) {
+        if (i < n_nodes && sdf) {
+            if (pack)
+                out_sdf[i] = sdf[i];
+            else
+                sdf[i] = out_sdf[i];
+        }
+        if (i < n_texels && planes) {
+            if (pack) {
+                out_tex[i] = make_float4(planes[3 * i], planes[3 * i + 1], planes[3 * i + 2], 0.f);
+            } else {
+                const float4 v = out_tex[i];
+                planes[3 * i] = v.x;
+                planes[3 * i + 1] = v.y;
+                planes[3 * i + 2] = v.z;
+            }
         }
     }
 }
@@ -321,6 +371,19 @@ cudaError_t launch_unpack_bf16(const void* packed, size_t feat_off, float* sdf, 
     return cudaGetLastError();
 }
 
+cudaError_t launch_tri_copy(const float* sdf, const float* planes, void* packed, size_t plane_off,
+                            int64_t n_nodes, int64_t n_texels, bool pack, cudaStream_t stream)
+{
+    const int threads = 256;
+    const int64_t n = n_nodes > n_texels ? n_nodes : n_texels;
+    const int64_t blocks = (n + threads - 1) / threads;
+    uint8_t* base = static_cast<uint8_t*>(packed);
+    tri_copy_kernel<<<(int)(blocks < 65535 * 16 ? blocks : 65535 * 16), threads, 0, stream>>>(
+        const_cast<float*>(sdf), const_cast<float*>(planes), reinterpret_cast<float*>(base),
+        reinterpret_cast<float4*>(base + plane_off), n_nodes, n_texels, pack);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_unpack(const float4* packed, float* sdf, float* feat, int64_t n_nodes,
                           cudaStream_t stream)
 {
@@ -375,6 +438,10 @@ psdf_status psdf_grid_bytes(const psdf_grid_desc* desc, size_t* values_bytes, si
     if (st != PSDF_OK) return st;
     if (!values_bytes || !grad_bytes) return PSDF_ERR_INVALID_ARG;
     const size_t n = static_cast<size_t>(grid_nodes(desc));
+    if (desc->feat_layout == PSDF_FEAT_TRIPLANE) {
+        *values_bytes = *grad_bytes = bf16_feat_offset(desc) + 16 * size_t(tri_texels(desc));
+        return PSDF_OK;
+    }
     *values_bytes = desc->feat_dtype == PSDF_BF16 ? bf16_feat_offset(desc) + 8 * n : 16 * n;
     *grad_bytes = 16 * n;
     return PSDF_OK;
@@ -404,6 +471,10 @@ psdf_status psdf_grid_pack(const psdf_grid_desc* desc, const float* sdf, const f
     if (!sdf || !feat || !packed) return PSDF_ERR_INVALID_ARG;
     if (!aligned16(packed)) return PSDF_ERR_MISALIGNED;
     const int64_t n = grid_nodes(desc);
+    if (desc->feat_layout == PSDF_FEAT_TRIPLANE)
+        return cuda_status(psdf::launch_tri_copy(sdf, feat, packed, bf16_feat_offset(desc), n,
+                                                 tri_texels(desc), true,
+                                                 static_cast<cudaStream_t>(stream)));
     if (desc->feat_dtype == PSDF_BF16)
         return cuda_status(psdf::launch_pack_bf16(sdf, feat, packed, bf16_feat_offset(desc), n,
                                                   static_cast<cudaStream_t>(stream)));
@@ -420,6 +491,10 @@ psdf_status psdf_grid_unpack(const psdf_grid_desc* desc, int32_t which, const vo
     if (which != PSDF_GRID_VALUES && which != PSDF_GRID_GRAD) return PSDF_ERR_INVALID_ARG;
     if (!aligned16(packed)) return PSDF_ERR_MISALIGNED;
     const int64_t n = grid_nodes(desc);
+    if (desc->feat_layout == PSDF_FEAT_TRIPLANE)
+        return cuda_status(psdf::launch_tri_copy(sdf, feat, const_cast<void*>(packed),
+                                                 bf16_feat_offset(desc), n, tri_texels(desc),
+                                                 false, static_cast<cudaStream_t>(stream)));
     if (which == PSDF_GRID_VALUES && desc->feat_dtype == PSDF_BF16)
         return cuda_status(psdf::launch_unpack_bf16(packed, bf16_feat_offset(desc), sdf, feat, n,
                                                     static_cast<cudaStream_t>(stream)));
@@ -594,13 +669,7 @@ psdf_status grid_view(const psdf_grid* grid, psdf::GridView& g)
     if (!grid || !grid->values) return PSDF_ERR_INVALID_ARG;
     const psdf_grid_desc& gd = grid->desc;
     std::memset(&g, 0, sizeof(g));
-    if (gd.feat_dtype == PSDF_BF16) {
-        const uint8_t* base = static_cast<const uint8_t*>(grid->values);
-        g.sdf = reinterpret_cast<const float*>(base);
-        g.feat16 = reinterpret_cast<const uint2*>(base + bf16_feat_offset(&gd));
-    } else {
-        g.nodes = static_cast<const float4*>(grid->values);
-    }
+    set_grid_view(gd, grid->values, g);
     for (int a = 0; a < 3; ++a) {
         g.R[a] = gd.dims[a];
         g.bmin[a] = gd.box_min[a];

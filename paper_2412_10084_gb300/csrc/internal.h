@@ -11,8 +11,9 @@ constexpr int kFwdThreads = 128;
 constexpr int kBwdThreads = 128;
 
 // Compile-time shape of a render kernel: angular channels, SH coefficients,
-// MLP width, Fresnel powers (3 spatial features), and storage precision:
-// BF16 features (fb), FP16 probes (ph), plain-FP16 MLP (mh).
+// MLP width, Fresnel powers (3 spatial features), and storage: feature
+// storage fb (0 FP32 node records, 1 BF16 node features, 2 tile tri-planes),
+// FP16 probes (ph), plain-FP16 MLP (mh).
 struct KernelShape {
     int na, l2, width, k, fb, ph, mh;
     bool match(int na_, int l2_, int w_, int k_, int fb_, int ph_, int mh_) const
@@ -24,13 +25,16 @@ struct KernelShape {
 
 // Shapes compiled into the library: the FP32 path (widths 16/32, 4 or 8
 // angular channels), the reduced-precision path (BF16 features, FP16 probes,
-// FP16 MLP), and BF16 features with FP32 probes and MLP.
+// FP16 MLP), BF16 features with FP32 probes and MLP, and tile tri-plane
+// features (widths 16/32).
 #define PSDF_FOR_EACH_SHAPE(X) \
     X(4, 9, 16, 3, 0, 0, 0)    \
     X(4, 9, 32, 3, 0, 0, 0)    \
     X(8, 9, 32, 3, 0, 0, 0)    \
     X(4, 9, 32, 3, 1, 1, 1)    \
-    X(8, 9, 32, 3, 1, 0, 0)
+    X(8, 9, 32, 3, 1, 0, 0)    \
+    X(4, 9, 16, 3, 2, 0, 0)    \
+    X(4, 9, 32, 3, 2, 0, 0)
 
 cudaError_t launch_forward(const RenderArgs& A, const KernelShape& ks, int grid_ctas,
                            cudaStream_t stream);
@@ -46,6 +50,8 @@ cudaError_t backward_ctas_per_sm(const KernelShape& ks, int* n);
 
 cudaError_t launch_adam(float* p, float* g, float* m, float* v, int64_t n, float lr, float beta1,
                         float beta2, float eps, int step, int clear_grad, cudaStream_t stream);
+cudaError_t launch_tri_copy(const float* sdf, const float* planes, void* packed, size_t plane_off,
+                            int64_t n_nodes, int64_t n_texels, bool pack, cudaStream_t stream);
 cudaError_t launch_pack(const float* sdf, const float* feat, float4* packed, int64_t n_nodes,
                         cudaStream_t stream);
 cudaError_t launch_unpack(const float4* packed, float* sdf, float* feat, int64_t n_nodes,

@@ -661,9 +661,41 @@ render_backward_kernel(RenderArgs A)
                         const float wc = wx * wy * wz;
                         const float dsdf = ds_own * wc + gxs * sgx * wy * wz +
                                            gys * wx * sgy * wz + gzs * wx * wy * sgz;
-                        float* dst =
-                            A.grad_grid + 4 * (size_t)(S.cell.base + cx + cy * sy + cz * sz);
-                        red_add_v4(dst, dsdf, wc * dx[0], wc * dx[1], wc * dx[2]);
+                        const size_t node = S.cell.base + cx + cy * sy + cz * sz;
+                        if constexpr (C::TP)
+                            red_add(A.grad_grid + node, dsdf);
+                        else
+                            red_add_v4(A.grad_grid + 4 * node, dsdf, wc * dx[0], wc * dx[1],
+                                       wc * dx[2]);
+                    }
+                    if constexpr (C::TP) {
+                        // F_s = b0 b1 b2 per channel: plane p's lookup gets dF_s times
+                        // the other two, spread over its 4 texels bilinearly
+                        float xw[3];
+                        point_at(R.o, R.d, t, xw);
+                        TriAt T;
+                        triplane_locate(A.grid, xw, T);
+                        float4 bp[3];
+                        float fs_unused[3];
+                        triplane_lookup(A.grid, T, fs_unused, bp);
+                        float4* gpl = reinterpret_cast<float4*>(A.grad_grid + A.grid.plane_off);
+#pragma unroll
+                        for (int p = 0; p < 3; ++p) {
+                            const float4 o1 = bp[(p + 1) % 3], o2 = bp[(p + 2) % 3];
+                            const float gx0 = dx[0] * o1.x * o2.x, gx1 = dx[1] * o1.y * o2.y;
+                            const float gx2 = dx[2] * o1.z * o2.z;
+                            const int ra = tri_row(p), ca = tri_col(p);
+                            const float fr = T.f[ra], fc = T.f[ca];
+                            float4* P = gpl + T.plane0 + p * kTile * kTile + T.i[ra] * kTile +
+                                        T.i[ca];
+                            const float w4[4] = {(1.0f - fr) * (1.0f - fc), (1.0f - fr) * fc,
+                                                 fr * (1.0f - fc), fr * fc};
+                            const int o4[4] = {0, 1, kTile, kTile + 1};
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                red_add_v4(reinterpret_cast<float*>(P + o4[e]), w4[e] * gx0,
+                                           w4[e] * gx1, w4[e] * gx2, 0.0f);
+                        }
                     }
                 } else if (active && ds_own != 0.0f) {
                     float w8[8];
@@ -671,8 +703,8 @@ render_backward_kernel(RenderArgs A)
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         const int cx = q & 1, cy = (q >> 1) & 1, cz = (q >> 2) & 1;
-                        red_add(A.grad_grid + 4 * (size_t)(S.cell.base + cx + cy * sy + cz * sz),
-                                ds_own * w8[q]);
+                        const size_t node = S.cell.base + cx + cy * sy + cz * sz;
+                        red_add(A.grad_grid + (C::TP ? node : 4 * node), ds_own * w8[q]);
                     }
                 }
                 if (extra) {
@@ -683,8 +715,8 @@ render_backward_kernel(RenderArgs A)
 #pragma unroll
                         for (int q = 0; q < 8; ++q) {
                             const int cx = q & 1, cy = (q >> 1) & 1, cz = (q >> 2) & 1;
-                            red_add(A.grad_grid + 4 * (size_t)(c1.base + cx + cy * sy + cz * sz),
-                                    ds1 * w1[q]);
+                            const size_t node = c1.base + cx + cy * sy + cz * sz;
+                            red_add(A.grad_grid + (C::TP ? node : 4 * node), ds1 * w1[q]);
                         }
                     }
                 }

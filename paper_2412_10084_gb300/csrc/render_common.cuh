@@ -16,8 +16,12 @@ constexpr float kNormalEps = 1e-12f;  // n = g / sqrt(|g|^2 + eps^2)
 // per node, x fastest.
 struct GridView {
     const float4* __restrict__ nodes;   // FP32 records {sdf, f0, f1, f2}
-    const float* __restrict__ sdf;      // BF16-feature layout: FP32 SDF per node ...
+    const float* __restrict__ sdf;      // BF16-feature / tri-plane layouts: FP32 SDF per node ...
     const uint2* __restrict__ feat16;   // ... and {f0, f1, f2, 0} as BF16 per node
+    const float4* __restrict__ planes;  // ... or tile tri-planes: [tile][3][16][16] {f0, f1, f2, 0}
+    int tiles[3];                       // tiles of 16 cells along x, y, z
+    int64_t plane_off;                  // tri-planes: float offset of the planes in the values
+                                        // and gradient buffers (the SDF array comes first)
     int R[3];
     float bmin[3];
     float bmax[3];
@@ -184,6 +188,81 @@ __device__ __forceinline__ void gather_corners_bf16(const GridView& g, const Cel
         const uint2 f = __ldg(g.feat16 + c.base + off[q]);
         k.v[q] = make_float4(s, bf16_lo(f.x), bf16_hi(f.x), bf16_lo(f.y));
     }
+}
+
+// SDF only (tri-plane layout): the features come from the tile planes.
+__device__ __forceinline__ void gather_corners_sdf(const GridView& g, const Cell& c, Corners& k)
+{
+    const int sx = 1, sy = g.R[0], sz = g.R[0] * g.R[1];
+    const int off[8] = {0, sx, sy, sx + sy, sz, sz + sx, sz + sy, sz + sy + sx};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) k.v[q] = make_float4(__ldg(g.sdf + c.base + off[q]), 0.f, 0.f, 0.f);
+}
+
+// ---------------------------------------------------------------------------
+// Tile tri-plane spatial features (Sec. 3.1, Sec. 4).  The cells form tiles of
+// 16^3; a tile holds three 16 x 16 planes of texels {f0, f1, f2}, orthogonal
+// to x ([z][y]), y ([z][x]) and z ([y][x]); F_s = F_x * F_y * F_z channel by
+// channel, each factor a bilinear lookup at the point's two in-plane
+// coordinates.  Texels sit at the centres of the tile's cells, the texel
+// coordinate is clamped to the tile.  The tile and texel follow exactly from
+// the FP32 grid coordinate u (u / 16 and u - 16 t are exact).
+// ---------------------------------------------------------------------------
+
+constexpr int kTile = 16;
+
+struct TriAt {
+    int plane0;  // texel index of the tile's first plane
+    int i[3];    // texel index along x, y, z (0..14)
+    float f[3];  // fraction to the next texel
+};
+
+__device__ __forceinline__ void triplane_locate(const GridView& g, const float x[3], TriAt& T)
+{
+    int t[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float u = __fmul_rn(__fsub_rn(x[a], g.bmin[a]), g.sc[a]);  // as locate_axis
+        float ta = floorf(u * (1.0f / kTile));
+        ta = ta >= 0.0f ? ta : 0.0f;  // also maps NaN to tile 0
+        ta = fminf(ta, static_cast<float>(g.tiles[a] - 1));
+        float tau = __fsub_rn(__fsub_rn(u, ta * kTile), 0.5f);
+        tau = fminf(fmaxf(tau, 0.0f), static_cast<float>(kTile - 1));
+        const float fi = fminf(floorf(tau), static_cast<float>(kTile - 2));
+        t[a] = static_cast<int>(ta);
+        T.i[a] = static_cast<int>(fi);
+        T.f[a] = __fsub_rn(tau, fi);
+    }
+    T.plane0 = ((t[2] * g.tiles[1] + t[1]) * g.tiles[0] + t[0]) * 3 * kTile * kTile;
+}
+
+// plane p: 0 is [z][y], 1 is [z][x], 2 is [y][x]
+__device__ __forceinline__ constexpr int tri_row(int p) { return p == 2 ? 1 : 2; }
+__device__ __forceinline__ constexpr int tri_col(int p) { return p == 0 ? 1 : 0; }
+
+// The three bilinear lookups b[p] ({f0, f1, f2} of plane p) and F_s.
+__device__ __forceinline__ void triplane_lookup(const GridView& g, const TriAt& T, float fs[3],
+                                                float4* b = nullptr)
+{
+    float4 v[3];
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        const int ra = tri_row(p), ca = tri_col(p);
+        const float fr = T.f[ra], fc = T.f[ca];
+        const float4* P = g.planes + T.plane0 + p * kTile * kTile + T.i[ra] * kTile + T.i[ca];
+        const float4 a00 = __ldg(P), a01 = __ldg(P + 1);
+        const float4 a10 = __ldg(P + kTile), a11 = __ldg(P + kTile + 1);
+        const float w00 = (1.0f - fr) * (1.0f - fc), w01 = (1.0f - fr) * fc;
+        const float w10 = fr * (1.0f - fc), w11 = fr * fc;
+        v[p].x = w00 * a00.x + w01 * a01.x + w10 * a10.x + w11 * a11.x;
+        v[p].y = w00 * a00.y + w01 * a01.y + w10 * a10.y + w11 * a11.y;
+        v[p].z = w00 * a00.z + w01 * a01.z + w10 * a10.z + w11 * a11.z;
+        v[p].w = 0.0f;
+        if (b) b[p] = v[p];
+    }
+    fs[0] = v[0].x * v[1].x * v[2].x;
+    fs[1] = v[0].y * v[1].y * v[2].y;
+    fs[2] = v[0].z * v[1].z * v[2].z;
 }
 
 // SDF value only (the extra point N of a ray's last full chunk).

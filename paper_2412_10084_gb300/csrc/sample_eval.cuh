@@ -10,13 +10,15 @@
 namespace psdf {
 
 // Compile-time shape and storage precision of a render kernel.
-//   FB: spatial features stored as BF16 (SDF stays FP32)
+//   FS: spatial-feature storage: 0 FP32 node records, 1 BF16 node features
+//       (SDF stays FP32), 2 tile tri-planes (Sec. 3.1)
 //   PH: probe coefficients stored as FP16
 //   MH: MLP on the tensor cores in plain FP16 (else the FP32-equivalent
 //       hi/lo split)
-template <int NA_, int L2_, int W_, int K_, int FB_ = 0, int PH_ = 0, int MH_ = 0>
+template <int NA_, int L2_, int W_, int K_, int FS_ = 0, int PH_ = 0, int MH_ = 0>
 struct Cfg {
-    static constexpr int FB = FB_;
+    static constexpr int FB = FS_ == 1;
+    static constexpr int TP = FS_ == 2;
     static constexpr int PH = PH_;
     static constexpr int MH = MH_;
     static constexpr int NS = 3;
@@ -42,7 +44,9 @@ struct Cfg {
 template <class C>
 __device__ __forceinline__ void gather_corners_t(const GridView& g, const Cell& c, Corners& k)
 {
-    if constexpr (C::FB)
+    if constexpr (C::TP)
+        gather_corners_sdf(g, c, k);
+    else if constexpr (C::FB)
         gather_corners_bf16(g, c, k);
     else
         gather_corners(g, c, k);
@@ -105,6 +109,11 @@ __device__ __forceinline__ void eval_sdf(const RenderArgs& A, const float o[3], 
     gather_corners_t<C>(A.grid, S.cell, k);
     float fs[3];
     sdf_full(A.grid, S.cell, k, S.s, S.g, fs);
+    if constexpr (C::TP) {
+        TriAt T;
+        triplane_locate(A.grid, xw, T);
+        triplane_lookup(A.grid, T, fs);
+    }
     S.x[0] = fs[0];
     S.x[1] = fs[1];
     S.x[2] = fs[2];
