@@ -256,6 +256,61 @@ psdf_status psdf_adam_step(float* param, float* grad, float* m, float* v, int64_
                            void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Grid-level training terms (Sec. 3.3, Eqs. 11-15).  The trained SDF
+ * parameter is a raw grid s_hat (device FP32 [Rz][Ry][Rx], x fastest, the
+ * caller's); the grid the renderer reads holds its smoothing s = G(s_hat),
+ * G the normalised 5^3 Gaussian (separable, 5 taps per axis, standard
+ * deviation one node spacing, edge nodes replicated).  One training step:
+ *   psdf_sdf_smooth -> render forward/backward -> psdf_grid_regularizers
+ *   (+ psdf_probe_smoothness) -> psdf_sdf_smooth_adjoint (accumulate) ->
+ *   psdf_adam_step on s_hat, the features, the probes and the MLP.
+ * Finite differences: grad s at a node is the central difference over its
+ * two neighbours per axis (node spacing h_a = (box_max - box_min) / (dims - 1)),
+ * defined at interior nodes only.  All calls run on `stream`, launch without
+ * synchronising and allocate nothing.
+ * ------------------------------------------------------------------------- */
+
+/* s = G(s_hat) written into the SDF slot of packed grid values (the layout of
+ * psdf_grid_bytes; the features are not touched).  sdf_hat and the packed
+ * values must not overlap. */
+psdf_status psdf_sdf_smooth(const psdf_grid_desc* desc, const float* sdf_hat, void* packed_values,
+                            void* stream);
+
+/* d_sdf_hat (+)= G^T dsdf: the SDF slot of a gradient buffer (psdf_grid_bytes'
+ * grad layout) taken back through the smoothing.  accumulate = 0 overwrites
+ * d_sdf_hat (device FP32 [Rz][Ry][Rx]), nonzero adds to it. */
+psdf_status psdf_sdf_smooth_adjoint(const psdf_grid_desc* desc, const void* grad_grid,
+                                    float* d_sdf_hat, int32_t accumulate, void* stream);
+
+/* The per-voxel terms on s = the SDF of packed_values, and the tri-plane term:
+ *   L_sdf      = sum_i |s_i - s_hat_i|^2                         (Eq. 11)
+ *   L_Eik      = sum_interior (||grad s|| - 1)^2                  (Eq. 12)
+ *   L_normal   = sum_interior sum_a ||n(i + e_a) - n(i)||^2 over the axes whose
+ *                neighbour is interior, n = grad s / sqrt(||grad s||^2 + 1e-24) (Eq. 13)
+ *   L_features = sum over the tile planes of the squared forward differences
+ *                between neighbouring texels, rows and columns     (Eq. 14)
+ * The gradient of lam_sdf L_sdf + lam_eik L_Eik + lam_normal L_normal, each
+ * voxel's term scaled by w_i = (1 + 5 |s_i|)^-1 (held fixed, not differentiated;
+ * Sec. 3.3), is ADDED to the SDF slot of grad_grid (w.r.t. s, with atomics) and
+ * to d_sdf_hat (w.r.t. s_hat directly); lam_features * L_features' gradient is
+ * added to the planes of grad_grid.  lam_features > 0 needs PSDF_FEAT_TRIPLANE
+ * (PSDF_ERR_UNSUPPORTED otherwise).  All weights >= 0.
+ *   loss : device FP32 [4] or NULL; {L_sdf, L_Eik, L_normal, L_features}
+ *          (unweighted) are ADDED to it. */
+psdf_status psdf_grid_regularizers(const psdf_grid_desc* desc, const float* sdf_hat,
+                                   const void* packed_values, float lam_sdf, float lam_eik,
+                                   float lam_normal, float lam_features, void* grad_grid,
+                                   float* d_sdf_hat, float* loss, void* stream);
+
+/* L_probes = sum_i sum_{k in V_i} ||b_i - b_k||^2 over the 6-neighbourhoods V_i
+ * of the probe grid (every ordered pair, Eq. 15); lam_probes * its gradient
+ * is ADDED to grad (device FP32, the coefficients' layout) and L_probes to
+ * loss[0] (device FP32 [1] or NULL).  FP32 coefficients with l*l*n_a a
+ * multiple of 4. */
+psdf_status psdf_probe_smoothness(const psdf_probe_desc* desc, const float* coeffs, float lam,
+                                  float* grad, float* loss, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Learned sample proposal.  The paper has no counterpart: it marches its
  * sparse grid.  A per-ray MLP [(o - box centre) / box extent, d, first
  * occupied position, occupied fraction of each of B equal bins of

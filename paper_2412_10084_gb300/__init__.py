@@ -25,7 +25,8 @@ __all__ = [
     "render_forward", "render_backward", "render", "device_status", "DIR_REFLECT", "DIR_VIEW",
     "ProposalDesc", "proposal_desc", "proposal_param_count", "occupancy_build",
     "weight_histogram", "proposal_forward", "proposal_backward", "adam_step", "Adam",
-    "occupancy_words", "occupancy_unpack",
+    "occupancy_words", "occupancy_unpack", "sdf_smooth", "sdf_smooth_adjoint",
+    "grid_regularizers", "probe_smoothness",
 ]
 
 DIR_REFLECT = 0
@@ -127,7 +128,13 @@ def library() -> ctypes.CDLL:
                                               ctypes.c_int32, _P, _P, _P]
         lib.psdf_proposal_backward.argtypes = [_P, _P, _P, _P, _P, _P, ctypes.c_int64, _P,
                                                ctypes.c_float, ctypes.c_float, _P, _P, _P]
-        for name in ("psdf_grid_bytes", "psdf_grid_create", "psdf_grid_pack", "psdf_grid_unpack",
+        lib.psdf_sdf_smooth.argtypes = [_P, _P, _P, _P]
+        lib.psdf_sdf_smooth_adjoint.argtypes = [_P, _P, _P, ctypes.c_int32, _P]
+        lib.psdf_grid_regularizers.argtypes = [_P, _P, _P, ctypes.c_float, ctypes.c_float,
+                                               ctypes.c_float, ctypes.c_float, _P, _P, _P, _P]
+        lib.psdf_probe_smoothness.argtypes = [_P, _P, ctypes.c_float, _P, _P, _P]
+        for name in ("psdf_sdf_smooth", "psdf_sdf_smooth_adjoint", "psdf_grid_regularizers",
+                     "psdf_probe_smoothness", "psdf_grid_bytes", "psdf_grid_create", "psdf_grid_pack", "psdf_grid_unpack",
                      "psdf_probes_create", "psdf_mlp_param_count", "psdf_mlp_create",
                      "psdf_render_forward", "psdf_render_backward", "psdf_render_occupancy",
                      "psdf_adam_step", "psdf_proposal_param_count", "psdf_occupancy_words",
@@ -500,6 +507,60 @@ class Adam:
         self.t += 1
         for p, g, lr, m, v in self.groups:
             adam_step(p, g, m, v, self.t, lr, self.beta1, self.beta2, self.eps)
+
+
+# ---------------------------------------------------------------------------
+# Grid-level training terms (Sec. 3.3, Eqs. 11-15)
+# ---------------------------------------------------------------------------
+
+def _check_dense_sdf(gd, t, what):
+    n = int(gd.dims[0]) * int(gd.dims[1]) * int(gd.dims[2])
+    if t.numel() != n or not t.is_contiguous():
+        raise LibraryError(f"{what}: expected a contiguous FP32 array of {n} nodes")
+
+
+def sdf_smooth(gd, sdf_hat, values):
+    """Write s = G(sdf_hat) (5^3 Gaussian, sigma = 1 node) into the SDF slot of
+    the packed grid `values`; the features are left as they are."""
+    _require_cuda(sdf_hat, values, dtypes=(torch.float32, torch.uint8, torch.bfloat16))
+    _check_dense_sdf(gd, sdf_hat, "sdf_smooth")
+    _check(library().psdf_sdf_smooth(ctypes.byref(gd), _ptr(sdf_hat), _ptr(values), _stream()),
+           "psdf_sdf_smooth")
+
+
+def sdf_smooth_adjoint(gd, grad_grid, d_sdf_hat, accumulate=True):
+    """d_sdf_hat (+)= G^T of the SDF slot of a grid gradient buffer."""
+    _require_cuda(grad_grid, d_sdf_hat)
+    _check_dense_sdf(gd, d_sdf_hat, "sdf_smooth_adjoint")
+    _check(library().psdf_sdf_smooth_adjoint(ctypes.byref(gd), _ptr(grad_grid), _ptr(d_sdf_hat),
+                                             int(bool(accumulate)), _stream()),
+           "psdf_sdf_smooth_adjoint")
+
+
+def grid_regularizers(gd, sdf_hat, values, grad_grid, d_sdf_hat, lam_sdf, lam_eik, lam_normal,
+                      lam_features=0.0, loss=None):
+    """Adds the gradients of the weighted L_sdf, L_Eik, L_normal (and, for
+    tri-planes, L_features) to grad_grid and d_sdf_hat; adds the unweighted
+    values {sdf, eik, normal, features} to `loss` (FP32 [4]) when given."""
+    _require_cuda(sdf_hat, grad_grid, d_sdf_hat, loss)
+    _require_cuda(values, dtypes=(torch.float32, torch.uint8, torch.bfloat16))
+    _check_dense_sdf(gd, sdf_hat, "grid_regularizers")
+    _check_dense_sdf(gd, d_sdf_hat, "grid_regularizers")
+    if loss is not None and loss.numel() < 4:
+        raise LibraryError("grid_regularizers: loss needs 4 entries")
+    _check(library().psdf_grid_regularizers(
+        ctypes.byref(gd), _ptr(sdf_hat), _ptr(values), float(lam_sdf), float(lam_eik),
+        float(lam_normal), float(lam_features), _ptr(grad_grid), _ptr(d_sdf_hat), _ptr(loss),
+        _stream()), "psdf_grid_regularizers")
+
+
+def probe_smoothness(pd, coeffs, grad, lam, loss=None):
+    """Adds lam * grad L_probes (6-neighbour pairs) to `grad` and L_probes to loss[0]."""
+    _require_cuda(coeffs, grad, loss)
+    if grad.numel() != coeffs.numel():
+        raise LibraryError("probe_smoothness: coeffs and grad must have the same size")
+    _check(library().psdf_probe_smoothness(ctypes.byref(pd), _ptr(coeffs), float(lam), _ptr(grad),
+                                           _ptr(loss), _stream()), "psdf_probe_smoothness")
 
 
 # ---------------------------------------------------------------------------

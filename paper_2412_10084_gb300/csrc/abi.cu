@@ -647,6 +647,101 @@ psdf_status psdf_adam_step(float* param, float* grad, float* m, float* v, int64_
 }
 
 // ---------------------------------------------------------------------------
+// Grid-level training terms
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// Element stride of the SDF slot in packed values / in a gradient buffer.
+int sdf_value_stride(const psdf_grid_desc* d)
+{
+    return (d->feat_layout == PSDF_FEAT_NODES && d->feat_dtype == PSDF_F32) ? 4 : 1;
+}
+
+int sdf_grad_stride(const psdf_grid_desc* d)
+{
+    return d->feat_layout == PSDF_FEAT_NODES ? 4 : 1;
+}
+
+}  // namespace
+
+psdf_status psdf_sdf_smooth(const psdf_grid_desc* desc, const float* sdf_hat, void* packed_values,
+                            void* stream)
+{
+    const psdf_status st = check_grid_desc(desc);
+    if (st != PSDF_OK) return st;
+    if (!sdf_hat || !packed_values) return PSDF_ERR_INVALID_ARG;
+    if (!aligned16(sdf_hat) || !aligned16(packed_values)) return PSDF_ERR_MISALIGNED;
+    return cuda_status(psdf::launch_smooth(desc->dims, sdf_hat, 1,
+                                           static_cast<float*>(packed_values),
+                                           sdf_value_stride(desc), false, false,
+                                           static_cast<cudaStream_t>(stream)));
+}
+
+psdf_status psdf_sdf_smooth_adjoint(const psdf_grid_desc* desc, const void* grad_grid,
+                                    float* d_sdf_hat, int32_t accumulate, void* stream)
+{
+    const psdf_status st = check_grid_desc(desc);
+    if (st != PSDF_OK) return st;
+    if (!grad_grid || !d_sdf_hat) return PSDF_ERR_INVALID_ARG;
+    if (!aligned16(grad_grid) || !aligned16(d_sdf_hat)) return PSDF_ERR_MISALIGNED;
+    return cuda_status(psdf::launch_smooth(desc->dims, static_cast<const float*>(grad_grid),
+                                           sdf_grad_stride(desc), d_sdf_hat, 1, true,
+                                           accumulate != 0, static_cast<cudaStream_t>(stream)));
+}
+
+psdf_status psdf_grid_regularizers(const psdf_grid_desc* desc, const float* sdf_hat,
+                                   const void* packed_values, float lam_sdf, float lam_eik,
+                                   float lam_normal, float lam_features, void* grad_grid,
+                                   float* d_sdf_hat, float* loss, void* stream)
+{
+    const psdf_status st = check_grid_desc(desc);
+    if (st != PSDF_OK) return st;
+    if (!sdf_hat || !packed_values || !grad_grid || !d_sdf_hat) return PSDF_ERR_INVALID_ARG;
+    if (!(lam_sdf >= 0.0f) || !(lam_eik >= 0.0f) || !(lam_normal >= 0.0f) ||
+        !(lam_features >= 0.0f))
+        return PSDF_ERR_INVALID_ARG;
+    if (lam_features > 0.0f && desc->feat_layout != PSDF_FEAT_TRIPLANE)
+        return PSDF_ERR_UNSUPPORTED;
+    if (!aligned16(sdf_hat) || !aligned16(packed_values) || !aligned16(grad_grid) ||
+        !aligned16(d_sdf_hat) || (loss && (reinterpret_cast<uintptr_t>(loss) & 3u)))
+        return PSDF_ERR_MISALIGNED;
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float h[3];
+    for (int a = 0; a < 3; ++a)
+        h[a] = (desc->box_max[a] - desc->box_min[a]) / static_cast<float>(desc->dims[a] - 1);
+    cudaError_t e = psdf::launch_sdf_reg(
+        desc->dims, h, sdf_hat, static_cast<const float*>(packed_values), sdf_value_stride(desc),
+        lam_sdf, lam_eik, lam_normal, static_cast<float*>(grad_grid), sdf_grad_stride(desc),
+        d_sdf_hat, loss, s);
+    if (e != cudaSuccess || desc->feat_layout != PSDF_FEAT_TRIPLANE) return cuda_status(e);
+    const size_t off = bf16_feat_offset(desc);
+    e = psdf::launch_plane_reg(
+        reinterpret_cast<const float4*>(static_cast<const uint8_t*>(packed_values) + off),
+        tri_texels(desc), lam_features,
+        reinterpret_cast<float4*>(static_cast<uint8_t*>(grad_grid) + off), loss ? loss + 3 : nullptr,
+        s);
+    return cuda_status(e);
+}
+
+psdf_status psdf_probe_smoothness(const psdf_probe_desc* desc, const float* coeffs, float lam,
+                                  float* grad, float* loss, void* stream)
+{
+    const psdf_status st = check_probe_desc(desc);
+    if (st != PSDF_OK) return st;
+    if (desc->dtype != PSDF_F32) return PSDF_ERR_BAD_DTYPE;
+    const int per = desc->sh_l * desc->sh_l * desc->n_ang;
+    if (per % 4 != 0) return PSDF_ERR_UNSUPPORTED;
+    if (!coeffs || !grad || !(lam >= 0.0f)) return PSDF_ERR_INVALID_ARG;
+    if (!aligned16(coeffs) || !aligned16(grad) ||
+        (loss && (reinterpret_cast<uintptr_t>(loss) & 3u)))
+        return PSDF_ERR_MISALIGNED;
+    return cuda_status(psdf::launch_probe_reg(reinterpret_cast<const float4*>(coeffs), desc->dims,
+                                              per / 4, lam, reinterpret_cast<float4*>(grad),
+                                              loss, static_cast<cudaStream_t>(stream)));
+}
+
+// ---------------------------------------------------------------------------
 // Learned sample proposal
 // ---------------------------------------------------------------------------
 

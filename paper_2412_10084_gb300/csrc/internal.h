@@ -50,6 +50,18 @@ cudaError_t backward_ctas_per_sm(const KernelShape& ks, int* n);
 
 cudaError_t launch_adam(float* p, float* g, float* m, float* v, int64_t n, float lr, float beta1,
                         float beta2, float eps, int step, int clear_grad, cudaStream_t stream);
+// Grid-level training terms (regularize.cu).  SDF arrays are read and written
+// with an element stride (4 in FP32 node records, 1 in a plain FP32 array).
+cudaError_t launch_smooth(const int R[3], const float* in, int in_stride, float* out,
+                          int out_stride, bool transpose, bool accumulate, cudaStream_t stream);
+cudaError_t launch_sdf_reg(const int R[3], const float h[3], const float* s_hat, const float* s,
+                           int s_stride, float lam_sdf, float lam_eik, float lam_normal,
+                           float* d_s, int d_stride, float* d_s_hat, float* loss,
+                           cudaStream_t stream);
+cudaError_t launch_plane_reg(const float4* planes, int64_t n_texels, float lam, float4* grad,
+                             float* loss, cudaStream_t stream);
+cudaError_t launch_probe_reg(const float4* b, const int P[3], int n4, float lam, float4* grad,
+                             float* loss, cudaStream_t stream);
 cudaError_t launch_tri_copy(const float* sdf, const float* planes, void* packed, size_t plane_off,
                             int64_t n_nodes, int64_t n_texels, bool pack, cudaStream_t stream);
 cudaError_t launch_pack(const float* sdf, const float* feat, float4* packed, int64_t n_nodes,

@@ -91,3 +91,32 @@ def test_kernel_sh_constants_match_closed_form():
     assert len(consts) == len(closed)
     for a, b in zip(consts, closed):
         assert abs(a - b) <= 1e-15 * b
+
+
+def test_regularizer_entry_points_reject_bad_arguments_on_the_host(lib):
+    import paper_2412_10084_gb300 as ps
+    P = ctypes.c_void_p
+    f = ctypes.c_float
+    gd = ps.grid_desc((9, 9, 9), (0, 0, 0), (1, 1, 1))
+    lib.psdf_sdf_smooth.argtypes = [P, P, P, P]
+    assert lib.psdf_sdf_smooth(ctypes.byref(gd), None, P(0x1000), None) == -1
+    assert lib.psdf_sdf_smooth(ctypes.byref(gd), P(0x1004), P(0x1000), None) == -4
+    lib.psdf_sdf_smooth_adjoint.argtypes = [P, P, P, ctypes.c_int32, P]
+    assert lib.psdf_sdf_smooth_adjoint(ctypes.byref(gd), P(0x1000), None, 1, None) == -1
+    lib.psdf_grid_regularizers.argtypes = [P, P, P, f, f, f, f, P, P, P, P]
+    args = (P(0x1000), P(0x2000))
+    assert lib.psdf_grid_regularizers(ctypes.byref(gd), *args, 1.0, 1.0, 1.0, 0.5, P(0x3000),
+                                      P(0x4000), None, None) == -6   # features need tri-planes
+    assert lib.psdf_grid_regularizers(ctypes.byref(gd), *args, 1.0, -1.0, 1.0, 0.0, P(0x3000),
+                                      P(0x4000), None, None) == -1
+    assert lib.psdf_grid_regularizers(ctypes.byref(gd), *args, 1.0, 1.0, 1.0, 0.0, P(0x3000),
+                                      P(0x4000), P(0x5002), None) == -4
+    pd = ps.ProbeDesc()
+    pd.dims[:] = (3, 3, 3)
+    pd.sh_l, pd.n_ang, pd.dtype = 3, 4, ps.F16
+    lib.psdf_probe_smoothness.argtypes = [P, P, f, P, P, P]
+    assert lib.psdf_probe_smoothness(ctypes.byref(pd), P(0x1000), 1.0, P(0x2000), None,
+                                     None) == -3
+    pd.dtype, pd.n_ang = ps.F32, 3
+    assert lib.psdf_probe_smoothness(ctypes.byref(pd), P(0x1000), 1.0, P(0x2000), None,
+                                     None) == -6
