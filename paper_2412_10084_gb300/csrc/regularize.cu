@@ -25,6 +25,7 @@ constexpr int TX = 32, TY = 8, TZ = 8, HALO = 2;
 constexpr int AX = TX + 2 * HALO, AY = TY + 2 * HALO, AZ = TZ + 2 * HALO;
 constexpr int kBufA = AZ * AY * AX;  // 5184 floats
 constexpr int kBufB = AZ * AY * TX;  // 4608 floats (>= TZ * AY * AX = 3456)
+constexpr int kSmoothThreads = 256;
 
 struct Taps {
     float w[5];
@@ -47,7 +48,7 @@ __device__ __forceinline__ float conv_weight(const Taps& T, int in, int out, int
 }
 
 template <bool TRANSPOSE>
-__global__ void __launch_bounds__(256) smooth_kernel(const float* __restrict__ in, int in_stride,
+__global__ void __launch_bounds__(kSmoothThreads) smooth_kernel(const float* __restrict__ in, int in_stride,
                                                      float* __restrict__ out, int out_stride,
                                                      int Rx, int Ry, int Rz, Taps T, int accumulate)
 {
@@ -56,24 +57,34 @@ __global__ void __launch_bounds__(256) smooth_kernel(const float* __restrict__ i
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
     const int tid = threadIdx.x;
     // tile + halo: forward reads replicate the edge nodes; the transposed
-    // operator has no input outside the grid (zeros)
-    for (int e = tid; e < kBufA; e += blockDim.x) {
+    // operator has no input outside the grid (zeros).  All of a thread's loads
+    // are issued before the first store to shared memory.
+    constexpr int kLoads = (kBufA + kSmoothThreads - 1) / kSmoothThreads;
+    float v[kLoads];
+#pragma unroll
+    for (int it = 0; it < kLoads; ++it) {
+        const int e = tid + it * kSmoothThreads;
         const int ax = e % AX, ay = (e / AX) % AY, az = e / (AX * AY);
         const int gx = x0 + ax - HALO, gy = y0 + ay - HALO, gz = z0 + az - HALO;
-        float v = 0.0f;
+        v[it] = 0.0f;
+        if (e >= kBufA) continue;
         if (!TRANSPOSE) {
             const size_t g = ((size_t)clampi(gz, 0, Rz - 1) * Ry + clampi(gy, 0, Ry - 1)) * Rx +
                              clampi(gx, 0, Rx - 1);
-            v = in[g * in_stride];
+            v[it] = __ldg(in + g * in_stride);
         } else if (gx >= 0 && gx < Rx && gy >= 0 && gy < Ry && gz >= 0 && gz < Rz) {
-            v = in[(((size_t)gz * Ry + gy) * Rx + gx) * in_stride];
+            v[it] = __ldg(in + (((size_t)gz * Ry + gy) * Rx + gx) * in_stride);
         }
-        A[e] = v;
+    }
+#pragma unroll
+    for (int it = 0; it < kLoads; ++it) {
+        const int e = tid + it * kSmoothThreads;
+        if (e < kBufA) A[e] = v[it];
     }
     __syncthreads();
     if (!TRANSPOSE) {
         // x: A[AZ][AY][AX] -> B[AZ][AY][TX]
-        for (int e = tid; e < AZ * AY * TX; e += blockDim.x) {
+        for (int e = tid; e < AZ * AY * TX; e += kSmoothThreads) {
             const int x = e % TX, ay = (e / TX) % AY, az = e / (TX * AY);
             const float* a = A + (az * AY + ay) * AX + x;
             float acc = 0.0f;
@@ -83,7 +94,7 @@ __global__ void __launch_bounds__(256) smooth_kernel(const float* __restrict__ i
         }
         __syncthreads();
         // y: B[AZ][AY][TX] -> A[AZ][TY][TX]
-        for (int e = tid; e < AZ * TY * TX; e += blockDim.x) {
+        for (int e = tid; e < AZ * TY * TX; e += kSmoothThreads) {
             const int x = e % TX, y = (e / TX) % TY, az = e / (TX * TY);
             const float* b = B + (az * AY + y) * TX + x;
             float acc = 0.0f;
@@ -93,7 +104,7 @@ __global__ void __launch_bounds__(256) smooth_kernel(const float* __restrict__ i
         }
         __syncthreads();
         // z: A[AZ][TY][TX] -> output
-        for (int e = tid; e < TZ * TY * TX; e += blockDim.x) {
+        for (int e = tid; e < TZ * TY * TX; e += kSmoothThreads) {
             const int x = e % TX, y = (e / TX) % TY, z = e / (TX * TY);
             const int gx = x0 + x, gy = y0 + y, gz = z0 + z;
             if (gx >= Rx || gy >= Ry || gz >= Rz) continue;
@@ -109,7 +120,7 @@ __global__ void __launch_bounds__(256) smooth_kernel(const float* __restrict__ i
         // inputs i = k - 2 .. k + 2 with the weight the forward gave node k in
         // its output i.
         // z: A[AZ][AY][AX] -> B[TZ][AY][AX]
-        for (int e = tid; e < TZ * AY * AX; e += blockDim.x) {
+        for (int e = tid; e < TZ * AY * AX; e += kSmoothThreads) {
             const int ax = e % AX, ay = (e / AX) % AY, z = e / (AX * AY);
             const int k = z0 + z;
             float acc = 0.0f;
@@ -123,7 +134,7 @@ __global__ void __launch_bounds__(256) smooth_kernel(const float* __restrict__ i
         }
         __syncthreads();
         // y: B[TZ][AY][AX] -> A[TZ][TY][AX]
-        for (int e = tid; e < TZ * TY * AX; e += blockDim.x) {
+        for (int e = tid; e < TZ * TY * AX; e += kSmoothThreads) {
             const int ax = e % AX, y = (e / AX) % TY, z = e / (AX * TY);
             const int k = y0 + y;
             float acc = 0.0f;
@@ -137,7 +148,7 @@ __global__ void __launch_bounds__(256) smooth_kernel(const float* __restrict__ i
         }
         __syncthreads();
         // x: A[TZ][TY][AX] -> output
-        for (int e = tid; e < TZ * TY * TX; e += blockDim.x) {
+        for (int e = tid; e < TZ * TY * TX; e += kSmoothThreads) {
             const int x = e % TX, y = (e / TX) % TY, z = e / (TX * TY);
             const int gx = x0 + x, gy = y0 + y, gz = z0 + z;
             if (gx >= Rx || gy >= Ry || gz >= Rz) continue;
@@ -413,10 +424,10 @@ cudaError_t launch_smooth(const int R[3], const float* in, int in_stride, float*
     const dim3 grid((R[0] + TX - 1) / TX, (R[1] + TY - 1) / TY, (R[2] + TZ - 1) / TZ);
     const Taps T = gauss_taps();
     if (transpose)
-        smooth_kernel<true><<<grid, 256, 0, stream>>>(in, in_stride, out, out_stride, R[0], R[1],
+        smooth_kernel<true><<<grid, kSmoothThreads, 0, stream>>>(in, in_stride, out, out_stride, R[0], R[1],
                                                        R[2], T, accumulate ? 1 : 0);
     else
-        smooth_kernel<false><<<grid, 256, 0, stream>>>(in, in_stride, out, out_stride, R[0], R[1],
+        smooth_kernel<false><<<grid, kSmoothThreads, 0, stream>>>(in, in_stride, out, out_stride, R[0], R[1],
                                                         R[2], T, accumulate ? 1 : 0);
     return cudaGetLastError();
 }
