@@ -129,6 +129,10 @@ def _load():
             lib.orc_proposal_backward.argtypes = [P, P, ctypes.c_int64, P, P, P, ctypes.c_double,
                                                   ctypes.c_double, P, P]
             lib.orc_proposal_backward.restype = ctypes.c_int32
+            lib.orc_shade_nodes.argtypes = [P, P, P, ctypes.c_double, P]
+            lib.orc_shade_nodes.restype = ctypes.c_int32
+            lib.orc_render_colour_field.argtypes = [P, P, P, ctypes.c_int64, P, P, P, P, P, P]
+            lib.orc_render_colour_field.restype = ctypes.c_int32
             _lib = lib
     return _lib
 
@@ -255,6 +259,41 @@ def render_backward(model: Model, rays_o, rays_d, d_rgb, tau, n_samples, d_depth
     if st != 0:
         raise ValueError(f"oracle backward rejected its arguments ({st})")
     return {"sdf": g_sdf, "feat": g_feat, "probes": g_probe, "mlp": g_mlp}
+
+
+def shade_nodes(model: Model, camera, band, dir_mode=DIR_REFLECT):
+    """Two-pass inference, first pass: the colour of every node seen from a
+    camera at `camera` ([Rz,Ry,Rx,3]; nodes with |s| >= band are 0)."""
+    lib = _load()
+    out = np.zeros(model.sdf.shape + (3,))
+    cam = _f64(camera).reshape(3)
+    p = _params(1.0, 1, dir_mode)
+    st = lib.orc_shade_nodes(ctypes.byref(model._s), ctypes.byref(p), _ptr(cam), float(band),
+                             _ptr(out))
+    if st != 0:
+        raise ValueError(f"oracle shade_nodes rejected its arguments ({st})")
+    return out
+
+
+def render_colour_field(model: Model, colours, rays_o, rays_d, tau, n_samples,
+                        bg=(0.0, 0.0, 0.0), t_samples=None):
+    """Two-pass inference, second pass: the NeuS march with every sample's
+    colour the trilinear blend of the node colours [Rz,Ry,Rx,3]."""
+    lib = _load()
+    o, d = _f32(rays_o).reshape(-1, 3), _f32(rays_d).reshape(-1, 3)
+    n = o.shape[0]
+    col = _f64(colours)
+    assert col.shape == model.sdf.shape + (3,), "colours [Rz,Ry,Rx,3]"
+    ts = None if t_samples is None else _f32(t_samples).reshape(n, n_samples + 1)
+    rgb = np.zeros((n, 3))
+    depth, wsum = np.zeros(n), np.zeros(n)
+    p = _params(tau, n_samples, DIR_REFLECT, bg)
+    st = lib.orc_render_colour_field(ctypes.byref(model._s), ctypes.byref(p), _ptr(col), n,
+                                     _ptr(o), _ptr(d), _ptr(ts), _ptr(rgb), _ptr(depth),
+                                     _ptr(wsum))
+    if st != 0:
+        raise ValueError(f"oracle render_colour_field rejected its arguments ({st})")
+    return {"rgb": rgb, "depth": depth, "wsum": wsum}
 
 
 def render_trace(model: Model, o, d, tau, n_samples, dir_mode=DIR_REFLECT, t_samples=None):

@@ -298,6 +298,80 @@ static void triplane_features(const orc_model* m, tri_at* T, double* fs)
     for (int q = 0; q < ns; ++q) fs[q] = T->b[0][q] * T->b[1][q] * T->b[2][q];
 }
 
+/* Colour inputs after the spatial features (Sec. 3.1-3.2): normal from S->g
+ * (Eq. 13, guarded against 0/0), the SH lookup direction (r = 2(n.v)n - v, or v),
+ * the probe-blended angular features of the probe cell in S->pi_, S->pf
+ * (Eqs. 5-7) and the Fresnel inputs (Eq. 4), into S->x after the n_s features. */
+static void angular_inputs(const orc_model* m, const orc_params* p, const double v[3],
+                           orc_sample* S)
+{
+    const int ns = m->n_s;
+    const double gg = S->g[0] * S->g[0] + S->g[1] * S->g[1] + S->g[2] * S->g[2];
+    S->rho = sqrt(gg + ORC_EPS_NORMAL * ORC_EPS_NORMAL);
+    for (int a = 0; a < 3; ++a) S->n[a] = S->g[a] / S->rho;
+    S->ndv = S->n[0] * v[0] + S->n[1] * v[1] + S->n[2] * v[2];
+    for (int a = 0; a < 3; ++a)
+        S->r[a] = (p->dir_mode == ORC_DIR_VIEW) ? v[a] : 2.0 * S->ndv * S->n[a] - v[a];
+
+    /* Angular features, Eqs. 5-7: bhat_j = sum_i w_i b_ij, F_a = sum_j bhat_j Y_j. */
+    const int L2 = m->sh_l * m->sh_l, na = m->n_a;
+    orc_sh_eval(m->sh_l, S->r, S->Y);
+    for (int k = 0; k < L2 * na; ++k) S->bhat[k] = 0.0;
+    for (int c = 0; c < 8; ++c) {
+        const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
+        double w;
+        corner_weight(S->pf, cx, cy, cz, &w, NULL);
+        const size_t pn = node_index(m->P, S->pi_[0] + cx, S->pi_[1] + cy, S->pi_[2] + cz);
+        const double* b = m->probes + pn * (size_t)(L2 * na);
+        for (int k = 0; k < L2 * na; ++k) S->bhat[k] += w * b[k];
+    }
+    for (int ch = 0; ch < na; ++ch) {
+        double fa = 0.0;
+        for (int j = 0; j < L2; ++j) fa += S->bhat[j * na + ch] * S->Y[j];
+        S->x[ns + ch] = fa;
+    }
+    /* Fresnel inputs (1 - n.v)^k, k = 1..K (Eq. 4). */
+    for (int k = 1; k <= m->n_fresnel; ++k) S->x[ns + na + k - 1] = pow(1.0 - S->ndv, (double)k);
+}
+
+/* Colour MLP on S->x: two ReLU layers and a sigmoid output (Sec. 4). */
+static void mlp_colour(const orc_model* m, orc_sample* S, double* margin)
+{
+    const int W = m->width, nin = mlp_n_in(m);
+    const double* W1 = m->mlp;
+    const double* b1 = W1 + W * nin;
+    const double* W2 = b1 + W;
+    const double* b2 = W2 + W * W;
+    const double* W3 = b2 + W;
+    const double* b3 = W3 + 3 * W;
+    for (int o2 = 0; o2 < W; ++o2) {
+        double z = b1[o2], mag = fabs(b1[o2]);
+        for (int i = 0; i < nin; ++i) {
+            z += W1[o2 * nin + i] * S->x[i];
+            mag += fabs(W1[o2 * nin + i] * S->x[i]);
+        }
+        S->z1[o2] = z;
+        S->h1[o2] = relu(z);
+        if (margin && mag > 0.0 && fabs(z) / mag < *margin) *margin = fabs(z) / mag;
+    }
+    for (int o2 = 0; o2 < W; ++o2) {
+        double z = b2[o2], mag = fabs(b2[o2]);
+        for (int i = 0; i < W; ++i) {
+            z += W2[o2 * W + i] * S->h1[i];
+            mag += fabs(W2[o2 * W + i] * S->h1[i]);
+        }
+        S->z2[o2] = z;
+        S->h2[o2] = relu(z);
+        if (margin && mag > 0.0 && fabs(z) / mag < *margin) *margin = fabs(z) / mag;
+    }
+    for (int c = 0; c < 3; ++c) {
+        double z = b3[c];
+        for (int i = 0; i < W; ++i) z += W3[c * W + i] * S->h2[i];
+        S->z3[c] = z;
+        S->C[c] = sigmoid(z);
+    }
+}
+
 /* Point geometry (positions, cells, SDF value and gradient, spatial
  * features).  `color` also asks for the rest of the colour inputs. */
 static void eval_point(const orc_model* m, const orc_params* p, const float o[3],
@@ -332,73 +406,11 @@ static void eval_point(const orc_model* m, const orc_params* p, const float o[3]
         triplane_features(m, &T, S->x);
     }
 
-    /* Normal (Eq. 13) with a guard against 0/0, view and reflected vectors. */
-    const double gg = S->g[0] * S->g[0] + S->g[1] * S->g[1] + S->g[2] * S->g[2];
-    S->rho = sqrt(gg + ORC_EPS_NORMAL * ORC_EPS_NORMAL);
     double v[3];
-    for (int a = 0; a < 3; ++a) {
-        S->n[a] = S->g[a] / S->rho;
-        v[a] = -(double)d[a];
-    }
-    S->ndv = S->n[0] * v[0] + S->n[1] * v[1] + S->n[2] * v[2];
-    for (int a = 0; a < 3; ++a)
-        S->r[a] = (p->dir_mode == ORC_DIR_VIEW) ? v[a] : 2.0 * S->ndv * S->n[a] - v[a];
-
-    /* Angular features, Eqs. 5-7: bhat_j = sum_i w_i b_ij, F_a = sum_j bhat_j Y_j. */
-    const int L2 = m->sh_l * m->sh_l, na = m->n_a;
-    orc_sh_eval(m->sh_l, S->r, S->Y);
+    for (int a = 0; a < 3; ++a) v[a] = -(double)d[a];
     locate_f32(x, m->bmin, scp, m->P, S->pi_, S->pf);
-    for (int k = 0; k < L2 * na; ++k) S->bhat[k] = 0.0;
-    for (int c = 0; c < 8; ++c) {
-        const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
-        double w;
-        corner_weight(S->pf, cx, cy, cz, &w, NULL);
-        const size_t pn = node_index(m->P, S->pi_[0] + cx, S->pi_[1] + cy, S->pi_[2] + cz);
-        const double* b = m->probes + pn * (size_t)(L2 * na);
-        for (int k = 0; k < L2 * na; ++k) S->bhat[k] += w * b[k];
-    }
-    for (int ch = 0; ch < na; ++ch) {
-        double fa = 0.0;
-        for (int j = 0; j < L2; ++j) fa += S->bhat[j * na + ch] * S->Y[j];
-        S->x[ns + ch] = fa;
-    }
-    /* Fresnel inputs (1 - n.v)^k, k = 1..K (Eq. 4). */
-    for (int k = 1; k <= m->n_fresnel; ++k) S->x[ns + na + k - 1] = pow(1.0 - S->ndv, (double)k);
-
-    /* Colour MLP: two ReLU layers and a sigmoid output (Sec. 4). */
-    const int W = m->width, nin = mlp_n_in(m);
-    const double* W1 = m->mlp;
-    const double* b1 = W1 + W * nin;
-    const double* W2 = b1 + W;
-    const double* b2 = W2 + W * W;
-    const double* W3 = b2 + W;
-    const double* b3 = W3 + 3 * W;
-    for (int o2 = 0; o2 < W; ++o2) {
-        double z = b1[o2], mag = fabs(b1[o2]);
-        for (int i = 0; i < nin; ++i) {
-            z += W1[o2 * nin + i] * S->x[i];
-            mag += fabs(W1[o2 * nin + i] * S->x[i]);
-        }
-        S->z1[o2] = z;
-        S->h1[o2] = relu(z);
-        if (margin && mag > 0.0 && fabs(z) / mag < *margin) *margin = fabs(z) / mag;
-    }
-    for (int o2 = 0; o2 < W; ++o2) {
-        double z = b2[o2], mag = fabs(b2[o2]);
-        for (int i = 0; i < W; ++i) {
-            z += W2[o2 * W + i] * S->h1[i];
-            mag += fabs(W2[o2 * W + i] * S->h1[i]);
-        }
-        S->z2[o2] = z;
-        S->h2[o2] = relu(z);
-        if (margin && mag > 0.0 && fabs(z) / mag < *margin) *margin = fabs(z) / mag;
-    }
-    for (int c = 0; c < 3; ++c) {
-        double z = b3[c];
-        for (int i = 0; i < W; ++i) z += W3[c * W + i] * S->h2[i];
-        S->z3[c] = z;
-        S->C[c] = sigmoid(z);
-    }
+    angular_inputs(m, p, v, S);
+    mlp_colour(m, S, margin);
 }
 
 /* Sample distances of one ray.  Returns 0 for a ray that misses the box. */
@@ -1218,5 +1230,143 @@ int32_t orc_proposal_backward(const orc_model* m, const orc_proposal* pr, int64_
         (void)dh1;
         (void)dh2;
     }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Two-pass inference (the paper's viewer: "shading" assigns a colour to    */
+/* every voxel for the current view, then "render" samples the SDF and the  */
+/* colour field along the rays; Sec. "Performance Analysis", Tab. 8).        */
+/* ------------------------------------------------------------------------ */
+
+int32_t orc_shade_nodes(const orc_model* m, const orc_params* p, const double cam[3],
+                        double band, double* colours)
+{
+    const int rc = check_model(m, p);
+    if (rc) return rc;
+    if (!cam || !colours) return -1;
+    double h[3];
+    for (int a = 0; a < 3; ++a)
+        h[a] = ((double)m->bmax[a] - (double)m->bmin[a]) / (double)(m->R[a] - 1);
+    const int ns = m->n_s;
+    orc_sample* S = (orc_sample*)calloc(1, sizeof(orc_sample));
+    if (!S) return -3;
+    for (int iz = 0; iz < m->R[2]; ++iz)
+        for (int iy = 0; iy < m->R[1]; ++iy)
+            for (int ix = 0; ix < m->R[0]; ++ix) {
+                const int i[3] = {ix, iy, iz};
+                const size_t nd = node_index(m->R, ix, iy, iz);
+                double* C = colours + 3 * nd;
+                const double s = m->sdf[nd];
+                if (!(fabs(s) < band)) { /* outside the band: not shaded */
+                    C[0] = C[1] = C[2] = 0.0;
+                    continue;
+                }
+                /* SDF gradient at the node: central differences, one-sided on the faces */
+                for (int a = 0; a < 3; ++a) {
+                    int ip[3] = {ix, iy, iz}, im[3] = {ix, iy, iz};
+                    ip[a] = i[a] + 1 < m->R[a] ? i[a] + 1 : i[a];
+                    im[a] = i[a] > 0 ? i[a] - 1 : 0;
+                    const double sp = m->sdf[node_index(m->R, ip[0], ip[1], ip[2])];
+                    const double sm = m->sdf[node_index(m->R, im[0], im[1], im[2])];
+                    S->g[a] = (sp - sm) / ((double)(ip[a] - im[a]) * h[a]);
+                }
+                /* direction from the node to the camera */
+                double v[3], len = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    v[a] = cam[a] - ((double)m->bmin[a] + (double)i[a] * h[a]);
+                    len += v[a] * v[a];
+                }
+                len = sqrt(len);
+                for (int a = 0; a < 3; ++a) v[a] /= len;
+                /* spatial features at the node */
+                if (m->feat_layout == ORC_FEAT_TRIPLANE) {
+                    int ci[3];
+                    double cf[3];
+                    for (int a = 0; a < 3; ++a) {
+                        ci[a] = i[a] < m->R[a] - 1 ? i[a] : m->R[a] - 2;
+                        cf[a] = (double)(i[a] - ci[a]);
+                    }
+                    tri_at T;
+                    triplane_locate(m, ci, cf, &T);
+                    triplane_features(m, &T, S->x);
+                } else {
+                    for (int q = 0; q < ns; ++q) S->x[q] = m->feat[nd * (size_t)ns + q];
+                }
+                /* probe cell of the node: u = i (P - 1) / (R - 1) */
+                for (int a = 0; a < 3; ++a) {
+                    const double u = (double)i[a] * (double)(m->P[a] - 1) / (double)(m->R[a] - 1);
+                    int pi = (int)floor(u);
+                    if (pi > m->P[a] - 2) pi = m->P[a] - 2;
+                    if (pi < 0) pi = 0;
+                    S->pi_[a] = pi;
+                    S->pf[a] = u - (double)pi;
+                }
+                angular_inputs(m, p, v, S);
+                mlp_colour(m, S, NULL);
+                for (int c = 0; c < 3; ++c) C[c] = S->C[c];
+            }
+    free(S);
+    return 0;
+}
+
+int32_t orc_render_colour_field(const orc_model* m, const orc_params* p, const double* colours,
+                                int64_t n_rays, const float* rays_o, const float* rays_d,
+                                const float* t_samples, double* rgb, double* depth, double* wsum)
+{
+    const int rc = check_model(m, p);
+    if (rc) return rc;
+    if (n_rays < 0 || (n_rays > 0 && (!colours || !rays_o || !rays_d || !rgb || !depth || !wsum)))
+        return -1;
+    const int N = p->n_samples;
+    float* t = (float*)malloc(sizeof(float) * (size_t)(N + 1));
+    double* s = (double*)malloc(sizeof(double) * (size_t)(N + 1));
+    double* col = (double*)malloc(sizeof(double) * 3 * (size_t)N);
+    orc_sample* S = (orc_sample*)calloc(1, sizeof(orc_sample));
+    if (!t || !s || !col || !S) {
+        free(t), free(s), free(col), free(S);
+        return -3;
+    }
+    for (int64_t r = 0; r < n_rays; ++r) {
+        const float* o = rays_o + 3 * r;
+        const float* d = rays_d + 3 * r;
+        const float* tg = t_samples ? t_samples + r * (int64_t)(N + 1) : NULL;
+        if (!ray_samples(m, p, o, d, tg, t)) {
+            for (int c = 0; c < 3; ++c) rgb[3 * r + c] = p->bg[c];
+            depth[r] = wsum[r] = 0.0;
+            continue;
+        }
+        /* SDF at the N + 1 points; colour of sample k: trilinear blend of the
+         * node colours of the cell holding point k */
+        for (int k = 0; k <= N; ++k) {
+            eval_point(m, p, o, d, t[k], 0, S, NULL);
+            s[k] = S->s;
+            if (k == N) break;
+            for (int c = 0; c < 3; ++c) col[3 * k + c] = 0.0;
+            for (int q = 0; q < 8; ++q) {
+                const int cx = q & 1, cy = (q >> 1) & 1, cz = (q >> 2) & 1;
+                double w;
+                corner_weight(S->cf, cx, cy, cz, &w, NULL);
+                const size_t nd = node_index(m->R, S->ci[0] + cx, S->ci[1] + cy, S->ci[2] + cz);
+                for (int c = 0; c < 3; ++c) col[3 * k + c] += w * colours[3 * nd + c];
+            }
+        }
+        /* NeuS opacity and compositing (Eqs. 8-10), as in the per-sample render */
+        double acc[3] = {0, 0, 0}, dep = 0.0, ws = 0.0, logT = 0.0;
+        for (int k = 0; k < N; ++k) {
+            const double diff = log_phi(p->tau, s[k + 1]) - log_phi(p->tau, s[k]);
+            const double lam = diff < 0.0 ? diff : 0.0;
+            const double w = exp(logT) * -expm1(lam);
+            for (int c = 0; c < 3; ++c) acc[c] += w * col[3 * k + c];
+            dep += w * (double)t[k];
+            ws += w;
+            logT += lam;
+        }
+        const double TN = exp(logT);
+        for (int c = 0; c < 3; ++c) rgb[3 * r + c] = acc[c] + TN * p->bg[c];
+        depth[r] = dep;
+        wsum[r] = ws;
+    }
+    free(t), free(s), free(col), free(S);
     return 0;
 }

@@ -98,4 +98,17 @@ int32_t orc_proposal_backward(const orc_model* m, const orc_proposal* pr, int64_
                               const float* rays_o, const float* rays_d, const double* hist,
                               double min_mass, double scale, double* g_params, double* loss);
 
+/* Two-pass inference.  orc_shade_nodes: colours [Rz][Ry][Rx][3] of every node
+ * for a camera at cam: nodes with |s| < band get the MLP colour of the node
+ * (gradient by central differences, one-sided on the faces; v towards the
+ * camera; the node's own features or its tri-plane features; probes
+ * interpolated at the node), the others 0.  orc_render_colour_field: the
+ * NeuS march of orc_render_forward with the colour of sample k the trilinear
+ * blend of `colours` over the cell holding point k. */
+int32_t orc_shade_nodes(const orc_model* m, const orc_params* p, const double cam[3],
+                        double band, double* colours);
+int32_t orc_render_colour_field(const orc_model* m, const orc_params* p, const double* colours,
+                                int64_t n_rays, const float* rays_o, const float* rays_d,
+                                const float* t_samples, double* rgb, double* depth, double* wsum);
+
 #endif
