@@ -256,6 +256,43 @@ psdf_status psdf_adam_step(float* param, float* grad, float* m, float* v, int64_
                            void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Two-pass inference (the paper's viewer; Tab. 8 times its two kernels:
+ * "shading" assigns every voxel a colour for the current view, "render"
+ * samples the SDF and that colour field along the rays).  Per frame:
+ * psdf_shade_nodes for the view's camera, then psdf_render_colour_field for
+ * its rays.  The colour field is device memory of psdf_colour_field_bytes:
+ * one 8-byte record {r, g, b, 0} of FP16 per grid node, x fastest.
+ * ------------------------------------------------------------------------- */
+
+psdf_status psdf_colour_field_bytes(const psdf_grid_desc* desc, size_t* bytes);
+
+/* Colour of every node seen from a pinhole camera at `camera` (host FP32
+ * [3], world units).  Nodes with |s| < band get the colour model's output
+ * at the node: normal from the SDF gradient by central differences over the
+ * node's neighbours (one-sided on the grid's faces; Eq. 13), v the unit
+ * vector from the node to the camera, r per params->dir_mode, the node's own
+ * spatial features (tri-planes: the lookup at the node), probes interpolated
+ * at the node (Eqs. 5-7), Fresnel inputs (Eq. 4), the MLP (Sec. 4).  The other
+ * nodes get 0.  Of params only dir_mode and n_fresnel are used (the rest must
+ * be valid).  band >= 0 (0 shades nothing; +inf shades every node).  Every
+ * record of `colours` is written. */
+psdf_status psdf_shade_nodes(const psdf_grid* grid, const psdf_probes* probes,
+                             const psdf_mlp* mlp, const psdf_render_params* params,
+                             const float camera[3], float band, void* colours, void* stream);
+
+/* The NeuS march of psdf_render_forward (same sample distances -- uniform,
+ * explicit or from bin densities --, opacities and compositing, Eqs. 8-10)
+ * with sample k's colour the trilinear blend of the colour field over the
+ * 8 nodes of the SDF cell holding point k, in place of the colour model.
+ * Outputs rgb [n_rays][3], depth, wsum [n_rays] as in psdf_render_forward.
+ * Of params dir_mode and n_fresnel are not used. */
+psdf_status psdf_render_colour_field(const psdf_grid* grid, const void* colours,
+                                     const psdf_render_params* params, const float* rays_o,
+                                     const float* rays_d, const float* t_samples,
+                                     int64_t n_rays, float* rgb, float* depth, float* wsum,
+                                     void* stream);
+
+/* ---------------------------------------------------------------------------
  * Grid-level training terms (Sec. 3.3, Eqs. 11-15).  The trained SDF
  * parameter is a raw grid s_hat (device FP32 [Rz][Ry][Rx], x fastest, the
  * caller's); the grid the renderer reads holds its smoothing s = G(s_hat),

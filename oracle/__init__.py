@@ -131,6 +131,8 @@ def _load():
             lib.orc_proposal_backward.restype = ctypes.c_int32
             lib.orc_shade_nodes.argtypes = [P, P, P, ctypes.c_double, P]
             lib.orc_shade_nodes.restype = ctypes.c_int32
+            lib.orc_shade_node_list.argtypes = [P, P, P, ctypes.c_double, ctypes.c_int64, P, P]
+            lib.orc_shade_node_list.restype = ctypes.c_int32
             lib.orc_render_colour_field.argtypes = [P, P, P, ctypes.c_int64, P, P, P, P, P, P]
             lib.orc_render_colour_field.restype = ctypes.c_int32
             _lib = lib
@@ -272,6 +274,20 @@ def shade_nodes(model: Model, camera, band, dir_mode=DIR_REFLECT):
                              _ptr(out))
     if st != 0:
         raise ValueError(f"oracle shade_nodes rejected its arguments ({st})")
+    return out
+
+
+def shade_node_list(model: Model, camera, band, nodes, dir_mode=DIR_REFLECT):
+    """shade_nodes for the listed linear node indices only -> [n, 3]."""
+    lib = _load()
+    idx = np.ascontiguousarray(nodes, dtype=np.int64).ravel()
+    out = np.zeros((idx.size, 3))
+    cam = _f64(camera).reshape(3)
+    p = _params(1.0, 1, dir_mode)
+    st = lib.orc_shade_node_list(ctypes.byref(model._s), ctypes.byref(p), _ptr(cam),
+                                 float(band), idx.size, _ptr(idx), _ptr(out))
+    if st != 0:
+        raise ValueError(f"oracle shade_node_list rejected its arguments ({st})")
     return out
 
 

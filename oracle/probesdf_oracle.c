@@ -1239,73 +1239,92 @@ int32_t orc_proposal_backward(const orc_model* m, const orc_proposal* pr, int64_
 /* colour field along the rays; Sec. "Performance Analysis", Tab. 8).        */
 /* ------------------------------------------------------------------------ */
 
+/* Colour of node nd (Rx Ry Rz order) seen from cam, or 0 outside the band. */
+static void shade_node(const orc_model* m, const orc_params* p, const double cam[3], double band,
+                       size_t nd, orc_sample* S, double C[3])
+{
+    const int i[3] = {(int)(nd % (size_t)m->R[0]), (int)((nd / (size_t)m->R[0]) % (size_t)m->R[1]),
+                      (int)(nd / ((size_t)m->R[0] * (size_t)m->R[1]))};
+    const double s = m->sdf[nd];
+    if (!(fabs(s) < band)) { /* outside the band: not shaded */
+        C[0] = C[1] = C[2] = 0.0;
+        return;
+    }
+    double h[3];
+    for (int a = 0; a < 3; ++a)
+        h[a] = ((double)m->bmax[a] - (double)m->bmin[a]) / (double)(m->R[a] - 1);
+    /* SDF gradient at the node: central differences, one-sided on the faces */
+    for (int a = 0; a < 3; ++a) {
+        int ip[3] = {i[0], i[1], i[2]}, im[3] = {i[0], i[1], i[2]};
+        ip[a] = i[a] + 1 < m->R[a] ? i[a] + 1 : i[a];
+        im[a] = i[a] > 0 ? i[a] - 1 : 0;
+        const double sp = m->sdf[node_index(m->R, ip[0], ip[1], ip[2])];
+        const double sm = m->sdf[node_index(m->R, im[0], im[1], im[2])];
+        S->g[a] = (sp - sm) / ((double)(ip[a] - im[a]) * h[a]);
+    }
+    /* direction from the node to the camera */
+    double v[3], len = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        v[a] = cam[a] - ((double)m->bmin[a] + (double)i[a] * h[a]);
+        len += v[a] * v[a];
+    }
+    len = sqrt(len);
+    for (int a = 0; a < 3; ++a) v[a] /= len;
+    /* spatial features at the node */
+    if (m->feat_layout == ORC_FEAT_TRIPLANE) {
+        int ci[3];
+        double cf[3];
+        for (int a = 0; a < 3; ++a) {
+            ci[a] = i[a] < m->R[a] - 1 ? i[a] : m->R[a] - 2;
+            cf[a] = (double)(i[a] - ci[a]);
+        }
+        tri_at T;
+        triplane_locate(m, ci, cf, &T);
+        triplane_features(m, &T, S->x);
+    } else {
+        for (int q = 0; q < m->n_s; ++q) S->x[q] = m->feat[nd * (size_t)m->n_s + q];
+    }
+    /* probe cell of the node: u = i (P - 1) / (R - 1) */
+    for (int a = 0; a < 3; ++a) {
+        const double u = (double)i[a] * (double)(m->P[a] - 1) / (double)(m->R[a] - 1);
+        int pi = (int)floor(u);
+        if (pi > m->P[a] - 2) pi = m->P[a] - 2;
+        if (pi < 0) pi = 0;
+        S->pi_[a] = pi;
+        S->pf[a] = u - (double)pi;
+    }
+    angular_inputs(m, p, v, S);
+    mlp_colour(m, S, NULL);
+    for (int c = 0; c < 3; ++c) C[c] = S->C[c];
+}
+
 int32_t orc_shade_nodes(const orc_model* m, const orc_params* p, const double cam[3],
                         double band, double* colours)
 {
     const int rc = check_model(m, p);
     if (rc) return rc;
     if (!cam || !colours) return -1;
-    double h[3];
-    for (int a = 0; a < 3; ++a)
-        h[a] = ((double)m->bmax[a] - (double)m->bmin[a]) / (double)(m->R[a] - 1);
-    const int ns = m->n_s;
     orc_sample* S = (orc_sample*)calloc(1, sizeof(orc_sample));
     if (!S) return -3;
-    for (int iz = 0; iz < m->R[2]; ++iz)
-        for (int iy = 0; iy < m->R[1]; ++iy)
-            for (int ix = 0; ix < m->R[0]; ++ix) {
-                const int i[3] = {ix, iy, iz};
-                const size_t nd = node_index(m->R, ix, iy, iz);
-                double* C = colours + 3 * nd;
-                const double s = m->sdf[nd];
-                if (!(fabs(s) < band)) { /* outside the band: not shaded */
-                    C[0] = C[1] = C[2] = 0.0;
-                    continue;
-                }
-                /* SDF gradient at the node: central differences, one-sided on the faces */
-                for (int a = 0; a < 3; ++a) {
-                    int ip[3] = {ix, iy, iz}, im[3] = {ix, iy, iz};
-                    ip[a] = i[a] + 1 < m->R[a] ? i[a] + 1 : i[a];
-                    im[a] = i[a] > 0 ? i[a] - 1 : 0;
-                    const double sp = m->sdf[node_index(m->R, ip[0], ip[1], ip[2])];
-                    const double sm = m->sdf[node_index(m->R, im[0], im[1], im[2])];
-                    S->g[a] = (sp - sm) / ((double)(ip[a] - im[a]) * h[a]);
-                }
-                /* direction from the node to the camera */
-                double v[3], len = 0.0;
-                for (int a = 0; a < 3; ++a) {
-                    v[a] = cam[a] - ((double)m->bmin[a] + (double)i[a] * h[a]);
-                    len += v[a] * v[a];
-                }
-                len = sqrt(len);
-                for (int a = 0; a < 3; ++a) v[a] /= len;
-                /* spatial features at the node */
-                if (m->feat_layout == ORC_FEAT_TRIPLANE) {
-                    int ci[3];
-                    double cf[3];
-                    for (int a = 0; a < 3; ++a) {
-                        ci[a] = i[a] < m->R[a] - 1 ? i[a] : m->R[a] - 2;
-                        cf[a] = (double)(i[a] - ci[a]);
-                    }
-                    tri_at T;
-                    triplane_locate(m, ci, cf, &T);
-                    triplane_features(m, &T, S->x);
-                } else {
-                    for (int q = 0; q < ns; ++q) S->x[q] = m->feat[nd * (size_t)ns + q];
-                }
-                /* probe cell of the node: u = i (P - 1) / (R - 1) */
-                for (int a = 0; a < 3; ++a) {
-                    const double u = (double)i[a] * (double)(m->P[a] - 1) / (double)(m->R[a] - 1);
-                    int pi = (int)floor(u);
-                    if (pi > m->P[a] - 2) pi = m->P[a] - 2;
-                    if (pi < 0) pi = 0;
-                    S->pi_[a] = pi;
-                    S->pf[a] = u - (double)pi;
-                }
-                angular_inputs(m, p, v, S);
-                mlp_colour(m, S, NULL);
-                for (int c = 0; c < 3; ++c) C[c] = S->C[c];
-            }
+    const size_t n = (size_t)m->R[0] * (size_t)m->R[1] * (size_t)m->R[2];
+    for (size_t nd = 0; nd < n; ++nd) shade_node(m, p, cam, band, nd, S, colours + 3 * nd);
+    free(S);
+    return 0;
+}
+
+int32_t orc_shade_node_list(const orc_model* m, const orc_params* p, const double cam[3],
+                            double band, int64_t n, const int64_t* nodes, double* colours)
+{
+    const int rc = check_model(m, p);
+    if (rc) return rc;
+    if (!cam || n < 0 || (n > 0 && (!nodes || !colours))) return -1;
+    const int64_t total = (int64_t)m->R[0] * m->R[1] * m->R[2];
+    for (int64_t k = 0; k < n; ++k)
+        if (nodes[k] < 0 || nodes[k] >= total) return -1;
+    orc_sample* S = (orc_sample*)calloc(1, sizeof(orc_sample));
+    if (!S) return -3;
+    for (int64_t k = 0; k < n; ++k)
+        shade_node(m, p, cam, band, (size_t)nodes[k], S, colours + 3 * k);
     free(S);
     return 0;
 }

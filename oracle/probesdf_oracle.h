@@ -107,6 +107,9 @@ int32_t orc_proposal_backward(const orc_model* m, const orc_proposal* pr, int64_
  * blend of `colours` over the cell holding point k. */
 int32_t orc_shade_nodes(const orc_model* m, const orc_params* p, const double cam[3],
                         double band, double* colours);
+/* orc_shade_nodes for the listed nodes only (linear indices, x fastest). */
+int32_t orc_shade_node_list(const orc_model* m, const orc_params* p, const double cam[3],
+                            double band, int64_t n, const int64_t* nodes, double* colours);
 int32_t orc_render_colour_field(const orc_model* m, const orc_params* p, const double* colours,
                                 int64_t n_rays, const float* rays_o, const float* rays_d,
                                 const float* t_samples, double* rgb, double* depth, double* wsum);

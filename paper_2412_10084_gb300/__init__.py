@@ -26,7 +26,8 @@ __all__ = [
     "ProposalDesc", "proposal_desc", "proposal_param_count", "occupancy_build",
     "weight_histogram", "proposal_forward", "proposal_backward", "adam_step", "Adam",
     "occupancy_words", "occupancy_unpack", "sdf_smooth", "sdf_smooth_adjoint",
-    "grid_regularizers", "probe_smoothness",
+    "grid_regularizers", "probe_smoothness", "shade_nodes", "render_colour_field",
+    "colour_field_bytes",
 ]
 
 DIR_REFLECT = 0
@@ -133,7 +134,12 @@ def library() -> ctypes.CDLL:
         lib.psdf_grid_regularizers.argtypes = [_P, _P, _P, ctypes.c_float, ctypes.c_float,
                                                ctypes.c_float, ctypes.c_float, _P, _P, _P, _P]
         lib.psdf_probe_smoothness.argtypes = [_P, _P, ctypes.c_float, _P, _P, _P]
-        for name in ("psdf_sdf_smooth", "psdf_sdf_smooth_adjoint", "psdf_grid_regularizers",
+        lib.psdf_colour_field_bytes.argtypes = [_P, ctypes.POINTER(ctypes.c_size_t)]
+        lib.psdf_shade_nodes.argtypes = [_P, _P, _P, _P, _P, ctypes.c_float, _P, _P]
+        lib.psdf_render_colour_field.argtypes = [_P, _P, _P, _P, _P, _P, ctypes.c_int64, _P, _P,
+                                                 _P, _P]
+        for name in ("psdf_colour_field_bytes", "psdf_shade_nodes", "psdf_render_colour_field",
+                     "psdf_sdf_smooth", "psdf_sdf_smooth_adjoint", "psdf_grid_regularizers",
                      "psdf_probe_smoothness", "psdf_grid_bytes", "psdf_grid_create", "psdf_grid_pack", "psdf_grid_unpack",
                      "psdf_probes_create", "psdf_mlp_param_count", "psdf_mlp_create",
                      "psdf_render_forward", "psdf_render_backward", "psdf_render_occupancy",
@@ -507,6 +513,68 @@ class Adam:
         self.t += 1
         for p, g, lr, m, v in self.groups:
             adam_step(p, g, m, v, self.t, lr, self.beta1, self.beta2, self.eps)
+
+
+# ---------------------------------------------------------------------------
+# Two-pass inference: per-view node colours, then a colour-field march
+# ---------------------------------------------------------------------------
+
+def colour_field_bytes(gd) -> int:
+    n = ctypes.c_size_t()
+    _check(library().psdf_colour_field_bytes(ctypes.byref(gd), ctypes.byref(n)),
+           "psdf_colour_field_bytes")
+    return n.value
+
+
+def shade_nodes(scene: Scene, camera, band, params: RenderParams, out=None):
+    """Colour of every grid node seen from `camera` (3 floats, world units):
+    FP16 [Rz, Ry, Rx, 4] = {r, g, b, 0}; nodes with |s| >= band are 0."""
+    _require_cuda(scene.grid, scene.probes, scene.mlp,
+                  dtypes=(torch.float32, torch.float16, torch.uint8))
+    gd, pd, md = scene.descs(params.n_fresnel)
+    Rx, Ry, Rz = (int(v) for v in scene.dims)
+    if out is None:
+        out = torch.empty((Rz, Ry, Rx, 4), dtype=torch.float16, device=scene.grid.device)
+    _require_cuda(out, dtypes=(torch.float16,))
+    if out.numel() * 2 != colour_field_bytes(gd) or not out.is_contiguous():
+        raise LibraryError("shade_nodes: out must be a contiguous FP16 [Rz, Ry, Rx, 4] tensor")
+    cam = (ctypes.c_float * 3)(*(float(v) for v in camera))
+    h = _Handles(scene.grid, scene.probes, scene.mlp, gd, pd, md)
+    try:
+        _check(library().psdf_shade_nodes(h.g, h.p, h.m, ctypes.byref(params), cam, float(band),
+                                          _ptr(out), _stream()), "psdf_shade_nodes")
+    finally:
+        h.close()
+    return out
+
+
+def render_colour_field(scene: Scene, colours, rays_o, rays_d, params: RenderParams,
+                        t_samples=None):
+    """The NeuS march over the SDF with every sample's colour interpolated from
+    the node colours -> rgb [n,3], depth [n], wsum [n]."""
+    _require_cuda(scene.grid, dtypes=(torch.float32, torch.float16, torch.uint8))
+    _require_cuda(colours, dtypes=(torch.float16,))
+    _require_cuda(rays_o, rays_d, t_samples)
+    gd, _, _ = scene.descs(params.n_fresnel)
+    if colours.numel() * 2 != colour_field_bytes(gd) or not colours.is_contiguous():
+        raise LibraryError("render_colour_field: colours must be FP16 [Rz, Ry, Rx, 4]")
+    n = rays_o.shape[0]
+    dev = rays_o.device
+    rgb = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    depth = torch.empty(n, dtype=torch.float32, device=dev)
+    wsum = torch.empty(n, dtype=torch.float32, device=dev)
+    lib = library()
+    g = _P()
+    _check(lib.psdf_grid_create(ctypes.byref(gd), _ptr(scene.grid), ctypes.byref(g)),
+           "psdf_grid_create")
+    try:
+        _check(lib.psdf_render_colour_field(g, _ptr(colours), ctypes.byref(params), _ptr(rays_o),
+                                            _ptr(rays_d), _ptr(t_samples), n, _ptr(rgb),
+                                            _ptr(depth), _ptr(wsum), _stream()),
+               "psdf_render_colour_field")
+    finally:
+        lib.psdf_grid_destroy(g)
+    return rgb, depth, wsum
 
 
 # ---------------------------------------------------------------------------

@@ -1,5 +1,6 @@
 // C ABI of the ProbeSDF render library: handles, host-side validation,
 // launch configuration, dense <-> packed grid conversion.
+#include <cmath>
 #include <cstdint>
 #include <cstdlib>
 #include <algorithm>
@@ -644,6 +645,87 @@ psdf_status psdf_adam_step(float* param, float* grad, float* m, float* v, int64_
         return PSDF_ERR_MISALIGNED;
     return cuda_status(psdf::launch_adam(param, grad, m, v, n, lr, beta1, beta2, eps, step,
                                          clear_grad, static_cast<cudaStream_t>(stream)));
+}
+
+// ---------------------------------------------------------------------------
+// Two-pass inference
+// ---------------------------------------------------------------------------
+
+psdf_status psdf_colour_field_bytes(const psdf_grid_desc* desc, size_t* bytes)
+{
+    const psdf_status st = check_grid_desc(desc);
+    if (st != PSDF_OK) return st;
+    if (!bytes) return PSDF_ERR_INVALID_ARG;
+    *bytes = 8 * static_cast<size_t>(grid_nodes(desc));
+    return PSDF_OK;
+}
+
+psdf_status psdf_shade_nodes(const psdf_grid* grid, const psdf_probes* probes,
+                             const psdf_mlp* mlp, const psdf_render_params* params,
+                             const float camera[3], float band, void* colours, void* stream)
+{
+    Resolved r;
+    psdf_status st = resolve(grid, probes, mlp, params, nullptr, nullptr, nullptr, 0, r);
+    if (st != PSDF_OK) return st;
+    if (!camera || !colours || !(band >= 0.0f)) return PSDF_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(camera[a])) return PSDF_ERR_INVALID_ARG;
+    if (!aligned16(colours)) return PSDF_ERR_MISALIGNED;
+    psdf::ShadeArgs S;
+    const psdf_grid_desc& gd = grid->desc;
+    for (int a = 0; a < 3; ++a) {
+        S.cam[a] = camera[a];
+        S.h[a] = (gd.box_max[a] - gd.box_min[a]) / static_cast<float>(gd.dims[a] - 1);
+    }
+    S.band = band;
+    S.colours = static_cast<uint2*>(colours);
+    return cuda_status(
+        psdf::launch_shade(r.args, r.shape, S, static_cast<cudaStream_t>(stream)));
+}
+
+psdf_status psdf_render_colour_field(const psdf_grid* grid, const void* colours,
+                                     const psdf_render_params* p, const float* rays_o,
+                                     const float* rays_d, const float* t_samples,
+                                     int64_t n_rays, float* rgb, float* depth, float* wsum,
+                                     void* stream)
+{
+    if (!grid || !grid->values || !p || !colours) return PSDF_ERR_INVALID_ARG;
+    if (n_rays < 0) return PSDF_ERR_INVALID_ARG;
+    if (!(p->tau > 0.0f) || p->n_samples < 1 || p->n_samples > 4096) return PSDF_ERR_BAD_SHAPE;
+    if (p->n_bins < 0 || p->n_bins > 32) return PSDF_ERR_BAD_SHAPE;
+    if (n_rays > 0 && (!rays_o || !rays_d || !rgb || !depth || !wsum))
+        return PSDF_ERR_INVALID_ARG;
+    if (p->n_bins > 0 && n_rays > 0 && !t_samples) return PSDF_ERR_INVALID_ARG;
+    if (!aligned16(grid->values) || !aligned16(colours) || !aligned16(rays_o) ||
+        !aligned16(rays_d) || !aligned16(t_samples) || !aligned16(rgb) || !aligned16(depth) ||
+        !aligned16(wsum))
+        return PSDF_ERR_MISALIGNED;
+    if (n_rays == 0) return PSDF_OK;
+    psdf::RenderArgs A;
+    std::memset(&A, 0, sizeof(A));
+    const psdf_grid_desc& gd = grid->desc;
+    set_grid_view(gd, grid->values, A.grid);
+    for (int a = 0; a < 3; ++a) {
+        A.grid.R[a] = gd.dims[a];
+        A.grid.bmin[a] = gd.box_min[a];
+        A.grid.bmax[a] = gd.box_max[a];
+        // the same FP32 scale as the per-sample render, so samples land on the same cells
+        const volatile float ext = gd.box_max[a] - gd.box_min[a];
+        A.grid.sc[a] = static_cast<float>(gd.dims[a] - 1) / ext;
+    }
+    A.tau = p->tau;
+    A.n_samples = p->n_samples;
+    for (int c = 0; c < 3; ++c) A.bg[c] = p->bg[c];
+    A.rays_o = rays_o;
+    A.rays_d = rays_d;
+    A.t_samples = t_samples;
+    A.n_bins = t_samples ? p->n_bins : 0;
+    A.n_rays = n_rays;
+    A.rgb = rgb;
+    A.depth = depth;
+    A.wsum = wsum;
+    return cuda_status(
+        psdf::launch_colour_render(A, colours, static_cast<cudaStream_t>(stream)));
 }
 
 // ---------------------------------------------------------------------------

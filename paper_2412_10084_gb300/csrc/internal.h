@@ -48,6 +48,17 @@ int resident_ctas(const cudaFuncAttributes& fa, int threads, size_t dyn_smem, un
 cudaError_t forward_ctas_per_sm(const KernelShape& ks, int* n);
 cudaError_t backward_ctas_per_sm(const KernelShape& ks, int* n);
 
+// Two-pass inference (twopass.cu): per-view node shading, colour-field march.
+struct ShadeArgs {
+    float cam[3];   // camera centre (world)
+    float band;     // nodes with |s| < band are shaded, the others get colour 0
+    float h[3];     // node spacing (bmax - bmin) / (R - 1), FP32
+    uint2* colours; // [R^3] FP16 {r, g, b, 0}
+};
+cudaError_t launch_shade(const RenderArgs& A, const KernelShape& ks, const ShadeArgs& S,
+                         cudaStream_t stream);
+cudaError_t launch_colour_render(const RenderArgs& A, const void* colours, cudaStream_t stream);
+
 cudaError_t launch_adam(float* p, float* g, float* m, float* v, int64_t n, float lr, float beta1,
                         float beta2, float eps, int step, int clear_grad, cudaStream_t stream);
 // Grid-level training terms (regularize.cu).  SDF arrays are read and written

@@ -217,12 +217,13 @@ struct TriAt {
     float f[3];  // fraction to the next texel
 };
 
-__device__ __forceinline__ void triplane_locate(const GridView& g, const float x[3], TriAt& T)
+// Tile and texel of FP32 grid coordinates u (node units).
+__device__ __forceinline__ void triplane_locate_u(const GridView& g, const float uu[3], TriAt& T)
 {
     int t[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float u = __fmul_rn(__fsub_rn(x[a], g.bmin[a]), g.sc[a]);  // as locate_axis
+        const float u = uu[a];
         float ta = floorf(u * (1.0f / kTile));
         ta = ta >= 0.0f ? ta : 0.0f;  // also maps NaN to tile 0
         ta = fminf(ta, static_cast<float>(g.tiles[a] - 1));
@@ -234,6 +235,14 @@ __device__ __forceinline__ void triplane_locate(const GridView& g, const float x
         T.f[a] = __fsub_rn(tau, fi);
     }
     T.plane0 = ((t[2] * g.tiles[1] + t[1]) * g.tiles[0] + t[0]) * 3 * kTile * kTile;
+}
+
+__device__ __forceinline__ void triplane_locate(const GridView& g, const float x[3], TriAt& T)
+{
+    float u[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u[a] = __fmul_rn(__fsub_rn(x[a], g.bmin[a]), g.sc[a]);  // as locate_axis
+    triplane_locate_u(g, u, T);
 }
 
 // plane p: 0 is [z][y], 1 is [z][x], 2 is [y][x]

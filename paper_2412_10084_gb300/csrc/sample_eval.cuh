@@ -119,22 +119,18 @@ __device__ __forceinline__ void eval_sdf(const RenderArgs& A, const float o[3], 
     S.x[2] = fs[2];
 }
 
-// Appearance part: normal (Eq. 13), SH lookup direction and basis, probe-
-// blended angular features (Eqs. 6-7) and Fresnel inputs (Eq. 4), the MLP
-// input columns 3.. .  Needed only where the sample's opacity is nonzero.
+// Appearance part at world point xw seen along v (towards the viewer): normal
+// (Eq. 13) from S.g, SH lookup direction and basis, probe-blended angular
+// features (Eqs. 6-7) and Fresnel inputs (Eq. 4), the MLP input columns 3.. .
 template <class C>
-__device__ __forceinline__ void eval_appearance(const RenderArgs& A, const float o[3],
-                                                const float d[3], float t, SampleGeom<C>& S)
+__device__ __forceinline__ void eval_appearance_at(const RenderArgs& A, const float xw[3],
+                                                   const float v[3], SampleGeom<C>& S)
 {
     const float gg = S.g[0] * S.g[0] + S.g[1] * S.g[1] + S.g[2] * S.g[2];
     S.rho = sqrtf(gg + kNormalEps * kNormalEps);
     const float inv = 1.0f / S.rho;
-    float v[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        S.n[a] = S.g[a] * inv;
-        v[a] = -d[a];
-    }
+    for (int a = 0; a < 3; ++a) S.n[a] = S.g[a] * inv;
     S.ndv = S.n[0] * v[0] + S.n[1] * v[1] + S.n[2] * v[2];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -142,8 +138,6 @@ __device__ __forceinline__ void eval_appearance(const RenderArgs& A, const float
     sh_basis<C::L2>(S.r, S.Y);
 
     // Angular features (Eqs. 6-7): F_a = sum_i w_i sum_j b_ij Y_j(r).
-    float xw[3];
-    point_at(o, d, t, xw);
     S.pcell = locate(xw, A.grid.bmin, A.probes.sc, A.probes.P);
     float wq[8];
     corner_weights(S.pcell.f, wq);
@@ -183,6 +177,19 @@ __device__ __forceinline__ void eval_appearance(const RenderArgs& A, const float
     }
 #pragma unroll
     for (int i = C::NIN; i < C::NINP; ++i) S.x[i] = 0.0f;
+}
+
+// Appearance part of a ray sample (v = -d at o + t d).  Needed only where the
+// sample's opacity is nonzero.
+template <class C>
+__device__ __forceinline__ void eval_appearance(const RenderArgs& A, const float o[3],
+                                                const float d[3], float t, SampleGeom<C>& S)
+{
+    float xw[3], v[3];
+    point_at(o, d, t, xw);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) v[a] = -d[a];
+    eval_appearance_at<C>(A, xw, v, S);
 }
 
 // eval_appearance that also returns the blended probe coefficients

@@ -120,3 +120,15 @@ def test_regularizer_entry_points_reject_bad_arguments_on_the_host(lib):
     pd.dtype, pd.n_ang = ps.F32, 3
     assert lib.psdf_probe_smoothness(ctypes.byref(pd), P(0x1000), 1.0, P(0x2000), None,
                                      None) == -6
+
+
+def test_two_pass_entry_points_on_the_host(lib):
+    import paper_2412_10084_gb300 as ps
+    P = ctypes.c_void_p
+    gd = ps.grid_desc((9, 10, 11), (0, 0, 0), (1, 1, 1))
+    assert ps.colour_field_bytes(gd) == 8 * 9 * 10 * 11
+    lib.psdf_render_colour_field.argtypes = [P, P, P, P, P, P, ctypes.c_int64, P, P, P, P]
+    assert lib.psdf_render_colour_field(None, P(0x1000), None, None, None, None, 0, None, None,
+                                        None, None) == -1
+    lib.psdf_shade_nodes.argtypes = [P, P, P, P, P, ctypes.c_float, P, P]
+    assert lib.psdf_shade_nodes(None, None, None, None, None, 0.1, None, None) == -1

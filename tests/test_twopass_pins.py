@@ -135,3 +135,11 @@ def test_two_pass_equals_per_sample_render_for_a_constant_mlp():
     ref = oracle.render_forward(m, o, d, 64.0, 50)
     for k in ("rgb", "depth", "wsum"):
         np.testing.assert_allclose(two[k], ref[k], rtol=0, atol=1e-12)
+
+
+def test_node_list_matches_the_full_pass():
+    sc = tiny_scene(R=(9, 8, 10))
+    m = oracle.Model.from_scene(sc)
+    full = oracle.shade_nodes(m, CAM, 0.2).reshape(-1, 3)
+    idx = synth.rng(4).choice(full.shape[0], 60, replace=False)
+    np.testing.assert_array_equal(oracle.shade_node_list(m, CAM, 0.2, idx), full[idx])
