@@ -86,12 +86,23 @@ typedef struct psdf_grid_desc {
                             feature c is the product of the three planes' bilinear lookups
                             at its in-plane coordinates (texel coordinate clamped to the
                             tile) */
+    int32_t n_bricks;    /* 0: dense.  > 0: sparse (FP32 node features only): the nodes
+                            form bricks of 16^3 (dims must be multiples of 16) and only
+                            n_bricks of them are stored; see psdf_grid_bytes */
+    float empty_sdf;     /* sparse: the SDF value of every node of a brick that is not
+                            stored (> 0: empty space outside the surface); its features
+                            are 0.  A sample whose 8 corners all lie in such bricks has
+                            s = empty_sdf exactly.  Sparse grids are read by the render
+                            forward and adjoint, the weight histogram and the colour-field
+                            march; the occupancy build, node shading and the grid-level
+                            training passes take dense grids only (PSDF_ERR_UNSUPPORTED) */
 } psdf_grid_desc;
 
 /* Light-field probe grid (Sec. 3.2): l*l SH coefficients of n_a channels. */
 typedef struct psdf_probe_desc {
     int32_t dims[3];     /* probe nodes along x, y, z over the grid's box; each >= 2 */
-    int32_t sh_l;        /* SH order l, 1-indexed as in Eq. 5 (l*l coefficients); 3 compiled in */
+    int32_t sh_l;        /* SH order l, 1-indexed as in Eq. 5 (l*l coefficients); 3 compiled
+                            in, and 4 (16 coefficients, Sec. 4) with 4 channels and width 32 */
     int32_t n_ang;       /* angular channels n_a; 4 and 8 compiled in */
     int32_t dtype;       /* PSDF_F32 or PSDF_F16 (storage of the coefficients) */
 } psdf_probe_desc;
@@ -146,6 +157,12 @@ psdf_status psdf_device_status(void* stream, int32_t* flags);
  * PSDF_FEAT_TRIPLANE, values and gradient alike: an FP32 SDF array, then (at the
  * next 16-byte boundary) the planes: [tz][ty][tx][3][16][16] texels of 16 bytes
  * {f0, f1, f2, 0}.
+ * Sparse (n_bricks > 0), values and gradient alike: the brick table, int32
+ * [Bz][By][Bx] (B_a = dims_a / 16; entry = the brick's slot in 0..n_bricks-1,
+ * or -1 when it is not stored; padded to 16 bytes), then n_bricks blocks of
+ * 16^3 FP32 node records {sdf, f0, f1, f2}, x fastest inside a block.  The
+ * caller writes the table (the gradient buffer's table region is unused); a
+ * slot must not appear twice.
  * Node order is x fastest. */
 psdf_status psdf_grid_bytes(const psdf_grid_desc* desc, size_t* values_bytes, size_t* grad_bytes);
 
@@ -159,7 +176,12 @@ void psdf_grid_destroy(psdf_grid* grid);
  *         -> packed values (device, values_bytes); BF16 features are rounded to
  *         nearest even.
  * unpack: packed values (which = PSDF_GRID_VALUES) or a gradient buffer
- *         (PSDF_GRID_GRAD) -> the dense arrays (either may be NULL). */
+ *         (PSDF_GRID_GRAD) -> the dense arrays (either may be NULL).
+ * Sparse grids: `packed` must already hold the brick table; pack copies the
+ * stored bricks' nodes out of the dense arrays, unpack writes the stored
+ * bricks and fills the others with {empty_sdf, 0, 0, 0} (values) or zeros
+ * (gradient).  The table is read on the host side of neither call: it stays
+ * in device memory. */
 psdf_status psdf_grid_pack(const psdf_grid_desc* desc, const float* sdf, const float* feat,
                            void* packed, void* stream);
 psdf_status psdf_grid_unpack(const psdf_grid_desc* desc, int32_t which, const void* packed,

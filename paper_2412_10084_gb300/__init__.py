@@ -27,7 +27,7 @@ __all__ = [
     "weight_histogram", "proposal_forward", "proposal_backward", "adam_step", "Adam",
     "occupancy_words", "occupancy_unpack", "sdf_smooth", "sdf_smooth_adjoint",
     "grid_regularizers", "probe_smoothness", "shade_nodes", "render_colour_field",
-    "colour_field_bytes",
+    "colour_field_bytes", "brick_table", "pack_sparse", "table_words",
 ]
 
 DIR_REFLECT = 0
@@ -54,7 +54,8 @@ class LibraryError(RuntimeError):
 class GridDesc(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int32 * 3), ("box_min", ctypes.c_float * 3),
                 ("box_max", ctypes.c_float * 3), ("n_feat", ctypes.c_int32),
-                ("feat_dtype", ctypes.c_int32), ("feat_layout", ctypes.c_int32)]
+                ("feat_dtype", ctypes.c_int32), ("feat_layout", ctypes.c_int32),
+                ("n_bricks", ctypes.c_int32), ("empty_sdf", ctypes.c_float)]
 
 
 class ProbeDesc(ctypes.Structure):
@@ -191,8 +192,12 @@ def _require_cuda(*tensors, dtypes=(torch.float32,)):
 
 
 def grid_desc(dims, box_min, box_max, n_feat=3, feat_dtype=F32,
-              feat_layout=FEAT_NODES) -> GridDesc:
+              feat_layout=FEAT_NODES, n_bricks=0, empty_sdf=1.0) -> GridDesc:
+    """n_bricks > 0: a sparse grid of 16^3-node bricks of which n_bricks are
+    stored (the others read as SDF empty_sdf, features 0)."""
     d = GridDesc()
+    d.n_bricks = int(n_bricks)
+    d.empty_sdf = float(empty_sdf)
     d.feat_layout = int(feat_layout)
     d.dims[:] = tuple(int(v) for v in dims)
     d.box_min[:] = tuple(float(v) for v in box_min)
@@ -218,11 +223,43 @@ def mlp_param_count(n_in: int, width: int) -> int:
     return n.value
 
 
+def brick_table(keep) -> torch.Tensor:
+    """int32 [Bz, By, Bx] brick table from a boolean brick mask: the kept
+    bricks get slots 0, 1, ... in x-fastest order, the others -1."""
+    keep = torch.as_tensor(keep, dtype=torch.bool)
+    flat = keep.reshape(-1)
+    table = torch.full(flat.shape, -1, dtype=torch.int32)
+    table[flat] = torch.arange(int(flat.sum()), dtype=torch.int32)
+    return table.reshape(keep.shape)
+
+
+def table_words(desc: GridDesc) -> int:
+    """float32 words in front of a sparse grid's brick records (the table)."""
+    nb = (desc.dims[0] // TILE) * (desc.dims[1] // TILE) * (desc.dims[2] // TILE)
+    return ((4 * nb + 15) // 16) * 4
+
+
+def pack_sparse(desc: GridDesc, table, sdf: torch.Tensor, feat: torch.Tensor) -> torch.Tensor:
+    """Sparse grid from dense sdf [Rz,Ry,Rx] + feat [Rz,Ry,Rx,3] and a brick
+    table [Bz,By,Bx] (slots 0..n_bricks-1 or -1): packed float32 [bytes/16, 4]."""
+    _require_cuda(sdf, feat)
+    nbytes, _ = grid_bytes(desc)
+    out = torch.zeros(nbytes // 4, dtype=torch.float32, device=sdf.device)
+    tab = torch.as_tensor(table, dtype=torch.int32).reshape(-1).to(sdf.device)
+    out[:tab.numel()] = tab.view(torch.float32)
+    out = out.view(-1, 4)
+    _check(library().psdf_grid_pack(ctypes.byref(desc), _ptr(sdf), _ptr(feat), _ptr(out),
+                                    _stream()), "psdf_grid_pack")
+    return out
+
+
 def pack_grid(desc: GridDesc, sdf: torch.Tensor, feat: torch.Tensor) -> torch.Tensor:
     """Dense sdf [Rz,Ry,Rx] + feat [Rz,Ry,Rx,3] (or tile planes
     [tz,ty,tx,3,16,16,3]) (device FP32) -> packed values: float32 [R^3, 4] for
     FP32 node features, [bytes/16, 4] for tri-planes, a uint8 buffer for BF16."""
     _require_cuda(sdf, feat)
+    if desc.n_bricks > 0:
+        raise LibraryError("pack_grid: a sparse grid needs its brick table (pack_sparse)")
     nbytes, _ = grid_bytes(desc)
     if desc.feat_layout == FEAT_TRIPLANE:
         out = torch.empty(nbytes // 4, dtype=torch.float32, device=sdf.device).view(-1, 4)
@@ -273,6 +310,8 @@ class Scene:
     feat_layout: int = FEAT_NODES  # node features or tile tri-planes
     probe_dtype: int = F32   # storage of the probe coefficients (F32 or F16)
     mlp_dtype: int = F32     # MLP arithmetic (F32-equivalent or F16)
+    n_bricks: int = 0        # sparse grid: stored 16^3-node bricks (0: dense)
+    empty_sdf: float = 1.0   # sparse grid: SDF of the bricks not stored
 
     @property
     def probe_dims(self):
@@ -285,7 +324,7 @@ class Scene:
 
     def descs(self, n_fresnel):
         gd = grid_desc(self.dims, self.box_min, self.box_max, self.n_feat, self.feat_dtype,
-                       self.feat_layout)
+                       self.feat_layout, self.n_bricks, self.empty_sdf)
         pd = ProbeDesc()
         pd.dims[:] = self.probe_dims
         pd.sh_l = self.sh_l
@@ -299,14 +338,20 @@ class Scene:
         gd, _, _ = self.descs(3)
         _, gbytes = grid_bytes(gd)
         dev = self.mlp.device
-        return (torch.zeros(gbytes // 16, 4, dtype=torch.float32, device=dev),
+        gg = torch.zeros(gbytes // 16, 4, dtype=torch.float32, device=dev)
+        if self.n_bricks > 0:  # the gradient buffer carries the table too (for unpacking)
+            w = table_words(gd)
+            gg.view(-1)[:w] = self.grid.view(-1)[:w]
+        return (gg,
                 torch.zeros(self.probes.shape, dtype=torch.float32, device=dev),
                 torch.zeros_like(self.mlp))
 
     @classmethod
-    def from_host(cls, sc, device="cuda", feat_dtype=F32, probe_dtype=F32, mlp_dtype=F32):
+    def from_host(cls, sc, device="cuda", feat_dtype=F32, probe_dtype=F32, mlp_dtype=F32,
+                  bricks=None, empty_sdf=1.0):
         """Upload a synth.Scene-like object (numpy arrays) and pack its grid in
-        the requested storage precision."""
+        the requested storage precision; `bricks` (a boolean [Bz,By,Bx] mask of
+        16^3-node bricks to keep) makes it a sparse grid."""
         dev = torch.device(device)
         sdf = torch.as_tensor(sc.sdf, dtype=torch.float32, device=dev).contiguous()
         planes = getattr(sc, "planes", None)
@@ -314,8 +359,16 @@ class Scene:
         feat = torch.as_tensor(sc.feat if planes is None else planes, dtype=torch.float32,
                                device=dev).contiguous()
         n_feat = int(feat.shape[-1])
-        gd = grid_desc(sc.dims, sc.box_min, sc.box_max, n_feat, feat_dtype, layout)
-        grid = pack_grid(gd, sdf, feat)
+        n_bricks = 0
+        if bricks is not None:
+            table = brick_table(bricks)
+            n_bricks = int((table >= 0).sum())
+            gd = grid_desc(sc.dims, sc.box_min, sc.box_max, n_feat, feat_dtype, layout,
+                           n_bricks, empty_sdf)
+            grid = pack_sparse(gd, table, sdf, feat)
+        else:
+            gd = grid_desc(sc.dims, sc.box_min, sc.box_max, n_feat, feat_dtype, layout)
+            grid = pack_grid(gd, sdf, feat)
         probes = torch.as_tensor(sc.probes, dtype=torch.float32, device=dev)
         if probe_dtype == F16:
             probes = probes.half()
@@ -324,7 +377,8 @@ class Scene:
                    box_min=tuple(float(v) for v in sc.box_min),
                    box_max=tuple(float(v) for v in sc.box_max), sh_l=int(sc.sh_l),
                    width=int(sc.width), n_feat=n_feat, feat_dtype=feat_dtype,
-                   probe_dtype=probe_dtype, mlp_dtype=mlp_dtype, feat_layout=layout)
+                   probe_dtype=probe_dtype, mlp_dtype=mlp_dtype, feat_layout=layout,
+                   n_bricks=n_bricks, empty_sdf=float(empty_sdf))
 
 
 def render_params(tau=64.0, n_samples=128, dir_mode=DIR_REFLECT, n_fresnel=3,

@@ -71,7 +71,29 @@ psdf_status check_grid_desc(const psdf_grid_desc* d)
         return PSDF_ERR_INVALID_ARG;
     if (d->feat_layout == PSDF_FEAT_TRIPLANE && d->feat_dtype != PSDF_F32)
         return PSDF_ERR_UNSUPPORTED;
+    if (d->n_bricks < 0) return PSDF_ERR_INVALID_ARG;
+    if (d->n_bricks > 0) {
+        if (d->feat_layout != PSDF_FEAT_NODES || d->feat_dtype != PSDF_F32)
+            return PSDF_ERR_UNSUPPORTED;
+        for (int a = 0; a < 3; ++a)
+            if (d->dims[a] % PSDF_TILE != 0) return PSDF_ERR_BAD_SHAPE;
+        if (d->n_bricks > n / 4096) return PSDF_ERR_BAD_SHAPE;
+        if (!std::isfinite(d->empty_sdf)) return PSDF_ERR_INVALID_ARG;
+    }
     return PSDF_OK;
+}
+
+bool sparse(const psdf_grid_desc* d) { return d->n_bricks > 0; }
+
+int64_t n_brick_cells(const psdf_grid_desc* d)
+{
+    return int64_t(d->dims[0] / PSDF_TILE) * (d->dims[1] / PSDF_TILE) * (d->dims[2] / PSDF_TILE);
+}
+
+// Bytes of the brick table (padded to 16).
+size_t brick_table_bytes(const psdf_grid_desc* d)
+{
+    return (static_cast<size_t>(n_brick_cells(d)) * 4 + 15) & ~size_t(15);
 }
 
 int tri_tiles(int32_t dims) { return (dims - 1 + PSDF_TILE - 1) / PSDF_TILE; }
@@ -97,7 +119,14 @@ size_t bf16_feat_offset(const psdf_grid_desc* d)
 void set_grid_view(const psdf_grid_desc& gd, const void* values, psdf::GridView& g)
 {
     const uint8_t* base = static_cast<const uint8_t*>(values);
-    if (gd.feat_layout == PSDF_FEAT_TRIPLANE) {
+    if (sparse(&gd)) {
+        g.table = reinterpret_cast<const int*>(base);
+        g.nodes = reinterpret_cast<const float4*>(base + brick_table_bytes(&gd));
+        for (int a = 0; a < 3; ++a) g.B[a] = gd.dims[a] / PSDF_TILE;
+        g.empty_sdf = gd.empty_sdf;
+        g.n_bricks = gd.n_bricks;
+        g.rec_off = static_cast<int64_t>(brick_table_bytes(&gd) / 4);
+    } else if (gd.feat_layout == PSDF_FEAT_TRIPLANE) {
         g.sdf = reinterpret_cast<const float*>(base);
         g.planes = reinterpret_cast<const float4*>(base + bf16_feat_offset(&gd));
         g.plane_off = static_cast<int64_t>(bf16_feat_offset(&gd) / 4);
@@ -170,7 +199,9 @@ psdf_status resolve(const psdf_grid* grid, const psdf_probes* probes, const psdf
     r.shape.l2 = pd.sh_l * pd.sh_l;
     r.shape.width = md.width;
     r.shape.k = p->n_fresnel;
-    r.shape.fb = gd.feat_layout == PSDF_FEAT_TRIPLANE ? 2 : (gd.feat_dtype == PSDF_BF16 ? 1 : 0);
+    r.shape.fb = sparse(&gd) ? 3
+                 : gd.feat_layout == PSDF_FEAT_TRIPLANE ? 2
+                                                         : (gd.feat_dtype == PSDF_BF16 ? 1 : 0);
     r.shape.ph = pd.dtype == PSDF_F16;
     r.shape.mh = md.dtype == PSDF_F16;
     bool known = false;
@@ -244,6 +275,38 @@ __global__ void unpack_kernel(const float4* __restrict__ in, float* __restrict__
             feat[3 * i] = v.y;
             feat[3 * i + 1] = v.z;
             feat[3 * i + 2] = v.w;
+        }
+    }
+}
+
+// Sparse bricks: dense SDF and features [R^3][3] <-> the stored bricks' node
+// records (the table in front of them says which).  Unpack fills the nodes of
+// bricks that are not stored with {fill, 0, 0, 0}.
+__global__ void brick_copy_kernel(int Rx, int Ry, int Rz, const int* __restrict__ table,
+                                  int n_bricks, float4* __restrict__ bricks,
+                                  float* __restrict__ sdf, float* __restrict__ feat, float fill,
+                                  bool pack)
+{
+    const int64_t n = int64_t(Rx) * Ry * Rz;
+    const int Bx = Rx / 16, By = Ry / 16;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(i % Rx), y = static_cast<int>((i / Rx) % Ry);
+        const int z = static_cast<int>(i / (int64_t(Rx) * Ry));
+        int slot = table[((z >> 4) * By + (y >> 4)) * Bx + (x >> 4)];
+        if (slot >= n_bricks) slot = -1;  // a table entry out of range stores nothing
+        const int64_t rec = int64_t(slot) * 4096 + (((z & 15) * 16 + (y & 15)) * 16 + (x & 15));
+        if (pack) {
+            if (slot >= 0)
+                bricks[rec] = make_float4(sdf[i], feat[3 * i], feat[3 * i + 1], feat[3 * i + 2]);
+        } else {
+            const float4 v = slot >= 0 ? bricks[rec] : make_float4(fill, 0.f, 0.f, 0.f);
+            if (sdf) sdf[i] = v.x;
+            if (feat) {
+                feat[3 * i] = v.y;
+                feat[3 * i + 1] = v.z;
+                feat[3 * i + 2] = v.w;
+            }
         }
     }
 }
@@ -372,6 +435,18 @@ cudaError_t launch_unpack_bf16(const void* packed, size_t feat_off, float* sdf, 
     return cudaGetLastError();
 }
 
+cudaError_t launch_brick_copy(const int dims[3], int n_bricks, const int* table, float4* bricks,
+                              float* sdf, float* feat, float fill, bool pack,
+                              cudaStream_t stream)
+{
+    const int threads = 256;
+    const int64_t n = int64_t(dims[0]) * dims[1] * dims[2];
+    const int64_t blocks = (n + threads - 1) / threads;
+    brick_copy_kernel<<<(int)(blocks < 65535 * 16 ? blocks : 65535 * 16), threads, 0, stream>>>(
+        dims[0], dims[1], dims[2], table, n_bricks, bricks, sdf, feat, fill, pack);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_tri_copy(const float* sdf, const float* planes, void* packed, size_t plane_off,
                             int64_t n_nodes, int64_t n_texels, bool pack, cudaStream_t stream)
 {
@@ -439,6 +514,11 @@ psdf_status psdf_grid_bytes(const psdf_grid_desc* desc, size_t* values_bytes, si
     if (st != PSDF_OK) return st;
     if (!values_bytes || !grad_bytes) return PSDF_ERR_INVALID_ARG;
     const size_t n = static_cast<size_t>(grid_nodes(desc));
+    if (sparse(desc)) {
+        *values_bytes = *grad_bytes =
+            brick_table_bytes(desc) + 16 * 4096 * static_cast<size_t>(desc->n_bricks);
+        return PSDF_OK;
+    }
     if (desc->feat_layout == PSDF_FEAT_TRIPLANE) {
         *values_bytes = *grad_bytes = bf16_feat_offset(desc) + 16 * size_t(tri_texels(desc));
         return PSDF_OK;
@@ -472,6 +552,12 @@ psdf_status psdf_grid_pack(const psdf_grid_desc* desc, const float* sdf, const f
     if (!sdf || !feat || !packed) return PSDF_ERR_INVALID_ARG;
     if (!aligned16(packed)) return PSDF_ERR_MISALIGNED;
     const int64_t n = grid_nodes(desc);
+    if (sparse(desc))
+        return cuda_status(psdf::launch_brick_copy(
+            desc->dims, desc->n_bricks, static_cast<const int*>(packed),
+            reinterpret_cast<float4*>(static_cast<uint8_t*>(packed) + brick_table_bytes(desc)),
+            const_cast<float*>(sdf), const_cast<float*>(feat), 0.0f, true,
+            static_cast<cudaStream_t>(stream)));
     if (desc->feat_layout == PSDF_FEAT_TRIPLANE)
         return cuda_status(psdf::launch_tri_copy(sdf, feat, packed, bf16_feat_offset(desc), n,
                                                  tri_texels(desc), true,
@@ -492,6 +578,13 @@ psdf_status psdf_grid_unpack(const psdf_grid_desc* desc, int32_t which, const vo
     if (which != PSDF_GRID_VALUES && which != PSDF_GRID_GRAD) return PSDF_ERR_INVALID_ARG;
     if (!aligned16(packed)) return PSDF_ERR_MISALIGNED;
     const int64_t n = grid_nodes(desc);
+    if (sparse(desc))
+        return cuda_status(psdf::launch_brick_copy(
+            desc->dims, desc->n_bricks, static_cast<const int*>(packed),
+            reinterpret_cast<float4*>(const_cast<uint8_t*>(static_cast<const uint8_t*>(packed)) +
+                                      brick_table_bytes(desc)),
+            sdf, feat, which == PSDF_GRID_VALUES ? desc->empty_sdf : 0.0f, false,
+            static_cast<cudaStream_t>(stream)));
     if (desc->feat_layout == PSDF_FEAT_TRIPLANE)
         return cuda_status(psdf::launch_tri_copy(sdf, feat, const_cast<void*>(packed),
                                                  bf16_feat_offset(desc), n, tri_texels(desc),
@@ -667,6 +760,7 @@ psdf_status psdf_shade_nodes(const psdf_grid* grid, const psdf_probes* probes,
     Resolved r;
     psdf_status st = resolve(grid, probes, mlp, params, nullptr, nullptr, nullptr, 0, r);
     if (st != PSDF_OK) return st;
+    if (sparse(&grid->desc)) return PSDF_ERR_UNSUPPORTED;
     if (!camera || !colours || !(band >= 0.0f)) return PSDF_ERR_INVALID_ARG;
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(camera[a])) return PSDF_ERR_INVALID_ARG;
@@ -752,6 +846,7 @@ psdf_status psdf_sdf_smooth(const psdf_grid_desc* desc, const float* sdf_hat, vo
 {
     const psdf_status st = check_grid_desc(desc);
     if (st != PSDF_OK) return st;
+    if (sparse(desc)) return PSDF_ERR_UNSUPPORTED;
     if (!sdf_hat || !packed_values) return PSDF_ERR_INVALID_ARG;
     if (!aligned16(sdf_hat) || !aligned16(packed_values)) return PSDF_ERR_MISALIGNED;
     return cuda_status(psdf::launch_smooth(desc->dims, sdf_hat, 1,
@@ -765,6 +860,7 @@ psdf_status psdf_sdf_smooth_adjoint(const psdf_grid_desc* desc, const void* grad
 {
     const psdf_status st = check_grid_desc(desc);
     if (st != PSDF_OK) return st;
+    if (sparse(desc)) return PSDF_ERR_UNSUPPORTED;
     if (!grad_grid || !d_sdf_hat) return PSDF_ERR_INVALID_ARG;
     if (!aligned16(grad_grid) || !aligned16(d_sdf_hat)) return PSDF_ERR_MISALIGNED;
     return cuda_status(psdf::launch_smooth(desc->dims, static_cast<const float*>(grad_grid),
@@ -779,6 +875,7 @@ psdf_status psdf_grid_regularizers(const psdf_grid_desc* desc, const float* sdf_
 {
     const psdf_status st = check_grid_desc(desc);
     if (st != PSDF_OK) return st;
+    if (sparse(desc)) return PSDF_ERR_UNSUPPORTED;
     if (!sdf_hat || !packed_values || !grad_grid || !d_sdf_hat) return PSDF_ERR_INVALID_ARG;
     if (!(lam_sdf >= 0.0f) || !(lam_eik >= 0.0f) || !(lam_normal >= 0.0f) ||
         !(lam_features >= 0.0f))
@@ -884,6 +981,7 @@ psdf_status psdf_occupancy_build(const psdf_grid* grid, const int32_t occ_res[3]
     psdf::GridView g;
     psdf_status st = grid_view(grid, g);
     if (st != PSDF_OK) return st;
+    if (sparse(&grid->desc)) return PSDF_ERR_UNSUPPORTED;
     int64_t words = 0;
     st = psdf_occupancy_words(occ_res, &words);
     if (st != PSDF_OK) return st;

@@ -12,7 +12,8 @@ constexpr int kBwdThreads = 128;
 
 // Compile-time shape of a render kernel: angular channels, SH coefficients,
 // MLP width, Fresnel powers (3 spatial features), and storage: feature
-// storage fb (0 FP32 node records, 1 BF16 node features, 2 tile tri-planes),
+// storage fb (0 FP32 node records, 1 BF16 node features, 2 tile tri-planes,
+// 3 sparse bricks of FP32 node records),
 // FP16 probes (ph), plain-FP16 MLP (mh).
 struct KernelShape {
     int na, l2, width, k, fb, ph, mh;
@@ -25,8 +26,9 @@ struct KernelShape {
 
 // Shapes compiled into the library: the FP32 path (widths 16/32, 4 or 8
 // angular channels), the reduced-precision path (BF16 features, FP16 probes,
-// FP16 MLP), BF16 features with FP32 probes and MLP, and tile tri-plane
-// features (widths 16/32).
+// FP16 MLP), BF16 features with FP32 probes and MLP, tile tri-plane
+// features (widths 16/32), l = 4 SH (16 coefficients, Sec. 4) with node
+// or tri-plane features, and sparse 16^3-node bricks (l = 3 and 4).
 #define PSDF_FOR_EACH_SHAPE(X) \
     X(4, 9, 16, 3, 0, 0, 0)    \
     X(4, 9, 32, 3, 0, 0, 0)    \
@@ -34,7 +36,11 @@ struct KernelShape {
     X(4, 9, 32, 3, 1, 1, 1)    \
     X(8, 9, 32, 3, 1, 0, 0)    \
     X(4, 9, 16, 3, 2, 0, 0)    \
-    X(4, 9, 32, 3, 2, 0, 0)
+    X(4, 9, 32, 3, 2, 0, 0)    \
+    X(4, 16, 32, 3, 0, 0, 0)   \
+    X(4, 16, 32, 3, 2, 0, 0)   \
+    X(4, 9, 32, 3, 3, 0, 0)    \
+    X(4, 16, 32, 3, 3, 0, 0)
 
 cudaError_t launch_forward(const RenderArgs& A, const KernelShape& ks, int grid_ctas,
                            cudaStream_t stream);
@@ -73,6 +79,9 @@ cudaError_t launch_plane_reg(const float4* planes, int64_t n_texels, float lam, 
                              float* loss, cudaStream_t stream);
 cudaError_t launch_probe_reg(const float4* b, const int P[3], int n4, float lam, float4* grad,
                              float* loss, cudaStream_t stream);
+cudaError_t launch_brick_copy(const int dims[3], int n_bricks, const int* table, float4* bricks,
+                              float* sdf, float* feat, float fill, bool pack,
+                              cudaStream_t stream);
 cudaError_t launch_tri_copy(const float* sdf, const float* planes, void* packed, size_t plane_off,
                             int64_t n_nodes, int64_t n_texels, bool pack, cudaStream_t stream);
 cudaError_t launch_pack(const float* sdf, const float* feat, float4* packed, int64_t n_nodes,

@@ -26,6 +26,17 @@
 
 namespace psdf {
 
+// Gradient-buffer record of corner q (cx + 2 cy + 4 cz) of cell c: the node's
+// linear index, or for sparse bricks its record index (-1: brick not stored).
+template <class C>
+__device__ __forceinline__ int64_t grad_record(const GridView& g, const Cell& c, int q)
+{
+    if constexpr (C::SP)
+        return brick_record(g, c.i[0] + (q & 1), c.i[1] + ((q >> 1) & 1), c.i[2] + (q >> 2));
+    else
+        return c.base + (q & 1) + ((q >> 1) & 1) * g.R[0] + (q >> 2) * g.R[0] * g.R[1];
+}
+
 template <class C>
 struct BwdLayout {
     using M = MlpTC<C>;
@@ -308,6 +319,7 @@ render_backward_kernel(RenderArgs A)
             bool unclipped = false;
             Cell c1;
             c1.base = 0;
+            c1.i[0] = c1.i[1] = c1.i[2] = 0;
             c1.f[0] = c1.f[1] = c1.f[2] = 0.0f;
             if (have) {
                 t = span_t(sp, k < N ? k : N - 1);
@@ -649,7 +661,6 @@ render_backward_kernel(RenderArgs A)
                     gys = (dn[1] - S.n[1] * ndn) * irho * A.grid.sc[1];
                     gzs = (dn[2] - S.n[2] * ndn) * irho * A.grid.sc[2];
                 }
-                const int sy = A.grid.R[0], sz = A.grid.R[0] * A.grid.R[1];
                 if (unclipped) {
                     const float fx = S.cell.f[0], fy = S.cell.f[1], fz = S.cell.f[2];
 #pragma unroll
@@ -661,12 +672,13 @@ render_backward_kernel(RenderArgs A)
                         const float wc = wx * wy * wz;
                         const float dsdf = ds_own * wc + gxs * sgx * wy * wz +
                                            gys * wx * sgy * wz + gzs * wx * wy * sgz;
-                        const size_t node = S.cell.base + cx + cy * sy + cz * sz;
+                        const int64_t node = grad_record<C>(A.grid, S.cell, q);
+                        if (C::SP && node < 0) continue;  // a brick that is not stored
                         if constexpr (C::TP)
                             red_add(A.grad_grid + node, dsdf);
                         else
-                            red_add_v4(A.grad_grid + 4 * node, dsdf, wc * dx[0], wc * dx[1],
-                                       wc * dx[2]);
+                            red_add_v4(A.grad_grid + A.grid.rec_off + 4 * node, dsdf, wc * dx[0],
+                                       wc * dx[1], wc * dx[2]);
                     }
                     if constexpr (C::TP) {
                         // F_s = b0 b1 b2 per channel: plane p's lookup gets dF_s times
@@ -702,9 +714,10 @@ render_backward_kernel(RenderArgs A)
                     corner_weights(S.cell.f, w8);
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
-                        const int cx = q & 1, cy = (q >> 1) & 1, cz = (q >> 2) & 1;
-                        const size_t node = S.cell.base + cx + cy * sy + cz * sz;
-                        red_add(A.grad_grid + (C::TP ? node : 4 * node), ds_own * w8[q]);
+                        const int64_t node = grad_record<C>(A.grid, S.cell, q);
+                        if (C::SP && node < 0) continue;
+                        red_add(A.grad_grid + (C::TP ? node : A.grid.rec_off + 4 * node),
+                                ds_own * w8[q]);
                     }
                 }
                 if (extra) {
@@ -714,9 +727,10 @@ render_backward_kernel(RenderArgs A)
                         corner_weights(c1.f, w1);
 #pragma unroll
                         for (int q = 0; q < 8; ++q) {
-                            const int cx = q & 1, cy = (q >> 1) & 1, cz = (q >> 2) & 1;
-                            const size_t node = c1.base + cx + cy * sy + cz * sz;
-                            red_add(A.grad_grid + (C::TP ? node : 4 * node), ds1 * w1[q]);
+                            const int64_t node = grad_record<C>(A.grid, c1, q);
+                            if (C::SP && node < 0) continue;
+                            red_add(A.grad_grid + (C::TP ? node : A.grid.rec_off + 4 * node),
+                                    ds1 * w1[q]);
                         }
                     }
                 }

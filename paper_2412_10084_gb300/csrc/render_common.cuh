@@ -22,6 +22,13 @@ struct GridView {
     int tiles[3];                       // tiles of 16 cells along x, y, z
     int64_t plane_off;                  // tri-planes: float offset of the planes in the values
                                         // and gradient buffers (the SDF array comes first)
+    const int* __restrict__ table;      // sparse: brick table [Bz][By][Bx] (slot or -1); the
+                                        // records of `nodes` are then the stored bricks'
+    int B[3];                           // sparse: bricks of 16^3 nodes along x, y, z
+    int n_bricks;                       // sparse: stored bricks (a slot beyond is not stored)
+    float empty_sdf;                    // sparse: SDF of the nodes of bricks not stored
+    int64_t rec_off;                    // sparse: float offset of the brick records in the
+                                        // values and gradient buffers (the table comes first)
     int R[3];
     float bmin[3];
     float bmax[3];
@@ -117,6 +124,7 @@ __device__ __forceinline__ void locate_axis(float x, float bmin, float sc, int R
 
 struct Cell {
     int base;  // linear index of corner (0,0,0)
+    int i[3];  // its node coordinates
     float f[3];
 };
 
@@ -128,7 +136,35 @@ __device__ __forceinline__ Cell locate(const float x[3], const float bmin[3], co
 #pragma unroll
     for (int a = 0; a < 3; ++a) locate_axis(x[a], bmin[a], sc[a], R[a], i[a], c.f[a]);
     c.base = (i[2] * R[1] + i[1]) * R[0] + i[0];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) c.i[a] = i[a];
     return c;
+}
+
+// ---------------------------------------------------------------------------
+// Sparse bricks: the nodes form bricks of 16^3; only the bricks the table
+// names are stored.  Record index of node (x, y, z), or -1 when its brick is
+// not stored (a table entry outside [0, n_bricks) counts as not stored).
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int64_t brick_record(const GridView& g, int x, int y, int z)
+{
+    const int slot = __ldg(g.table + ((z >> 4) * g.B[1] + (y >> 4)) * g.B[0] + (x >> 4));
+    if (slot < 0 || slot >= g.n_bricks) return -1;
+    return int64_t(slot) * 4096 + (((z & 15) << 8) | ((y & 15) << 4) | (x & 15));
+}
+
+// Record indices of a cell's 8 corners (corner q = cx + 2 cy + 4 cz); returns
+// how many are stored.
+__device__ __forceinline__ int brick_corners(const GridView& g, const int i[3], int64_t rec[8])
+{
+    int stored = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        rec[q] = brick_record(g, i[0] + (q & 1), i[1] + ((q >> 1) & 1), i[2] + (q >> 2));
+        stored += rec[q] >= 0;
+    }
+    return stored;
 }
 
 __device__ __forceinline__ void point_at(const float o[3], const float d[3], float t, float x[3])
@@ -274,9 +310,34 @@ __device__ __forceinline__ void triplane_lookup(const GridView& g, const TriAt& 
     fs[2] = v[0].z * v[1].z * v[2].z;
 }
 
+// Corner records of a sparse grid; returns the stored count (0: every corner
+// is empty and the caller takes s = empty_sdf exactly).
+__device__ __forceinline__ int gather_corners_sparse(const GridView& g, const Cell& c, Corners& k)
+{
+    int64_t rec[8];
+    const int stored = brick_corners(g, c.i, rec);
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        k.v[q] = rec[q] >= 0 ? __ldg(g.nodes + rec[q]) : make_float4(g.empty_sdf, 0.f, 0.f, 0.f);
+    return stored;
+}
+
 // SDF value only (the extra point N of a ray's last full chunk).
 __device__ __forceinline__ float sdf_value(const GridView& g, const Cell& c)
 {
+    if (g.table) {
+        int64_t rec[8];
+        if (brick_corners(g, c.i, rec) == 0) return g.empty_sdf;
+        float w[8];
+        corner_weights(c.f, w);
+        float s = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            s = fmaf(w[q], rec[q] >= 0 ? __ldg(reinterpret_cast<const float*>(g.nodes + rec[q]))
+                                       : g.empty_sdf,
+                     s);
+        return s;
+    }
     const int sx = 1, sy = g.R[0], sz = g.R[0] * g.R[1];
     const bool split = g.sdf != nullptr;  // BF16-feature layout: SDF in its own array
     const float* p = split ? g.sdf + c.base : reinterpret_cast<const float*>(g.nodes + c.base);

@@ -11,7 +11,8 @@ namespace psdf {
 
 // Compile-time shape and storage precision of a render kernel.
 //   FS: spatial-feature storage: 0 FP32 node records, 1 BF16 node features
-//       (SDF stays FP32), 2 tile tri-planes (Sec. 3.1)
+//       (SDF stays FP32), 2 tile tri-planes (Sec. 3.1), 3 sparse bricks of
+//       FP32 node records
 //   PH: probe coefficients stored as FP16
 //   MH: MLP on the tensor cores in plain FP16 (else the FP32-equivalent
 //       hi/lo split)
@@ -19,6 +20,7 @@ template <int NA_, int L2_, int W_, int K_, int FS_ = 0, int PH_ = 0, int MH_ = 
 struct Cfg {
     static constexpr int FB = FS_ == 1;
     static constexpr int TP = FS_ == 2;
+    static constexpr int SP = FS_ == 3;
     static constexpr int PH = PH_;
     static constexpr int MH = MH_;
     static constexpr int NS = 3;
@@ -44,7 +46,9 @@ struct Cfg {
 template <class C>
 __device__ __forceinline__ void gather_corners_t(const GridView& g, const Cell& c, Corners& k)
 {
-    if constexpr (C::TP)
+    if constexpr (C::SP)
+        gather_corners_sparse(g, c, k);
+    else if constexpr (C::TP)
         gather_corners_sdf(g, c, k);
     else if constexpr (C::FB)
         gather_corners_bf16(g, c, k);
@@ -106,8 +110,18 @@ __device__ __forceinline__ void eval_sdf(const RenderArgs& A, const float o[3], 
     point_at(o, d, t, xw);
     S.cell = locate(xw, A.grid.bmin, A.grid.sc, A.grid.R);
     Corners k;
-    gather_corners_t<C>(A.grid, S.cell, k);
     float fs[3];
+    if constexpr (C::SP) {
+        if (gather_corners_sparse(A.grid, S.cell, k) == 0) {
+            // every corner is empty space: s is the empty value exactly
+            S.s = A.grid.empty_sdf;
+            S.g[0] = S.g[1] = S.g[2] = 0.0f;
+            S.x[0] = S.x[1] = S.x[2] = 0.0f;
+            return;
+        }
+    } else {
+        gather_corners_t<C>(A.grid, S.cell, k);
+    }
     sdf_full(A.grid, S.cell, k, S.s, S.g, fs);
     if constexpr (C::TP) {
         TriAt T;

@@ -151,6 +151,23 @@ def test_width32_and_eight_channels():
     assert spec["n_a"] == 8
 
 
+@pytest.mark.parametrize("triplane", [False, True])
+def test_sh_order_four(triplane):
+    """l = 4 (16 SH coefficients per probe, Sec. 4), width 32, node features or
+    tile tri-planes: forward and adjoint against the oracle."""
+    g = synth.rng(78)
+    sc = synth.make_scene("sphere64", dims=(34, 30, 33), probe_dims=(5, 4, 6))
+    sc.probes = g.normal(0, 0.1, size=(6, 4, 5, 16, 4)).astype(np.float32)
+    sc.sh_l = 4
+    sc.width = 32
+    sc.mlp = synth.mlp_params(3 + 4 + 3, 32, g)
+    if triplane:
+        sc = synth.with_triplanes(sc, 79)
+    rays = synth.make_rays("sphere64", n_rays=500, seed_offset=19)
+    check_forward(sc, rays.o, rays.d, 64.0, 80)
+    check_backward(sc, rays.o, rays.d, 64.0, 80)
+
+
 def test_explicit_sample_distances():
     sc = synth.make_scene("sphere64", dims=(32, 32, 32), probe_dims=(8, 8, 8))
     rays = synth.make_rays("sphere64", n_rays=256, seed_offset=11)

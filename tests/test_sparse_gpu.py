@@ -1,0 +1,171 @@
+"""Sparse 16^3-node bricks on the GPU against the FP64 oracle.
+
+A sparse grid stores only the bricks its table names; every other node reads
+as SDF = empty_sdf with zero features.  The oracle therefore renders the dense
+grid with those values written into the bricks that are not stored, and the
+adjoints are compared on the stored nodes (the others have no storage)."""
+import dataclasses
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from helpers import (GRAD_RTOL, RGB_DEPTH_RTOL, clean_rays, log_errors, oracle_backward,
+                     oracle_forward, rel_err_elementwise, rel_err_tensor)
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    import paper_2412_10084_gb300 as ps
+
+EMPTY = 1.0
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+
+
+def brick_mask(sdf, thr):
+    """Bricks whose nodes come within thr of the surface."""
+    Rz, Ry, Rx = sdf.shape
+    b = np.abs(sdf).reshape(Rz // 16, 16, Ry // 16, 16, Rx // 16, 16).min(axis=(1, 3, 5))
+    return b < thr
+
+
+def sparse_case(dims=(96, 80, 112), probe_dims=(4, 4, 5), thr=0.1, sh_l=3, seed=41):
+    """(dense-equivalent synth scene for the oracle, sparse ps.Scene, node mask):
+    a sphere of radius 0.22 in the unit box, bricks within thr of its surface,
+    MLP width 32 (the sparse shapes compiled in)."""
+    sc = synth.make_scene("sphere64", dims=dims, probe_dims=probe_dims)
+    g = synth.rng(seed)
+    sdf = synth.sphere_sdf(dims, sc.box_min, sc.box_max, (0.45, 0.5, 0.55), 0.22)
+    sc = dataclasses.replace(sc, sdf=(sdf + g.normal(0, 0.003, size=sdf.shape))
+                             .astype(np.float32), width=32, mlp=synth.mlp_params(10, 32, g))
+    if sh_l == 4:
+        Px, Py, Pz = probe_dims
+        sc = dataclasses.replace(sc, sh_l=4, probes=g.normal(0, 0.1, size=(Pz, Py, Px, 16, 4))
+                                 .astype(np.float32))
+    keep = brick_mask(sc.sdf, thr)
+    assert keep.any() and (~keep).any()
+    s = ps.Scene.from_host(sc, bricks=keep, empty_sdf=EMPTY)
+    node_keep = np.repeat(np.repeat(np.repeat(keep, 16, 0), 16, 1), 16, 2)
+    sdf = np.where(node_keep, sc.sdf, np.float32(EMPTY)).astype(np.float32)
+    feat = np.where(node_keep[..., None], sc.feat, np.float32(0)).astype(np.float32)
+    return dataclasses.replace(sc, sdf=sdf, feat=feat), s, node_keep
+
+
+def test_sparse_pack_unpack_and_bytes():
+    sc, s, node_keep = sparse_case()
+    gd, _, _ = s.descs(3)
+    n_b = int(node_keep.sum()) // 4096
+    vb, gb = ps.grid_bytes(gd)
+    assert gd.n_bricks == n_b and vb == gb == ps.table_words(gd) * 4 + 16 * 4096 * n_b
+    sdf, feat = ps.unpack_grid(gd, s.grid, which=ps.GRID_VALUES)
+    assert np.array_equal(sdf.cpu().numpy(), sc.sdf)
+    assert np.array_equal(feat.cpu().numpy(), sc.feat)
+    gg, _, _ = s.grad_buffers()
+    gsdf, gfeat = ps.unpack_grid(gd, gg, which=ps.GRID_GRAD)
+    assert float(gsdf.abs().max()) == 0.0 and float(gfeat.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("sh_l,N", [(3, 96), (4, 64), (3, 33)])
+def test_sparse_forward_parity(sh_l, N):
+    sc, s, _ = sparse_case(sh_l=sh_l)
+    rays = synth.make_rays("sphere64", n_rays=700, seed_offset=70 + N)
+    params = ps.render_params(64.0, N, 0, sc.n_fresnel, (0.1, 0.2, 0.3))
+    rgb, depth, wsum, logT = ps.render_forward(s, dev(rays.o), dev(rays.d), params)
+    assert ps.device_status() == 0
+    ref = oracle_forward(sc, rays.o, rays.d, 64.0, N, bg=(0.1, 0.2, 0.3))
+    errs = {k: rel_err_elementwise(v.cpu().numpy(), ref[k])
+            for k, v in (("rgb", rgb), ("depth", depth), ("wsum", wsum))}
+    log_errors(f"sparse forward l={sh_l} N={N}", errs)
+    for k, e in errs.items():
+        assert e <= RGB_DEPTH_RTOL, (k, e)
+    assert float(wsum.max()) > 0.5
+
+
+@pytest.mark.parametrize("sh_l", [3, 4])
+def test_sparse_backward_parity(sh_l):
+    sc, s, node_keep = sparse_case(sh_l=sh_l, seed=43)
+    rays = synth.make_rays("sphere64", n_rays=600, seed_offset=80 + sh_l)
+    tau, N = 64.0, 64
+    keep = clean_rays(sc, rays.o, rays.d, tau, N)
+    o, d = rays.o[keep], rays.d[keep]
+    n = o.shape[0]
+    drgb = (synth.rng(9).normal(size=(n, 3)) / n).astype(np.float32)
+    params = ps.render_params(tau, N, 0, sc.n_fresnel)
+    o_, d_ = dev(o), dev(d)
+    _, _, _, logT, live = ps.render_forward(s, o_, d_, params, want_live=True)
+    gg, gp, gm = ps.render_backward(s, o_, d_, params, dev(drgb), logT, n_live=live)
+    assert ps.device_status() == 0
+    gd, _, _ = s.descs(3)
+    gsdf, gfeat = ps.unpack_grid(gd, gg, which=ps.GRID_GRAD)
+    ref = oracle_backward(sc, o, d, drgb.astype(np.float64), tau, N)
+    ref_sdf = np.where(node_keep, ref["sdf"], 0.0)
+    ref_feat = np.where(node_keep[..., None], ref["feat"], 0.0)
+    errs = {"sdf": rel_err_tensor(gsdf.cpu().numpy(), ref_sdf),
+            "feat": rel_err_tensor(gfeat.cpu().numpy(), ref_feat),
+            "probes": rel_err_tensor(gp.cpu().numpy(), ref["probes"]),
+            "mlp": rel_err_tensor(gm.cpu().numpy(), ref["mlp"])}
+    log_errors(f"sparse backward l={sh_l}", errs)
+    assert np.abs(ref_sdf).max() > 0
+    for k, e in errs.items():
+        assert e <= GRAD_RTOL, (k, e)
+
+
+def test_empty_space_is_exactly_empty():
+    """A ray that meets only bricks that are not stored has s = empty_sdf at
+    every sample: zero weight, the background colour, exactly."""
+    sc, s, _ = sparse_case()
+    o = np.array([[0.03, 0.02, -1.0], [0.97, 0.03, 2.0]], np.float32)  # along two box edges
+    d = np.array([[0.0, 0.0, 1.0], [0.0, 0.0, -1.0]], np.float32)
+    params = ps.render_params(64.0, 128, 0, sc.n_fresnel, (0.25, 0.5, 0.75))
+    rgb, depth, wsum, _ = ps.render_forward(s, dev(o), dev(d), params)
+    assert np.array_equal(rgb.cpu().numpy(), np.tile([0.25, 0.5, 0.75], (2, 1)).astype(np.float32))
+    assert float(wsum.abs().max()) == 0.0 and float(depth.abs().max()) == 0.0
+
+
+def test_sparse_weight_histogram_matches_oracle():
+    sc, s, _ = sparse_case()
+    rays = synth.make_rays("sphere64", n_rays=400, seed_offset=7)
+    params = ps.render_params(64.0, 64, 0, sc.n_fresnel)
+    h = ps.weight_histogram(s, dev(rays.o), dev(rays.d), params, n_bins=8)
+    ref = oracle.weight_histogram(oracle.Model.from_scene(sc), rays.o, rays.d, 64.0, 64, 8)
+    assert float(np.abs(h.cpu().numpy() - ref).max()) <= 2e-6
+
+
+def test_sparse_table_out_of_range_reads_as_empty():
+    """A table entry beyond n_bricks stores nothing: the brick reads as empty."""
+    sc, s, node_keep = sparse_case()
+    gd, _, _ = s.descs(3)
+    bad = s.grid.clone()
+    tab = bad.view(-1)[:ps.table_words(gd)].view(torch.int32)
+    first = int(torch.nonzero(tab >= 0)[0])
+    tab[first] = gd.n_bricks + 5
+    sdf, _ = ps.unpack_grid(gd, bad, which=ps.GRID_VALUES)
+    Bx, By = sc.dims[0] // 16, sc.dims[1] // 16
+    bz, by, bx = first // (Bx * By), (first // Bx) % By, first % Bx
+    blk = sdf.cpu().numpy()[bz * 16:(bz + 1) * 16, by * 16:(by + 1) * 16, bx * 16:(bx + 1) * 16]
+    assert np.all(blk == EMPTY)
+    s2 = dataclasses.replace(s, grid=bad)
+    rays = synth.make_rays("sphere64", n_rays=64, seed_offset=2)
+    rgb, _, _, _ = ps.render_forward(s2, dev(rays.o), dev(rays.d),
+                                     ps.render_params(64.0, 32, 0, sc.n_fresnel))
+    assert torch.isfinite(rgb).all() and ps.device_status() == 0
+
+
+def test_sparse_validation():
+    sc, s, _ = sparse_case()
+    with pytest.raises(ps.LibraryError, match="shape"):
+        ps.grid_bytes(ps.grid_desc((40, 32, 64), (0, 0, 0), (1, 1, 1), n_bricks=3))
+    with pytest.raises(ps.LibraryError, match="compiled"):
+        ps.grid_bytes(ps.grid_desc((48, 32, 64), (0, 0, 0), (1, 1, 1), feat_dtype=ps.BF16,
+                                   n_bricks=3))
+    with pytest.raises(ps.LibraryError, match="shape"):  # more bricks than the grid has
+        ps.grid_bytes(ps.grid_desc((32, 32, 32), (0, 0, 0), (1, 1, 1), n_bricks=9))
+    with pytest.raises(ps.LibraryError, match="compiled"):
+        ps.occupancy_build(s, (8, 8, 8), 0.1)
+    with pytest.raises(ps.LibraryError, match="compiled"):
+        ps.shade_nodes(s, (2.0, 2.0, 2.0), 0.1, ps.render_params(64.0, 16, 0, sc.n_fresnel))
