@@ -27,7 +27,7 @@ __all__ = [
     "weight_histogram", "proposal_forward", "proposal_backward", "adam_step", "Adam",
     "occupancy_words", "occupancy_unpack", "sdf_smooth", "sdf_smooth_adjoint",
     "grid_regularizers", "probe_smoothness", "shade_nodes", "render_colour_field",
-    "colour_field_bytes", "brick_table", "pack_sparse", "table_words",
+    "colour_field_bytes", "brick_table", "pack_sparse", "table_words", "sparse_scene",
 ]
 
 DIR_REFLECT = 0
@@ -379,6 +379,32 @@ class Scene:
                    width=int(sc.width), n_feat=n_feat, feat_dtype=feat_dtype,
                    probe_dtype=probe_dtype, mlp_dtype=mlp_dtype, feat_layout=layout,
                    n_bricks=n_bricks, empty_sdf=float(empty_sdf))
+
+
+def sparse_scene(keep, brick_sdf, brick_feat, probes, mlp, dims, box_min, box_max, sh_l,
+                 width, empty_sdf=1.0, device="cuda") -> Scene:
+    """Scene over a sparse grid given brick by brick: keep [Bz,By,Bx] (bool),
+    brick_sdf [n,16,16,16] and brick_feat [n,16,16,16,3] (FP32, bricks in the
+    x-fastest order of `keep`).  The packed buffer is assembled with tensor
+    copies: the table, then one {sdf, f0, f1, f2} record per stored node."""
+    dev = torch.device(device)
+    table = brick_table(keep)
+    n = int((table >= 0).sum())
+    gd = grid_desc(dims, box_min, box_max, 3, F32, FEAT_NODES, n, empty_sdf)
+    nbytes, _ = grid_bytes(gd)
+    out = torch.empty(nbytes // 4, dtype=torch.float32, device=dev)
+    w = table_words(gd)
+    out[:w] = 0.0
+    out[:table.numel()] = table.reshape(-1).to(dev).view(torch.float32)
+    rec = out[w:].view(n * 4096, 4)
+    rec[:, 0] = torch.as_tensor(brick_sdf, device=dev).reshape(-1)
+    rec[:, 1:] = torch.as_tensor(brick_feat, device=dev).reshape(-1, 3)
+    return Scene(grid=out.view(-1, 4),
+                 probes=torch.as_tensor(probes, dtype=torch.float32, device=dev).contiguous(),
+                 mlp=torch.as_tensor(mlp, dtype=torch.float32, device=dev).contiguous(),
+                 dims=tuple(int(v) for v in dims), box_min=tuple(float(v) for v in box_min),
+                 box_max=tuple(float(v) for v in box_max), sh_l=int(sh_l), width=int(width),
+                 n_feat=3, n_bricks=n, empty_sdf=float(empty_sdf))
 
 
 def render_params(tau=64.0, n_samples=128, dir_mode=DIR_REFLECT, n_fresnel=3,

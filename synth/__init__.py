@@ -159,12 +159,13 @@ def _object_dist(P, shapes, k=0.05):
     import torch
     acc = None
     for kind, c, prm in shapes:
-        q = P - torch.as_tensor(c, dtype=torch.float64)
+        q = P - torch.as_tensor(c, dtype=torch.float64, device=P.device)
         if kind == "sphere":
             dist = q.norm(dim=-1) - prm
         else:
             radii, e, Rm = prm
-            ql = (q @ torch.as_tensor(Rm, dtype=torch.float64)) / torch.as_tensor(radii)
+            ql = (q @ torch.as_tensor(Rm, dtype=torch.float64, device=P.device)) / \
+                torch.as_tensor(radii, device=P.device)
             f = ql.abs().pow(e).sum(-1).pow(1.0 / e)
             dist = (f - 1.0) * float(radii.min())
         acc = dist if acc is None else _torch_smin(acc, dist, k)
@@ -352,6 +353,55 @@ def _make_scene_arrays(name, g, spec, dims=None, probe_dims=None):
     return Scene(sdf=sdf, feat=feat, probes=probes.astype(np.float32), mlp=mlp,
                  box_min=bmin.astype(np.float32), box_max=bmax.astype(np.float32),
                  sh_l=spec["sh_l"], width=spec["width"], n_fresnel=spec["K"])
+
+
+def sparse_object(R, band, seed=1240, probe_every=16, n_s=3, n_a=4, sh_l=3, width=32, K=3,
+                  chunk=1 << 21, device="cpu"):
+    """An object-capture scene (smooth-min union of 16 spheres and 16
+    superquadrics, as object256) sampled on an R^3 node grid over [0,1]^3 and
+    stored sparsely: only the 16^3-node bricks that come within `band` of the
+    surface.  The bricks are chosen from the SDF at the brick's nodes on a
+    4x coarser lattice, widened by that lattice's half diagonal.  Returns
+    (keep [Bz,By,Bx] bool, brick SDF [n,16,16,16] FP32, brick features
+    [n,16,16,16,n_s] FP32, probes [P,P,P,l*l,n_a], MLP parameters), bricks in
+    x-fastest brick order and nodes x fastest inside a brick.  `device` is
+    where torch evaluates the shapes (FP64)."""
+    import torch
+    g = rng(seed)
+    shapes = object_shapes(g, 32)
+    B = R // 16
+    h = 1.0 / (R - 1)
+    # coarse test: every 4th node of every brick (5 per axis incl. the far face)
+    lo = torch.arange(B, dtype=torch.float64) * 16 * h
+    off = torch.arange(5, dtype=torch.float64) * 4 * h
+    keep = np.zeros((B, B, B), bool)
+    for bz in range(B):
+        zs = (lo[bz] + off).clamp(max=1.0)
+        ys = (lo[:, None] + off[None]).clamp(max=1.0)          # [B, 5]
+        xs = (lo[:, None] + off[None]).clamp(max=1.0)
+        Z = zs[None, None, :, None, None].expand(B, B, 5, 5, 5)
+        Y = ys[:, None, None, :, None].expand(B, B, 5, 5, 5)
+        X = xs[None, :, None, None, :].expand(B, B, 5, 5, 5)
+        P = torch.stack([X, Y, Z], -1).to(device)               # [by, bx, z, y, x, 3]
+        d = _object_dist(P, shapes).abs().amin(dim=(2, 3, 4))
+        keep[bz] = (d < band + 2.0 * 3 ** 0.5 * h * 2).cpu().numpy()
+    idx = np.argwhere(keep)                                     # (bz, by, bx), x fastest
+    n = idx.shape[0]
+    local = torch.arange(16, dtype=torch.float64) * h
+    Z, Y, X = torch.meshgrid(local, local, local, indexing="ij")
+    base = torch.stack([X, Y, Z], -1).reshape(-1, 3).to(device)  # [4096, 3]
+    sdf = np.empty((n, 16, 16, 16), np.float32)
+    per = max(1, chunk // 4096)
+    corner = torch.as_tensor(idx[:, ::-1].copy() * 16 * h, dtype=torch.float64,
+                             device=device)                     # brick origins (x, y, z)
+    for i in range(0, n, per):
+        P = corner[i:i + per, None, :] + base[None]
+        sdf[i:i + per] = _object_dist(P, shapes).reshape(-1, 16, 16, 16).cpu().numpy()
+    feat = g.normal(0.0, 0.1, size=(n, 16, 16, 16, n_s)).astype(np.float32)
+    Pn = (R - 1) // probe_every + 1
+    probes = g.normal(0.0, 0.1, size=(Pn, Pn, Pn, sh_l * sh_l, n_a)).astype(np.float32)
+    mlp = mlp_params(n_s + n_a + K, width, g)
+    return keep, sdf, feat, probes, mlp
 
 
 def make_scene(name: str, dims=None, probe_dims=None) -> Scene:

@@ -169,3 +169,25 @@ def test_sparse_validation():
         ps.occupancy_build(s, (8, 8, 8), 0.1)
     with pytest.raises(ps.LibraryError, match="compiled"):
         ps.shade_nodes(s, (2.0, 2.0, 2.0), 0.1, ps.render_params(64.0, 16, 0, sc.n_fresnel))
+
+
+def test_sparse_scene_from_bricks_matches_packing_from_dense_arrays():
+    """Assembling the packed buffer brick by brick gives the same bytes as
+    packing the dense arrays with the same brick table."""
+    keep, bsdf, bfeat, probes, mlp = synth.sparse_object(128, 0.01)
+    assert 0 < keep.sum() < keep.size
+    s1 = ps.sparse_scene(keep, bsdf, bfeat, probes, mlp, (128, 128, 128), (0, 0, 0), (1, 1, 1),
+                         3, 32, empty_sdf=EMPTY)
+    sdf = np.full((128, 128, 128), EMPTY, np.float32)
+    feat = np.zeros((128, 128, 128, 3), np.float32)
+    for k, (bz, by, bx) in enumerate(np.argwhere(keep)):
+        sl = (slice(bz * 16, bz * 16 + 16), slice(by * 16, by * 16 + 16),
+              slice(bx * 16, bx * 16 + 16))
+        sdf[sl] = bsdf[k]
+        feat[sl] = bfeat[k]
+    sc = synth.Scene(sdf=sdf, feat=feat, probes=probes, mlp=mlp,
+                     box_min=np.zeros(3, np.float32), box_max=np.ones(3, np.float32), sh_l=3,
+                     width=32, n_fresnel=3)
+    s2 = ps.Scene.from_host(sc, bricks=keep, empty_sdf=EMPTY)
+    assert s1.n_bricks == s2.n_bricks
+    assert torch.equal(s1.grid.view(torch.int32), s2.grid.view(torch.int32))  # bitwise
