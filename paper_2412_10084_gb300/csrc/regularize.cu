@@ -6,8 +6,8 @@
 //   smooth_kernel<true>   G^T: the same tiles with the transposed 1D operators,
 //                         applied z, y, x (edge outputs gather the replicated taps)
 //   sdf_reg_kernel        L_sdf, L_Eik and L_normal on the smoothed SDF, their
-//                         gradients scaled by (1 + 5 |s|)^-1; the central-
-//                         difference adjoint is reduced into the 6 neighbours
+//                         gradients scaled by (1 + 5 |s|)^-1: a z-streaming
+//                         stencil whose central-difference adjoint is a gather
 //   plane_reg_kernel      L_features: forward differences inside each tile plane
 //   probe_reg_kernel      L_probes: ordered pairs of 6-neighbour probes
 //
@@ -203,106 +203,190 @@ struct SdfReg {
     float lam_sdf, lam_eik, lam_normal;
 };
 
-__device__ __forceinline__ float sv(const SdfReg& P, int x, int y, int z)
-{
-    return __ldg(P.s + (((size_t)z * P.R[1] + y) * P.R[0] + x) * P.s_stride);
-}
+// z-streaming stencil.  A CTA owns a 32 x 8 column tile and ZC output planes
+// and walks z with three shared-memory rings of 3 planes each:
+//   s  (halo 3)  the smoothed SDF,
+//   N  (halo 2)  normal n, voxel weight w, rho = sqrt(|g|^2 + eps^2) (0 marks a
+//                node that is not interior), |g|,
+//   G  (halo 1)  dg = dObjective/d(grad s) of the node's Eikonal and normal
+//                terms.
+// Step t loads s plane zs, computes N at zs - 1, G at zs - 2 and the outputs
+// at zs - 3: ds_i = own L_sdf term + sum_a (dg_a(i - e_a) - dg_a(i + e_a)) / 2h_a
+// (the central-difference adjoint as a gather), so every output has one
+// writer and no atomics are needed.
+constexpr int RX = 32, RY = 8, ZC = 32;
+constexpr int SX = RX + 6, SY = RY + 6;
+constexpr int NX = RX + 4, NY = RY + 4;
+constexpr int GX = RX + 2, GY = RY + 2;
+constexpr int kRegThreads = RX * RY;
 
-__device__ __forceinline__ bool interior(const SdfReg& P, int x, int y, int z)
-{
-    return x > 0 && y > 0 && z > 0 && x < P.R[0] - 1 && y < P.R[1] - 1 && z < P.R[2] - 1;
-}
+struct RegSmem {
+    float s[3][SY * SX];
+    float n[3][6][NY * NX];  // n.x n.y n.z w rho |g|
+    float g[3][3][GY * GX];  // dg
+};
 
-// Central-difference gradient at an interior node.
-__device__ __forceinline__ void cgrad(const SdfReg& P, int x, int y, int z, float g[3])
-{
-    g[0] = (sv(P, x + 1, y, z) - sv(P, x - 1, y, z)) * P.inv2h[0];
-    g[1] = (sv(P, x, y + 1, z) - sv(P, x, y - 1, z)) * P.inv2h[1];
-    g[2] = (sv(P, x, y, z + 1) - sv(P, x, y, z - 1)) * P.inv2h[2];
-}
+__device__ __forceinline__ int ring(int z) { return (z + 6) % 3; }  // z >= -6
 
-__device__ __forceinline__ void unit_normal(const float g[3], float n[3], float& rho)
+__global__ void __launch_bounds__(kRegThreads) sdf_reg_kernel(SdfReg P)
 {
-    rho = sqrtf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2] + 1e-24f);
-    const float r = 1.0f / rho;
-    n[0] = g[0] * r;
-    n[1] = g[1] * r;
-    n[2] = g[2] * r;
-}
-
-__global__ void __launch_bounds__(256) sdf_reg_kernel(SdfReg P)
-{
-    const int64_t n = int64_t(P.R[0]) * P.R[1] * P.R[2];
+    extern __shared__ __align__(16) float reg_smem[];
+    RegSmem& S = *reinterpret_cast<RegSmem*>(reg_smem);
+    const int tid = threadIdx.x;
+    const int Rx = P.R[0], Ry = P.R[1], Rz = P.R[2];
+    const int x0 = blockIdx.x * RX, y0 = blockIdx.y * RY, z0 = blockIdx.z * ZC;
+    const int z1 = min(z0 + ZC, Rz);
+    const float cn = 2.0f * P.lam_normal;
     float l_sdf = 0.0f, l_eik = 0.0f, l_nrm = 0.0f;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-         i += int64_t(gridDim.x) * blockDim.x) {
-        const int x = static_cast<int>(i % P.R[0]);
-        const int y = static_cast<int>((i / P.R[0]) % P.R[1]);
-        const int z = static_cast<int>(i / (int64_t(P.R[0]) * P.R[1]));
-        const float s = sv(P, x, y, z);
-        const float w = 1.0f / (1.0f + 5.0f * fabsf(s));
-        // Eq. 11
-        const float r = s - __ldg(P.s_hat + i);
-        l_sdf += r * r;
-        float ds_own = P.lam_sdf * w * 2.0f * r;
-        P.d_s_hat[i] -= P.lam_sdf * w * 2.0f * r;
-        if (interior(P, x, y, z)) {
-            float g[3], nrm[3], rho;
-            cgrad(P, x, y, z, g);
-            unit_normal(g, nrm, rho);
-            // Eq. 12
-            const float gn = sqrtf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
-            const float e = gn - 1.0f;
-            l_eik += e * e;
-            const float ce = gn > 0.0f ? P.lam_eik * w * 2.0f * e / gn : 0.0f;
-            float dg[3] = {ce * g[0], ce * g[1], ce * g[2]};
-            // Eq. 13: pairs (i, i + e_a) owned by node i, and (i - e_a, i) owned
-            // by the neighbour, both between interior nodes
-            float dn[3] = {0.f, 0.f, 0.f};
-            const int off[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+
+    // s plane loads are software-pipelined: the values of plane zs + 1 are in
+    // flight while plane zs is processed
+    constexpr int kPer = (SY * SX + kRegThreads - 1) / kRegThreads;
+    float pre[kPer];
+    auto load_plane = [&](int z) {
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const int xp = x + off[a][0], yp = y + off[a][1], zp = z + off[a][2];
-                if (interior(P, xp, yp, zp)) {
-                    float gp[3], np_[3], rp;
-                    cgrad(P, xp, yp, zp, gp);
-                    unit_normal(gp, np_, rp);
-                    const float d0 = np_[0] - nrm[0], d1 = np_[1] - nrm[1], d2 = np_[2] - nrm[2];
-                    l_nrm += d0 * d0 + d1 * d1 + d2 * d2;
-                    const float c = P.lam_normal * w * 2.0f;
-                    dn[0] -= c * d0;
-                    dn[1] -= c * d1;
-                    dn[2] -= c * d2;
-                }
-                const int xm = x - off[a][0], ym = y - off[a][1], zm = z - off[a][2];
-                if (interior(P, xm, ym, zm)) {
-                    float gm[3], nm[3], rm;
-                    cgrad(P, xm, ym, zm, gm);
-                    unit_normal(gm, nm, rm);
-                    const float wm = 1.0f / (1.0f + 5.0f * fabsf(sv(P, xm, ym, zm)));
-                    const float c = P.lam_normal * wm * 2.0f;
-                    dn[0] += c * (nrm[0] - nm[0]);
-                    dn[1] += c * (nrm[1] - nm[1]);
-                    dn[2] += c * (nrm[2] - nm[2]);
-                }
-            }
-            const float ndn = nrm[0] * dn[0] + nrm[1] * dn[1] + nrm[2] * dn[2];
-            const float ir = 1.0f / rho;
+        for (int k = 0; k < kPer; ++k) {
+            const int e = tid + k * kRegThreads;
+            const int x = x0 - 3 + e % SX, y = y0 - 3 + e / SX;
+            pre[k] = 0.0f;
+            if (e < SY * SX && x >= 0 && x < Rx && y >= 0 && y < Ry && z >= 0 && z < Rz)
+                pre[k] = __ldg(P.s + (((size_t)z * Ry + y) * Rx + x) * P.s_stride);
+        }
+    };
+    load_plane(z0 - 3);
+    const int ox = tid % RX, oy = tid / RX;
+    const int x_o = x0 + ox, y_o = y0 + oy;
+    for (int zs = z0 - 3; zs <= z1 + 2; ++zs) {
+        // ---- s plane zs (zeros outside the grid), then the next plane's loads ----
+        {
+            float* sp = S.s[ring(zs)];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) dg[a] += (dn[a] - nrm[a] * ndn) * ir;
-            // central-difference adjoint into the neighbours
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const float v = dg[a] * P.inv2h[a];
-                const size_t ip = ((size_t)(z + off[a][2]) * P.R[1] + (y + off[a][1])) * P.R[0] +
-                                  (x + off[a][0]);
-                const size_t im = ((size_t)(z - off[a][2]) * P.R[1] + (y - off[a][1])) * P.R[0] +
-                                  (x - off[a][0]);
-                atomicAdd(P.d_s + ip * P.d_stride, v);
-                atomicAdd(P.d_s + im * P.d_stride, -v);
+            for (int k = 0; k < kPer; ++k) {
+                const int e = tid + k * kRegThreads;
+                if (e < SY * SX) sp[e] = pre[k];
             }
         }
-        atomicAdd(P.d_s + i * P.d_stride, ds_own);
+        if (zs + 1 <= z1 + 2) load_plane(zs + 1);
+        // the output node's own values, consumed after the G stage
+        const int zo = zs - 3;
+        const bool out = zo >= z0 && zo < z1 && x_o < Rx && y_o < Ry;
+        size_t io = 0;
+        float s_o = 0.f, sh_o = 0.f, ds_o = 0.f, dsh_o = 0.f;
+        if (out) {
+            io = ((size_t)zo * Ry + y_o) * Rx + x_o;
+            s_o = __ldg(P.s + io * P.s_stride);
+            sh_o = __ldg(P.s_hat + io);
+            ds_o = P.d_s[io * P.d_stride];
+            dsh_o = P.d_s_hat[io];
+        }
+        __syncthreads();
+        // ---- N plane zn = zs - 1: gradient, normal, weight at interior nodes ----
+        // (the outputs need N at z0 - 2 .. z1 + 1 and G at z0 - 1 .. z1)
+        if (zs - 1 >= z0 - 2) {
+            const int zn = zs - 1;
+            const float* sm = S.s[ring(zn - 1)];
+            const float* sc = S.s[ring(zn)];
+            const float* sp = S.s[ring(zn + 1)];
+            const int r = ring(zn);
+            for (int e = tid; e < NY * NX; e += kRegThreads) {
+                const int nx = e % NX, ny = e / NX;
+                const int x = x0 - 2 + nx, y = y0 - 2 + ny;
+                const int c = (ny + 1) * SX + nx + 1;
+                const bool inner = x > 0 && y > 0 && zn > 0 && x < Rx - 1 && y < Ry - 1 &&
+                                   zn < Rz - 1;
+                float n0 = 0.f, n1 = 0.f, n2 = 0.f, w = 0.f, rho = 0.f, gn = 0.f;
+                if (inner) {
+                    const float g0 = (sc[c + 1] - sc[c - 1]) * P.inv2h[0];
+                    const float g1 = (sc[c + SX] - sc[c - SX]) * P.inv2h[1];
+                    const float g2 = (sp[c] - sm[c]) * P.inv2h[2];
+                    const float gg = g0 * g0 + g1 * g1 + g2 * g2;
+                    rho = sqrtf(gg + 1e-24f);
+                    const float ir = 1.0f / rho;
+                    n0 = g0 * ir;
+                    n1 = g1 * ir;
+                    n2 = g2 * ir;
+                    gn = sqrtf(gg);
+                    w = 1.0f / (1.0f + 5.0f * fabsf(sc[c]));
+                }
+                S.n[r][0][e] = n0;
+                S.n[r][1][e] = n1;
+                S.n[r][2][e] = n2;
+                S.n[r][3][e] = w;
+                S.n[r][4][e] = rho;
+                S.n[r][5][e] = gn;
+            }
+        }
+        __syncthreads();
+        // ---- G plane zg = zs - 2: Eikonal and normal adjoints w.r.t. grad s ----
+        if (zs - 2 >= z0 - 1) {
+            const int zg = zs - 2;
+            const int rm = ring(zg - 1), rc = ring(zg), rp = ring(zg + 1);
+            for (int e = tid; e < GY * GX; e += kRegThreads) {
+                const int gx = e % GX, gy = e / GX;
+                const int x = x0 - 1 + gx, y = y0 - 1 + gy;
+                const int c = (gy + 1) * NX + gx + 1;
+                const float rho = S.n[rc][4][c];
+                float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+                if (rho > 0.0f) {
+                    const bool own = x >= x0 && x < x0 + RX && y >= y0 && y < y0 + RY &&
+                                     zg >= z0 && zg < z1;
+                    const float n0 = S.n[rc][0][c], n1 = S.n[rc][1][c], n2 = S.n[rc][2][c];
+                    const float w = S.n[rc][3][c], gn = S.n[rc][5][c];
+                    // Eq. 12
+                    const float ee = gn - 1.0f;
+                    if (own) l_eik += ee * ee;
+                    const float ce = gn > 0.0f ? P.lam_eik * w * 2.0f * ee / gn : 0.0f;
+                    // Eq. 13: pairs (j, j + e_a) owned by j, (j - e_a, j) owned by the neighbour
+                    float dn0 = 0.f, dn1 = 0.f, dn2 = 0.f;
+                    const int pr[3] = {rc, rc, rp}, po[3] = {c + 1, c + NX, c};
+                    const int mr[3] = {rc, rc, rm}, mo[3] = {c - 1, c - NX, c};
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        if (S.n[pr[a]][4][po[a]] > 0.0f) {
+                            const float q0 = S.n[pr[a]][0][po[a]] - n0;
+                            const float q1 = S.n[pr[a]][1][po[a]] - n1;
+                            const float q2 = S.n[pr[a]][2][po[a]] - n2;
+                            if (own) l_nrm += q0 * q0 + q1 * q1 + q2 * q2;
+                            const float k = cn * w;
+                            dn0 -= k * q0;
+                            dn1 -= k * q1;
+                            dn2 -= k * q2;
+                        }
+                        if (S.n[mr[a]][4][mo[a]] > 0.0f) {
+                            const float k = cn * S.n[mr[a]][3][mo[a]];
+                            dn0 += k * (n0 - S.n[mr[a]][0][mo[a]]);
+                            dn1 += k * (n1 - S.n[mr[a]][1][mo[a]]);
+                            dn2 += k * (n2 - S.n[mr[a]][2][mo[a]]);
+                        }
+                    }
+                    const float ndn = n0 * dn0 + n1 * dn1 + n2 * dn2;
+                    const float ir = 1.0f / rho;
+                    // dg = ce g + (dn - n (n . dn)) / rho, with g = n rho
+                    d0 = ce * n0 * rho + (dn0 - n0 * ndn) * ir;
+                    d1 = ce * n1 * rho + (dn1 - n1 * ndn) * ir;
+                    d2 = ce * n2 * rho + (dn2 - n2 * ndn) * ir;
+                }
+                S.g[rc][0][e] = d0;
+                S.g[rc][1][e] = d1;
+                S.g[rc][2][e] = d2;
+            }
+        }
+        __syncthreads();
+        // ---- outputs at zo = zs - 3 ----
+        if (out) {
+            const float w = 1.0f / (1.0f + 5.0f * fabsf(s_o));
+            // Eq. 11
+            const float r = s_o - sh_o;
+            l_sdf += r * r;
+            const float own = P.lam_sdf * w * 2.0f * r;
+            P.d_s_hat[io] = dsh_o - own;
+            const int c = (oy + 1) * GX + ox + 1;
+            const int rc = ring(zo);
+            const float adj = (S.g[rc][0][c - 1] - S.g[rc][0][c + 1]) * P.inv2h[0] +
+                              (S.g[rc][1][c - GX] - S.g[rc][1][c + GX]) * P.inv2h[1] +
+                              (S.g[ring(zo - 1)][2][c] - S.g[ring(zo + 1)][2][c]) * P.inv2h[2];
+            P.d_s[io * P.d_stride] = ds_o + (own + adj);
+        }
     }
     block_loss(l_sdf, l_eik, l_nrm, P.loss, 3);
 }
@@ -452,7 +536,12 @@ cudaError_t launch_sdf_reg(const int R[3], const float h[3], const float* s_hat,
     P.lam_sdf = lam_sdf;
     P.lam_eik = lam_eik;
     P.lam_normal = lam_normal;
-    sdf_reg_kernel<<<blocks(int64_t(R[0]) * R[1] * R[2]), 256, 0, stream>>>(P);
+    constexpr int kBytes = static_cast<int>(sizeof(RegSmem));
+    cudaError_t e =
+        cudaFuncSetAttribute(sdf_reg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBytes);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((R[0] + RX - 1) / RX, (R[1] + RY - 1) / RY, (R[2] + ZC - 1) / ZC);
+    sdf_reg_kernel<<<grid, kRegThreads, kBytes, stream>>>(P);
     return cudaGetLastError();
 }
 
