@@ -36,15 +36,19 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi)
     return v < lo ? lo : (v > hi ? hi : v);
 }
 
-// Weight with which input node `in` enters output node `out` of the 1D
-// convolution along an axis of n nodes (tap j reads clamp(out + j - 2)).
-__device__ __forceinline__ float conv_weight(const Taps& T, int in, int out, int n)
+// Transposed 1D pass at output node k of an axis of n nodes; p[j * st] holds
+// input node k - 2 + j (0 outside the grid).  Inside the axis, output k takes
+// input i with the weight w[k - i + 2] that the forward gave input k in output
+// i; the replicated edge taps add (w0 + w1) x in[0] + w0 x in[1] at k = 0 and
+// (w3 + w4) x in[n-1] + w4 x in[n-2] at k = n - 1.
+__device__ __forceinline__ float tconv(const float* p, int st, int k, int n, const Taps& T)
 {
-    float w = 0.0f;
+    float acc = 0.0f;
 #pragma unroll
-    for (int j = 0; j < 5; ++j)
-        if (clampi(out + j - HALO, 0, n - 1) == in) w += T.w[j];
-    return w;
+    for (int j = 0; j < 5; ++j) acc = fmaf(T.w[4 - j], p[j * st], acc);
+    if (k == 0) acc = fmaf(T.w[0] + T.w[1], p[2 * st], fmaf(T.w[0], p[3 * st], acc));
+    if (k == n - 1) acc = fmaf(T.w[3] + T.w[4], p[2 * st], fmaf(T.w[4], p[st], acc));
+    return acc;
 }
 
 template <bool TRANSPOSE>
@@ -116,35 +120,18 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_kernel(const float* __r
             *o = accumulate ? *o + acc : acc;
         }
     } else {
-        // G^T = Gx^T Gy^T Gz^T.  Output k of a transposed pass gathers the
-        // inputs i = k - 2 .. k + 2 with the weight the forward gave node k in
-        // its output i.
+        // G^T = Gx^T Gy^T Gz^T, applied z, y, x with tconv (zeros outside the
+        // grid, as loaded)
         // z: A[AZ][AY][AX] -> B[TZ][AY][AX]
         for (int e = tid; e < TZ * AY * AX; e += kSmoothThreads) {
             const int ax = e % AX, ay = (e / AX) % AY, z = e / (AX * AY);
-            const int k = z0 + z;
-            float acc = 0.0f;
-#pragma unroll
-            for (int j = 0; j < 5; ++j) {
-                const int i = k + j - HALO;
-                if (i >= 0 && i < Rz)
-                    acc = fmaf(conv_weight(T, k, i, Rz), A[((z + j) * AY + ay) * AX + ax], acc);
-            }
-            B[e] = acc;
+            B[e] = tconv(A + (z * AY + ay) * AX + ax, AY * AX, z0 + z, Rz, T);
         }
         __syncthreads();
         // y: B[TZ][AY][AX] -> A[TZ][TY][AX]
         for (int e = tid; e < TZ * TY * AX; e += kSmoothThreads) {
             const int ax = e % AX, y = (e / AX) % TY, z = e / (AX * TY);
-            const int k = y0 + y;
-            float acc = 0.0f;
-#pragma unroll
-            for (int j = 0; j < 5; ++j) {
-                const int i = k + j - HALO;
-                if (i >= 0 && i < Ry)
-                    acc = fmaf(conv_weight(T, k, i, Ry), B[(z * AY + y + j) * AX + ax], acc);
-            }
-            A[e] = acc;
+            A[e] = tconv(B + (z * AY + y) * AX + ax, AX, y0 + y, Ry, T);
         }
         __syncthreads();
         // x: A[TZ][TY][AX] -> output
@@ -152,13 +139,7 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_kernel(const float* __r
             const int x = e % TX, y = (e / TX) % TY, z = e / (TX * TY);
             const int gx = x0 + x, gy = y0 + y, gz = z0 + z;
             if (gx >= Rx || gy >= Ry || gz >= Rz) continue;
-            float acc = 0.0f;
-#pragma unroll
-            for (int j = 0; j < 5; ++j) {
-                const int i = gx + j - HALO;
-                if (i >= 0 && i < Rx)
-                    acc = fmaf(conv_weight(T, gx, i, Rx), A[(z * TY + y) * AX + x + j], acc);
-            }
+            const float acc = tconv(A + (z * TY + y) * AX + x, 1, gx, Rx, T);
             float* o = out + (((size_t)gz * Ry + gy) * Rx + gx) * out_stride;
             *o = accumulate ? *o + acc : acc;
         }
