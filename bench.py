@@ -303,6 +303,12 @@ def run_reference(args, world, rank):
     if args.workload == "inference1080":
         return run_reference_inference(args)
     wl = WORKLOADS[args.workload]
+    if wl.get("sparse"):
+        print(json.dumps({"impl": "reference",
+                          "unavailable": "the oracle renders dense grids; the dense FP64 copy of "
+                                         "the 1024^3 sparse workload would need 34 GB of host "
+                                         "memory"}), flush=True)
+        return
     base = wl.get("base", args.workload)
     spec = synth.WORKLOADS[base]
     sc = synth.make_scene(base)
