@@ -69,7 +69,8 @@ WORKLOADS = {
         R=1024, band=0.03, tau=256.0),
     "inference1080": dict(
         desc=("real-time inference on the object-capture scene (256^3, probes 32^3, MLP "
-              "10->32->32->3) after 200 steps of appearance fitting to teacher images: 8 "
+              "10->32->32->3; features smooth noise over ~3 voxels) after 200 steps of "
+              "appearance fitting to teacher images: 8 "
               "novel 1920x1080 views per step, forward only; plain FP32 uniform 256-sample "
               "march vs BF16 features + FP16 probes + FP16 MLP with the learned proposal "
               "(64^3 occupancy bitmask, 16 bins, width 32, mix 0.6, 2000 training steps) "
@@ -264,7 +265,7 @@ def run_reference_inference(args):
     import synth
     base = WORKLOADS[args.workload]["base"]
     spec = synth.WORKLOADS[base]
-    sc = synth.make_scene(base)
+    sc = synth.inference_scene(base)
     m = oracle.Model.from_scene(sc)
     cams = synth.novel_cameras(base, 8)
     rays = [synth.image_rays(c, 1920, 1080, spec["fov"]) for c in cams]
@@ -656,7 +657,7 @@ def run_inference(args, world, rank, local):
     spec = synth.WORKLOADS[base]
     tau = spec["tau"]
     t_setup = time.perf_counter()
-    sc = synth.make_scene(base)
+    sc = synth.inference_scene(base)
     scene = ps.Scene.from_host(sc, device=device)
     # appearance: fitted to teacher images of the analytic shape (geometry frozen)
     pool = synth.training_pool(base, 1 << 16, seed_offset=1000 + rank)

@@ -404,6 +404,33 @@ def sparse_object(R, band, seed=1240, probe_every=16, n_s=3, n_a=4, sh_l=3, widt
     return keep, sdf, feat, probes, mlp
 
 
+def smooth_features(dims, n_s, g: np.random.Generator, sigma_vox=3.0, std=0.1) -> np.ndarray:
+    """Spatial features [Rz,Ry,Rx,n_s] drawn as white noise filtered by a
+    Gaussian of sigma_vox nodes (in Fourier space, periodic) and rescaled to
+    the given standard deviation: features that vary over a few voxels, like
+    those of a scene trained with a smoothness term, instead of per-node
+    noise."""
+    Rx, Ry, Rz = (int(v) for v in dims)
+    out = np.empty((Rz, Ry, Rx, n_s), np.float32)
+    kz = np.fft.fftfreq(Rz)[:, None, None]
+    ky = np.fft.fftfreq(Ry)[None, :, None]
+    kx = np.fft.rfftfreq(Rx)[None, None, :]
+    filt = np.exp(-2.0 * (np.pi * sigma_vox) ** 2 * (kx ** 2 + ky ** 2 + kz ** 2))
+    for c in range(n_s):
+        f = np.fft.irfftn(np.fft.rfftn(g.normal(size=(Rz, Ry, Rx))) * filt, s=(Rz, Ry, Rx))
+        out[..., c] = (f * (std / f.std())).astype(np.float32)
+    return out
+
+
+def inference_scene(name: str) -> Scene:
+    """The workload's scene with smooth spatial features (the starting point of
+    the real-time inference workload's appearance fit)."""
+    sc = make_scene(name)
+    spec = WORKLOADS[name]
+    return dataclasses.replace(sc, feat=smooth_features(sc.dims, spec["n_s"],
+                                                        rng(spec["seed"] + 29)))
+
+
 def make_scene(name: str, dims=None, probe_dims=None) -> Scene:
     spec = WORKLOADS[name]
     return _make_scene_arrays(name, rng(spec["seed"]), spec, dims, probe_dims)
