@@ -118,7 +118,7 @@ def captured_traffic(workload, kernel, rays):
             rec = json.load(f)
         sys.path.insert(0, os.path.join(ROOT, "paper_2412_10084_gb300"))
         import build as _b
-        if rec.get("source_digest") != _b.source_digest():
+        if rec.get("render_digest") != _b.render_digest():
             return None
         w = rec.get(workload)
         if not w or w.get("rays") != rays or kernel not in w:

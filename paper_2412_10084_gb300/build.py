@@ -33,11 +33,19 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def _inputs_digest(flags):
+# Files the two render kernels are built from (their code, shared headers, and
+# the launch configuration in the C ABI layer).
+RENDER_FILES = ("render_fwd.cu", "render_bwd.cu", "render_common.cuh", "sample_eval.cuh",
+                "mlp_tc.cuh", "tc_sm100.cuh", "internal.h", "abi.cu", "probesdf.h")
+
+
+def _inputs_digest(flags, only=None):
     h = hashlib.sha256()
     for d in (CSRC, INCLUDE):
         for f in sorted(os.listdir(d)):
             p = os.path.join(d, f)
+            if only is not None and f not in only:
+                continue
             if os.path.isfile(p):
                 h.update(f.encode())
                 with open(p, "rb") as fh:
@@ -56,6 +64,12 @@ def base_flags():
 def source_digest() -> str:
     """Digest of the kernel sources, headers and default flags (the build stamp)."""
     return _inputs_digest(base_flags())
+
+
+def render_digest() -> str:
+    """Digest of the render kernels' sources and the default flags: profile
+    figures of those kernels stay valid while it is unchanged."""
+    return _inputs_digest(base_flags(), RENDER_FILES)
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
