@@ -36,7 +36,7 @@ struct FwdLayout {
 };
 
 template <class C>
-__global__ void __launch_bounds__(kFwdThreads, 6)
+__global__ void __launch_bounds__(kFwdThreads, 5)
 render_forward_kernel(RenderArgs A)
 {
     using M = MlpTC<C>;
