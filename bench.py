@@ -866,12 +866,17 @@ def run_inference(args, world, rank, local):
     if not args.no_cpu_baseline:
         import oracle
         threads = cpu_cores()
-        nr = args.cpu_rays or 4096
         m = oracle.Model.from_scene(sc_fitted(scene, sc))
-        idx = np.linspace(0, n - 1, nr).astype(np.int64)
-        t0 = time.perf_counter()
-        oracle.render_forward(m, h_o.numpy()[idx], h_d.numpy()[idx], tau, 256, n_threads=threads)
-        secs = time.perf_counter() - t0
+        nr = args.cpu_rays or 4096
+        while True:  # grow the evenly spaced sample until it takes about 10 s
+            idx = np.linspace(0, n - 1, nr).astype(np.int64)
+            t0 = time.perf_counter()
+            oracle.render_forward(m, h_o.numpy()[idx], h_d.numpy()[idx], tau, 256,
+                                  n_threads=threads)
+            secs = time.perf_counter() - t0
+            if args.cpu_rays or secs >= 5.0 or nr >= n:
+                break
+            nr = int(min(n, nr * max(2.0, 10.0 / max(secs, 1e-3))))
         out["cpu_baseline"] = {"value": secs * 1e3 * (n / nr) / n_views, "unit": "ms/frame",
                                "cores": threads, "kind": "oracle",
                                "sample": f"{nr} evenly spaced pixels of the 8 views, FP64 "
