@@ -191,3 +191,24 @@ def test_sparse_scene_from_bricks_matches_packing_from_dense_arrays():
     s2 = ps.Scene.from_host(sc, bricks=keep, empty_sdf=EMPTY)
     assert s1.n_bricks == s2.n_bricks
     assert torch.equal(s1.grid.view(torch.int32), s2.grid.view(torch.int32))  # bitwise
+
+
+def test_sparse_colour_field_march_matches_oracle():
+    """The colour-field march reads the SDF through the brick table too."""
+    sc, s, _ = sparse_case()
+    g = synth.rng(19)
+    Rx, Ry, Rz = sc.dims
+    c16 = np.zeros((Rz, Ry, Rx, 4), np.float16)
+    c16[..., :3] = g.uniform(0.0, 1.0, size=(Rz, Ry, Rx, 3)).astype(np.float16)
+    rays = synth.make_rays("sphere64", n_rays=600, seed_offset=23)
+    params = ps.render_params(64.0, 80, 0, sc.n_fresnel, (0.2, 0.1, 0.4))
+    rgb, depth, wsum = ps.render_colour_field(s, torch.as_tensor(c16, device="cuda"),
+                                              dev(rays.o), dev(rays.d), params)
+    ref = oracle.render_colour_field(oracle.Model.from_scene(sc),
+                                     c16[..., :3].astype(np.float64), rays.o, rays.d, 64.0, 80,
+                                     bg=(0.2, 0.1, 0.4))
+    errs = {k: rel_err_elementwise(v.cpu().numpy(), ref[k])
+            for k, v in (("rgb", rgb), ("depth", depth), ("wsum", wsum))}
+    log_errors("sparse colour field", errs)
+    for k, e in errs.items():
+        assert e <= RGB_DEPTH_RTOL, (k, e)
