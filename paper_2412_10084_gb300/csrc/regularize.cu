@@ -51,68 +51,86 @@ __device__ __forceinline__ float tconv(const float* p, int st, int k, int n, con
     return acc;
 }
 
+// Work is laid out in rows along x: warp w takes rows w, w + 8, ..., lane =
+// x (a 36-wide halo row takes a second slot on lanes 0..3), so no element
+// index is ever divided or reduced modulo a tile size.
+constexpr int kSmoothWarps = kSmoothThreads / 32;
+
 template <bool TRANSPOSE>
-__global__ void __launch_bounds__(kSmoothThreads) smooth_kernel(const float* __restrict__ in, int in_stride,
-                                                     float* __restrict__ out, int out_stride,
-                                                     int Rx, int Ry, int Rz, Taps T, int accumulate)
+__global__ void __launch_bounds__(kSmoothThreads) smooth_kernel(const float* __restrict__ in,
+                                                                 int in_stride,
+                                                                 float* __restrict__ out,
+                                                                 int out_stride, int Rx, int Ry,
+                                                                 int Rz, Taps T, int accumulate)
 {
     __shared__ float A[kBufA];
     __shared__ float B[kBufB];
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
-    const int tid = threadIdx.x;
-    // tile + halo: forward reads replicate the edge nodes; the transposed
-    // operator has no input outside the grid (zeros).  All of a thread's loads
-    // are issued before the first store to shared memory.
-    constexpr int kLoads = (kBufA + kSmoothThreads - 1) / kSmoothThreads;
-    float v[kLoads];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // ---- tile + halo, rows (az, ay) of AX nodes: forward reads replicate the
+    // edge nodes; the transposed operator has no input outside the grid ----
+    {
+        const int gx0 = x0 - HALO + lane, gx1 = x0 - HALO + 32 + lane;
+        const bool in0 = gx0 >= 0 && gx0 < Rx, in1 = lane < AX - 32 && gx1 >= 0 && gx1 < Rx;
+        const int cx0 = clampi(gx0, 0, Rx - 1), cx1 = clampi(gx1, 0, Rx - 1);
+        constexpr int kRows = AZ * AY / kSmoothWarps;  // 18
+        constexpr int kBatch = 6;
+#pragma unroll 1
+        for (int i0 = 0; i0 < kRows; i0 += kBatch) {
+            float v0[kBatch], v1[kBatch];
 #pragma unroll
-    for (int it = 0; it < kLoads; ++it) {
-        const int e = tid + it * kSmoothThreads;
-        const int ax = e % AX, ay = (e / AX) % AY, az = e / (AX * AY);
-        const int gx = x0 + ax - HALO, gy = y0 + ay - HALO, gz = z0 + az - HALO;
-        v[it] = 0.0f;
-        if (e >= kBufA) continue;
-        if (!TRANSPOSE) {
-            const size_t g = ((size_t)clampi(gz, 0, Rz - 1) * Ry + clampi(gy, 0, Ry - 1)) * Rx +
-                             clampi(gx, 0, Rx - 1);
-            v[it] = __ldg(in + g * in_stride);
-        } else if (gx >= 0 && gx < Rx && gy >= 0 && gy < Ry && gz >= 0 && gz < Rz) {
-            v[it] = __ldg(in + (((size_t)gz * Ry + gy) * Rx + gx) * in_stride);
+            for (int i = 0; i < kBatch; ++i) {
+                const int r = warp + kSmoothWarps * (i0 + i);
+                const int ay = r % AY, az = r / AY;
+                const int gy = y0 + ay - HALO, gz = z0 + az - HALO;
+                v0[i] = v1[i] = 0.0f;
+                if (!TRANSPOSE) {
+                    const size_t row =
+                        ((size_t)clampi(gz, 0, Rz - 1) * Ry + clampi(gy, 0, Ry - 1)) * Rx;
+                    v0[i] = __ldg(in + (row + cx0) * in_stride);
+                    if (lane < AX - 32) v1[i] = __ldg(in + (row + cx1) * in_stride);
+                } else if (gy >= 0 && gy < Ry && gz >= 0 && gz < Rz) {
+                    const size_t row = ((size_t)gz * Ry + gy) * Rx;
+                    if (in0) v0[i] = __ldg(in + (row + gx0) * in_stride);
+                    if (in1) v1[i] = __ldg(in + (row + gx1) * in_stride);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < kBatch; ++i) {
+                const int r = warp + kSmoothWarps * (i0 + i);
+                A[r * AX + lane] = v0[i];
+                if (lane < AX - 32) A[r * AX + 32 + lane] = v1[i];
+            }
         }
-    }
-#pragma unroll
-    for (int it = 0; it < kLoads; ++it) {
-        const int e = tid + it * kSmoothThreads;
-        if (e < kBufA) A[e] = v[it];
     }
     __syncthreads();
     if (!TRANSPOSE) {
         // x: A[AZ][AY][AX] -> B[AZ][AY][TX]
-        for (int e = tid; e < AZ * AY * TX; e += kSmoothThreads) {
-            const int x = e % TX, ay = (e / TX) % AY, az = e / (TX * AY);
-            const float* a = A + (az * AY + ay) * AX + x;
+        for (int r = warp; r < AZ * AY; r += kSmoothWarps) {
+            const float* a = A + r * AX + lane;
             float acc = 0.0f;
 #pragma unroll
             for (int j = 0; j < 5; ++j) acc = fmaf(T.w[j], a[j], acc);
-            B[e] = acc;
+            B[r * TX + lane] = acc;
         }
         __syncthreads();
         // y: B[AZ][AY][TX] -> A[AZ][TY][TX]
-        for (int e = tid; e < AZ * TY * TX; e += kSmoothThreads) {
-            const int x = e % TX, y = (e / TX) % TY, az = e / (TX * TY);
-            const float* b = B + (az * AY + y) * TX + x;
+        for (int r = warp; r < AZ * TY; r += kSmoothWarps) {
+            const int y = r % TY, az = r / TY;
+            const float* b = B + (az * AY + y) * TX + lane;
             float acc = 0.0f;
 #pragma unroll
             for (int j = 0; j < 5; ++j) acc = fmaf(T.w[j], b[j * TX], acc);
-            A[e] = acc;
+            A[r * TX + lane] = acc;
         }
         __syncthreads();
         // z: A[AZ][TY][TX] -> output
-        for (int e = tid; e < TZ * TY * TX; e += kSmoothThreads) {
-            const int x = e % TX, y = (e / TX) % TY, z = e / (TX * TY);
-            const int gx = x0 + x, gy = y0 + y, gz = z0 + z;
+        const int gx = x0 + lane;
+        for (int r = warp; r < TZ * TY; r += kSmoothWarps) {
+            const int y = r % TY, z = r / TY;
+            const int gy = y0 + y, gz = z0 + z;
             if (gx >= Rx || gy >= Ry || gz >= Rz) continue;
-            const float* a = A + (z * TY + y) * TX + x;
+            const float* a = A + r * TX + lane;
             float acc = 0.0f;
 #pragma unroll
             for (int j = 0; j < 5; ++j) acc = fmaf(T.w[j], a[j * TY * TX], acc);
@@ -123,23 +141,28 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_kernel(const float* __r
         // G^T = Gx^T Gy^T Gz^T, applied z, y, x with tconv (zeros outside the
         // grid, as loaded)
         // z: A[AZ][AY][AX] -> B[TZ][AY][AX]
-        for (int e = tid; e < TZ * AY * AX; e += kSmoothThreads) {
-            const int ax = e % AX, ay = (e / AX) % AY, z = e / (AX * AY);
-            B[e] = tconv(A + (z * AY + ay) * AX + ax, AY * AX, z0 + z, Rz, T);
+        for (int r = warp; r < TZ * AY; r += kSmoothWarps) {
+            const int z = r / AY;
+            const float* a = A + r * AX + lane;  // rows (z, ay) of A start the tap column
+            B[r * AX + lane] = tconv(a, AY * AX, z0 + z, Rz, T);
+            if (lane < AX - 32) B[r * AX + 32 + lane] = tconv(a + 32, AY * AX, z0 + z, Rz, T);
         }
         __syncthreads();
         // y: B[TZ][AY][AX] -> A[TZ][TY][AX]
-        for (int e = tid; e < TZ * TY * AX; e += kSmoothThreads) {
-            const int ax = e % AX, y = (e / AX) % TY, z = e / (AX * TY);
-            A[e] = tconv(B + (z * AY + y) * AX + ax, AX, y0 + y, Ry, T);
+        for (int r = warp; r < TZ * TY; r += kSmoothWarps) {
+            const int y = r % TY, z = r / TY;
+            const float* b = B + (z * AY + y) * AX + lane;
+            A[r * AX + lane] = tconv(b, AX, y0 + y, Ry, T);
+            if (lane < AX - 32) A[r * AX + 32 + lane] = tconv(b + 32, AX, y0 + y, Ry, T);
         }
         __syncthreads();
         // x: A[TZ][TY][AX] -> output
-        for (int e = tid; e < TZ * TY * TX; e += kSmoothThreads) {
-            const int x = e % TX, y = (e / TX) % TY, z = e / (TX * TY);
-            const int gx = x0 + x, gy = y0 + y, gz = z0 + z;
+        const int gx = x0 + lane;
+        for (int r = warp; r < TZ * TY; r += kSmoothWarps) {
+            const int y = r % TY, z = r / TY;
+            const int gy = y0 + y, gz = z0 + z;
             if (gx >= Rx || gy >= Ry || gz >= Rz) continue;
-            const float acc = tconv(A + (z * TY + y) * AX + x, 1, gx, Rx, T);
+            const float acc = tconv(A + r * AX + lane, 1, gx, Rx, T);
             float* o = out + (((size_t)gz * Ry + gy) * Rx + gx) * out_stride;
             *o = accumulate ? *o + acc : acc;
         }
