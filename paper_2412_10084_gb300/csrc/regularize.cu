@@ -230,8 +230,6 @@ struct RegSmem {
     float g[3][3][GY * GX];  // dg
 };
 
-__device__ __forceinline__ int ring(int z) { return (z + 6) % 3; }  // z >= -6
-
 __global__ void __launch_bounds__(kRegThreads) sdf_reg_kernel(SdfReg P)
 {
     extern __shared__ __align__(16) float reg_smem[];
@@ -241,34 +239,68 @@ __global__ void __launch_bounds__(kRegThreads) sdf_reg_kernel(SdfReg P)
     const int x0 = blockIdx.x * RX, y0 = blockIdx.y * RY, z0 = blockIdx.z * ZC;
     const int z1 = min(z0 + ZC, Rz);
     const float cn = 2.0f * P.lam_normal;
+    const size_t plane = (size_t)Ry * Rx;
     float l_sdf = 0.0f, l_eik = 0.0f, l_nrm = 0.0f;
+
+    // A thread's elements of each plane are the same at every step: their
+    // (x, y) offsets and in-grid tests are computed once.
+    constexpr int kPerS = (SY * SX + kRegThreads - 1) / kRegThreads;  // 3
+    constexpr int kPerN = (NY * NX + kRegThreads - 1) / kRegThreads;  // 2
+    constexpr int kPerG = (GY * GX + kRegThreads - 1) / kRegThreads;  // 2
+    size_t s_xy[kPerS];
+    bool s_in[kPerS];
+#pragma unroll
+    for (int k = 0; k < kPerS; ++k) {
+        const int e = tid + k * kRegThreads;
+        const int x = x0 - 3 + e % SX, y = y0 - 3 + e / SX;
+        s_in[k] = e < SY * SX && x >= 0 && x < Rx && y >= 0 && y < Ry;
+        s_xy[k] = s_in[k] ? (size_t)y * Rx + x : 0;
+    }
+    int n_c[kPerN];
+    bool n_ok[kPerN], n_xy[kPerN];
+#pragma unroll
+    for (int k = 0; k < kPerN; ++k) {
+        const int e = tid + k * kRegThreads;
+        const int nx = e % NX, ny = e / NX, x = x0 - 2 + nx, y = y0 - 2 + ny;
+        n_ok[k] = e < NY * NX;
+        n_c[k] = (ny + 1) * SX + nx + 1;  // the node in the s planes
+        n_xy[k] = x > 0 && y > 0 && x < Rx - 1 && y < Ry - 1;
+    }
+    int g_c[kPerG];
+    bool g_ok[kPerG], g_xy[kPerG];
+#pragma unroll
+    for (int k = 0; k < kPerG; ++k) {
+        const int e = tid + k * kRegThreads;
+        const int gx = e % GX, gy = e / GX, x = x0 - 1 + gx, y = y0 - 1 + gy;
+        g_ok[k] = e < GY * GX;
+        g_c[k] = (gy + 1) * NX + gx + 1;  // the node in the N planes
+        g_xy[k] = x >= x0 && x < x0 + RX && y >= y0 && y < y0 + RY;  // owned in x, y
+    }
 
     // s plane loads are software-pipelined: the values of plane zs + 1 are in
     // flight while plane zs is processed
-    constexpr int kPer = (SY * SX + kRegThreads - 1) / kRegThreads;
-    float pre[kPer];
+    float pre[kPerS];
     auto load_plane = [&](int z) {
+        const bool zin = z >= 0 && z < Rz;
 #pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            const int e = tid + k * kRegThreads;
-            const int x = x0 - 3 + e % SX, y = y0 - 3 + e / SX;
-            pre[k] = 0.0f;
-            if (e < SY * SX && x >= 0 && x < Rx && y >= 0 && y < Ry && z >= 0 && z < Rz)
-                pre[k] = __ldg(P.s + (((size_t)z * Ry + y) * Rx + x) * P.s_stride);
-        }
+        for (int k = 0; k < kPerS; ++k)
+            pre[k] = (zin && s_in[k]) ? __ldg(P.s + ((size_t)z * plane + s_xy[k]) * P.s_stride)
+                                      : 0.0f;
     };
     load_plane(z0 - 3);
     const int ox = tid % RX, oy = tid / RX;
     const int x_o = x0 + ox, y_o = y0 + oy;
+    const int c_o = (oy + 1) * GX + ox + 1;  // the output node in the G planes
+    // ring slots of the planes of two steps back (ra), one step back (rb) and
+    // this step (rc): s holds zs, zs - 1, zs - 2; N holds zs - 1 .. zs - 3; G
+    // holds zs - 2 .. zs - 4
+    int ra = 0, rb = 1, rc = 2;
     for (int zs = z0 - 3; zs <= z1 + 2; ++zs) {
         // ---- s plane zs (zeros outside the grid), then the next plane's loads ----
-        {
-            float* sp = S.s[ring(zs)];
 #pragma unroll
-            for (int k = 0; k < kPer; ++k) {
-                const int e = tid + k * kRegThreads;
-                if (e < SY * SX) sp[e] = pre[k];
-            }
+        for (int k = 0; k < kPerS; ++k) {
+            const int e = tid + k * kRegThreads;
+            if (e < SY * SX) S.s[rc][e] = pre[k];
         }
         if (zs + 1 <= z1 + 2) load_plane(zs + 1);
         // the output node's own values, consumed after the G stage
@@ -277,7 +309,7 @@ __global__ void __launch_bounds__(kRegThreads) sdf_reg_kernel(SdfReg P)
         size_t io = 0;
         float s_o = 0.f, sh_o = 0.f, ds_o = 0.f, dsh_o = 0.f;
         if (out) {
-            io = ((size_t)zo * Ry + y_o) * Rx + x_o;
+            io = (size_t)zo * plane + (size_t)y_o * Rx + x_o;
             s_o = __ldg(P.s + io * P.s_stride);
             sh_o = __ldg(P.s_hat + io);
             ds_o = P.d_s[io * P.d_stride];
@@ -288,18 +320,17 @@ __global__ void __launch_bounds__(kRegThreads) sdf_reg_kernel(SdfReg P)
         // (the outputs need N at z0 - 2 .. z1 + 1 and G at z0 - 1 .. z1)
         if (zs - 1 >= z0 - 2) {
             const int zn = zs - 1;
-            const float* sm = S.s[ring(zn - 1)];
-            const float* sc = S.s[ring(zn)];
-            const float* sp = S.s[ring(zn + 1)];
-            const int r = ring(zn);
-            for (int e = tid; e < NY * NX; e += kRegThreads) {
-                const int nx = e % NX, ny = e / NX;
-                const int x = x0 - 2 + nx, y = y0 - 2 + ny;
-                const int c = (ny + 1) * SX + nx + 1;
-                const bool inner = x > 0 && y > 0 && zn > 0 && x < Rx - 1 && y < Ry - 1 &&
-                                   zn < Rz - 1;
+            const float* sm = S.s[ra];
+            const float* sc = S.s[rb];
+            const float* sp = S.s[rc];
+            const bool zin = zn > 0 && zn < Rz - 1;
+#pragma unroll
+            for (int k = 0; k < kPerN; ++k) {
+                if (!n_ok[k]) continue;
+                const int e = tid + k * kRegThreads;
+                const int c = n_c[k];
                 float n0 = 0.f, n1 = 0.f, n2 = 0.f, w = 0.f, rho = 0.f, gn = 0.f;
-                if (inner) {
+                if (zin && n_xy[k]) {
                     const float g0 = (sc[c + 1] - sc[c - 1]) * P.inv2h[0];
                     const float g1 = (sc[c + SX] - sc[c - SX]) * P.inv2h[1];
                     const float g2 = (sp[c] - sm[c]) * P.inv2h[2];
@@ -312,38 +343,38 @@ __global__ void __launch_bounds__(kRegThreads) sdf_reg_kernel(SdfReg P)
                     gn = sqrtf(gg);
                     w = 1.0f / (1.0f + 5.0f * fabsf(sc[c]));
                 }
-                S.n[r][0][e] = n0;
-                S.n[r][1][e] = n1;
-                S.n[r][2][e] = n2;
-                S.n[r][3][e] = w;
-                S.n[r][4][e] = rho;
-                S.n[r][5][e] = gn;
+                S.n[rc][0][e] = n0;
+                S.n[rc][1][e] = n1;
+                S.n[rc][2][e] = n2;
+                S.n[rc][3][e] = w;
+                S.n[rc][4][e] = rho;
+                S.n[rc][5][e] = gn;
             }
         }
         __syncthreads();
         // ---- G plane zg = zs - 2: Eikonal and normal adjoints w.r.t. grad s ----
         if (zs - 2 >= z0 - 1) {
             const int zg = zs - 2;
-            const int rm = ring(zg - 1), rc = ring(zg), rp = ring(zg + 1);
-            for (int e = tid; e < GY * GX; e += kRegThreads) {
-                const int gx = e % GX, gy = e / GX;
-                const int x = x0 - 1 + gx, y = y0 - 1 + gy;
-                const int c = (gy + 1) * NX + gx + 1;
-                const float rho = S.n[rc][4][c];
+            const bool zown = zg >= z0 && zg < z1;
+#pragma unroll
+            for (int k = 0; k < kPerG; ++k) {
+                if (!g_ok[k]) continue;
+                const int e = tid + k * kRegThreads;
+                const int c = g_c[k];
+                const float rho = S.n[rb][4][c];
                 float d0 = 0.f, d1 = 0.f, d2 = 0.f;
                 if (rho > 0.0f) {
-                    const bool own = x >= x0 && x < x0 + RX && y >= y0 && y < y0 + RY &&
-                                     zg >= z0 && zg < z1;
-                    const float n0 = S.n[rc][0][c], n1 = S.n[rc][1][c], n2 = S.n[rc][2][c];
-                    const float w = S.n[rc][3][c], gn = S.n[rc][5][c];
+                    const bool own = zown && g_xy[k];
+                    const float n0 = S.n[rb][0][c], n1 = S.n[rb][1][c], n2 = S.n[rb][2][c];
+                    const float w = S.n[rb][3][c], gn = S.n[rb][5][c];
                     // Eq. 12
                     const float ee = gn - 1.0f;
                     if (own) l_eik += ee * ee;
                     const float ce = gn > 0.0f ? P.lam_eik * w * 2.0f * ee / gn : 0.0f;
                     // Eq. 13: pairs (j, j + e_a) owned by j, (j - e_a, j) owned by the neighbour
                     float dn0 = 0.f, dn1 = 0.f, dn2 = 0.f;
-                    const int pr[3] = {rc, rc, rp}, po[3] = {c + 1, c + NX, c};
-                    const int mr[3] = {rc, rc, rm}, mo[3] = {c - 1, c - NX, c};
+                    const int pr[3] = {rb, rb, rc}, po[3] = {c + 1, c + NX, c};
+                    const int mr[3] = {rb, rb, ra}, mo[3] = {c - 1, c - NX, c};
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         if (S.n[pr[a]][4][po[a]] > 0.0f) {
@@ -351,16 +382,16 @@ __global__ void __launch_bounds__(kRegThreads) sdf_reg_kernel(SdfReg P)
                             const float q1 = S.n[pr[a]][1][po[a]] - n1;
                             const float q2 = S.n[pr[a]][2][po[a]] - n2;
                             if (own) l_nrm += q0 * q0 + q1 * q1 + q2 * q2;
-                            const float k = cn * w;
-                            dn0 -= k * q0;
-                            dn1 -= k * q1;
-                            dn2 -= k * q2;
+                            const float kk = cn * w;
+                            dn0 -= kk * q0;
+                            dn1 -= kk * q1;
+                            dn2 -= kk * q2;
                         }
                         if (S.n[mr[a]][4][mo[a]] > 0.0f) {
-                            const float k = cn * S.n[mr[a]][3][mo[a]];
-                            dn0 += k * (n0 - S.n[mr[a]][0][mo[a]]);
-                            dn1 += k * (n1 - S.n[mr[a]][1][mo[a]]);
-                            dn2 += k * (n2 - S.n[mr[a]][2][mo[a]]);
+                            const float kk = cn * S.n[mr[a]][3][mo[a]];
+                            dn0 += kk * (n0 - S.n[mr[a]][0][mo[a]]);
+                            dn1 += kk * (n1 - S.n[mr[a]][1][mo[a]]);
+                            dn2 += kk * (n2 - S.n[mr[a]][2][mo[a]]);
                         }
                     }
                     const float ndn = n0 * dn0 + n1 * dn1 + n2 * dn2;
@@ -376,7 +407,7 @@ __global__ void __launch_bounds__(kRegThreads) sdf_reg_kernel(SdfReg P)
             }
         }
         __syncthreads();
-        // ---- outputs at zo = zs - 3 ----
+        // ---- outputs at zo = zs - 3 (G planes zo - 1, zo, zo + 1 in ra, rb, rc) ----
         if (out) {
             const float w = 1.0f / (1.0f + 5.0f * fabsf(s_o));
             // Eq. 11
@@ -384,13 +415,16 @@ __global__ void __launch_bounds__(kRegThreads) sdf_reg_kernel(SdfReg P)
             l_sdf += r * r;
             const float own = P.lam_sdf * w * 2.0f * r;
             P.d_s_hat[io] = dsh_o - own;
-            const int c = (oy + 1) * GX + ox + 1;
-            const int rc = ring(zo);
-            const float adj = (S.g[rc][0][c - 1] - S.g[rc][0][c + 1]) * P.inv2h[0] +
-                              (S.g[rc][1][c - GX] - S.g[rc][1][c + GX]) * P.inv2h[1] +
-                              (S.g[ring(zo - 1)][2][c] - S.g[ring(zo + 1)][2][c]) * P.inv2h[2];
+            const int c = c_o;
+            const float adj = (S.g[rb][0][c - 1] - S.g[rb][0][c + 1]) * P.inv2h[0] +
+                              (S.g[rb][1][c - GX] - S.g[rb][1][c + GX]) * P.inv2h[1] +
+                              (S.g[ra][2][c] - S.g[rc][2][c]) * P.inv2h[2];
             P.d_s[io * P.d_stride] = ds_o + (own + adj);
         }
+        const int t = ra;  // rotate: this step's slots become one step back
+        ra = rb;
+        rb = rc;
+        rc = t;
     }
     block_loss(l_sdf, l_eik, l_nrm, P.loss, 3);
 }
