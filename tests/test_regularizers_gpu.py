@@ -233,3 +233,23 @@ def test_regularizer_validation():
     with pytest.raises(ps.LibraryError, match="not compiled in"):
         ps.probe_smoothness(pd, b3, b3.clone(), 1.0)
     assert ps.device_status() == 0
+
+
+def test_zero_weights_add_nothing_but_report_the_terms():
+    """With every weight 0 the gradients are left as they were (bit for bit)
+    and the unweighted loss values are still reported."""
+    dims = (33, 20, 18)
+    s, s_hat, bmin, bmax = fields(dims, 61)
+    gd, values, _ = make_grid(dims, bmin, bmax, s, 0, 0, 61)
+    _, gbytes = ps.grid_bytes(gd)
+    g = synth.rng(62)
+    grad = dev(g.normal(size=gbytes // 4))
+    d_hat = dev(g.normal(size=s.shape))
+    grad0, d_hat0 = grad.clone(), d_hat.clone()
+    loss = torch.zeros(4, dtype=torch.float32, device="cuda")
+    ps.grid_regularizers(gd, dev(s_hat), values, grad, d_hat, 0.0, 0.0, 0.0, loss=loss)
+    assert torch.equal(grad, grad0) and torch.equal(d_hat, d_hat0)
+    h = R.spacing(dims, np.float32(bmin), np.float32(bmax))
+    vals, _, _ = R.sdf_terms(s_hat, s, h, 0.0, 0.0, 0.0)
+    for i, k in enumerate(("sdf", "eik", "normal")):
+        assert abs(float(loss[i]) - vals[k]) <= LOSS_RTOL * abs(vals[k])

@@ -212,3 +212,22 @@ def test_sparse_colour_field_march_matches_oracle():
     log_errors("sparse colour field", errs)
     for k, e in errs.items():
         assert e <= RGB_DEPTH_RTOL, (k, e)
+
+
+def test_sparse_view_mode_background_and_explicit_distances():
+    sc, s, _ = sparse_case(seed=47)
+    rays = synth.make_rays("sphere64", n_rays=500, seed_offset=31)
+    from helpers import box_interval
+    g = synth.rng(13)
+    N = 40
+    tn, tf, hit = box_interval(rays.o, rays.d, sc.box_min, sc.box_max)
+    u = np.sort(g.uniform(0.0, 1.0, size=(rays.o.shape[0], N + 1)), axis=1)
+    t = (tn[:, None] + 1e-3 + u * np.maximum(tf - tn - 2e-3, 0.0)[:, None]).astype(np.float32)
+    t[~hit] = 0.0
+    bg = (0.4, 0.2, 0.6)
+    params = ps.render_params(48.0, N, ps.DIR_VIEW, sc.n_fresnel, bg)
+    rgb, depth, wsum, _ = ps.render_forward(s, dev(rays.o), dev(rays.d), params, dev(t))
+    ref = oracle_forward(sc, rays.o, rays.d, 48.0, N, dir_mode=oracle.DIR_VIEW, bg=bg,
+                         t_samples=t)
+    for k, v in (("rgb", rgb), ("depth", depth), ("wsum", wsum)):
+        assert rel_err_elementwise(v.cpu().numpy(), ref[k]) <= RGB_DEPTH_RTOL, k
