@@ -6,7 +6,9 @@
  * batch of camera rays, and its adjoint:
  *   - an explicit SDF grid, read by trilinear interpolation, with the normal
  *     taken from the SDF gradient (Sec. 3, Eq. 13);
- *   - spatial features F_s interpolated from the same grid nodes (Sec. 3.1);
+ *   - spatial features F_s interpolated from the same grid nodes, or the
+ *     product of three bilinear lookups in per-tile tri-planes (Sec. 3.1,
+ *     Sec. 4); the grid dense or stored as sparse 16^3-node bricks;
  *   - angular features F_a: spherical-harmonic coefficients stored on a
  *     coarse probe grid, blended trilinearly and evaluated in the reflected
  *     (or view) direction (Sec. 3.2, Eqs. 5-7);
@@ -14,6 +16,11 @@
  *   - a 2-hidden-layer ReLU MLP with a sigmoid output (Sec. 4);
  *   - NeuS opacities and front-to-back alpha compositing of colour, depth
  *     and accumulated weight (Sec. 3.3, Eqs. 8-10).
+ * Beside the render: the grid-level training terms (Gaussian smoothing of the
+ * raw SDF, Eikonal / normal / feature / probe smoothness, Eqs. 11-15) and an
+ * Adam step; the two-pass inference of the paper's viewer (per-view node
+ * colours, then a march over the colour field); and a learned sample proposal
+ * (not in the paper).
  *
  * Conventions for every entry point:
  *   - Every pointer marked "device" is a CUDA device pointer owned by the
