@@ -245,6 +245,20 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
+def cpu_model():
+    """The host CPU as /proc/cpuinfo names it (model name, or the Arm part)."""
+    import platform
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return platform.machine()
+    for key in ("model name", "Model", "CPU part"):
+        for line in info:
+            if line.split(":")[0].strip() == key:
+                return f"{platform.machine()} {key.lower()} {line.split(':', 1)[1].strip()}"
+    return platform.machine()
+
+
 def auto_cpu_rays(sc, rays, tau, N, threads, target_s=12.0):
     """Rays of the oracle sample sized to about target_s seconds of CPU work."""
     n = max(256, 16 * threads)
@@ -289,7 +303,7 @@ def run_reference_inference(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload]["desc"], "rays_per_step": nr},
         "cpu_baseline": {"value": ms_frame, "unit": "ms/frame", "cores": threads,
-                         "kind": "oracle",
+                         "cpu": cpu_model(), "kind": "oracle",
                          "sample": f"{nr} evenly spaced pixels of the 8 views per step, FP64 "
                                    f"uniform 256-sample forward, scaled to a frame"},
         "e2e": {"value": ms_frame, "unit": "ms/frame", "h2d_bytes_per_step": 0,
@@ -336,7 +350,7 @@ def run_reference(args, world, rank):
         "config": {"workload": WORKLOADS[args.workload]["desc"], "rays_per_step": n,
                    "samples_per_ray": N},
         "cpu_baseline": {"value": value, "unit": "samples/s", "cores": threads,
-                         "kind": "oracle", "sample": sample},
+                         "cpu": cpu_model(), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -544,7 +558,7 @@ def run_ours(args, world, rank, local):
         nr = args.cpu_rays or auto_cpu_rays(proxy, rays, tau, N, threads)
         rate, secs = oracle_rate(proxy, rays, nr, tau, N, threads)
         out["cpu_baseline"] = {"value": rate, "unit": "samples/s", "cores": threads,
-                               "kind": "oracle",
+                               "cpu": cpu_model(), "kind": "oracle",
                                "sample": f"{nr} rays x {N} samples, FP64 forward + adjoint on "
                                          f"the dense 256^3 object scene ({secs:.1f} s): the "
                                          f"oracle takes dense grids"}
@@ -555,7 +569,7 @@ def run_ours(args, world, rank, local):
         nr = args.cpu_rays or auto_cpu_rays(sc, rays, tau, N, threads)
         rate, secs = oracle_rate(sc, rays, nr, tau, N, threads)
         out["cpu_baseline"] = {"value": rate, "unit": "samples/s", "cores": threads,
-                               "kind": "oracle",
+                               "cpu": cpu_model(), "kind": "oracle",
                                "sample": f"{nr} rays x {N} samples of the same workload, FP64 "
                                          f"forward + adjoint, {secs:.1f} s"}
     print(json.dumps(out), flush=True)
@@ -912,7 +926,7 @@ def run_inference(args, world, rank, local):
                 break
             nr = int(min(n, nr * max(2.0, 10.0 / max(secs, 1e-3))))
         out["cpu_baseline"] = {"value": secs * 1e3 * (n / nr) / n_views, "unit": "ms/frame",
-                               "cores": threads, "kind": "oracle",
+                               "cores": threads, "cpu": cpu_model(), "kind": "oracle",
                                "sample": f"{nr} evenly spaced pixels of the 8 views, FP64 "
                                          f"uniform 256-sample forward, {secs:.1f} s, scaled "
                                          f"to a frame"}
