@@ -417,7 +417,8 @@ def smooth_features(dims, n_s, g: np.random.Generator, sigma_vox=3.0, std=0.1) -
     kx = np.fft.rfftfreq(Rx)[None, None, :]
     filt = np.exp(-2.0 * (np.pi * sigma_vox) ** 2 * (kx ** 2 + ky ** 2 + kz ** 2))
     for c in range(n_s):
-        f = np.fft.irfftn(np.fft.rfftn(g.normal(size=(Rz, Ry, Rx))) * filt, s=(Rz, Ry, Rx))
+        f = np.fft.irfftn(np.fft.rfftn(g.normal(size=(Rz, Ry, Rx))) * filt, s=(Rz, Ry, Rx),
+                          axes=(0, 1, 2))
         out[..., c] = (f * (std / f.std())).astype(np.float32)
     return out
 
