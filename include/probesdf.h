@@ -100,8 +100,8 @@ typedef struct psdf_grid_desc {
                             stored (> 0: empty space outside the surface); its features
                             are 0.  A sample whose 8 corners all lie in such bricks has
                             s = empty_sdf exactly.  Sparse grids are read by the render
-                            forward and adjoint, the weight histogram and the colour-field
-                            march; the occupancy build, node shading and the grid-level
+                            forward and adjoint, the occupancy build, the weight histogram,
+                            node shading and the colour-field march; the grid-level
                             training passes take dense grids only (PSDF_ERR_UNSUPPORTED) */
 } psdf_grid_desc;
 
@@ -304,7 +304,9 @@ psdf_status psdf_colour_field_bytes(const psdf_grid_desc* desc, size_t* bytes);
  * at the node (Eqs. 5-7), Fresnel inputs (Eq. 4), the MLP (Sec. 4).  The other
  * nodes get 0.  Of params only dir_mode and n_fresnel are used (the rest must
  * be valid).  band >= 0 (0 shades nothing; +inf shades every node).  Every
- * record of `colours` is written. */
+ * record of `colours` is written.  A sparse grid's colour field is still one
+ * record per node of the full grid; a node of a brick that is not stored
+ * has s = empty_sdf and zero features. */
 psdf_status psdf_shade_nodes(const psdf_grid* grid, const psdf_probes* probes,
                              const psdf_mlp* mlp, const psdf_render_params* params,
                              const float camera[3], float band, void* colours, void* stream);
@@ -411,7 +413,8 @@ psdf_status psdf_occupancy_words(const int32_t occ_res[3], int64_t* words);
 
 /* Coarse occupancy of the grid's SDF: cell c of occ_res cells along an axis
  * covers the nodes floor(c (R-1)/res) .. ceil((c+1)(R-1)/res); it is set where
- * the smallest |sdf| over them is below `threshold` (world units).
+ * the smallest |sdf| over them is below `threshold` (world units); in a
+ * sparse grid the nodes of bricks that are not stored count with empty_sdf.
  *   occ_bits : device [psdf_occupancy_words] words; cell
  *              i = (z res_y + y) res_x + x is bit (i & 31) of word i >> 5
  *              (bits past the last cell are 0). */

@@ -760,7 +760,6 @@ psdf_status psdf_shade_nodes(const psdf_grid* grid, const psdf_probes* probes,
     Resolved r;
     psdf_status st = resolve(grid, probes, mlp, params, nullptr, nullptr, nullptr, 0, r);
     if (st != PSDF_OK) return st;
-    if (sparse(&grid->desc)) return PSDF_ERR_UNSUPPORTED;
     if (!camera || !colours || !(band >= 0.0f)) return PSDF_ERR_INVALID_ARG;
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(camera[a])) return PSDF_ERR_INVALID_ARG;
@@ -981,7 +980,6 @@ psdf_status psdf_occupancy_build(const psdf_grid* grid, const int32_t occ_res[3]
     psdf::GridView g;
     psdf_status st = grid_view(grid, g);
     if (st != PSDF_OK) return st;
-    if (sparse(&grid->desc)) return PSDF_ERR_UNSUPPORTED;
     int64_t words = 0;
     st = psdf_occupancy_words(occ_res, &words);
     if (st != PSDF_OK) return st;

@@ -33,8 +33,15 @@ struct PropShape {
     static constexpr int kParams = kPW * kIn + kPW + kPW * kPW + kPW + B * kPW + B;
 };
 
-__device__ __forceinline__ float grid_sdf_node(const GridView& g, int idx)
+// SDF of node (x, y, z); in a sparse grid a node of a brick that is not
+// stored reads as empty_sdf.
+__device__ __forceinline__ float grid_sdf_node(const GridView& g, int x, int y, int z)
 {
+    if (g.table) {
+        const int64_t rec = brick_record(g, x, y, z);
+        return rec < 0 ? g.empty_sdf : __ldg(reinterpret_cast<const float*>(g.nodes + rec));
+    }
+    const int idx = (z * g.R[1] + y) * g.R[0] + x;
     return g.sdf ? __ldg(g.sdf + idx) : __ldg(reinterpret_cast<const float*>(g.nodes + idx));
 }
 
@@ -65,7 +72,7 @@ __global__ void occupancy_kernel(GridView g, int rx, int ry, int rz, float thres
             for (int iz = lo[2]; iz <= hi[2]; ++iz)
                 for (int iy = lo[1]; iy <= hi[1]; ++iy)
                     for (int ix = lo[0]; ix <= hi[0]; ++ix)
-                        mn = fminf(mn, fabsf(grid_sdf_node(g, (iz * g.R[1] + iy) * g.R[0] + ix)));
+                        mn = fminf(mn, fabsf(grid_sdf_node(g, ix, iy, iz)));
             occupied = mn < threshold;
         }
         const uint32_t word = __ballot_sync(0xffffffffu, occupied);

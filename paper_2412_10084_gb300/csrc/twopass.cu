@@ -40,8 +40,16 @@ struct ShadeLayout {
     static constexpr uint32_t kTmemCols = 64;  // layer 1 at column 0, layer 2 at 32
 };
 
+// SDF of the node with linear index i (x fastest); in a sparse grid a node of
+// a brick that is not stored reads as empty_sdf.
 __device__ __forceinline__ float node_sdf(const GridView& g, int64_t i)
 {
+    if (g.table) {
+        const int x = static_cast<int>(i % g.R[0]), y = static_cast<int>((i / g.R[0]) % g.R[1]);
+        const int z = static_cast<int>(i / (int64_t(g.R[0]) * g.R[1]));
+        const int64_t rec = brick_record(g, x, y, z);
+        return rec < 0 ? g.empty_sdf : __ldg(reinterpret_cast<const float*>(g.nodes + rec));
+    }
     return g.sdf ? __ldg(g.sdf + i) : __ldg(reinterpret_cast<const float*>(g.nodes + i));
 }
 
@@ -84,6 +92,12 @@ __device__ __forceinline__ void node_inputs(const RenderArgs& A, const ShadeArgs
         G.x[0] = bf16_lo(f.x);
         G.x[1] = bf16_hi(f.x);
         G.x[2] = bf16_lo(f.y);
+    } else if constexpr (C::SP) {
+        const int64_t rec = brick_record(g, i[0], i[1], i[2]);
+        const float4 r = rec >= 0 ? __ldg(g.nodes + rec) : make_float4(0.f, 0.f, 0.f, 0.f);
+        G.x[0] = r.y;
+        G.x[1] = r.z;
+        G.x[2] = r.w;
     } else {
         const float4 r = __ldg(g.nodes + node);
         G.x[0] = r.y;

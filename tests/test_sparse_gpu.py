@@ -165,10 +165,10 @@ def test_sparse_validation():
                                    n_bricks=3))
     with pytest.raises(ps.LibraryError, match="shape"):  # more bricks than the grid has
         ps.grid_bytes(ps.grid_desc((32, 32, 32), (0, 0, 0), (1, 1, 1), n_bricks=9))
-    with pytest.raises(ps.LibraryError, match="compiled"):
-        ps.occupancy_build(s, (8, 8, 8), 0.1)
-    with pytest.raises(ps.LibraryError, match="compiled"):
-        ps.shade_nodes(s, (2.0, 2.0, 2.0), 0.1, ps.render_params(64.0, 16, 0, sc.n_fresnel))
+    gd, _, _ = s.descs(3)
+    hat = torch.zeros(tuple(reversed(sc.dims)), dtype=torch.float32, device="cuda")
+    with pytest.raises(ps.LibraryError, match="compiled"):  # grid passes: dense grids only
+        ps.sdf_smooth(gd, hat, s.grid)
 
 
 def test_sparse_scene_from_bricks_matches_packing_from_dense_arrays():
@@ -229,5 +229,91 @@ def test_sparse_view_mode_background_and_explicit_distances():
     rgb, depth, wsum, _ = ps.render_forward(s, dev(rays.o), dev(rays.d), params, dev(t))
     ref = oracle_forward(sc, rays.o, rays.d, 48.0, N, dir_mode=oracle.DIR_VIEW, bg=bg,
                          t_samples=t)
+    for k, v in (("rgb", rgb), ("depth", depth), ("wsum", wsum)):
+        assert rel_err_elementwise(v.cpu().numpy(), ref[k]) <= RGB_DEPTH_RTOL, k
+
+
+# A node colour is FP16-rounded FP32 (as in the dense two-pass tests).
+COLOUR_ATOL = 2.0 ** -12 + 2e-5
+CAM = (1.9, -0.7, 1.4)
+
+
+@pytest.mark.parametrize("res,thr", [((8, 8, 8), 0.8), ((7, 5, 9), 2.0 / 95), ((24, 20, 28), 1.0 / 95)])
+def test_sparse_occupancy_exact(res, thr):
+    """The occupancy build reads the nodes of bricks that are not stored as
+    empty_sdf: bit-exact against the oracle on the dense-equivalent grid and
+    against the dense kernel on that grid.  thr = 0.8 lies between the
+    largest stored |s| and empty_sdf, so exactly the cells that reach a stored
+    node are set."""
+    sc, s, _ = sparse_case()
+    thr = float(np.float32(thr))
+    occ = ps.occupancy_unpack(ps.occupancy_build(s, res, thr), res).numpy()
+    ref = oracle.occupancy(oracle.Model.from_scene(sc), res, thr)
+    assert np.array_equal(occ, ref)
+    assert 0 < occ.mean() < 1
+    dense = ps.Scene.from_host(sc)
+    assert np.array_equal(occ, ps.occupancy_unpack(ps.occupancy_build(dense, res, thr),
+                                                   res).numpy())
+
+
+@pytest.mark.parametrize("mode,band", [(0, 0.08), (1, 0.08), (0, float("inf"))])
+def test_sparse_shade_parity(mode, band):
+    """Node shading through the brick table: a node of a brick that is not
+    stored has s = empty_sdf and zero features (band = inf shades them too);
+    the colour field stays one record per node of the full grid."""
+    sc, s, node_keep = sparse_case()
+    params = ps.render_params(64.0, 64, mode, sc.n_fresnel)
+    c16 = ps.shade_nodes(s, CAM, band, params)
+    assert ps.device_status() == 0
+    assert tuple(c16.shape) == tuple(reversed(sc.dims)) + (4,)
+    ref = oracle.shade_nodes(oracle.Model.from_scene(sc), CAM, band, dir_mode=mode)
+    got = c16.float().cpu().numpy()[..., :3]
+    inside = np.abs(sc.sdf.astype(np.float64)) < band
+    assert np.all(got[~inside] == 0.0)
+    if np.isinf(band):
+        assert (~node_keep).sum() > 0 and np.all(got[~node_keep] > 0.0)
+    err = float(np.abs(got - ref).max())
+    log_errors(f"sparse shade mode={mode} band={band}", {"abs": err})
+    assert err <= COLOUR_ATOL, err
+
+
+def test_sparse_two_pass_end_to_end():
+    sc, s, _ = sparse_case(seed=45)
+    band = 0.1
+    params = ps.render_params(64.0, 96, 0, sc.n_fresnel)
+    rays = synth.make_rays("sphere64", n_rays=600, seed_offset=79)
+    o, d = rays.o, rays.d
+    cam = tuple(float(v) for v in o[0])
+    c16 = ps.shade_nodes(s, cam, band, params)
+    rgb, _, wsum = ps.render_colour_field(s, c16, dev(o), dev(d), params)
+    m = oracle.Model.from_scene(sc)
+    col = oracle.shade_nodes(m, cam, band).astype(np.float16).astype(np.float64)
+    ref = oracle.render_colour_field(m, col, o, d, 64.0, 96)
+    err = float(np.abs(rgb.cpu().numpy() - ref["rgb"]).max())
+    log_errors("sparse two-pass end to end", {"rgb_abs": err})
+    assert err <= 2.0 ** -11 + 1e-5
+    np.testing.assert_allclose(wsum.cpu().numpy(), ref["wsum"], rtol=0, atol=1e-5)
+    assert float(wsum.max()) > 0.5
+
+
+def test_sparse_proposal_drives_the_render():
+    """Occupancy, proposal placement and the render, all on the sparse grid,
+    against the oracle's render of the dense-equivalent grid at the placed
+    distances."""
+    sc, s, _ = sparse_case(seed=49)
+    rays = synth.make_rays("sphere64", n_rays=400, seed_offset=93)
+    res, n_out = (16, 16, 16), 32
+    occ = ps.occupancy_build(s, res, float(np.float32(2.0 / 95)))
+    prm = synth.proposal_params(synth.rng(3), n_bins=8).astype(np.float32)
+    prm[-8 - 8 * 32:] *= 4.0
+    desc = ps.proposal_desc(res, mix=0.1, theta=0.0)
+    o_, d_ = dev(rays.o), dev(rays.d)
+    t, _ = ps.proposal_forward(s, desc, dev(prm), occ, o_, d_, n_out, want_probs=False)
+    hit = (t[:, -1] > t[:, 0]).cpu().numpy()
+    assert hit.sum() > 100
+    params = ps.render_params(64.0, n_out, n_fresnel=sc.n_fresnel)
+    rgb, depth, wsum, _ = ps.render_forward(s, o_[hit], d_[hit], params, t[hit].contiguous())
+    ref = oracle_forward(sc, rays.o[hit], rays.d[hit], 64.0, n_out,
+                         t_samples=t[hit].cpu().numpy())
     for k, v in (("rgb", rgb), ("depth", depth), ("wsum", wsum)):
         assert rel_err_elementwise(v.cpu().numpy(), ref[k]) <= RGB_DEPTH_RTOL, k
