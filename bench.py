@@ -498,9 +498,7 @@ def run_ours(args, world, rank, local):
     for p in diff:
         p.requires_grad_(False)
 
-    # the grid-level passes take dense grids
-    grid_terms = None if sparse_info else time_grid_passes(ps, scene, sc, gg, gp, masters, device,
-                                                           stream, args.steps)
+    grid_terms = time_grid_passes(ps, scene, sc, gg, gp, masters, device, stream, args.steps)
 
     if rank != 0:
         return
@@ -548,7 +546,7 @@ def run_ours(args, world, rank, local):
     if sparse_info:
         out["config"]["sparse"] = sparse_info
         out["config"]["tau"] = tau
-    if grid_terms and not args.no_cpu_baseline:
+    if grid_terms and not sparse_info and not args.no_cpu_baseline:
         out["grid_passes"]["cpu_oracle"] = oracle_grid_passes_ms(grid_terms["nodes"])
     if sparse_info and not args.no_cpu_baseline:
         # the oracle takes dense grids (the dense FP64 1024^3 model would hold 34 GB): it
@@ -591,7 +589,15 @@ def time_grid_passes(ps, scene, sc, gg, gp, masters, device, stream, steps):
     import torch
 
     gd, pd, _ = scene.descs(3)
-    s_hat = torch.as_tensor(sc.sdf, device=device).contiguous()
+    sparse = scene.n_bricks > 0
+    if sparse:
+        # the stored bricks' raw SDF starts as the scene's; the gradient buffer
+        # gets its copy of the brick table back (the steps zeroed all of it)
+        w = ps.table_words(gd)
+        s_hat = scene.grid.view(-1)[w:].view(-1, 4)[:, 0].clone().view(-1, 16, 16, 16)
+        gg.view(-1)[:w] = scene.grid.view(-1)[:w]
+    else:
+        s_hat = torch.as_tensor(sc.sdf, device=device).contiguous()
     d_hat = torch.zeros_like(s_hat)
     m_hat, v_hat = torch.zeros_like(s_hat), torch.zeros_like(s_hat)
     loss = torch.zeros(5, dtype=torch.float32, device=device)
@@ -599,7 +605,18 @@ def time_grid_passes(ps, scene, sc, gg, gp, masters, device, stream, steps):
     pd.dtype = ps.F32
     tri = scene.feat_layout == ps.FEAT_TRIPLANE
     lam = GRID_LAMBDAS
-    names = ("smooth", "regularizers", "probe_smoothness", "smooth_adjoint", "adam_sdf")
+    passes = [("smooth", lambda t: ps.sdf_smooth(gd, s_hat, scene.grid)),
+              ("regularizers", lambda t: ps.grid_regularizers(
+                  gd, s_hat, scene.grid, gg, d_hat, lam["sdf"], lam["eik"], lam["normal"],
+                  lam["features"] if tri else 0.0, loss=loss[:4])),
+              ("probe_smoothness", lambda t: ps.probe_smoothness(pd, probes, gp, lam["probes"],
+                                                                 loss=loss[4:])),
+              ("smooth_adjoint", lambda t: ps.sdf_smooth_adjoint(gd, gg, d_hat, accumulate=True)),
+              ("adam_sdf", lambda t: ps.adam_step(s_hat, d_hat, m_hat, v_hat, t, 1e-3, 0.9,
+                                                  0.995))]
+    if sparse:  # the SDF terms take dense grids
+        passes = [p for p in passes if p[0] != "regularizers"]
+    names = tuple(k for k, _ in passes)
     ev = {k: [] for k in names}
     flush = torch.empty(64 << 20, dtype=torch.float32, device=device)
 
@@ -607,17 +624,9 @@ def time_grid_passes(ps, scene, sc, gg, gp, masters, device, stream, steps):
         flush.zero_()
         marks = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
         marks[0].record(stream)
-        ps.sdf_smooth(gd, s_hat, scene.grid)
-        marks[1].record(stream)
-        ps.grid_regularizers(gd, s_hat, scene.grid, gg, d_hat, lam["sdf"], lam["eik"],
-                             lam["normal"], lam["features"] if tri else 0.0, loss=loss[:4])
-        marks[2].record(stream)
-        ps.probe_smoothness(pd, probes, gp, lam["probes"], loss=loss[4:])
-        marks[3].record(stream)
-        ps.sdf_smooth_adjoint(gd, gg, d_hat, accumulate=True)
-        marks[4].record(stream)
-        ps.adam_step(s_hat, d_hat, m_hat, v_hat, t, 1e-3, 0.9, 0.995)
-        marks[5].record(stream)
+        for i, (_, fn) in enumerate(passes):
+            fn(t)
+            marks[i + 1].record(stream)
         if record:
             for i, k in enumerate(names):
                 ev[k].append((marks[i], marks[i + 1]))
@@ -637,7 +646,8 @@ def time_grid_passes(ps, scene, sc, gg, gp, masters, device, stream, steps):
               "smooth_adjoint": 12 * nodes,               # d_s in; d_s_hat rmw
               "adam_sdf": 32 * nodes}                     # p, g, m, v in; p, g, m, v out
     return {"ms": {k: statistics.mean(a.elapsed_time(b) for a, b in ev[k]) for k in names},
-            "bytes": bytes_, "nodes": nodes, "texels": texels, "probe_coeffs": coeffs,
+            "bytes": {k: bytes_[k] for k in names}, "nodes": nodes, "texels": texels,
+            "probe_coeffs": coeffs, "sparse": sparse,
             "lambdas": lam, "sdf_stride_bytes": 16 if (scene.feat_layout == ps.FEAT_NODES and
                                                        scene.feat_dtype == ps.F32) else 4}
 
@@ -677,7 +687,9 @@ def finish_grid_passes(gt, peak):
             "unit": "GB/s", "peak": peak, "bound": "hbm", "kernels": kernels,
             "nodes": gt["nodes"], "texels": gt["texels"], "probe_coeffs": gt["probe_coeffs"],
             "sdf_slot_stride_bytes": gt["sdf_stride_bytes"], "lambdas": gt["lambdas"],
-            "note": "timed after the training step, 256 MB L2 flush before each pass set"}
+            "note": "timed after the training step, 256 MB L2 flush before each pass set"
+                    + ("; sparse grid: nodes = stored nodes, the SDF regularisers take dense "
+                       "grids and are not run" if gt["sparse"] else "")}
 
 
 # ---------------------------------------------------------------------------

@@ -101,8 +101,9 @@ typedef struct psdf_grid_desc {
                             are 0.  A sample whose 8 corners all lie in such bricks has
                             s = empty_sdf exactly.  Sparse grids are read by the render
                             forward and adjoint, the occupancy build, the weight histogram,
-                            node shading and the colour-field march; the grid-level
-                            training passes take dense grids only (PSDF_ERR_UNSUPPORTED) */
+                            node shading, the colour-field march and the SDF smoothing
+                            and its adjoint; psdf_grid_regularizers takes dense grids
+                            only (PSDF_ERR_UNSUPPORTED) */
 } psdf_grid_desc;
 
 /* Light-field probe grid (Sec. 3.2): l*l SH coefficients of n_a channels. */
@@ -340,13 +341,22 @@ psdf_status psdf_render_colour_field(const psdf_grid* grid, const void* colours,
 
 /* s = G(s_hat) written into the SDF slot of packed grid values (the layout of
  * psdf_grid_bytes; the features are not touched).  sdf_hat and the packed
- * values must not overlap. */
+ * values must not overlap.
+ * Sparse grids (n_bricks > 0): s_hat is device FP32 [n_bricks][16][16][16],
+ * the stored bricks in slot order, x fastest inside a brick.  G is that of the
+ * full grid in which every node of an absent brick holds empty_sdf (in s_hat
+ * and s alike); s is written at the stored nodes only, the table is read from
+ * packed_values. */
 psdf_status psdf_sdf_smooth(const psdf_grid_desc* desc, const float* sdf_hat, void* packed_values,
                             void* stream);
 
 /* d_sdf_hat (+)= G^T dsdf: the SDF slot of a gradient buffer (psdf_grid_bytes'
  * grad layout) taken back through the smoothing.  accumulate = 0 overwrites
- * d_sdf_hat (device FP32 [Rz][Ry][Rx]), nonzero adds to it. */
+ * d_sdf_hat (device FP32 [Rz][Ry][Rx]), nonzero adds to it.
+ * Sparse grids: d_sdf_hat is [n_bricks][16][16][16] as s_hat above; the brick
+ * table is read from the gradient buffer's copy (so a caller that zeroes the
+ * buffer zeroes its records, not the table), and the nodes of absent bricks
+ * carry no gradient (their s is fixed). */
 psdf_status psdf_sdf_smooth_adjoint(const psdf_grid_desc* desc, const void* grad_grid,
                                     float* d_sdf_hat, int32_t accumulate, void* stream);
 

@@ -667,19 +667,34 @@ def _check_dense_sdf(gd, t, what):
         raise LibraryError(f"{what}: expected a contiguous FP32 array of {n} nodes")
 
 
+def _check_sdf_param(gd, t, what):
+    """The raw SDF: [Rz,Ry,Rx] for a dense grid, [n_bricks,16,16,16] (slot
+    order) for a sparse one."""
+    if gd.n_bricks > 0:
+        n = int(gd.n_bricks) * TILE ** 3
+        if t.numel() != n or not t.is_contiguous():
+            raise LibraryError(f"{what}: expected a contiguous FP32 array of {n} stored nodes")
+    else:
+        _check_dense_sdf(gd, t, what)
+
+
 def sdf_smooth(gd, sdf_hat, values):
     """Write s = G(sdf_hat) (5^3 Gaussian, sigma = 1 node) into the SDF slot of
-    the packed grid `values`; the features are left as they are."""
+    the packed grid `values`; the features are left as they are.  For a sparse
+    grid sdf_hat holds the stored bricks, [n_bricks, 16, 16, 16] in slot order,
+    and the nodes of absent bricks count as empty_sdf."""
     _require_cuda(sdf_hat, values, dtypes=(torch.float32, torch.uint8, torch.bfloat16))
-    _check_dense_sdf(gd, sdf_hat, "sdf_smooth")
+    _check_sdf_param(gd, sdf_hat, "sdf_smooth")
     _check(library().psdf_sdf_smooth(ctypes.byref(gd), _ptr(sdf_hat), _ptr(values), _stream()),
            "psdf_sdf_smooth")
 
 
 def sdf_smooth_adjoint(gd, grad_grid, d_sdf_hat, accumulate=True):
-    """d_sdf_hat (+)= G^T of the SDF slot of a grid gradient buffer."""
+    """d_sdf_hat (+)= G^T of the SDF slot of a grid gradient buffer.  For a
+    sparse grid d_sdf_hat is [n_bricks, 16, 16, 16] and the brick table is read
+    from the gradient buffer's copy (zero only its records)."""
     _require_cuda(grad_grid, d_sdf_hat)
-    _check_dense_sdf(gd, d_sdf_hat, "sdf_smooth_adjoint")
+    _check_sdf_param(gd, d_sdf_hat, "sdf_smooth_adjoint")
     _check(library().psdf_sdf_smooth_adjoint(ctypes.byref(gd), _ptr(grad_grid), _ptr(d_sdf_hat),
                                              int(bool(accumulate)), _stream()),
            "psdf_sdf_smooth_adjoint")

@@ -845,9 +845,13 @@ psdf_status psdf_sdf_smooth(const psdf_grid_desc* desc, const float* sdf_hat, vo
 {
     const psdf_status st = check_grid_desc(desc);
     if (st != PSDF_OK) return st;
-    if (sparse(desc)) return PSDF_ERR_UNSUPPORTED;
     if (!sdf_hat || !packed_values) return PSDF_ERR_INVALID_ARG;
     if (!aligned16(sdf_hat) || !aligned16(packed_values)) return PSDF_ERR_MISALIGNED;
+    if (sparse(desc))  // table, then {sdf, f0, f1, f2} records
+        return cuda_status(psdf::launch_smooth_sparse(
+            desc->dims, static_cast<const int*>(packed_values), desc->n_bricks, sdf_hat, 0, 1,
+            static_cast<float*>(packed_values), static_cast<int64_t>(brick_table_bytes(desc) / 4),
+            4, desc->empty_sdf, false, false, static_cast<cudaStream_t>(stream)));
     return cuda_status(psdf::launch_smooth(desc->dims, sdf_hat, 1,
                                            static_cast<float*>(packed_values),
                                            sdf_value_stride(desc), false, false,
@@ -859,9 +863,14 @@ psdf_status psdf_sdf_smooth_adjoint(const psdf_grid_desc* desc, const void* grad
 {
     const psdf_status st = check_grid_desc(desc);
     if (st != PSDF_OK) return st;
-    if (sparse(desc)) return PSDF_ERR_UNSUPPORTED;
     if (!grad_grid || !d_sdf_hat) return PSDF_ERR_INVALID_ARG;
     if (!aligned16(grad_grid) || !aligned16(d_sdf_hat)) return PSDF_ERR_MISALIGNED;
+    if (sparse(desc))  // the gradient buffer's copy of the table, then its records
+        return cuda_status(psdf::launch_smooth_sparse(
+            desc->dims, static_cast<const int*>(grad_grid), desc->n_bricks,
+            static_cast<const float*>(grad_grid),
+            static_cast<int64_t>(brick_table_bytes(desc) / 4), 4, d_sdf_hat, 0, 1, 0.0f, true,
+            accumulate != 0, static_cast<cudaStream_t>(stream)));
     return cuda_status(psdf::launch_smooth(desc->dims, static_cast<const float*>(grad_grid),
                                            sdf_grad_stride(desc), d_sdf_hat, 1, true,
                                            accumulate != 0, static_cast<cudaStream_t>(stream)));

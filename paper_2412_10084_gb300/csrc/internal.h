@@ -71,6 +71,14 @@ cudaError_t launch_adam(float* p, float* g, float* m, float* v, int64_t n, float
 // with an element stride (4 in FP32 node records, 1 in a plain FP32 array).
 cudaError_t launch_smooth(const int R[3], const float* in, int in_stride, float* out,
                           int out_stride, bool transpose, bool accumulate, cudaStream_t stream);
+// s = G(s_hat) or G^T on sparse 16^3-node bricks (R a multiple of 16): the
+// stored nodes of the full grid whose absent bricks hold `empty` (forward) or
+// carry no input (transpose); node `local` of slot b at
+// buf[base + (b * 4096 + local) * stride].
+cudaError_t launch_smooth_sparse(const int R[3], const int* table, int n_bricks, const float* in,
+                                 int64_t in_base, int in_stride, float* out, int64_t out_base,
+                                 int out_stride, float empty, bool transpose, bool accumulate,
+                                 cudaStream_t stream);
 cudaError_t launch_sdf_reg(const int R[3], const float h[3], const float* s_hat, const float* s,
                            int s_stride, float lam_sdf, float lam_eik, float lam_normal,
                            float* d_s, int d_stride, float* d_s_hat, float* loss,

@@ -5,6 +5,9 @@
 //                         (32 x 8 x 8 outputs, 2-node halo) per CTA
 //   smooth_kernel<true>   G^T: the same tiles with the transposed 1D operators,
 //                         applied z, y, x (edge outputs gather the replicated taps)
+//   sparse_smooth_kernel  both on sparse 16^3-node bricks: one CTA per stored
+//                         brick, its 16^3 nodes plus a 2-node halo gathered
+//                         through the brick table into a 20^3 tile
 //   sdf_reg_kernel        L_sdf, L_Eik and L_normal on the smoothed SDF, their
 //                         gradients scaled by (1 + 5 |s|)^-1: a z-streaming
 //                         stencil whose central-difference adjoint is a gather
@@ -166,6 +169,130 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_kernel(const float* __r
             float* o = out + (((size_t)gz * Ry + gy) * Rx + gx) * out_stride;
             *o = accumulate ? *o + acc : acc;
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Sparse bricks.  The grid is the full R^3 grid in which every node of a
+// brick that is not stored holds `empty` (forward: s_hat = s = empty_sdf
+// there); G and G^T are those of the full grid, evaluated at the stored nodes
+// only.  The transposed pass has no input at absent nodes (their s is fixed,
+// so they carry no gradient) nor outside the grid.  One CTA per table entry;
+// absent entries return at once.
+// ---------------------------------------------------------------------------
+
+constexpr int SB = 16, SA = SB + 2 * HALO;  // brick edge, tile edge (20)
+constexpr int kSpTile = SA * SA * SA;       // 8000 floats
+constexpr int kSpPass = SA * SA * SB;       // 6400 floats
+constexpr int kSpThreads = 256;
+constexpr int kSpBytes = static_cast<int>(sizeof(float)) * (kSpTile + kSpPass);
+
+struct SparseSmooth {
+    const int* table;  // [B2][B1][B0]: slot, or -1 (outside [0, n_bricks) counts as absent)
+    int B[3], R[3], n_bricks;
+    const float* in;   // node `local` of slot b at in[in_base + (b * 4096 + local) * in_stride]
+    int64_t in_base;
+    int in_stride;
+    float* out;        // likewise
+    int64_t out_base;
+    int out_stride;
+    float empty;       // forward: the value of a node of an absent brick
+    int accumulate;
+};
+
+__device__ __forceinline__ int sparse_slot(const SparseSmooth& P, int bx, int by, int bz)
+{
+    const int s = __ldg(P.table + (int64_t(bz) * P.B[1] + by) * P.B[0] + bx);
+    return s >= 0 && s < P.n_bricks ? s : -1;
+}
+
+template <bool TRANSPOSE>
+__global__ void __launch_bounds__(kSpThreads) sparse_smooth_kernel(SparseSmooth P, Taps T)
+{
+    extern __shared__ float sp_smem[];
+    float* A = sp_smem;            // tile [SA][SA][SA] (z, y, x), later the y pass
+    float* Bp = sp_smem + kSpTile; // x pass [SA][SA][SB]
+    __shared__ int nb[27];         // slots of the brick and its 26 neighbours
+    const int e = blockIdx.x;
+    const int bx = e % P.B[0], by = (e / P.B[0]) % P.B[1], bz = e / (P.B[0] * P.B[1]);
+    const int slot = sparse_slot(P, bx, by, bz);
+    if (slot < 0) return;  // CTA-uniform
+    const int tid = threadIdx.x;
+    if (tid < 27) {
+        const int nx = bx + tid % 3 - 1, ny = by + (tid / 3) % 3 - 1, nz = bz + tid / 9 - 1;
+        const bool in_grid = nx >= 0 && nx < P.B[0] && ny >= 0 && ny < P.B[1] && nz >= 0 &&
+                             nz < P.B[2];
+        nb[tid] = in_grid ? sparse_slot(P, nx, ny, nz) : -1;
+    }
+    __syncthreads();
+    // ---- tile: node g = 16 b - 2 + l.  Forward: the replicated edge node
+    // outside the grid, `empty` in an absent brick.  Transposed: 0 for both ----
+    const int g0[3] = {bx * SB - HALO, by * SB - HALO, bz * SB - HALO};
+    const int b0[3] = {bx, by, bz};
+    for (int i = tid; i < kSpTile; i += kSpThreads) {
+        const int l[3] = {i % SA, (i / SA) % SA, i / (SA * SA)};
+        int g[3];
+        bool inside = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            g[a] = g0[a] + l[a];
+            inside = inside && g[a] >= 0 && g[a] < P.R[a];
+            g[a] = clampi(g[a], 0, P.R[a] - 1);
+        }
+        float v = TRANSPOSE ? 0.0f : P.empty;
+        if (!TRANSPOSE || inside) {
+            // the clamped node lies in this brick or a face / edge / corner neighbour
+            const int q = ((g[2] >> 4) - b0[2] + 1) * 9 + ((g[1] >> 4) - b0[1] + 1) * 3 +
+                          ((g[0] >> 4) - b0[0] + 1);
+            const int s = nb[q];
+            if (s >= 0) {
+                const int local = ((g[2] & 15) << 8) | ((g[1] & 15) << 4) | (g[0] & 15);
+                v = __ldg(P.in + P.in_base + (int64_t(s) * 4096 + local) * P.in_stride);
+            }
+        }
+        A[i] = v;
+    }
+    __syncthreads();
+    // ---- x: A[SA][SA][SA] -> Bp[SA][SA][SB] ----
+    for (int i = tid; i < kSpPass; i += kSpThreads) {
+        const int x = i % SB, r = i / SB;
+        const float* a = A + r * SA + x;
+        float acc = 0.0f;
+        if (TRANSPOSE) {
+            acc = tconv(a, 1, bx * SB + x, P.R[0], T);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 5; ++j) acc = fmaf(T.w[j], a[j], acc);
+        }
+        Bp[i] = acc;
+    }
+    __syncthreads();
+    // ---- y: Bp[SA][SA][SB] -> A[SA][SB][SB] ----
+    for (int i = tid; i < SA * SB * SB; i += kSpThreads) {
+        const int x = i % SB, y = (i / SB) % SB, z = i / (SB * SB);
+        const float* b = Bp + (z * SA + y) * SB + x;
+        float acc = 0.0f;
+        if (TRANSPOSE) {
+            acc = tconv(b, SB, by * SB + y, P.R[1], T);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 5; ++j) acc = fmaf(T.w[j], b[j * SB], acc);
+        }
+        A[i] = acc;
+    }
+    __syncthreads();
+    // ---- z: A[SA][SB][SB] -> the brick's 16^3 outputs ----
+    for (int i = tid; i < SB * SB * SB; i += kSpThreads) {
+        const float* a = A + i;
+        float acc = 0.0f;
+        if (TRANSPOSE) {
+            acc = tconv(a, SB * SB, bz * SB + (i >> 8), P.R[2], T);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 5; ++j) acc = fmaf(T.w[j], a[j * SB * SB], acc);
+        }
+        float* o = P.out + P.out_base + (int64_t(slot) * 4096 + i) * P.out_stride;
+        *o = P.accumulate ? *o + acc : acc;
     }
 }
 
@@ -551,6 +678,38 @@ cudaError_t launch_smooth(const int R[3], const float* in, int in_stride, float*
     else
         smooth_kernel<false><<<grid, kSmoothThreads, 0, stream>>>(in, in_stride, out, out_stride, R[0], R[1],
                                                         R[2], T, accumulate ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_smooth_sparse(const int R[3], const int* table, int n_bricks, const float* in,
+                                 int64_t in_base, int in_stride, float* out, int64_t out_base,
+                                 int out_stride, float empty, bool transpose, bool accumulate,
+                                 cudaStream_t stream)
+{
+    SparseSmooth P;
+    P.table = table;
+    int64_t entries = 1;
+    for (int a = 0; a < 3; ++a) {
+        P.R[a] = R[a];
+        P.B[a] = R[a] / SB;
+        entries *= P.B[a];
+    }
+    P.n_bricks = n_bricks;
+    P.in = in;
+    P.in_base = in_base;
+    P.in_stride = in_stride;
+    P.out = out;
+    P.out_base = out_base;
+    P.out_stride = out_stride;
+    P.empty = empty;
+    P.accumulate = accumulate ? 1 : 0;
+    if (entries < 1 || entries > 0x7fffffff) return cudaErrorInvalidValue;
+    const Taps T = gauss_taps();
+    auto kernel = transpose ? sparse_smooth_kernel<true> : sparse_smooth_kernel<false>;
+    const cudaError_t e =
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSpBytes);
+    if (e != cudaSuccess) return e;
+    kernel<<<static_cast<unsigned>(entries), kSpThreads, kSpBytes, stream>>>(P, T);
     return cudaGetLastError();
 }
 

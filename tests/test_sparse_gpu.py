@@ -34,10 +34,10 @@ def brick_mask(sdf, thr):
     return b < thr
 
 
-def sparse_case(dims=(96, 80, 112), probe_dims=(4, 4, 5), thr=0.1, sh_l=3, seed=41):
+def sparse_case(dims=(96, 80, 112), probe_dims=(4, 4, 5), thr=0.1, sh_l=3, seed=41, keep=None):
     """(dense-equivalent synth scene for the oracle, sparse ps.Scene, node mask):
-    a sphere of radius 0.22 in the unit box, bricks within thr of its surface,
-    MLP width 32 (the sparse shapes compiled in)."""
+    a sphere of radius 0.22 in the unit box, bricks within thr of its surface
+    (or the given brick mask), MLP width 32 (the sparse shapes compiled in)."""
     sc = synth.make_scene("sphere64", dims=dims, probe_dims=probe_dims)
     g = synth.rng(seed)
     sdf = synth.sphere_sdf(dims, sc.box_min, sc.box_max, (0.45, 0.5, 0.55), 0.22)
@@ -47,7 +47,8 @@ def sparse_case(dims=(96, 80, 112), probe_dims=(4, 4, 5), thr=0.1, sh_l=3, seed=
         Px, Py, Pz = probe_dims
         sc = dataclasses.replace(sc, sh_l=4, probes=g.normal(0, 0.1, size=(Pz, Py, Px, 16, 4))
                                  .astype(np.float32))
-    keep = brick_mask(sc.sdf, thr)
+    if keep is None:
+        keep = brick_mask(sc.sdf, thr)
     assert keep.any() and (~keep).any()
     s = ps.Scene.from_host(sc, bricks=keep, empty_sdf=EMPTY)
     node_keep = np.repeat(np.repeat(np.repeat(keep, 16, 0), 16, 1), 16, 2)
@@ -167,7 +168,10 @@ def test_sparse_validation():
         ps.grid_bytes(ps.grid_desc((32, 32, 32), (0, 0, 0), (1, 1, 1), n_bricks=9))
     gd, _, _ = s.descs(3)
     hat = torch.zeros(tuple(reversed(sc.dims)), dtype=torch.float32, device="cuda")
-    with pytest.raises(ps.LibraryError, match="compiled"):  # grid passes: dense grids only
+    gg, _, _ = s.grad_buffers()
+    with pytest.raises(ps.LibraryError, match="compiled"):  # the SDF terms: dense grids only
+        ps.grid_regularizers(gd, hat, s.grid, gg, torch.zeros_like(hat), 1.0, 1.0, 1.0)
+    with pytest.raises(ps.LibraryError, match="stored nodes"):  # s_hat holds the bricks
         ps.sdf_smooth(gd, hat, s.grid)
 
 
@@ -317,3 +321,74 @@ def test_sparse_proposal_drives_the_render():
                          t_samples=t[hit].cpu().numpy())
     for k, v in (("rgb", rgb), ("depth", depth), ("wsum", wsum)):
         assert rel_err_elementwise(v.cpu().numpy(), ref[k]) <= RGB_DEPTH_RTOL, k
+
+
+def brick_array(dense, keep):
+    """The stored bricks of a dense [Rz,Ry,Rx] array, [n,16,16,16] in slot order."""
+    return np.stack([dense[bz * 16:bz * 16 + 16, by * 16:by * 16 + 16, bx * 16:bx * 16 + 16]
+                     for bz, by, bx in np.argwhere(keep)])
+
+
+def random_bricks(dims, seed):
+    """About half the bricks, the grid's corner bricks always among them (so
+    the replicated edges and absent neighbours both occur)."""
+    Bx, By, Bz = (d // 16 for d in dims)
+    keep = synth.rng(seed).uniform(size=(Bz, By, Bx)) < 0.5
+    keep[0, 0, 0] = keep[-1, -1, -1] = True
+    keep[0, -1, 0] = False
+    return keep
+
+
+@pytest.mark.parametrize("dims", [(96, 80, 112), (48, 32, 64)])
+def test_sparse_smoothing_matches_the_full_grid(dims):
+    """s = G(s_hat) on a sparse grid is the full grid's smoothing, absent bricks
+    holding empty_sdf, at the stored nodes; the features are not touched and
+    absent nodes still read as empty_sdf."""
+    from oracle import regularizers as ORC
+    sc, s, node_keep = sparse_case(dims=dims, probe_dims=(3, 3, 3),
+                                   keep=random_bricks(dims, sum(dims)))
+    keep = node_keep[::16, ::16, ::16]
+    gd, _, _ = s.descs(3)
+    g = synth.rng(61)
+    hat = np.where(node_keep, sc.sdf + g.normal(0, 0.05, size=sc.sdf.shape),
+                   EMPTY).astype(np.float32)
+    values = s.grid.clone()
+    ps.sdf_smooth(gd, dev(brick_array(hat, keep)), values)
+    assert ps.device_status() == 0
+    sdf, feat = ps.unpack_grid(gd, values, which=ps.GRID_VALUES)
+    got = sdf.cpu().numpy()
+    ref = ORC.smooth(hat.astype(np.float64))
+    err = float(np.abs(got - ref)[node_keep].max())
+    log_errors(f"sparse smoothing {dims}", {"abs": err})
+    assert err <= 4e-6 * float(np.abs(hat).max())
+    assert np.all(got[~node_keep] == EMPTY)
+    assert np.array_equal(feat.cpu().numpy(), sc.feat)
+
+
+@pytest.mark.parametrize("accumulate", [False, True])
+def test_sparse_smoothing_adjoint_matches_the_full_grid(accumulate):
+    """G^T on a sparse grid: the full grid's transposed smoothing of a gradient
+    that is zero on absent bricks, at the stored nodes; the table comes from
+    the gradient buffer and the feature slots are not read."""
+    from oracle import regularizers as ORC
+    dims = (64, 48, 80)
+    sc, s, node_keep = sparse_case(dims=dims, probe_dims=(3, 3, 3), keep=random_bricks(dims, 5))
+    keep = node_keep[::16, ::16, ::16]
+    gd, _, _ = s.descs(3)
+    g = synth.rng(67)
+    ds = np.where(node_keep, g.normal(0, 1, size=sc.sdf.shape), 0.0).astype(np.float32)
+    gg, _, _ = s.grad_buffers()
+    rec = gg.view(-1)[ps.table_words(gd):].view(-1, 4)
+    rec[:, 0] = dev(brick_array(ds, keep)).reshape(-1)
+    rec[:, 1:] = 7.0
+    n = int(keep.sum())
+    base = g.normal(0, 1, size=(n, 16, 16, 16)).astype(np.float32)
+    d_hat = dev(base) if accumulate else torch.full((n, 16, 16, 16), 123.0, device="cuda")
+    ps.sdf_smooth_adjoint(gd, gg, d_hat, accumulate=accumulate)
+    assert ps.device_status() == 0
+    ref = brick_array(ORC.smooth_adjoint(ds.astype(np.float64)), keep)
+    if accumulate:
+        ref = ref + base
+    err = float(np.abs(d_hat.cpu().numpy() - ref).max())
+    log_errors(f"sparse smoothing adjoint acc={accumulate}", {"abs": err})
+    assert err <= 4e-5 * float(np.abs(ds).max())
