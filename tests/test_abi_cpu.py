@@ -132,3 +132,33 @@ def test_two_pass_entry_points_on_the_host(lib):
                                         None, None) == -1
     lib.psdf_shade_nodes.argtypes = [P, P, P, P, P, ctypes.c_float, P, P]
     assert lib.psdf_shade_nodes(None, None, None, None, None, 0.1, None, None) == -1
+
+
+def test_sparse_grid_descriptors_on_the_host(lib):
+    """Sparse (brick) descriptors: sizes, and what the host rejects before any
+    CUDA call."""
+    import paper_2412_10084_gb300 as ps
+    P = ctypes.c_void_p
+    gd = ps.grid_desc((32, 48, 64), (0, 0, 0), (1, 1, 1), n_bricks=5, empty_sdf=1.0)
+    table = ((2 * 3 * 4 * 4 + 15) // 16) * 16
+    assert ps.grid_bytes(gd) == (table + 5 * 4096 * 16,) * 2
+    assert ps.table_words(gd) * 4 == table
+    assert ps.colour_field_bytes(gd) == 8 * 32 * 48 * 64  # one record per node of the full grid
+    for kw, what in ((dict(dims=(40, 48, 64)), "shape"),            # not whole bricks
+                     (dict(n_bricks=25), "shape"),                   # more than 2 x 3 x 4
+                     (dict(feat_dtype=ps.BF16), "compiled"),         # FP32 node records only
+                     (dict(empty_sdf=float("nan")), "argument")):
+        args = dict(dims=(32, 48, 64), n_bricks=5, empty_sdf=1.0)
+        args.update(kw)
+        d = ps.grid_desc(args.pop("dims"), (0, 0, 0), (1, 1, 1), **args)
+        with pytest.raises(ps.LibraryError, match=what):
+            ps.grid_bytes(d)
+    f = ctypes.c_float
+    lib.psdf_sdf_smooth.argtypes = [P, P, P, P]
+    assert lib.psdf_sdf_smooth(ctypes.byref(gd), None, P(0x1000), None) == -1
+    assert lib.psdf_sdf_smooth(ctypes.byref(gd), P(0x1000), P(0x2008), None) == -4
+    lib.psdf_sdf_smooth_adjoint.argtypes = [P, P, P, ctypes.c_int32, P]
+    assert lib.psdf_sdf_smooth_adjoint(ctypes.byref(gd), P(0x1004), P(0x2000), 0, None) == -4
+    lib.psdf_grid_regularizers.argtypes = [P, P, P, f, f, f, f, P, P, P, P]
+    assert lib.psdf_grid_regularizers(ctypes.byref(gd), P(0x1000), P(0x2000), 1.0, 1.0, 1.0,
+                                      0.0, P(0x3000), P(0x4000), None, None) == -6
