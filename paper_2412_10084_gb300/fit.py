@@ -24,13 +24,29 @@ import dataclasses
 
 import torch
 
-from . import (F32, Adam, LibraryError, RenderParams, Scene, occupancy_build, proposal_backward,
-               proposal_desc, proposal_forward, proposal_param_count, render_backward,
-               render_forward, render_params, weight_histogram)
+from . import (F32, FEAT_TRIPLANE, Adam, LibraryError, RenderParams, Scene, occupancy_build,
+               proposal_backward, proposal_desc, proposal_forward, proposal_param_count,
+               render_backward, render_forward, render_params, table_words, weight_histogram)
 
 
 def _batch(gen, n_pool, batch, device):
     return torch.randint(0, n_pool, (batch,), generator=gen, device=device)
+
+
+def trainable_grid(gd, values, grad):
+    """Flat views of an FP32-stored grid's values and gradient that an
+    optimiser may update (a sparse grid's brick table left out), and the view
+    of the gradient's SDF entries: column 0 of the {sdf, f0, f1, f2} records,
+    or the leading FP32 SDF array of the tri-plane layout."""
+    vals, grads = values.view(-1), grad.view(-1)
+    if gd.n_bricks > 0:
+        w = table_words(gd)
+        vals, grads = vals[w:], grads[w:]
+    if gd.feat_layout == FEAT_TRIPLANE:
+        sdf = grads[:int(gd.dims[0]) * int(gd.dims[1]) * int(gd.dims[2])]
+    else:
+        sdf = grads.view(-1, 4)[:, 0]
+    return vals, grads, sdf
 
 
 def fit_appearance(scene: Scene, rays_o, rays_d, target, params: RenderParams, steps=200,
@@ -41,7 +57,8 @@ def fit_appearance(scene: Scene, rays_o, rays_d, target, params: RenderParams, s
         raise LibraryError("fit_appearance trains FP32 storage; convert afterwards")
     dev = scene.grid.device
     gg, gp, gm = scene.grad_buffers()
-    opt = Adam([(scene.grid.view(-1), gg.view(-1), lr_grid),
+    grid_vals, grid_grads, sdf_grads = trainable_grid(scene.descs(3)[0], scene.grid, gg)
+    opt = Adam([(grid_vals, grid_grads, lr_grid),
                 (scene.probes.view(-1), gp.view(-1), lr_probes),
                 (scene.mlp.view(-1), gm.view(-1), lr_mlp)])
     gen = torch.Generator(device=dev)
@@ -57,7 +74,7 @@ def fit_appearance(scene: Scene, rays_o, rays_d, target, params: RenderParams, s
         render_backward(scene, o, d, params, d_rgb.contiguous(), logT, grads=(gg, gp, gm),
                         n_live=live)
         if not train_sdf:
-            gg[:, 0].zero_()
+            sdf_grads.zero_()
         opt.step()
         if step % log_every == 0 or step == steps:
             log.append((step, float((diff * diff).sum(1).mean())))
