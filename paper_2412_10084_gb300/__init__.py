@@ -552,13 +552,20 @@ class RenderFunction(torch.autograd.Function):
         gg, gp, gm = render_backward(ctx.scene, rays_o, rays_d, ctx.params, d_rgb, logT,
                                      d_depth=d_depth, d_wsum=d_wsum, t_samples=t_samples,
                                      grid=grid, probes=probes, mlp=mlp, n_live=live)
+        if ctx.scene.n_bricks > 0:
+            # a sparse grid's brick table is not a parameter: zero gradient there
+            # (the buffer came with a copy of the table bits, which are no gradient)
+            gg.view(-1)[:table_words(ctx.scene.descs(ctx.params.n_fresnel)[0])] = 0.0
         return gg, gp, gm, None, None, None, None, None
 
 
 def render(scene: Scene, rays_o, rays_d, params: RenderParams, t_samples=None, masters=None):
     """Differentiable w.r.t. the scene's FP32 parameters: scene.grid,
     scene.probes and scene.mlp, or, for reduced-precision storage, the FP32
-    masters=(grid [R^3,4], probes) that the storage was packed from."""
+    masters=(grid [R^3,4], probes) that the storage was packed from.  On a
+    sparse grid the brick table at the front of scene.grid gets zero gradient;
+    keep it out of any update that changes parameters without a gradient
+    (weight decay)."""
     grid_p, probes_p = (scene.grid, scene.probes) if masters is None else masters
     return RenderFunction.apply(grid_p, probes_p, scene.mlp, rays_o, rays_d, t_samples, scene,
                                 params)

@@ -1,4 +1,4 @@
-"""Host logic of the training loops (no GPU): which parts of a packed grid
+"""Host logic of training (no GPU): which parts of a packed grid
 the optimiser updates and where the gradient's SDF entries sit, in every
 FP32 grid layout."""
 import torch
@@ -45,3 +45,21 @@ def test_triplanes_sdf_array_first():
     sdf.zero_()
     flat = grad.view(-1)
     assert float(flat[:n].abs().sum()) == 0 and bool((flat[n:] == 1).all())
+
+
+def test_autograd_gives_a_sparse_brick_table_zero_gradient(monkeypatch):
+    """The gradient buffer of a sparse grid starts with a copy of the table's
+    bits (for unpacking); the autograd gradient of scene.grid must not carry
+    them (as floats, a -1 entry is a NaN)."""
+    import types
+    gd = ps.grid_desc((32, 16, 16), (0, 0, 0), (1, 1, 1), n_bricks=1, empty_sdf=1.0)
+    _, gb = ps.grid_bytes(gd)
+    w = ps.table_words(gd)
+    gg = torch.full((gb // 4,), float("nan"))
+    monkeypatch.setattr(ps, "render_backward", lambda *a, **k: (gg, None, None))
+    scene = types.SimpleNamespace(n_bricks=1, descs=lambda n_fresnel: (gd, None, None))
+    empty = torch.empty(0)
+    ctx = types.SimpleNamespace(saved_tensors=(empty,) * 6, storage=(None, None), has_t=False,
+                                scene=scene, params=types.SimpleNamespace(n_fresnel=3))
+    d_grid = ps.RenderFunction.backward(ctx, torch.zeros(0, 3), None, None)[0]
+    assert bool((d_grid[:w] == 0).all()) and bool(d_grid[w:].isnan().all())
