@@ -244,8 +244,13 @@ def pack_sparse(desc: GridDesc, table, sdf: torch.Tensor, feat: torch.Tensor) ->
     table [Bz,By,Bx] (slots 0..n_bricks-1 or -1): packed float32 [bytes/16, 4]."""
     _require_cuda(sdf, feat)
     nbytes, _ = grid_bytes(desc)
+    shape = tuple(int(desc.dims[a]) // TILE for a in (2, 1, 0))
+    tab = torch.as_tensor(table, dtype=torch.int32)
+    if tuple(tab.shape) != shape:
+        raise LibraryError(f"pack_sparse: the brick table must be {shape} (Bz, By, Bx), "
+                           f"got {tuple(tab.shape)}")
     out = torch.zeros(nbytes // 4, dtype=torch.float32, device=sdf.device)
-    tab = torch.as_tensor(table, dtype=torch.int32).reshape(-1).to(sdf.device)
+    tab = tab.reshape(-1).to(sdf.device)
     out[:tab.numel()] = tab.view(torch.float32)
     out = out.view(-1, 4)
     _check(library().psdf_grid_pack(ctypes.byref(desc), _ptr(sdf), _ptr(feat), _ptr(out),
@@ -334,7 +339,9 @@ class Scene:
         return gd, pd, md
 
     def grad_buffers(self):
-        """Zeroed FP32 gradient buffers: grid [R^3, 4], probes, MLP."""
+        """Zeroed FP32 gradient buffers: the grid's in its packed gradient
+        layout ([R^3, 4] node records; a sparse grid's starts with a copy of
+        the brick table), probes, MLP."""
         gd, _, _ = self.descs(3)
         _, gbytes = grid_bytes(gd)
         dev = self.mlp.device
@@ -389,6 +396,10 @@ def sparse_scene(keep, brick_sdf, brick_feat, probes, mlp, dims, box_min, box_ma
     copies: the table, then one {sdf, f0, f1, f2} record per stored node."""
     dev = torch.device(device)
     table = brick_table(keep)
+    shape = tuple(int(dims[a]) // TILE for a in (2, 1, 0))
+    if tuple(table.shape) != shape:
+        raise LibraryError(f"sparse_scene: keep must be {shape} (Bz, By, Bx), "
+                           f"got {tuple(table.shape)}")
     n = int((table >= 0).sum())
     gd = grid_desc(dims, box_min, box_max, 3, F32, FEAT_NODES, n, empty_sdf)
     nbytes, _ = grid_bytes(gd)

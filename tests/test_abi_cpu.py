@@ -162,3 +162,12 @@ def test_sparse_grid_descriptors_on_the_host(lib):
     lib.psdf_grid_regularizers.argtypes = [P, P, P, f, f, f, f, P, P, P, P]
     assert lib.psdf_grid_regularizers(ctypes.byref(gd), P(0x1000), P(0x2000), 1.0, 1.0, 1.0,
                                       0.0, P(0x3000), P(0x4000), None, None) == -6
+
+
+def test_sparse_scene_checks_the_brick_mask_shape():
+    import numpy as np
+    import paper_2412_10084_gb300 as ps
+    keep = np.ones((2, 3, 4), bool)  # (Bz, By, Bx) of a 64 x 48 x 32 grid, given for 32 x 48 x 64
+    with pytest.raises(ps.LibraryError, match=r"\(4, 3, 2\)"):
+        ps.sparse_scene(keep, None, None, None, None, (32, 48, 64), (0, 0, 0), (1, 1, 1), 3, 32,
+                        device="cpu")
