@@ -106,6 +106,9 @@ def parse():
     ap.add_argument("--rays", type=int, default=0, help="rays per step (0 = the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rays", type=int, default=0, help="rays of the oracle sample (0 = auto)")
+    ap.add_argument("--no-inference", action="store_true",
+                    help="object256: skip the 1080p inference leg (ms per frame at matched "
+                         "PSNR; also skipped when --rays sets a batch of another size)")
     return ap.parse_args()
 
 
@@ -126,6 +129,15 @@ def captured_traffic(workload, kernel, rays):
         return int(w[kernel]["read"] + w[kernel]["write"])
     except (OSError, ValueError, KeyError, ImportError):
         return None
+
+
+def dram_rate(traffic, launch_ms, peak):
+    """Measured DRAM rate of a kernel (ncu bytes per launch over its CUDA-event
+    time) beside the algorithmic figure, when the capture matches the sources."""
+    if traffic is None:
+        return {"measured_dram_gbs": None, "measured_dram_frac": None}
+    gbs = traffic / (launch_ms * 1e-3) / 1e9
+    return {"measured_dram_gbs": gbs, "measured_dram_frac": gbs / peak}
 
 
 def measured_peaks():
@@ -462,6 +474,9 @@ def run_ours(args, world, rank, local):
     barrier(world, device)
     elapsed_ms = start.elapsed_time(stop)
     clk = clocks.stop()
+    # a render kernel that gave up waiting on its tensor-core work returns early
+    # (shorter launch, partial gradients): such a run is not a measurement
+    dev_status = ps.device_status()
     elapsed_ms = reduce_max(elapsed_ms, world, device)
     fwd_ms = statistics.mean(a.elapsed_time(b) for a, b in ev["fwd0"])
     bwd_ms = statistics.mean(a.elapsed_time(b) for a, b in ev["bwd1"])
@@ -495,16 +510,19 @@ def run_ours(args, world, rank, local):
         e2e_step()
     torch.cuda.synchronize(device)
     e2e_s = reduce_max(time.perf_counter() - t0, world, device)
+    dev_status |= ps.device_status()
     for p in diff:
         p.requires_grad_(False)
 
     grid_terms = time_grid_passes(ps, scene, sc, gg, gp, masters, device, stream, args.steps)
 
     if rank != 0:
-        return
+        return None
     peak, peak_kind = measured_peaks()
     bwd_gbs = BYTES_BWD * samples / (bwd_ms * 1e-3) / 1e9
     fwd_gbs = BYTES_FWD * samples / (fwd_ms * 1e-3) / 1e9
+    bwd_traffic = captured_traffic(args.workload, "render_backward_kernel", n)
+    fwd_traffic = captured_traffic(args.workload, "render_forward_kernel", n)
     ms_per_step = elapsed_ms / args.steps
     value = world * samples / (ms_per_step * 1e-3)
     step_gbs = BYTES_STEP * samples / (ms_per_step * 1e-3) / 1e9
@@ -522,16 +540,14 @@ def run_ours(args, world, rank, local):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": "render_backward_kernel",
                      "achieved": bwd_gbs, "peak": peak, "unit": "GB/s",
-                     "frac": bwd_gbs / peak,
-                     "traffic": captured_traffic(args.workload, "render_backward_kernel", n),
+                     "frac": bwd_gbs / peak, "traffic": bwd_traffic,
                      "bytes_per_sample": BYTES_BWD, "peak_kind": peak_kind,
-                     "launch_ms": bwd_ms},
+                     "launch_ms": bwd_ms, **dram_rate(bwd_traffic, bwd_ms, peak)},
         "roofline_forward": {"bound": "hbm", "kernel": "render_forward_kernel",
                              "achieved": fwd_gbs, "peak": peak, "unit": "GB/s",
                              "frac": fwd_gbs / peak, "bytes_per_sample": BYTES_FWD,
-                             "traffic": captured_traffic(args.workload, "render_forward_kernel",
-                                                         n),
-                             "launch_ms": fwd_ms},
+                             "traffic": fwd_traffic, "launch_ms": fwd_ms,
+                             **dram_rate(fwd_traffic, fwd_ms, peak)},
         "roofline_step": {"achieved": step_gbs, "peak": peak, "unit": "GB/s",
                           "frac": step_gbs / peak, "bytes_per_sample": BYTES_STEP},
         "e2e": {"value": world * samples / (e2e_s / args.steps), "unit": "samples/s",
@@ -542,7 +558,12 @@ def run_ours(args, world, rank, local):
         "gpu_launches": 2 * args.steps,
         "rays_per_s": world * n / (ms_per_step * 1e-3),
         "grid_passes": finish_grid_passes(grid_terms, peak) if grid_terms else None,
+        "device_status": dev_status,
     }
+    if dev_status:
+        out["failed"] = (f"device status {dev_status:#x}: a render kernel stopped waiting on "
+                         f"its tensor-core work and returned early; not a measurement")
+        out["value"] = None
     if sparse_info:
         out["config"]["sparse"] = sparse_info
         out["config"]["tau"] = tau
@@ -570,7 +591,7 @@ def run_ours(args, world, rank, local):
                                "cpu": cpu_model(), "kind": "oracle",
                                "sample": f"{nr} rays x {N} samples of the same workload, FP64 "
                                          f"forward + adjoint, {secs:.1f} s"}
-    print(json.dumps(out), flush=True)
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -614,8 +635,6 @@ def time_grid_passes(ps, scene, sc, gg, gp, masters, device, stream, steps):
               ("smooth_adjoint", lambda t: ps.sdf_smooth_adjoint(gd, gg, d_hat, accumulate=True)),
               ("adam_sdf", lambda t: ps.adam_step(s_hat, d_hat, m_hat, v_hat, t, 1e-3, 0.9,
                                                   0.995))]
-    if sparse:  # the SDF terms take dense grids
-        passes = [p for p in passes if p[0] != "regularizers"]
     names = tuple(k for k, _ in passes)
     ev = {k: [] for k in names}
     flush = torch.empty(64 << 20, dtype=torch.float32, device=device)
@@ -878,9 +897,10 @@ def run_inference(args, world, rank, local):
     for _ in range(args.steps):
         e2e()
     e2e_s = reduce_max((time.perf_counter() - t0) / args.steps, world, device)
+    dev_status = ps.device_status()
 
     if rank != 0:
-        return
+        return None
     peak, peak_kind = measured_peaks()
     bfwd, _ = bytes_per_sample(wl["feat"])
     samples = n * chosen
@@ -922,7 +942,12 @@ def run_inference(args, world, rank, local):
         "gpu_launches": 2 * args.steps,
         "training": {"appearance_l2": [fit_log[0][1], fit_log[-1][1]],
                      "proposal_ce": [prop_log[0][1], prop_log[-1][1]], "setup_s": setup_s},
+        "device_status": dev_status,
     }
+    if dev_status:
+        out["failed"] = (f"device status {dev_status:#x}: a render kernel stopped waiting on "
+                         f"its tensor-core work and returned early; not a measurement")
+        out["value"] = None
     if not args.no_cpu_baseline:
         import oracle
         threads = cpu_cores()
@@ -962,7 +987,7 @@ def run_inference(args, world, rank, local):
             "sample": f"{pick.size} of {inside.size} band nodes shaded and {nv} evenly spaced "
                       f"pixels of one view marched ({bf['samples']} uniform samples) by the "
                       f"single-threaded FP64 oracle, scaled to the view"}
-    print(json.dumps(out), flush=True)
+    return out
 
 
 def sc_fitted(scene, sc):
@@ -977,18 +1002,62 @@ def sc_fitted(scene, sc):
                                mlp=scene.mlp.cpu().numpy())
 
 
+def inference_summary(inf):
+    """Key figures of the 1080p inference leg for the training-step line."""
+    ch = inf["config"]["chosen_samples"]
+    form = inf["proposal_forms"][str(ch)]
+    tp = inf["two_pass"]
+    return {
+        "metric": INFER_METRIC, "unit": "ms/frame", "value": inf["value"],
+        "workload": inf["config"]["workload"], "matched": inf["config"]["matched"],
+        "chosen_samples": ch,
+        "reduced_proposal": {"ms_per_frame": form["ms_per_frame"], "psnr_db": form["psnr_db"],
+                             "depth_mae_vs_ref": form["depth_mae_vs_ref"]},
+        "uniform256_fp32": inf["uniform256_fp32"],
+        "speedup_vs_uniform256": inf["speedup_vs_uniform256"],
+        "kernels_ms": inf["kernels_ms"], "roofline": inf["roofline"], "e2e": inf["e2e"],
+        "two_pass": {k: tp[k] for k in ("chosen", "matched", "ms_per_frame", "psnr_db",
+                                        "speedup_vs_uniform256", "kernels_ms_per_view")},
+        "two_pass_forms": {k: {"ms_per_frame": v["ms_per_frame"], "psnr_db": v["psnr_db"]}
+                           for k, v in tp["forms"].items()},
+        "cpu_baseline": inf.get("cpu_baseline"), "clocks": inf["clocks"],
+        "gpu_launches": inf["gpu_launches"], "training": inf["training"],
+        "device_status": inf["device_status"],
+    }
+
+
+def emit(out):
+    if out is None:
+        return 0
+    print(json.dumps(out), flush=True)
+    return 1 if out.get("failed") else 0
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
+    rc = 0
     if args.impl == "reference":
         run_reference(args, world, rank)
     elif args.workload == "inference1080":
-        run_inference(args, world, rank, local)
+        rc = emit(run_inference(args, world, rank, local))
     else:
-        run_ours(args, world, rank, local)
+        out = run_ours(args, world, rank, local)
+        if args.workload == "object256" and not args.no_inference and not args.rays:
+            # the metric's second half: ms per 1080p frame at matched PSNR, same process
+            inf = run_inference(argparse.Namespace(**{**vars(args), "workload": "inference1080"}),
+                                world, rank, local)
+            if out is not None and inf is not None:
+                out["inference1080"] = inference_summary(inf)
+                out["ms_per_1080p_frame_at_matched_psnr"] = inf["value"]
+                if inf.get("failed"):
+                    out["failed"] = inf["failed"]
+                    out["value"] = None
+        rc = emit(out)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+    sys.exit(rc)
 
 
 if __name__ == "__main__":

@@ -101,9 +101,8 @@ typedef struct psdf_grid_desc {
                             are 0.  A sample whose 8 corners all lie in such bricks has
                             s = empty_sdf exactly.  Sparse grids are read by the render
                             forward and adjoint, the occupancy build, the weight histogram,
-                            node shading, the colour-field march and the SDF smoothing
-                            and its adjoint; psdf_grid_regularizers takes dense grids
-                            only (PSDF_ERR_UNSUPPORTED) */
+                            node shading, the colour-field march, the SDF smoothing
+                            and its adjoint, and the SDF regularisers */
 } psdf_grid_desc;
 
 /* Light-field probe grid (Sec. 3.2): l*l SH coefficients of n_a channels. */
@@ -157,6 +156,17 @@ int32_t psdf_version(void);
  * record the condition here and return. */
 psdf_status psdf_device_status(void* stream, int32_t* flags);
 
+/* How many times each kernel launched afterwards from this host thread polls
+ * a tensor-core completion (an mbarrier phase) before it gives up, records
+ * bit 0 of the device status word, frees its tensor memory and returns
+ * (after one more wait of the default length for the work already issued).
+ * Default 2^24; 0xFFFFFFFF restores it.  A small value makes the waits run
+ * out on purpose (a test of that path: every output of such a launch is then
+ * invalid); the default is long enough that a wait only runs out when the
+ * tensor core stops answering.  Thread-local, like psdf_last_cuda_error. */
+psdf_status psdf_set_wait_polls(uint32_t polls);
+uint32_t psdf_wait_polls(void);
+
 /* Bytes of the packed grid values and of the grid gradient buffer.
  * Values, PSDF_F32 features: one 16-byte record {sdf, f0, f1, f2} per node.
  * Values, PSDF_BF16 features: an FP32 SDF array, then (at the next 16-byte
@@ -169,8 +179,11 @@ psdf_status psdf_device_status(void* stream, int32_t* flags);
  * [Bz][By][Bx] (B_a = dims_a / 16; entry = the brick's slot in 0..n_bricks-1,
  * or -1 when it is not stored; padded to 16 bytes), then n_bricks blocks of
  * 16^3 FP32 node records {sdf, f0, f1, f2}, x fastest inside a block.  The
- * caller writes the table (the gradient buffer's table region is unused); a
- * slot must not appear twice.
+ * caller writes the table (the gradient buffer's table region is unused); each
+ * slot in [0, n_bricks) may appear at most once (two entries naming one slot
+ * would alias one record block: pack would write it from two threads at once
+ * and the adjoint would add both bricks' gradients into it).  The library does
+ * not check this: the table stays in device memory.
  * Node order is x fastest. */
 psdf_status psdf_grid_bytes(const psdf_grid_desc* desc, size_t* values_bytes, size_t* grad_bytes);
 
@@ -369,12 +382,20 @@ psdf_status psdf_sdf_smooth_adjoint(const psdf_grid_desc* desc, const void* grad
  *                between neighbouring texels, rows and columns     (Eq. 14)
  * The gradient of lam_sdf L_sdf + lam_eik L_Eik + lam_normal L_normal, each
  * voxel's term scaled by w_i = (1 + 5 |s_i|)^-1 (held fixed, not differentiated;
- * Sec. 3.3), is ADDED to the SDF slot of grad_grid (w.r.t. s, with atomics) and
+ * Sec. 3.3), is ADDED to the SDF slot of grad_grid (w.r.t. s) and
  * to d_sdf_hat (w.r.t. s_hat directly); lam_features * L_features' gradient is
  * added to the planes of grad_grid.  lam_features > 0 needs PSDF_FEAT_TRIPLANE
  * (PSDF_ERR_UNSUPPORTED otherwise).  All weights >= 0.
  *   loss : device FP32 [4] or NULL; {L_sdf, L_Eik, L_normal, L_features}
- *          (unweighted) are ADDED to it. */
+ *          (unweighted) are ADDED to it.
+ * Sparse grids (n_bricks > 0): s_hat and d_sdf_hat are [n_bricks][16][16][16]
+ * as for psdf_sdf_smooth; s is that of the full grid in which every node of
+ * an absent brick holds empty_sdf (the table is read from packed_values), and
+ * the sums run over the stored nodes: the terms a stored node owns (its
+ * L_sdf and L_Eik, and its L_normal pairs with the next node along each axis,
+ * whose normal may come from absent nodes' empty_sdf), with gradients added
+ * at the stored nodes only (an absent node's s is not a parameter).  The
+ * grid's faces are the full grid's. */
 psdf_status psdf_grid_regularizers(const psdf_grid_desc* desc, const float* sdf_hat,
                                    const void* packed_values, float lam_sdf, float lam_eik,
                                    float lam_normal, float lam_features, void* grad_grid,

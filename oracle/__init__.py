@@ -81,6 +81,8 @@ class _Params(ctypes.Structure):
         ("n_samples", ctypes.c_int32),
         ("dir_mode", ctypes.c_int32),
         ("bg", ctypes.c_double * 3),
+        ("sdf_fp32", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -205,19 +207,23 @@ class Model:
                    sc.width, sc.n_fresnel, planes=getattr(sc, "planes", None))
 
 
-def _params(tau, n_samples, dir_mode=DIR_REFLECT, bg=(0.0, 0.0, 0.0)):
+def _params(tau, n_samples, dir_mode=DIR_REFLECT, bg=(0.0, 0.0, 0.0), sdf_fp32=False):
     p = _Params()
     p.tau = float(tau)
     p.n_samples = int(n_samples)
     p.dir_mode = int(dir_mode)
     p.bg[:] = tuple(float(v) for v in bg)
+    p.sdf_fp32 = int(bool(sdf_fp32))
     return p
 
 
 def render_forward(model: Model, rays_o, rays_d, tau, n_samples, dir_mode=DIR_REFLECT,
-                   bg=(0.0, 0.0, 0.0), t_samples=None, n_threads=1, margin=False):
+                   bg=(0.0, 0.0, 0.0), t_samples=None, n_threads=1, margin=False,
+                   sdf_fp32=False):
     """rgb [n,3], depth [n], wsum [n], logT_final [n] (and the per-ray
-    smallest relative distance to a ReLU or alpha-clip kink if asked)."""
+    smallest relative distance to a ReLU or alpha-clip kink if asked).
+    sdf_fp32: the SDF at each point rounded as the FP32 evaluation rounds it
+    (everything else in FP64), to isolate that rounding in a comparison."""
     lib = _load()
     o, d = _f32(rays_o).reshape(-1, 3), _f32(rays_d).reshape(-1, 3)
     n = o.shape[0]
@@ -225,7 +231,7 @@ def render_forward(model: Model, rays_o, rays_d, tau, n_samples, dir_mode=DIR_RE
     rgb = np.zeros((n, 3))
     depth, wsum, logT = np.zeros(n), np.zeros(n), np.zeros(n)
     mg = np.full(n, np.inf) if margin else None
-    p = _params(tau, n_samples, dir_mode, bg)
+    p = _params(tau, n_samples, dir_mode, bg, sdf_fp32)
     st = lib.orc_render_forward(ctypes.byref(model._s), ctypes.byref(p), n, _ptr(o), _ptr(d),
                                 _ptr(ts), _ptr(rgb), _ptr(depth), _ptr(wsum), _ptr(logT),
                                 _ptr(mg), int(n_threads))
@@ -330,15 +336,16 @@ def render_trace(model: Model, o, d, tau, n_samples, dir_mode=DIR_REFLECT, t_sam
     return {"hit": bool(hit), "t": t, "s": s, "w": w, "C": C, "normal": nrm}
 
 
-def point_eval(model: Model, o, d, t, dir_mode=DIR_REFLECT):
-    """SDF value, gradient, MLP input vector and colour at the point o + t d."""
+def point_eval(model: Model, o, d, t, dir_mode=DIR_REFLECT, sdf_fp32=False):
+    """SDF value, gradient, MLP input vector and colour at the point o + t d
+    (sdf_fp32: the SDF value rounded as the FP32 evaluation rounds it)."""
     lib = _load()
     o, d = _f32(o).reshape(3), _f32(d).reshape(3)
     s = np.zeros(1)
     g = np.zeros(3)
     x = np.zeros(model.n_s + model.n_a + model.n_fresnel)
     C = np.zeros(3)
-    p = _params(1.0, 1, dir_mode)
+    p = _params(1.0, 1, dir_mode, sdf_fp32=sdf_fp32)
     st = lib.orc_point_eval(ctypes.byref(model._s), ctypes.byref(p), _ptr(o), _ptr(d),
                             ctypes.c_float(t), _ptr(s), _ptr(g), _ptr(x), _ptr(C))
     if st != 0:

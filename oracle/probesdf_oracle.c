@@ -399,6 +399,21 @@ static void eval_point(const orc_model* m, const orc_params* p, const float o[3]
         if (color && m->feat_layout == ORC_FEAT_NODES)
             for (int q = 0; q < ns; ++q) S->x[q] += w * m->feat[nd * (size_t)ns + q];
     }
+    if (p->sdf_fp32) {
+        /* the same value rounded as a FP32 evaluation rounds it: corner weights
+         * as products of (1 - f) and f in FP32, then a fused multiply-add per
+         * corner in corner order (the fractions are exact in FP32) */
+        const float fx = (float)S->cf[0], fy = (float)S->cf[1], fz = (float)S->cf[2];
+        const float wx[2] = {1.0f - fx, fx}, wy[2] = {1.0f - fy, fy}, wz[2] = {1.0f - fz, fz};
+        float s32 = 0.0f;
+        for (int c = 0; c < 8; ++c) {
+            const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
+            const float w32 = wx[cx] * wy[cy] * wz[cz];
+            const size_t nd = node_index(m->R, S->ci[0] + cx, S->ci[1] + cy, S->ci[2] + cz);
+            s32 = fmaf(w32, (float)m->sdf[nd], s32);
+        }
+        S->s = (double)s32;
+    }
     if (!color) return;
     if (m->feat_layout == ORC_FEAT_TRIPLANE) {
         tri_at T;

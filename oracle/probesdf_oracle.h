@@ -46,6 +46,11 @@ typedef struct orc_params {
     int32_t n_samples;     /* N colour samples, N+1 SDF points */
     int32_t dir_mode;      /* ORC_DIR_REFLECT or ORC_DIR_VIEW */
     double bg[3];          /* background colour */
+    int32_t sdf_fp32;      /* 1: the SDF value at a point by the FP32 sequence of the
+                              render kernels (weights and fused multiply-adds in FP32,
+                              corner order x fastest) instead of FP64; only tests that
+                              isolate FP32 rounding of s set it */
+    int32_t reserved;
 } orc_params;
 
 void orc_sh_eval(int32_t l, const double r[3], double* Y);

@@ -119,17 +119,22 @@ def spacing(dims, box_min, box_max):
                      for a in range(3)])
 
 
-def sdf_terms(s_hat, s, h, lam_sdf, lam_eik, lam_normal, weights=None):
+def sdf_terms(s_hat, s, h, lam_sdf, lam_eik, lam_normal, weights=None, owner=None):
     """Per-voxel terms on the smoothed s.  Returns the three loss values, the
     weighted objective sum_i w_i (lam_sdf sdf_i + lam_eik eik_i + lam_normal
     normal_i) whose gradient the two arrays are (w.r.t. s, and w.r.t. s_hat
-    directly), with w_i = (1 + 5 |s_i|)^-1 (or the given weights, held fixed)."""
+    directly), with w_i = (1 + 5 |s_i|)^-1 (or the given weights, held fixed).
+    owner (bool, the grid's shape, default all): only the voxels it marks
+    contribute their terms (their sdf_i, eik_i and the normal pairs they own);
+    the others still enter those terms as neighbours (a sparse grid's absent
+    nodes, whose s is fixed)."""
     s_hat = np.asarray(s_hat, np.float64)
     s = np.asarray(s, np.float64)
     wv = voxel_weight(s) if weights is None else np.asarray(weights, np.float64)
+    own = np.ones(s.shape, bool) if owner is None else np.asarray(owner, bool)
     inner = _interior(s.shape)
     # L_sdf
-    r = s - s_hat
+    r = (s - s_hat) * own
     l_sdf = float(np.sum(r * r))
     objective = lam_sdf * float(np.sum(wv * r * r))
     ds = lam_sdf * wv * 2 * r
@@ -137,7 +142,7 @@ def sdf_terms(s_hat, s, h, lam_sdf, lam_eik, lam_normal, weights=None):
     # L_Eik on interior nodes
     g = _central_grad(s, h)
     gn = np.sqrt(np.sum(g * g, axis=0))
-    e = np.where(inner, gn - 1.0, 0.0)
+    e = np.where(inner & own, gn - 1.0, 0.0)
     l_eik = float(np.sum(e * e))
     objective += lam_eik * float(np.sum(wv * e * e))
     unit = g / np.maximum(gn, 1e-300)
@@ -156,7 +161,7 @@ def sdf_terms(s_hat, s, h, lam_sdf, lam_eik, lam_normal, weights=None):
         lo[2 - a] = slice(0, -1)
         hi[2 - a] = slice(1, None)
         lo, hi = tuple(lo), tuple(hi)
-        both = inner[lo] & inner[hi]
+        both = inner[lo] & inner[hi] & own[lo]
         diff = (n[(slice(None),) + hi] - n[(slice(None),) + lo]) * both[None]
         l_norm += float(np.sum(diff * diff))
         objective += lam_normal * float(np.sum(wv[lo] * np.sum(diff * diff, axis=0)))

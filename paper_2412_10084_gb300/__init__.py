@@ -22,7 +22,8 @@ __all__ = [
     "GridDesc", "ProbeDesc", "MlpDesc", "RenderParams", "Scene", "LibraryError",
     "library", "grid_bytes", "mlp_param_count", "pack_grid", "unpack_grid", "BF16", "F16", "F32",
     "FEAT_NODES", "FEAT_TRIPLANE", "tri_tiles",
-    "render_forward", "render_backward", "render", "device_status", "DIR_REFLECT", "DIR_VIEW",
+    "render_forward", "render_backward", "render", "device_status", "set_wait_polls",
+    "wait_polls", "DIR_REFLECT", "DIR_VIEW",
     "ProposalDesc", "proposal_desc", "proposal_param_count", "occupancy_build",
     "weight_histogram", "proposal_forward", "proposal_backward", "adam_step", "Adam",
     "occupancy_words", "occupancy_unpack", "sdf_smooth", "sdf_smooth_adjoint",
@@ -98,6 +99,9 @@ def library() -> ctypes.CDLL:
         lib.psdf_version.restype = ctypes.c_int32
         lib.psdf_device_status.argtypes = [_P, ctypes.POINTER(ctypes.c_int32)]
         lib.psdf_device_status.restype = ctypes.c_int32
+        lib.psdf_set_wait_polls.argtypes = [ctypes.c_uint32]
+        lib.psdf_set_wait_polls.restype = ctypes.c_int32
+        lib.psdf_wait_polls.restype = ctypes.c_uint32
         lib.psdf_grid_bytes.argtypes = [_P, ctypes.POINTER(ctypes.c_size_t),
                                          ctypes.POINTER(ctypes.c_size_t)]
         lib.psdf_grid_create.argtypes = [_P, _P, ctypes.POINTER(_P)]
@@ -171,6 +175,19 @@ def device_status(stream=None) -> int:
     return flags.value
 
 
+def set_wait_polls(polls=None):
+    """Polls of each tensor-core completion wait in the kernels this thread
+    launches next (None: the default).  A small value makes the waits run out
+    on purpose: the kernels then stop early, set bit 0 of the device status
+    word and free their tensor memory; their outputs are invalid."""
+    _check(library().psdf_set_wait_polls(0xFFFFFFFF if polls is None else int(polls)),
+           "psdf_set_wait_polls")
+
+
+def wait_polls() -> int:
+    return int(library().psdf_wait_polls())
+
+
 def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
@@ -242,13 +259,20 @@ def table_words(desc: GridDesc) -> int:
 def pack_sparse(desc: GridDesc, table, sdf: torch.Tensor, feat: torch.Tensor) -> torch.Tensor:
     """Sparse grid from dense sdf [Rz,Ry,Rx] + feat [Rz,Ry,Rx,3] and a brick
     table [Bz,By,Bx] (slots 0..n_bricks-1 or -1): packed float32 [bytes/16, 4]."""
-    _require_cuda(sdf, feat)
     nbytes, _ = grid_bytes(desc)
     shape = tuple(int(desc.dims[a]) // TILE for a in (2, 1, 0))
     tab = torch.as_tensor(table, dtype=torch.int32)
     if tuple(tab.shape) != shape:
         raise LibraryError(f"pack_sparse: the brick table must be {shape} (Bz, By, Bx), "
                            f"got {tuple(tab.shape)}")
+    slots = tab[tab >= 0]
+    if slots.numel() > desc.n_bricks or slots.unique().numel() != slots.numel():
+        # a slot named twice would alias one record block (racing pack writes,
+        # two bricks' gradients added into one)
+        raise LibraryError(f"pack_sparse: the brick table names {slots.numel()} slots "
+                           f"({slots.unique().numel()} distinct) for {desc.n_bricks} stored "
+                           f"bricks; each slot may appear at most once")
+    _require_cuda(sdf, feat)
     out = torch.zeros(nbytes // 4, dtype=torch.float32, device=sdf.device)
     tab = tab.reshape(-1).to(sdf.device)
     out[:tab.numel()] = tab.view(torch.float32)
@@ -533,10 +557,14 @@ class RenderFunction(torch.autograd.Function):
     records and [Pz,Py,Px,l*l,n_a]) when the scene stores BF16 features or
     FP16 probes; the kernels read the scene's storage either way.  The
     backward recomputes per-sample activations in the library's adjoint
-    kernel; only log T_N and the live extent per ray are saved."""
+    kernel; only log T_N and the live extent per ray are saved.  With
+    check_status (the default) the backward synchronises the stream and
+    raises if a render kernel stopped early, instead of handing on partial
+    gradients."""
 
     @staticmethod
-    def forward(ctx, grid_p, probes_p, mlp, rays_o, rays_d, t_samples, scene, params):
+    def forward(ctx, grid_p, probes_p, mlp, rays_o, rays_d, t_samples, scene, params,
+                check_status=True):
         grid = grid_p if scene.feat_dtype == F32 else scene.grid
         probes = probes_p if scene.probe_dtype == F32 else scene.probes
         rgb, depth, wsum, logT, live = render_forward(scene, rays_o, rays_d, params, t_samples,
@@ -548,6 +576,7 @@ class RenderFunction(torch.autograd.Function):
         ctx.has_t = t_samples is not None
         ctx.scene = scene
         ctx.params = params
+        ctx.check_status = check_status
         ctx.mark_non_differentiable(logT, live)
         return rgb, depth, wsum
 
@@ -567,19 +596,26 @@ class RenderFunction(torch.autograd.Function):
             # a sparse grid's brick table is not a parameter: zero gradient there
             # (the buffer came with a copy of the table bits, which are no gradient)
             gg.view(-1)[:table_words(ctx.scene.descs(ctx.params.n_fresnel)[0])] = 0.0
-        return gg, gp, gm, None, None, None, None, None
+        if ctx.check_status:
+            flags = device_status()
+            if flags:
+                raise LibraryError(f"render: a render kernel stopped early (device status "
+                                   f"{flags:#x}); its outputs and gradients are incomplete")
+        return gg, gp, gm, None, None, None, None, None, None
 
 
-def render(scene: Scene, rays_o, rays_d, params: RenderParams, t_samples=None, masters=None):
+def render(scene: Scene, rays_o, rays_d, params: RenderParams, t_samples=None, masters=None,
+           check_status=True):
     """Differentiable w.r.t. the scene's FP32 parameters: scene.grid,
     scene.probes and scene.mlp, or, for reduced-precision storage, the FP32
     masters=(grid [R^3,4], probes) that the storage was packed from.  On a
     sparse grid the brick table at the front of scene.grid gets zero gradient;
     keep it out of any update that changes parameters without a gradient
-    (weight decay)."""
+    (weight decay).  check_status: the backward checks the device status word
+    (a stream synchronisation) and raises if a render kernel stopped early."""
     grid_p, probes_p = (scene.grid, scene.probes) if masters is None else masters
     return RenderFunction.apply(grid_p, probes_p, scene.mlp, rays_o, rays_d, t_samples, scene,
-                                params)
+                                params, check_status)
 
 
 # ---------------------------------------------------------------------------
@@ -722,11 +758,13 @@ def grid_regularizers(gd, sdf_hat, values, grad_grid, d_sdf_hat, lam_sdf, lam_ei
                       lam_features=0.0, loss=None):
     """Adds the gradients of the weighted L_sdf, L_Eik, L_normal (and, for
     tri-planes, L_features) to grad_grid and d_sdf_hat; adds the unweighted
-    values {sdf, eik, normal, features} to `loss` (FP32 [4]) when given."""
+    values {sdf, eik, normal, features} to `loss` (FP32 [4]) when given.  For
+    a sparse grid sdf_hat and d_sdf_hat hold the stored bricks ([n_bricks, 16,
+    16, 16], slot order) and the sums run over the stored nodes' terms."""
     _require_cuda(sdf_hat, grad_grid, d_sdf_hat, loss)
     _require_cuda(values, dtypes=(torch.float32, torch.uint8, torch.bfloat16))
-    _check_dense_sdf(gd, sdf_hat, "grid_regularizers")
-    _check_dense_sdf(gd, d_sdf_hat, "grid_regularizers")
+    _check_sdf_param(gd, sdf_hat, "grid_regularizers")
+    _check_sdf_param(gd, d_sdf_hat, "grid_regularizers")
     if loss is not None and loss.numel() < 4:
         raise LibraryError("grid_regularizers: loss needs 4 entries")
     _check(library().psdf_grid_regularizers(

@@ -10,6 +10,7 @@
 #include "internal.h"
 #include "probesdf.h"
 #include "proposal.h"
+#include "tc_sm100.cuh"
 
 struct psdf_grid {
     psdf_grid_desc desc;
@@ -31,6 +32,8 @@ __device__ int g_device_status;
 namespace {
 
 thread_local int32_t g_last_cuda_error = 0;
+// Polls of each tensor-core completion wait in the kernels this thread launches.
+thread_local uint32_t g_wait_polls = psdf::tc::kWaitPolls;
 
 // Address of g_device_status on the current device (looked up once per device).
 int* device_status_ptr()
@@ -239,6 +242,7 @@ psdf_status resolve(const psdf_grid* grid, const psdf_probes* probes, const psdf
     A.n_bins = t_samples ? p->n_bins : 0;
     A.n_rays = n_rays;
     A.status = device_status_ptr();
+    A.wait_polls = g_wait_polls;
     if (!A.status) return cuda_status(cudaErrorInvalidDevice);
     return PSDF_OK;
 }
@@ -491,6 +495,14 @@ const char* psdf_status_string(psdf_status s)
 int32_t psdf_last_cuda_error(void) { return g_last_cuda_error; }
 
 int32_t psdf_version(void) { return 200; }
+
+psdf_status psdf_set_wait_polls(uint32_t polls)
+{
+    g_wait_polls = polls == 0xFFFFFFFFu ? psdf::tc::kWaitPolls : polls;
+    return PSDF_OK;
+}
+
+uint32_t psdf_wait_polls(void) { return g_wait_polls; }
 
 psdf_status psdf_device_status(void* stream, int32_t* flags)
 {
@@ -883,7 +895,6 @@ psdf_status psdf_grid_regularizers(const psdf_grid_desc* desc, const float* sdf_
 {
     const psdf_status st = check_grid_desc(desc);
     if (st != PSDF_OK) return st;
-    if (sparse(desc)) return PSDF_ERR_UNSUPPORTED;
     if (!sdf_hat || !packed_values || !grad_grid || !d_sdf_hat) return PSDF_ERR_INVALID_ARG;
     if (!(lam_sdf >= 0.0f) || !(lam_eik >= 0.0f) || !(lam_normal >= 0.0f) ||
         !(lam_features >= 0.0f))
@@ -897,6 +908,13 @@ psdf_status psdf_grid_regularizers(const psdf_grid_desc* desc, const float* sdf_
     float h[3];
     for (int a = 0; a < 3; ++a)
         h[a] = (desc->box_max[a] - desc->box_min[a]) / static_cast<float>(desc->dims[a] - 1);
+    if (sparse(desc)) {  // the values' table, then {sdf, f0, f1, f2} records (and in the gradient)
+        const int64_t rec = static_cast<int64_t>(brick_table_bytes(desc) / 4);
+        return cuda_status(psdf::launch_sdf_reg(
+            desc->dims, h, sdf_hat, static_cast<const float*>(packed_values) + rec, 4, lam_sdf,
+            lam_eik, lam_normal, static_cast<float*>(grad_grid) + rec, 4, d_sdf_hat, loss, s,
+            static_cast<const int*>(packed_values), desc->n_bricks, desc->empty_sdf));
+    }
     cudaError_t e = psdf::launch_sdf_reg(
         desc->dims, h, sdf_hat, static_cast<const float*>(packed_values), sdf_value_stride(desc),
         lam_sdf, lam_eik, lam_normal, static_cast<float*>(grad_grid), sdf_grad_stride(desc),

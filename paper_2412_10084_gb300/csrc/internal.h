@@ -79,10 +79,14 @@ cudaError_t launch_smooth_sparse(const int R[3], const int* table, int n_bricks,
                                  int64_t in_base, int in_stride, float* out, int64_t out_base,
                                  int out_stride, float empty, bool transpose, bool accumulate,
                                  cudaStream_t stream);
+// Dense grids (table null), or sparse 16^3-node bricks behind `table` (R
+// multiples of 16; s_hat, s, d_s, d_s_hat then hold the stored bricks' nodes,
+// slot-major; absent nodes read `empty`).
 cudaError_t launch_sdf_reg(const int R[3], const float h[3], const float* s_hat, const float* s,
                            int s_stride, float lam_sdf, float lam_eik, float lam_normal,
                            float* d_s, int d_stride, float* d_s_hat, float* loss,
-                           cudaStream_t stream);
+                           cudaStream_t stream, const int* table = nullptr, int n_bricks = 0,
+                           float empty = 0.0f);
 cudaError_t launch_plane_reg(const float4* planes, int64_t n_texels, float lam, float4* grad,
                              float* loss, cudaStream_t stream);
 cudaError_t launch_probe_reg(const float4* b, const int P[3], int n4, float lam, float4* grad,

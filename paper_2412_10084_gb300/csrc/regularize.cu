@@ -322,19 +322,25 @@ __device__ __forceinline__ void block_loss(float a, float b, float c, float* acc
 }
 
 struct SdfReg {
-    const float* s_hat;  // dense [R^3]
-    const float* s;      // smoothed, element stride s_stride
+    const float* s_hat;  // dense [R^3], or sparse [n_bricks][16^3] in slot order
+    const float* s;      // smoothed, element stride s_stride (sparse: the brick records)
     int s_stride;
     float* d_s;          // gradient w.r.t. s (accumulated), stride d_stride
     int d_stride;
-    float* d_s_hat;      // gradient w.r.t. s_hat (accumulated), dense
+    float* d_s_hat;      // gradient w.r.t. s_hat (accumulated), laid out as s_hat
     float* loss;         // [3]: L_sdf, L_Eik, L_normal (accumulated)
     int R[3];
     float inv2h[3];      // 1 / (2 h_a)
     float lam_sdf, lam_eik, lam_normal;
+    // sparse 16^3-node bricks: brick table [B2][B1][B0] (slot, or -1; a slot
+    // outside [0, n_bricks) counts as absent); node `local` of slot b is
+    // element b * 4096 + local of every array above; absent nodes read `empty`
+    const int* table;
+    int B[3], n_bricks;
+    float empty;
 };
 
-// z-streaming stencil.  A CTA owns a 32 x 8 column tile and ZC output planes
+// z-streaming stencil.  A CTA owns an RX x RY column tile and ZC output planes
 // and walks z with three shared-memory rings of 3 planes each:
 //   s  (halo 3)  the smoothed SDF,
 //   N  (halo 2)  normal n, voxel weight w, rho = sqrt(|g|^2 + eps^2) (0 marks a
@@ -345,45 +351,99 @@ struct SdfReg {
 // at zs - 3: ds_i = own L_sdf term + sum_a (dg_a(i - e_a) - dg_a(i + e_a)) / 2h_a
 // (the central-difference adjoint as a gather), so every output has one
 // writer and no atomics are needed.
-constexpr int RX = 32, RY = 8, ZC = 32;
-constexpr int SX = RX + 6, SY = RY + 6;
-constexpr int NX = RX + 4, NY = RY + 4;
-constexpr int GX = RX + 2, GY = RY + 2;
-constexpr int kRegThreads = RX * RY;
-
-struct RegSmem {
-    float s[3][SY * SX];
-    float n[3][6][NY * NX];  // n.x n.y n.z w rho |g|
-    float g[3][3][GY * GX];  // dg
+//
+// Dense grids: 32 x 8 columns, 32 planes per CTA.  Sparse bricks: one CTA per
+// brick-table entry (absent entries return at once), 16 x 16 columns and the
+// brick's 16 planes; s is that of the full grid with every node of an absent
+// brick at `empty` (as the render and the smoothing read it), and the terms
+// are those of the stored nodes: an absent node gets voxel weight 0, so its
+// own Eikonal term and the normal pairs it owns add nothing, while its
+// normal still enters the pairs its stored neighbours own.  Gradients are
+// written for the stored nodes only (an absent node's s is not a parameter).
+template <int RX_, int RY_, int ZC_>
+struct RegTile {
+    static constexpr int RX = RX_, RY = RY_, ZC = ZC_;
+    static constexpr int SX = RX + 6, SY = RY + 6;
+    static constexpr int NX = RX + 4, NY = RY + 4;
+    static constexpr int GX = RX + 2, GY = RY + 2;
+    static constexpr int kThreads = RX * RY;
+    struct Smem {
+        float s[3][SY * SX];
+        float n[3][6][NY * NX];  // n.x n.y n.z w rho |g|
+        float g[3][3][GY * GX];  // dg
+    };
 };
+using DenseReg = RegTile<32, 8, 32>;
+using SparseReg = RegTile<16, 16, 16>;
+constexpr int kRegThreads = 256;
+static_assert(DenseReg::kThreads == kRegThreads && SparseReg::kThreads == kRegThreads, "");
 
+template <class T, bool SPARSE>
 __global__ void __launch_bounds__(kRegThreads) sdf_reg_kernel(SdfReg P)
 {
+    constexpr int RX = T::RX, RY = T::RY, ZC = T::ZC;
+    constexpr int SX = T::SX, SY = T::SY, NX = T::NX, NY = T::NY, GX = T::GX, GY = T::GY;
     extern __shared__ __align__(16) float reg_smem[];
-    RegSmem& S = *reinterpret_cast<RegSmem*>(reg_smem);
+    typename T::Smem& S = *reinterpret_cast<typename T::Smem*>(reg_smem);
+    __shared__ int nb[27];  // sparse: slots of the brick and its 26 neighbours
     const int tid = threadIdx.x;
     const int Rx = P.R[0], Ry = P.R[1], Rz = P.R[2];
-    const int x0 = blockIdx.x * RX, y0 = blockIdx.y * RY, z0 = blockIdx.z * ZC;
+    int x0, y0, z0, slot = 0;
+    if constexpr (SPARSE) {
+        const int e = blockIdx.x;
+        const int bx = e % P.B[0], by = (e / P.B[0]) % P.B[1], bz = e / (P.B[0] * P.B[1]);
+        const int sv = __ldg(P.table + e);
+        if (sv < 0 || sv >= P.n_bricks) return;  // CTA-uniform
+        slot = sv;
+        if (tid < 27) {
+            const int nx = bx + tid % 3 - 1, ny = by + (tid / 3) % 3 - 1, nz = bz + tid / 9 - 1;
+            int q = -1;
+            if (nx >= 0 && nx < P.B[0] && ny >= 0 && ny < P.B[1] && nz >= 0 && nz < P.B[2]) {
+                q = __ldg(P.table + (int64_t(nz) * P.B[1] + ny) * P.B[0] + nx);
+                if (q >= P.n_bricks) q = -1;
+            }
+            nb[tid] = q < 0 ? -1 : q;
+        }
+        __syncthreads();
+        x0 = bx * RX;
+        y0 = by * RY;
+        z0 = bz * ZC;
+    } else {
+        x0 = blockIdx.x * RX;
+        y0 = blockIdx.y * RY;
+        z0 = blockIdx.z * ZC;
+    }
     const int z1 = min(z0 + ZC, Rz);
     const float cn = 2.0f * P.lam_normal;
     const size_t plane = (size_t)Ry * Rx;
     float l_sdf = 0.0f, l_eik = 0.0f, l_nrm = 0.0f;
+    // sparse: element of in-grid node (x, y, z) in the arrays, or -1 if its
+    // brick is not stored (the node then lies in this brick or a neighbour)
+    auto sparse_elem = [&](int x, int y, int z) -> int64_t {
+        const int q = ((z >> 4) - (z0 >> 4) + 1) * 9 + ((y >> 4) - (y0 >> 4) + 1) * 3 +
+                      ((x >> 4) - (x0 >> 4) + 1);
+        const int b = nb[q];
+        return b < 0 ? -1 : int64_t(b) * 4096 + (((z & 15) << 8) | ((y & 15) << 4) | (x & 15));
+    };
 
     // A thread's elements of each plane are the same at every step: their
     // (x, y) offsets and in-grid tests are computed once.
-    constexpr int kPerS = (SY * SX + kRegThreads - 1) / kRegThreads;  // 3
-    constexpr int kPerN = (NY * NX + kRegThreads - 1) / kRegThreads;  // 2
-    constexpr int kPerG = (GY * GX + kRegThreads - 1) / kRegThreads;  // 2
+    constexpr int kPerS = (SY * SX + kRegThreads - 1) / kRegThreads;
+    constexpr int kPerN = (NY * NX + kRegThreads - 1) / kRegThreads;
+    constexpr int kPerG = (GY * GX + kRegThreads - 1) / kRegThreads;
     size_t s_xy[kPerS];
     bool s_in[kPerS];
+    int s_x[kPerS], s_y[kPerS];
 #pragma unroll
     for (int k = 0; k < kPerS; ++k) {
         const int e = tid + k * kRegThreads;
         const int x = x0 - 3 + e % SX, y = y0 - 3 + e / SX;
         s_in[k] = e < SY * SX && x >= 0 && x < Rx && y >= 0 && y < Ry;
         s_xy[k] = s_in[k] ? (size_t)y * Rx + x : 0;
+        s_x[k] = x;
+        s_y[k] = y;
     }
-    int n_c[kPerN];
+    int n_c[kPerN], n_x[kPerN], n_y[kPerN];
     bool n_ok[kPerN], n_xy[kPerN];
 #pragma unroll
     for (int k = 0; k < kPerN; ++k) {
@@ -392,6 +452,8 @@ __global__ void __launch_bounds__(kRegThreads) sdf_reg_kernel(SdfReg P)
         n_ok[k] = e < NY * NX;
         n_c[k] = (ny + 1) * SX + nx + 1;  // the node in the s planes
         n_xy[k] = x > 0 && y > 0 && x < Rx - 1 && y < Ry - 1;
+        n_x[k] = x;
+        n_y[k] = y;
     }
     int g_c[kPerG];
     bool g_ok[kPerG], g_xy[kPerG];
@@ -410,9 +472,20 @@ __global__ void __launch_bounds__(kRegThreads) sdf_reg_kernel(SdfReg P)
     auto load_plane = [&](int z) {
         const bool zin = z >= 0 && z < Rz;
 #pragma unroll
-        for (int k = 0; k < kPerS; ++k)
-            pre[k] = (zin && s_in[k]) ? __ldg(P.s + ((size_t)z * plane + s_xy[k]) * P.s_stride)
-                                      : 0.0f;
+        for (int k = 0; k < kPerS; ++k) {
+            if constexpr (SPARSE) {
+                float v = 0.0f;
+                if (zin && s_in[k]) {
+                    const int64_t el = sparse_elem(s_x[k], s_y[k], z);
+                    v = el < 0 ? P.empty : __ldg(P.s + el * P.s_stride);
+                }
+                pre[k] = v;
+            } else {
+                pre[k] = (zin && s_in[k])
+                             ? __ldg(P.s + ((size_t)z * plane + s_xy[k]) * P.s_stride)
+                             : 0.0f;
+            }
+        }
     };
     load_plane(z0 - 3);
     const int ox = tid % RX, oy = tid / RX;
@@ -436,7 +509,10 @@ __global__ void __launch_bounds__(kRegThreads) sdf_reg_kernel(SdfReg P)
         size_t io = 0;
         float s_o = 0.f, sh_o = 0.f, ds_o = 0.f, dsh_o = 0.f;
         if (out) {
-            io = (size_t)zo * plane + (size_t)y_o * Rx + x_o;
+            if constexpr (SPARSE)
+                io = size_t(slot) * 4096 + (((zo & 15) << 8) | ((y_o & 15) << 4) | (x_o & 15));
+            else
+                io = (size_t)zo * plane + (size_t)y_o * Rx + x_o;
             s_o = __ldg(P.s + io * P.s_stride);
             sh_o = __ldg(P.s_hat + io);
             ds_o = P.d_s[io * P.d_stride];
@@ -469,6 +545,8 @@ __global__ void __launch_bounds__(kRegThreads) sdf_reg_kernel(SdfReg P)
                     n2 = g2 * ir;
                     gn = sqrtf(gg);
                     w = 1.0f / (1.0f + 5.0f * fabsf(sc[c]));
+                    if constexpr (SPARSE)
+                        if (sparse_elem(n_x[k], n_y[k], zn) < 0) w = 0.0f;  // no terms of its own
                 }
                 S.n[rc][0][e] = n0;
                 S.n[rc][1][e] = n1;
@@ -716,7 +794,7 @@ cudaError_t launch_smooth_sparse(const int R[3], const int* table, int n_bricks,
 cudaError_t launch_sdf_reg(const int R[3], const float h[3], const float* s_hat, const float* s,
                            int s_stride, float lam_sdf, float lam_eik, float lam_normal,
                            float* d_s, int d_stride, float* d_s_hat, float* loss,
-                           cudaStream_t stream)
+                           cudaStream_t stream, const int* table, int n_bricks, float empty)
 {
     SdfReg P;
     P.s_hat = s_hat;
@@ -726,19 +804,38 @@ cudaError_t launch_sdf_reg(const int R[3], const float h[3], const float* s_hat,
     P.d_stride = d_stride;
     P.d_s_hat = d_s_hat;
     P.loss = loss;
+    int64_t entries = 1;
     for (int a = 0; a < 3; ++a) {
         P.R[a] = R[a];
         P.inv2h[a] = 0.5f / h[a];
+        P.B[a] = R[a] / SB;
+        entries *= P.B[a];
     }
     P.lam_sdf = lam_sdf;
     P.lam_eik = lam_eik;
     P.lam_normal = lam_normal;
-    constexpr int kBytes = static_cast<int>(sizeof(RegSmem));
+    P.table = table;
+    P.n_bricks = n_bricks;
+    P.empty = empty;
+    if (table) {
+        if (entries < 1 || entries > 0x7fffffff) return cudaErrorInvalidValue;
+        constexpr int kBytes = static_cast<int>(sizeof(SparseReg::Smem));
+        auto kernel = sdf_reg_kernel<SparseReg, true>;
+        cudaError_t e =
+            cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBytes);
+        if (e != cudaSuccess) return e;
+        kernel<<<static_cast<unsigned>(entries), kRegThreads, kBytes, stream>>>(P);
+        return cudaGetLastError();
+    }
+    constexpr int kBytes = static_cast<int>(sizeof(DenseReg::Smem));
+    auto kernel = sdf_reg_kernel<DenseReg, false>;
     cudaError_t e =
-        cudaFuncSetAttribute(sdf_reg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBytes);
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBytes);
     if (e != cudaSuccess) return e;
-    const dim3 grid((R[0] + RX - 1) / RX, (R[1] + RY - 1) / RY, (R[2] + ZC - 1) / ZC);
-    sdf_reg_kernel<<<grid, kRegThreads, kBytes, stream>>>(P);
+    const dim3 grid((R[0] + DenseReg::RX - 1) / DenseReg::RX,
+                    (R[1] + DenseReg::RY - 1) / DenseReg::RY,
+                    (R[2] + DenseReg::ZC - 1) / DenseReg::ZC);
+    kernel<<<grid, kRegThreads, kBytes, stream>>>(P);
     return cudaGetLastError();
 }
 

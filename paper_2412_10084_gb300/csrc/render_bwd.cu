@@ -81,10 +81,11 @@ __device__ __forceinline__ float warp_max(float v)
 // Probe-coefficient gradient (Eqs. 6-7): dL/db_ijc = sum_k w_i(k) Y_j(k) dF_a,c(k).
 // Samples of a chunk that share a probe cell are consecutive; lane (corner i,
 // channel c) sums each run over the rows in `live` and issues one reduction
-// per coefficient.
+// per coefficient at the run's last sample (the bits of `ends`).  The next
+// row's operands are loaded while the current row is summed.
 template <class C, int PST>
 __device__ __forceinline__ void scatter_probe_grad(const RenderArgs& A, const float* pst,
-                                                   uint32_t live, int lane)
+                                                   uint32_t live, uint32_t ends, int lane)
 {
     constexpr int L2 = C::L2, NA = C::NA;
     constexpr int CPL = (8 * NA) / 32;
@@ -92,6 +93,7 @@ __device__ __forceinline__ void scatter_probe_grad(const RenderArgs& A, const fl
     static_assert(PST % 4 == 0, "rows of whole 16-byte vectors");
     constexpr int L2V = (L2 + 3) / 4;  // Y_j starts at float 8: 16-byte aligned
     static_assert(8 + 4 * L2V <= PST, "vector reads stay inside the row");
+    if (!live) return;
     const int Px = A.probes.P[0], Pxy = A.probes.P[0] * A.probes.P[1];
     int q[CPL], ch[CPL], qoff[CPL];
     float acc[CPL][L2];
@@ -104,31 +106,31 @@ __device__ __forceinline__ void scatter_probe_grad(const RenderArgs& A, const fl
 #pragma unroll
         for (int j = 0; j < L2; ++j) acc[m][j] = 0.f;
     }
-    // only rows of samples with a nonzero opacity carry a gradient (dx = 0
-    // elsewhere); a run of rows in one probe cell is summed, then flushed
-    while (live) {
-        const int s = __ffs(live) - 1;
-        live &= live - 1;
+    // row s: w_i at [0, 8), Y_j at 8, dF_a at 8 + L2, the probe cell at 8 + L2 + NA
+    auto load = [&](int s, float4 (&y)[L2V], float (&coef)[CPL]) {
         const float* row = pst + s * PST;
-        const int cell = __float_as_int(row[8 + L2 + NA]);
-        float Y[4 * L2V];
 #pragma unroll
-        for (int v = 0; v < L2V; ++v) {
-            const float4 y4 = *reinterpret_cast<const float4*>(row + 8 + 4 * v);
-            Y[4 * v + 0] = y4.x;
-            Y[4 * v + 1] = y4.y;
-            Y[4 * v + 2] = y4.z;
-            Y[4 * v + 3] = y4.w;
-        }
+        for (int v = 0; v < L2V; ++v) y[v] = *reinterpret_cast<const float4*>(row + 8 + 4 * v);
 #pragma unroll
-        for (int m = 0; m < CPL; ++m) {
-            const float coef = row[q[m]] * row[8 + L2 + ch[m]];
+        for (int m = 0; m < CPL; ++m) coef[m] = row[q[m]] * row[8 + L2 + ch[m]];
+    };
+    int s = __ffs(live) - 1;
+    uint32_t rem = live & (live - 1);
+    float4 y[L2V];
+    float coef[CPL];
+    load(s, y, coef);
+    for (;;) {
+        const int sn = rem ? __ffs(rem) - 1 : s;
+        float4 yn[L2V];
+        float coefn[CPL];
+        load(sn, yn, coefn);
+        const float* Y = reinterpret_cast<const float*>(y);
 #pragma unroll
-            for (int j = 0; j < L2; ++j) acc[m][j] = fmaf(coef, Y[j], acc[m][j]);
-        }
-        const int next =
-            live ? __float_as_int(pst[(__ffs(live) - 1) * PST + 8 + L2 + NA]) : -1;
-        if (next != cell) {
+        for (int m = 0; m < CPL; ++m)
+#pragma unroll
+            for (int j = 0; j < L2; ++j) acc[m][j] = fmaf(coef[m], Y[j], acc[m][j]);
+        if ((ends >> s) & 1u) {
+            const int cell = __float_as_int(pst[s * PST + 8 + L2 + NA]);
 #pragma unroll
             for (int m = 0; m < CPL; ++m) {
                 float* dst = A.grad_probes + (size_t)(cell + qoff[m]) * (L2 * NA) + ch[m];
@@ -139,6 +141,13 @@ __device__ __forceinline__ void scatter_probe_grad(const RenderArgs& A, const fl
                 }
             }
         }
+        if (!rem) break;
+        rem &= rem - 1;
+        s = sn;
+#pragma unroll
+        for (int v = 0; v < L2V; ++v) y[v] = yn[v];
+#pragma unroll
+        for (int m = 0; m < CPL; ++m) coef[m] = coefn[m];
     }
 }
 
@@ -271,10 +280,15 @@ render_backward_kernel(RenderArgs A)
     // A ray starts at the chunk that holds sample n_live: every later sample
     // has alpha = 0 and a zero adjoint, and lam = 0 there leaves log T and the
     // suffix term of Eq. 10 at their end-of-ray values.
+    // The point after a chunk's last sample is the first sample of the chunk
+    // processed just before it (back to front), whose SDF value lane 0 carries
+    // over (s_first, valid while have_first); only a ray's first chunk, and
+    // the point after the ray's last sample, gather it.
     RayIn R;
     RaySpan sp;
-    bool have = false;
+    bool have = false, have_first = false;
     int ch = -1;
+    float s_first = 0.0f;
     float drgb[3] = {0.f, 0.f, 0.f}, ddepth = 0.f, dwsum = 0.f, logT_end = 0.f, s_carry = 0.f;
     const int nch = (N + 31) >> 5;
     for (;;) {
@@ -286,14 +300,18 @@ render_backward_kernel(RenderArgs A)
                 sp = ray_span(A, R, ray, stab + 64 * warp);
                 const int live = A.n_live ? __ldg(A.n_live + ray) : N;
                 if (sp.hit && live > 0) {
+                    // the chunk of the last sample with alpha > 0; sample
+                    // n_live (alpha = 0) enters only through that sample's
+                    // opacity, as the point after it
                     have = true;
-                    ch = min(nch - 1, live >> 5);
+                    ch = min(nch - 1, (live - 1) >> 5);
                     break;
                 }
                 ray += stride;
             }
             drgb[0] = drgb[1] = drgb[2] = 0.f;
             ddepth = dwsum = logT_end = 0.f;
+            have_first = false;
             if (have) {
                 drgb[0] = __ldg(A.d_rgb + 3 * ray);
                 drgb[1] = __ldg(A.d_rgb + 3 * ray + 1);
@@ -323,14 +341,24 @@ render_backward_kernel(RenderArgs A)
             c1.f[0] = c1.f[1] = c1.f[2] = 0.0f;
             if (have) {
                 t = span_t(sp, k < N ? k : N - 1);
-                eval_sdf<C>(A, R.o, R.d, t, S);
-                s_next = __shfl_down_sync(FULL, S.s, 1);
+                // the extra point's SDF: carried from the previous chunk's lane
+                // 0 (the same point, the same arithmetic, so the same bits), or
+                // gathered in a ray's first chunk and after its last sample
+                const bool carried = have_first && k + 1 < N;
                 if (extra) {
                     float xw[3];
                     point_at(R.o, R.d, span_t(sp, k + 1), xw);
                     c1 = locate(xw, A.grid.bmin, A.grid.sc, A.grid.R);
-                    s_next = sdf_value(A.grid, c1);
                 }
+                eval_sdf<C>(A, R.o, R.d, t, S);
+                s_next = __shfl_down_sync(FULL, S.s, 1);
+                if (extra) {
+                    if (carried)
+                        s_next = s_first;
+                    else
+                        s_next = sdf_value(A.grid, c1);
+                }
+                s_first = __shfl_sync(FULL, S.s, 0);
                 if (active) {
                     const float diff = log_transmittance(tau, S.s, s_next);
                     unclipped = diff < 0.0f;
@@ -389,7 +417,7 @@ render_backward_kernel(RenderArgs A)
             const float Tk = expf(logTk);
             const float Tk1 = expf(logTk + lam);
             const float alpha = -expm1f(lam);
-            bad |= !tc::mbar_wait(mbar, phase);
+            bad |= !tc::mbar_wait(mbar, phase, A.wait_polls);
             phase ^= 1;
             tc::fence_after();
             uint32_t mask1 = 0;
@@ -421,7 +449,7 @@ render_backward_kernel(RenderArgs A)
                          w2l + s * 256, 128, L::kSboXH, 128, (W / 8) * 128, M::kIdescL, s > 0);
                 tc::commit(mbar);
             }
-            bad |= !tc::mbar_wait(mbar, phase);
+            bad |= !tc::mbar_wait(mbar, phase, A.wait_polls);
             phase ^= 1;
             tc::fence_after();
             float h2[W];
@@ -539,7 +567,7 @@ render_backward_kernel(RenderArgs A)
                          L::kSboDZ, (W / 8) * 128, 128, idesc, s > 0);
                 tc::commit(mbar);
             }
-            bad |= !tc::mbar_wait(mbar, phase);
+            bad |= !tc::mbar_wait(mbar, phase, A.wait_polls);
             phase ^= 1;
             tc::fence_after();
             {
@@ -571,7 +599,7 @@ render_backward_kernel(RenderArgs A)
                 dw_started = true;
                 tc::commit(mbar);
             }
-            bad |= !tc::mbar_wait(mbar, phase);
+            bad |= !tc::mbar_wait(mbar, phase, A.wait_polls);
             phase ^= 1;
             tc::fence_after();
             float dx[16];
@@ -734,11 +762,20 @@ render_backward_kernel(RenderArgs A)
                         }
                     }
                 }
+                // runs of live samples in one probe cell end where the next live
+                // sample's cell differs (or no live sample follows)
                 const uint32_t live = __ballot_sync(FULL, unclipped);
+                const int my_cell = unclipped ? S.pcell.base : -1;
+                const uint32_t later = lane == 31 ? 0u : live & (0xffffffffu << (lane + 1));
+                const int nl = __ffs(later) - 1;
+                const int next_cell = __shfl_sync(FULL, my_cell, nl >= 0 ? nl : lane);
+                const uint32_t ends =
+                    __ballot_sync(FULL, unclipped && (nl < 0 || next_cell != my_cell));
                 __syncwarp();
-                scatter_probe_grad<C, L::PST>(A, pst, live, lane);
+                scatter_probe_grad<C, L::PST>(A, pst, live, ends, lane);
                 logT_end = __shfl_sync(FULL, logTk, 0);
                 s_carry = next_carry;
+                have_first = true;
             }
         }
         if (have) --ch;
@@ -748,7 +785,8 @@ done:
     // above are CTA-uniform), so the flag can be made uniform here
     bad = __syncthreads_or(bad);
     if (bad) {
-        tc::mbar_wait(mbar, phase);
+        // the last commit's phase has the parity before the final flip
+        tc::mbar_wait(mbar, phase ^ 1u);
         if (tid == 0) atomicOr(A.status, 1);
     }
     tc::fence_before();

@@ -73,6 +73,7 @@ struct RenderArgs {
     float* grad_probes;
     float* grad_mlp;
     int* status;  // device status word: bit 0 = a tensor-core wait ran out
+    uint32_t wait_polls;  // polls of each tensor-core completion wait before it gives up
 };
 
 // ---------------------------------------------------------------------------
@@ -322,7 +323,33 @@ __device__ __forceinline__ int gather_corners_sparse(const GridView& g, const Ce
     return stored;
 }
 
-// SDF value only (the extra point N of a ray's last full chunk).
+// The 8 corner SDF values of a cell of a dense grid (FP32 node records, or
+// the SDF array of the BF16-feature and tri-plane layouts), loaded but not yet
+// combined, so that a caller can have them in flight with other loads.
+__device__ __forceinline__ void sdf_corners_load(const GridView& g, const Cell& c, float v[8])
+{
+    const int sx = 1, sy = g.R[0], sz = g.R[0] * g.R[1];
+    const bool split = g.sdf != nullptr;  // BF16-feature layout: SDF in its own array
+    const float* p = split ? g.sdf + c.base : reinterpret_cast<const float*>(g.nodes + c.base);
+    const int st = split ? 1 : 4;
+    const int off[8] = {0, sx, sy, sx + sy, sz, sz + sx, sz + sy, sz + sy + sx};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = __ldg(p + st * off[q]);
+}
+
+// Trilinear SDF value from the corner values: the same weights and summation
+// order as sdf_full, so both give the same bits for the same point.
+__device__ __forceinline__ float sdf_corners_combine(const Cell& c, const float v[8])
+{
+    float w[8];
+    corner_weights(c.f, w);
+    float s = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s = fmaf(w[q], v[q], s);
+    return s;
+}
+
+// SDF value only (the point after a chunk's last sample).
 __device__ __forceinline__ float sdf_value(const GridView& g, const Cell& c)
 {
     if (g.table) {
@@ -338,17 +365,9 @@ __device__ __forceinline__ float sdf_value(const GridView& g, const Cell& c)
                      s);
         return s;
     }
-    const int sx = 1, sy = g.R[0], sz = g.R[0] * g.R[1];
-    const bool split = g.sdf != nullptr;  // BF16-feature layout: SDF in its own array
-    const float* p = split ? g.sdf + c.base : reinterpret_cast<const float*>(g.nodes + c.base);
-    const int st = split ? 1 : 4;
-    float w[8];
-    corner_weights(c.f, w);
-    const int off[8] = {0, sx, sy, sx + sy, sz, sz + sx, sz + sy, sz + sy + sx};
-    float s = 0.0f;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) s = fmaf(w[q], __ldg(p + st * off[q]), s);
-    return s;
+    float v[8];
+    sdf_corners_load(g, c, v);
+    return sdf_corners_combine(c, v);
 }
 
 // Value, analytic gradient (world units) and 3 features at a point.

@@ -164,7 +164,7 @@ render_forward_kernel(RenderArgs A)
                 comp = (tt - carry) - y;
                 carry = tt;
             }
-            bad |= !tc::mbar_wait(mbar, phase);
+            bad |= !tc::mbar_wait(mbar, phase, A.wait_polls);
             phase ^= 1;
             tc::fence_after();
             {
@@ -187,7 +187,7 @@ render_forward_kernel(RenderArgs A)
                                      (W / 8) * 128, 128, (W / 8) * 128, M::kIdescL, s > 0);
                 tc::commit(mbar);
             }
-            bad |= !tc::mbar_wait(mbar, phase);
+            bad |= !tc::mbar_wait(mbar, phase, A.wait_polls);
             phase ^= 1;
             tc::fence_after();
             {
@@ -235,7 +235,8 @@ done:
     if (bad) {
         // an MMA never signalled completion: give it one more bounded wait
         // before the tensor memory is released, and report the failure
-        tc::mbar_wait(mbar, phase);
+        // the last commit's phase has the parity before the final flip
+        tc::mbar_wait(mbar, phase ^ 1u);
         if (tid == 0) atomicOr(A.status, 1);
     }
     tc::fence_before();

@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(kFwdThreads, 4) shade_kernel(RenderArgs A, Sha
                                  (M::K1 / 8) * 128, 128, (M::K1 / 8) * 128, M::kIdescL, false);
                 tc::commit(mbar);
             }
-            bad |= !tc::mbar_wait(mbar, phase);
+            bad |= !tc::mbar_wait(mbar, phase, A.wait_polls);
             phase ^= 1;
             tc::fence_after();
             {
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(kFwdThreads, 4) shade_kernel(RenderArgs A, Sha
                                      (W / 8) * 128, 128, (W / 8) * 128, M::kIdescL, s > 0);
                 tc::commit(mbar);
             }
-            bad |= !tc::mbar_wait(mbar, phase);
+            bad |= !tc::mbar_wait(mbar, phase, A.wait_polls);
             phase ^= 1;
             tc::fence_after();
             {
@@ -249,7 +249,8 @@ done:
     if (bad) {
         // an MMA never signalled completion: give it one more bounded wait
         // before the tensor memory is released, and report the failure
-        tc::mbar_wait(mbar, phase);
+        // the last commit's phase has the parity before the final flip
+        tc::mbar_wait(mbar, phase ^ 1u);
         if (tid == 0) atomicOr(A.status, 1);
     }
     tc::fence_before();

@@ -24,9 +24,20 @@ import dataclasses
 
 import torch
 
-from . import (F32, FEAT_TRIPLANE, Adam, LibraryError, RenderParams, Scene, occupancy_build,
-               proposal_backward, proposal_desc, proposal_forward, proposal_param_count,
-               render_backward, render_forward, render_params, table_words, weight_histogram)
+from . import (F32, FEAT_TRIPLANE, Adam, LibraryError, RenderParams, Scene, device_status,
+               occupancy_build, proposal_backward, proposal_desc, proposal_forward,
+               proposal_param_count, render_backward, render_forward, render_params, table_words,
+               weight_histogram)
+
+
+def _check_device(what: str, step: int):
+    """Raises if a kernel since the last check gave up waiting on its
+    tensor-core work (it then returned with part of its rays or gradients
+    missing, so the parameters updated from them are not to be trusted)."""
+    flags = device_status()
+    if flags:
+        raise LibraryError(f"{what}: a render kernel stopped early (device status {flags:#x}) "
+                           f"before step {step}")
 
 
 def _batch(gen, n_pool, batch, device):
@@ -77,6 +88,7 @@ def fit_appearance(scene: Scene, rays_o, rays_d, target, params: RenderParams, s
             sdf_grads.zero_()
         opt.step()
         if step % log_every == 0 or step == steps:
+            _check_device("fit_appearance", step)
             log.append((step, float((diff * diff).sum(1).mean())))
     return log
 

@@ -10,7 +10,11 @@ import synth
 # Parity tolerances of the FP32 path against the FP64 oracle.
 RGB_DEPTH_RTOL = 1e-5     # |gpu - ref| <= 1e-5 * max(|ref|, REL_FLOOR), elementwise
 REL_FLOOR = 1e-2          # outputs under 1% of the unit colour / weight scale are held
-                          # to an absolute 1e-7
+                          # to an absolute 1e-7 against the FP64 oracle ...
+REL_FLOOR_S32 = 1e-3      # ... and to 1e-8 against the oracle whose SDF values are rounded
+                          # as the FP32 evaluation rounds them (the rest FP64): what the
+                          # 1e-2 floor allows beyond 1e-3 is that rounding, amplified by
+                          # tau in the opacity of nearly transparent rays
 GRAD_RTOL = 1e-4          # per tensor: max|g - g_ref| <= 1e-4 * max|g_ref|
 KINK_MARGIN = 3e-5        # rays closer than this (relative) to a ReLU or alpha-clip
                           # kink are left out of gradient comparisons

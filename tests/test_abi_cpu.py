@@ -48,6 +48,23 @@ def test_status_strings_and_version(lib):
     assert lib.psdf_version() >= 100
 
 
+def test_wait_polls_setting_is_thread_local(lib):
+    """The tensor-core wait limit: set, read back, restored by 0xFFFFFFFF, and
+    private to the host thread that set it (no CUDA call involved)."""
+    import threading
+    lib.psdf_wait_polls.restype = ctypes.c_uint32
+    lib.psdf_set_wait_polls.argtypes = [ctypes.c_uint32]
+    default = lib.psdf_wait_polls()
+    assert default == 1 << 24
+    assert lib.psdf_set_wait_polls(7) == 0 and lib.psdf_wait_polls() == 7
+    seen = []
+    t = threading.Thread(target=lambda: seen.append(lib.psdf_wait_polls()))
+    t.start()
+    t.join()
+    assert seen == [default]
+    assert lib.psdf_set_wait_polls(0xFFFFFFFF) == 0 and lib.psdf_wait_polls() == default
+
+
 def test_host_validation_without_gpu(lib):
     import paper_2412_10084_gb300 as ps
     gd = ps.grid_desc((64, 64, 64), (0, 0, 0), (1, 1, 1))

@@ -1,6 +1,7 @@
 """Host logic of training (no GPU): which parts of a packed grid
 the optimiser updates and where the gradient's SDF entries sit, in every
 FP32 grid layout."""
+import pytest
 import torch
 
 import paper_2412_10084_gb300 as ps
@@ -60,6 +61,42 @@ def test_autograd_gives_a_sparse_brick_table_zero_gradient(monkeypatch):
     scene = types.SimpleNamespace(n_bricks=1, descs=lambda n_fresnel: (gd, None, None))
     empty = torch.empty(0)
     ctx = types.SimpleNamespace(saved_tensors=(empty,) * 6, storage=(None, None), has_t=False,
-                                scene=scene, params=types.SimpleNamespace(n_fresnel=3))
+                                scene=scene, params=types.SimpleNamespace(n_fresnel=3),
+                                check_status=False)
     d_grid = ps.RenderFunction.backward(ctx, torch.zeros(0, 3), None, None)[0]
     assert bool((d_grid[:w] == 0).all()) and bool(d_grid[w:].isnan().all())
+
+
+def test_autograd_backward_raises_when_a_kernel_stopped_early(monkeypatch):
+    """With the status check on (the default), a nonzero device status word
+    (a render kernel gave up waiting on its tensor-core work and returned with
+    part of its gradients missing) raises instead of handing them on."""
+    import types
+    gd = ps.grid_desc((16, 16, 16), (0, 0, 0), (1, 1, 1))
+    monkeypatch.setattr(ps, "render_backward", lambda *a, **k: (torch.zeros(4), None, None))
+    monkeypatch.setattr(ps, "device_status", lambda stream=None: 1)
+    scene = types.SimpleNamespace(n_bricks=0, descs=lambda n_fresnel: (gd, None, None))
+    empty = torch.empty(0)
+    ctx = types.SimpleNamespace(saved_tensors=(empty,) * 6, storage=(None, None), has_t=False,
+                                scene=scene, params=types.SimpleNamespace(n_fresnel=3),
+                                check_status=True)
+    with pytest.raises(ps.LibraryError, match="stopped early"):
+        ps.RenderFunction.backward(ctx, torch.zeros(0, 3), None, None)
+    ctx.check_status = False
+    assert ps.RenderFunction.backward(ctx, torch.zeros(0, 3), None, None)[0].numel() == 4
+
+
+def test_pack_sparse_rejects_a_slot_named_twice():
+    """Two table entries naming one slot would alias one record block; more
+    named slots than stored bricks would index past the records."""
+    gd = ps.grid_desc((32, 32, 16), (0, 0, 0), (1, 1, 1), n_bricks=2, empty_sdf=1.0)
+    sdf, feat = torch.zeros(16, 32, 32), torch.zeros(16, 32, 32, 3)
+    dup = torch.tensor([[[0, -1], [0, 1]]], dtype=torch.int32)
+    with pytest.raises(ps.LibraryError, match="at most once"):
+        ps.pack_sparse(gd, dup, sdf, feat)
+    too_many = torch.tensor([[[0, 1], [2, -1]]], dtype=torch.int32)
+    with pytest.raises(ps.LibraryError, match="at most once"):
+        ps.pack_sparse(gd, too_many, sdf, feat)
+    ok = torch.tensor([[[1, -1], [0, -1]]], dtype=torch.int32)
+    with pytest.raises(ps.LibraryError, match="CUDA"):  # valid table: fails only on the CPU tensors
+        ps.pack_sparse(gd, ok, sdf, feat)

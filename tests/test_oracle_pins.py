@@ -309,6 +309,42 @@ def test_mlp_layer_wiring_identity_construction():
 # Compositing (Eqs. 8-10): closed forms and invariants
 # ----------------------------------------------------------------------------
 
+def test_fp32_sdf_option_is_the_same_trilinear_value_rounded():
+    """The oracle's FP32-rounded SDF option (used only to isolate the FP32
+    rounding of s in a GPU comparison) returns a FP32 number within a few FP32
+    units of the FP64 trilinear value at every point, equals it exactly where
+    the corner values and weights are exact in FP32, and does change some
+    values (it is not a no-op)."""
+    sc = tiny_scene(R=(9, 8, 7))
+    m = oracle.Model.from_scene(sc)
+    g = synth.rng(41)
+    scale = float(np.max(np.abs(sc.sdf)))
+    differ = 0
+    for _ in range(300):
+        o = g.uniform(0.05, 0.95, 3).astype(np.float32)
+        d = g.normal(size=3)
+        d = (d / np.linalg.norm(d)).astype(np.float32)
+        t = float(g.uniform(0.0, 0.05))
+        s64 = oracle.point_eval(m, o, d, t)["s"]
+        s32 = oracle.point_eval(m, o, d, t, sdf_fp32=True)["s"]
+        assert float(np.float32(s32)) == s32
+        assert abs(s32 - s64) <= 8 * np.finfo(np.float32).eps * scale, (s32, s64)
+        differ += s32 != s64
+    assert differ > 10
+    # dyadic corner values at points with dyadic fractions (node spacing 1/8):
+    # every FP32 weight, product and sum is exact, so the two agree exactly
+    sc2 = tiny_scene(R=(9, 9, 9))
+    sc2.sdf = (np.round(sc2.sdf * 64) / 64).astype(np.float32)
+    m2 = oracle.Model.from_scene(sc2)
+    d = np.array([0.0, 0.0, 1.0], np.float32)
+    for cell, frac in (((3, 2, 4), (0.5, 0.5, 0.5)), ((0, 6, 1), (0.25, 0.75, 0.125))):
+        x = (np.array(cell) + np.array(frac)) / 8.0
+        o = np.array([x[0], x[1], 0.0], np.float32)
+        a = oracle.point_eval(m2, o, d, float(x[2]))["s"]
+        b = oracle.point_eval(m2, o, d, float(x[2]), sdf_fp32=True)["s"]
+        assert a == b, (cell, a, b)
+
+
 def test_weights_plus_final_transmittance_is_one():
     sc = tiny_scene(R=(12, 12, 12))
     m = oracle.Model.from_scene(sc)

@@ -108,6 +108,44 @@ def test_sdf_terms_gradient_central_differences(which):
             assert abs(fd - gflat[i]) <= 1e-6 * max(1.0, abs(gflat).max()), (which, i, fd, gflat[i])
 
 
+@pytest.mark.parametrize("which", ["sdf", "eik", "normal"])
+def test_owned_sdf_terms_gradient_central_differences(which):
+    """The terms of a subset of owner voxels (a sparse grid's stored nodes):
+    gradients against central differences of the owned objective, everywhere
+    (unowned voxels enter as neighbours); with every voxel an owner the result
+    is the unrestricted one; owned and unowned terms add up to the whole."""
+    dims = (9, 8, 10)
+    h = R.spacing(dims, (0, 0, 0), (1.0, 0.9, 1.2))
+    s_hat = synth.sphere_sdf(dims, np.zeros(3), np.array([1.0, 0.9, 1.2]), (0.5, 0.45, 0.6), 0.3)
+    s_hat = s_hat + 0.02 * _field(s_hat.shape, 5)
+    s = R.smooth(s_hat)
+    lam = {"sdf": (1.0, 0, 0), "eik": (0, 1.0, 0), "normal": (0, 0, 1.0)}[which]
+    w = R.voxel_weight(s)
+    own = synth.rng(6).uniform(size=s.shape) < 0.5
+    vals, ds, ds_hat = R.sdf_terms(s_hat, s, h, *lam, weights=w, owner=own)
+    full = R.sdf_terms(s_hat, s, h, *lam, weights=w)
+    every = R.sdf_terms(s_hat, s, h, *lam, weights=w, owner=np.ones(s.shape, bool))
+    assert every[0] == full[0]
+    assert np.array_equal(every[1], full[1]) and np.array_equal(every[2], full[2])
+    rest = R.sdf_terms(s_hat, s, h, *lam, weights=w, owner=~own)
+    for k in ("sdf", "eik", "normal", "objective"):
+        assert abs(vals[k] + rest[0][k] - full[0][k]) <= 1e-12 * max(1.0, abs(full[0][k]))
+    assert np.allclose(ds + rest[1], full[1], rtol=0, atol=1e-12)
+    g = synth.rng(7)
+    eps = 1e-6
+    for arr, grad in ((s, ds), (s_hat, ds_hat)):
+        flat, gflat = arr.reshape(-1), grad.reshape(-1)
+        for i in g.choice(flat.size, 60, replace=False):
+            old = flat[i]
+            flat[i] = old + eps
+            lp = R.sdf_terms(s_hat, s, h, *lam, weights=w, owner=own)[0]["objective"]
+            flat[i] = old - eps
+            lm = R.sdf_terms(s_hat, s, h, *lam, weights=w, owner=own)[0]["objective"]
+            flat[i] = old
+            fd = (lp - lm) / (2 * eps)
+            assert abs(fd - gflat[i]) <= 1e-6 * max(1.0, abs(gflat).max()), (which, i, fd, gflat[i])
+
+
 def test_probe_and_plane_gradients_central_differences():
     # both losses are quadratic: central differences are exact for any step
     b = _field((3, 4, 3, 9, 4), 5)

@@ -12,8 +12,9 @@ import os
 
 import oracle
 import synth
-from helpers import (GRAD_RTOL, RGB_DEPTH_RTOL, box_interval, clean_rays, log_errors,
-                     oracle_backward, oracle_forward, rel_err_elementwise, rel_err_tensor, worst)
+from helpers import (GRAD_RTOL, KINK_MARGIN, REL_FLOOR_S32, RGB_DEPTH_RTOL, box_interval,
+                     clean_rays, log_errors, oracle_backward, oracle_forward,
+                     rel_err_elementwise, rel_err_tensor, worst)
 
 pytestmark = pytest.mark.gpu
 
@@ -58,6 +59,12 @@ def check_forward(sc, o, d, tau, N, dir_mode=0, bg=(0, 0, 0), t_samples=None):
     errs["logT"] = float(np.max(np.abs(g["logT"] - r["logT"]) /
                                 np.maximum(np.abs(r["logT"]), 1.0)))
     detail = {k: worst(g[k], r[k]) for k in ("rgb", "depth", "wsum")}
+    # against the oracle with FP32-rounded SDF values, at the 1e-3 floor
+    r32 = oracle_forward(sc, o, d, tau, N, dir_mode=dir_mode, bg=bg, t_samples=t_samples,
+                         sdf_fp32=True)
+    for k in ("rgb", "depth", "wsum"):
+        errs[k + "_s32"] = rel_err_elementwise(g[k], r32[k], floor=REL_FLOOR_S32)
+        detail[k + "_s32"] = worst(g[k], r32[k], floor=REL_FLOOR_S32)
     log_errors(os.environ.get("PYTEST_CURRENT_TEST", "?") + " forward", errs)
     for k, e in errs.items():
         assert e <= RGB_DEPTH_RTOL, (k, e, detail)
@@ -344,15 +351,46 @@ def test_full_size_forward_sampled_parity_and_invariants(object256):
     assert float(rgb.min()) >= 0.0 and float(rgb.max()) <= 1.0 + 1e-6
     idx = synth.rng(3).choice(rays.o.shape[0], 256, replace=False)
     r = oracle_forward(sc, rays.o[idx], rays.d[idx], 64.0, 256)
+    r32 = oracle_forward(sc, rays.o[idx], rays.d[idx], 64.0, 256, sdf_fp32=True)
     for k, v in (("rgb", rgb), ("depth", depth), ("wsum", wsum)):
         e = rel_err_elementwise(v.cpu().numpy()[idx], r[k])
         assert e <= RGB_DEPTH_RTOL, (k, e)
+        e32 = rel_err_elementwise(v.cpu().numpy()[idx], r32[k], floor=REL_FLOOR_S32)
+        assert e32 <= RGB_DEPTH_RTOL, (k + " (FP32-rounded s, 1e-3 floor)", e32)
 
 
 def test_full_size_backward_subset_parity(object256):
     sc, rays = object256
     idx = synth.rng(4).choice(rays.o.shape[0], 384, replace=False)
     check_backward(sc, rays.o[idx], rays.d[idx], 64.0, 256, min_kept=0.3)
+
+
+def test_full_batch_adjoint_parity_at_the_bench_launch(object256):
+    """The adjoint of the benchmark's whole launch (2^18 rays x 256 samples,
+    its kernel configuration and live extents) against the FP64 oracle's over
+    the same rays: all four gradient tensors at the FP32 bar, with every
+    CTA-level probe / MLP reduction and the contention of the grid reductions
+    of the timed launch.  The cotangent is the L1 loss gradient of the
+    oracle's colours against the targets, zeroed on the rays that pass within
+    the kink margin of a ReLU or alpha-clip decision (the launch keeps its
+    shape; those rays add exactly nothing on either side)."""
+    sc, rays = object256
+    n = rays.o.shape[0]
+    tau, N = 64.0, 256
+    r = oracle_forward(sc, rays.o, rays.d, tau, N, margin=True)
+    keep = r["margin"] > KINK_MARGIN
+    assert keep.mean() > 0.5, keep.mean()
+    drgb = (np.sign(r["rgb"] - rays.target) / (3.0 * n) * keep[:, None]).astype(np.float32)
+    scene = ps.Scene.from_host(sc)
+    params = ps.render_params(tau, N, 0, 3)
+    gg = gpu_backward(scene, rays.o, rays.d, params, drgb)
+    gr = oracle_backward(sc, rays.o, rays.d, drgb.astype(np.float64), tau, N)
+    errs = {k: rel_err_tensor(gg[k], gr[k]) for k in ("sdf", "feat", "probes", "mlp")}
+    errs["rays_kept"] = int(keep.sum())
+    log_errors("full-batch adjoint object256", errs)
+    errs.pop("rays_kept")
+    for k, e in errs.items():
+        assert e <= GRAD_RTOL, (k, e, errs)
 
 
 def test_full_size_backward_runs_and_is_finite(object256):
@@ -446,6 +484,40 @@ def test_gpu_central_differences():
     assert np.linalg.norm(fds - ans) <= 2.5e-2 * np.linalg.norm(ans)
 
 
+def test_tensor_core_waits_that_run_out_are_reported_and_the_gpu_stays_usable(sphere64):
+    """With the wait limit at 0 polls every tensor-core completion wait runs out
+    at once (no tensor core can answer that fast): the forward, the adjoint
+    and node shading stop early, set bit 0 of the device status word, free
+    their tensor memory and return, without a trap or a hang.  With the
+    default limit restored, the next launches (which allocate tensor memory
+    again) match the oracle."""
+    sc, rays = sphere64
+    o, d = rays.o[:512], rays.d[:512]
+    tau, N = 64.0, 128
+    scene = ps.Scene.from_host(sc)
+    params = ps.render_params(tau, N, 0, 3)
+    o_, d_ = dev(o), dev(d)
+    _, _, _, logT, live = ps.render_forward(scene, o_, d_, params, want_live=True)
+    assert ps.device_status() == 0
+    drgb = dev(synth.rng(31).normal(size=(512, 3)) / 512)
+    ps.set_wait_polls(0)
+    try:
+        assert ps.wait_polls() == 0
+        ps.render_forward(scene, o_, d_, params)
+        assert ps.device_status() & 1
+        gg, gp, gm = scene.grad_buffers()
+        ps.render_backward(scene, o_, d_, params, drgb, logT, grads=(gg, gp, gm), n_live=live)
+        assert ps.device_status() & 1
+        ps.shade_nodes(scene, (2.0, 0.5, 0.5), 0.1, params)
+        assert ps.device_status() & 1
+    finally:
+        ps.set_wait_polls(None)
+    assert ps.wait_polls() == 1 << 24
+    assert ps.device_status() == 0
+    check_forward(sc, o, d, tau, N)
+    check_backward(sc, o, d, tau, N)
+
+
 def test_live_extent_matches_oracle_and_skipping_is_exact(sphere64):
     """n_live (1 + the last sample with a nonzero opacity) equals the oracle's
     on rays away from the clip kink, and the adjoint that skips the samples
@@ -471,3 +543,94 @@ def test_live_extent_matches_oracle_and_skipping_is_exact(sphere64):
     b = gpu_backward(scene, o, d, params, drgb, use_live=False)
     for k in a:
         assert rel_err_tensor(a[k], b[k]) <= 1e-6, (k, rel_err_tensor(a[k], b[k]))
+
+
+# ---------------------------------------------------------------------------
+# The adjoint-stress configuration: 512^3 FP32 SDF + 3 BF16 features per node,
+# probes 64^3 x 9 SH x 8 channels FP32, MLP 14 -> 32 -> 32 -> 3 (FP32-equivalent
+# on the tensor cores), 2^20 rays x 512 samples, activations recomputed
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def stress512():
+    sc = synth.make_scene("stress512")
+    rays = synth.make_rays("stress512")
+    return sc, rays
+
+
+def test_adjoint_stress_oracle_subset(stress512):
+    """The full 2^20 x 512 launch with a cotangent that is nonzero on 1024
+    random rays only (rays away from the ReLU / alpha-clip kinks): its
+    gradients are those rays' alone, and equal the FP64 oracle's on them (on
+    the BF16-rounded feature values the kernels read) at the FP32 bar."""
+    sc, rays = stress512
+    tau, N = 64.0, 512
+    n = rays.o.shape[0]
+    ref_sc = stored_values(sc, feat_bf16=True)
+    cand = synth.rng(91).choice(n, 2048, replace=False)
+    clean = clean_rays(ref_sc, rays.o[cand], rays.d[cand], tau, N)
+    assert clean.size >= 1024, clean.size
+    sub = np.sort(cand[clean[:1024]])
+    drgb = np.zeros((n, 3), np.float32)
+    drgb[sub] = (synth.rng(92).normal(size=(sub.size, 3)) / sub.size).astype(np.float32)
+    scene = ps.Scene.from_host(sc, feat_dtype=ps.BF16)
+    params = ps.render_params(tau, N, 0, 3)
+    gg = gpu_backward(scene, rays.o, rays.d, params, drgb)
+    gr = oracle_backward(ref_sc, rays.o[sub], rays.d[sub], drgb[sub].astype(np.float64), tau, N)
+    errs = {k: rel_err_tensor(gg[k], gr[k]) for k in ("sdf", "feat", "probes", "mlp")}
+    log_errors("adjoint stress oracle subset", errs)
+    for k, e in errs.items():
+        assert e <= GRAD_RTOL, (k, e, errs)
+
+
+def test_adjoint_stress_central_differences(stress512):
+    """torch.autograd.Function gradients of L = sum(wts * rgb) over all 2^20
+    rays x 512 samples against central differences of the FP32 forward,
+    h = 1e-3, on 64 random parameters with significant gradients: probe
+    coefficients and MLP weights (the BF16 feature storage cannot represent a
+    1e-3 step, and an SDF step moves the alpha-clip kinks of Eq. 9; both are
+    held to the oracle above).  Bars as the small-scene test: 10% per
+    parameter, 2.5% over the 64 in the L2 sense."""
+    sc, rays = stress512
+    tau, N = 64.0, 512
+    scene = ps.Scene.from_host(sc, feat_dtype=ps.BF16)
+    gd32 = ps.grid_desc(sc.dims, sc.box_min, sc.box_max, 3, ps.F32)
+    grid_master = ps.pack_grid(gd32, torch.as_tensor(sc.sdf, device="cuda"),
+                               torch.as_tensor(sc.feat, device="cuda")).requires_grad_(True)
+    probes = scene.probes.requires_grad_(True)
+    mlp = scene.mlp.requires_grad_(True)
+    params = ps.render_params(tau, N, 0, 3)
+    o, d = dev(rays.o), dev(rays.d)
+    wts = dev(synth.rng(93).normal(size=(rays.o.shape[0], 3)))
+    rgb, _, _ = ps.render(scene, o, d, params, masters=(grid_master, probes))
+    (rgb * wts).sum().backward()
+    gp, gm = probes.grad.detach(), mlp.grad.detach()
+    probes.requires_grad_(False)
+    mlp.requires_grad_(False)
+
+    def loss():
+        out, _, _, _ = ps.render_forward(scene, o, d, params)
+        return float((out.double() * wts.double()).sum())
+
+    g = synth.rng(94)
+    h = 1e-3
+    fds, ans = [], []
+    for tensor, grad, count in ((scene.probes, gp, 32), (scene.mlp, gm, 32)):
+        flat, gflat = tensor.view(-1), grad.reshape(-1)
+        nz = torch.nonzero(gflat.abs() > 0.1 * gflat.abs().max()).view(-1).cpu().numpy()
+        for i in g.choice(nz, min(count, nz.size), replace=False):
+            old = float(flat[i])
+            flat[i] = old + h
+            lp = loss()
+            flat[i] = old - h
+            lm = loss()
+            flat[i] = old
+            fd, an = (lp - lm) / (2 * h), float(gflat[i])
+            assert abs(fd - an) <= 1e-1 * abs(an), (i, fd, an)
+            fds.append(fd)
+            ans.append(an)
+    fds, ans = np.array(fds), np.array(ans)
+    assert fds.size == 64
+    rel = float(np.linalg.norm(fds - ans) / np.linalg.norm(ans))
+    log_errors("adjoint stress central differences", {"l2_rel": rel})
+    assert rel <= 2.5e-2, rel

@@ -169,8 +169,12 @@ def test_sparse_validation():
     gd, _, _ = s.descs(3)
     hat = torch.zeros(tuple(reversed(sc.dims)), dtype=torch.float32, device="cuda")
     gg, _, _ = s.grad_buffers()
-    with pytest.raises(ps.LibraryError, match="compiled"):  # the SDF terms: dense grids only
+    with pytest.raises(ps.LibraryError, match="stored nodes"):  # s_hat holds the bricks
         ps.grid_regularizers(gd, hat, s.grid, gg, torch.zeros_like(hat), 1.0, 1.0, 1.0)
+    hb = torch.zeros((s.n_bricks, 16, 16, 16), dtype=torch.float32, device="cuda")
+    with pytest.raises(ps.LibraryError, match="compiled"):  # L_features: tile tri-planes only
+        ps.grid_regularizers(gd, hb, s.grid, gg, torch.zeros_like(hb), 1.0, 1.0, 1.0,
+                             lam_features=1.0)
     with pytest.raises(ps.LibraryError, match="stored nodes"):  # s_hat holds the bricks
         ps.sdf_smooth(gd, hat, s.grid)
 
@@ -392,3 +396,50 @@ def test_sparse_smoothing_adjoint_matches_the_full_grid(accumulate):
     err = float(np.abs(d_hat.cpu().numpy() - ref).max())
     log_errors(f"sparse smoothing adjoint acc={accumulate}", {"abs": err})
     assert err <= 4e-5 * float(np.abs(ds).max())
+
+
+@pytest.mark.parametrize("dims", [(96, 80, 112), (48, 32, 64)])
+def test_sparse_sdf_regularizers_match_the_full_grid(dims):
+    """L_sdf, L_Eik and L_normal on a sparse grid against the oracle's terms
+    of the stored nodes on the dense-equivalent grid (every node of an absent
+    brick at empty_sdf, in s and s_hat): the three loss values, and the
+    gradients w.r.t. s and s_hat at the stored nodes.  Random brick masks that
+    keep the grid's corner bricks, so grid faces, absent neighbours across a
+    brick face and stored neighbours across one all occur."""
+    from oracle import regularizers as ORC
+    sc, s, node_keep = sparse_case(dims=dims, probe_dims=(3, 3, 3),
+                                   keep=random_bricks(dims, 3 * sum(dims)))
+    keep = node_keep[::16, ::16, ::16]
+    gd, _, _ = s.descs(3)
+    g = synth.rng(71)
+    hat = np.where(node_keep, sc.sdf + g.normal(0, 0.05, size=sc.sdf.shape),
+                   EMPTY).astype(np.float32)
+    # the smoothed SDF both sides read: the oracle's smoothing, rounded to FP32,
+    # written into the stored records (absent nodes read empty_sdf)
+    s_ref = np.where(node_keep, ORC.smooth(hat.astype(np.float64)), EMPTY).astype(np.float32)
+    values = s.grid.clone()
+    w = ps.table_words(gd)
+    values.view(-1)[w:].view(-1, 4)[:, 0] = dev(brick_array(s_ref, keep)).reshape(-1)
+    gg, _, _ = s.grad_buffers()
+    gg.zero_()
+    n = int(keep.sum())
+    base = g.normal(0, 1, size=(n, 16, 16, 16)).astype(np.float32)
+    d_hat = dev(base)
+    loss = torch.zeros(4, dtype=torch.float32, device="cuda")
+    lam = (1.0, 0.1, 0.02)
+    ps.grid_regularizers(gd, dev(brick_array(hat, keep)), values, gg, d_hat, *lam, loss=loss)
+    assert ps.device_status() == 0
+    h = ORC.spacing(dims, sc.box_min, sc.box_max)
+    vals, ds, ds_hat = ORC.sdf_terms(hat, s_ref, h, *lam, owner=node_keep)
+    got_ds = gg.view(-1)[w:].view(-1, 4)[:, 0].reshape(n, 16, 16, 16).cpu().numpy()
+    errs = {"ds": rel_err_tensor(got_ds, brick_array(ds, keep)),
+            "ds_hat": rel_err_tensor(d_hat.cpu().numpy() - base, brick_array(ds_hat, keep))}
+    lv = loss.cpu().numpy()
+    for i, k in enumerate(("sdf", "eik", "normal")):
+        errs[k] = abs(float(lv[i]) - vals[k]) / max(abs(vals[k]), 1e-30)
+    log_errors(f"sparse sdf terms {dims}", errs)
+    assert errs["ds"] <= GRAD_RTOL and errs["ds_hat"] <= GRAD_RTOL, errs
+    for k in ("sdf", "eik", "normal"):
+        assert vals[k] > 0.0 and errs[k] <= 1e-4, (k, errs)
+    # the features' gradient slots stay zero
+    assert float(gg.view(-1)[w:].view(-1, 4)[:, 1:].abs().max()) == 0.0
