@@ -177,8 +177,12 @@ def test_sparse_grid_descriptors_on_the_host(lib):
     lib.psdf_sdf_smooth_adjoint.argtypes = [P, P, P, ctypes.c_int32, P]
     assert lib.psdf_sdf_smooth_adjoint(ctypes.byref(gd), P(0x1004), P(0x2000), 0, None) == -4
     lib.psdf_grid_regularizers.argtypes = [P, P, P, f, f, f, f, P, P, P, P]
+    # the SDF terms take sparse grids; L_features needs tile tri-planes, and the
+    # buffers must be 16-byte aligned (both refused before any CUDA call)
     assert lib.psdf_grid_regularizers(ctypes.byref(gd), P(0x1000), P(0x2000), 1.0, 1.0, 1.0,
-                                      0.0, P(0x3000), P(0x4000), None, None) == -6
+                                      1.0, P(0x3000), P(0x4000), None, None) == -6
+    assert lib.psdf_grid_regularizers(ctypes.byref(gd), P(0x1000), P(0x2004), 1.0, 1.0, 1.0,
+                                      0.0, P(0x3000), P(0x4000), None, None) == -4
 
 
 def test_sparse_scene_checks_the_brick_mask_shape():

