@@ -28,7 +28,11 @@ struct FwdLayout {
     static constexpr int oW = 0;
     static constexpr int oF32 = oW + M::kWeightBytes;
     static constexpr int oX = (oF32 + 4 * M::kF32 + 127) & ~127;
-    static constexpr int oH = oX + M::kSplit * kXT;
+    // the hidden tile reuses the input tile's bytes: layer 1 has read the
+    // input (its MMA completed) before the hidden rows are written, and layer
+    // 2 has completed before the next chunk writes its input rows
+    static constexpr int oH = oX;
+    static_assert(kHT >= kXT, "the hidden tile covers the input tile");
     static constexpr int oTab = oH + M::kSplit * kHT;  // per warp: 64-float placement table
     static constexpr int oBar = oTab + 4 * 64 * 4;
     static constexpr int kBytes = oBar + 16;
@@ -36,7 +40,7 @@ struct FwdLayout {
 };
 
 template <class C>
-__global__ void __launch_bounds__(kFwdThreads, 5)
+__global__ void __launch_bounds__(kFwdThreads, 4)
 render_forward_kernel(RenderArgs A)
 {
     using M = MlpTC<C>;
@@ -52,11 +56,15 @@ render_forward_kernel(RenderArgs A)
     float* stab = reinterpret_cast<float*>(smem + L::oTab);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::oBar);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::oBar + 8);
+    int* sbad = reinterpret_cast<int*>(smem + L::oBar + 12);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     load_mlp_tc<C>(A.mlp, wt, f32);
     if (warp == 0) tc::tmem_alloc(tslot, L::kTmemCols);
-    if (tid == 0) tc::mbar_init(mbar, 1);
+    if (tid == 0) {
+        tc::mbar_init(mbar, 1);
+        *sbad = 0;
+    }
     tc::fence_smem_to_async();
     tc::fence_before();
     __syncthreads();
@@ -99,6 +107,22 @@ render_forward_kernel(RenderArgs A)
         float acc_r = 0.f, acc_g = 0.f, acc_b = 0.f, acc_d = 0.f, acc_w = 0.f;
         float carry = 0.f, comp = 0.f;  // Kahan sum of log T over chunks
         int n_live = 0;                 // 1 + last sample with lam < 0
+        // Lane l of a chunk gathers point k + 1 (the opacity of sample k needs
+        // both ends of its interval) and takes sample k's SDF value, gradient
+        // and spatial features from lane l - 1; lane 0 takes them from the
+        // previous chunk's lane 31, and in a ray's first chunk from point 0,
+        // gathered here.  So no lane gathers a second point after its own.
+        float c_s = 0.f, c_g[3] = {0.f, 0.f, 0.f}, c_f[3] = {0.f, 0.f, 0.f};
+        if (have) {
+            SampleGeom<C> P;
+            eval_sdf<C>(A, R.o, R.d, span_t(sp, 0), P);
+            c_s = P.s;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                c_g[a] = P.g[a];
+                c_f[a] = P.x[a];
+            }
+        }
         for (int base = 0; base < N; base += 32) {
             const int k = base + lane;
             const bool active = have && k < N;
@@ -106,14 +130,30 @@ render_forward_kernel(RenderArgs A)
             // ---- P0: geometry, angular and spatial features -> input row ----
             if (have) {
                 t = span_t(sp, k < N ? k : N - 1);
-                SampleGeom<C> S;
-                eval_sdf<C>(A, R.o, R.d, t, S);
-                float s_next = __shfl_down_sync(FULL, S.s, 1);
-                if (active && (lane == 31 || k + 1 >= N)) {
-                    float xw[3];
-                    point_at(R.o, R.d, span_t(sp, k + 1), xw);
-                    s_next = sdf_value(A.grid, locate(xw, A.grid.bmin, A.grid.sc, A.grid.R));
+                SampleGeom<C> P;  // point k + 1 (lanes past the ray's end: point N)
+                eval_sdf<C>(A, R.o, R.d, span_t(sp, k < N ? k + 1 : N), P);
+                SampleGeom<C> S;  // sample k
+                S.s = __shfl_up_sync(FULL, P.s, 1);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    S.g[a] = __shfl_up_sync(FULL, P.g[a], 1);
+                    S.x[a] = __shfl_up_sync(FULL, P.x[a], 1);
                 }
+                if (lane == 0) {
+                    S.s = c_s;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        S.g[a] = c_g[a];
+                        S.x[a] = c_f[a];
+                    }
+                }
+                c_s = __shfl_sync(FULL, P.s, 31);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    c_g[a] = __shfl_sync(FULL, P.g[a], 31);
+                    c_f[a] = __shfl_sync(FULL, P.x[a], 31);
+                }
+                const float s_next = P.s;
                 bool opaque = false;
                 if (active) {
                     const float diff = log_transmittance(A.tau, S.s, s_next);
@@ -135,10 +175,18 @@ render_forward_kernel(RenderArgs A)
             }
             tc::fence_smem_to_async();
             tc::fence_before();
-            if (__syncthreads_or(bad)) goto done;
+            // One barrier both publishes the input rows and tells whether any
+            // sample of the CTA's 128 has a nonzero opacity; a failed wait
+            // (rare) is passed on through shared memory
+            if (bad) *sbad = 1;
+            const bool run_mlp = __syncthreads_or(lam < 0.0f);
+            if (*sbad) goto done;
             tc::fence_after();
             // ---- P1: layer 1 on the tensor cores ----
-            if (tid == 0) {
+            // Without an opaque sample every weight of the chunk is zero and
+            // no colour reaches an output: the MLP is skipped (the outputs are
+            // the same bits), only the transmittance carry below is updated.
+            if (run_mlp && tid == 0) {
                 mma_k<M::kSplit>(tmem + 0, xh, xl, M::w1h(wt), M::w1l(wt), 128,
                                  (M::K1 / 8) * 128, 128, (M::K1 / 8) * 128, M::kIdescL, false);
                 tc::commit(mbar);
@@ -164,6 +212,7 @@ render_forward_kernel(RenderArgs A)
                 comp = (tt - carry) - y;
                 carry = tt;
             }
+            if (!run_mlp) continue;
             bad |= !tc::mbar_wait(mbar, phase, A.wait_polls);
             phase ^= 1;
             tc::fence_after();
