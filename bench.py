@@ -721,6 +721,73 @@ def psnr_inside(rgb, ref_rgb, mask):
     return 10.0 * math.log10(1.0 / max(mse, 1e-20))
 
 
+# L_features / L_probes weights of the tri-plane appearance fit behind the
+# two-pass viewer form
+TRIPLANE_FIT_LAMBDAS = (1e-4, 1e-3)
+
+
+def twopass_triplane(ps, fit, synth, base, spec, tau, o, d, cam_of, n_views, timed, device,
+                     shape):
+    """The paper's viewer (per-view node shading, then the colour-field march)
+    on the inference scene with tile tri-plane features (the paper's F_s),
+    its appearance fitted with the paper's smoothness terms L_features and
+    L_probes (Eqs. 14-15) at each weight of TRIPLANE_FIT_LAMBDAS; PSNR inside
+    the silhouette of the scene's own FP32 uniform 1024-sample render, against
+    the per-sample FP32 uniform 256-sample form of the same scene."""
+    import numpy as np
+    import torch
+
+    n = o.shape[0]
+    view_n = n // n_views
+    sc = synth.with_triplanes(synth.inference_scene(base), spec["seed"] + 31)
+    pool = synth.training_pool(base, 1 << 16, seed_offset=1000)
+    p256 = ps.render_params(tau, 256, n_fresnel=sc.n_fresnel)
+    p1024 = ps.render_params(tau, 1024, n_fresnel=sc.n_fresnel)
+    Rz, Ry, Rx = shape
+    col16 = torch.empty((Rz, Ry, Rx, 4), dtype=torch.float16, device=device)
+    out = {}
+    for lam in TRIPLANE_FIT_LAMBDAS:
+        scene = ps.Scene.from_host(sc, device=device)
+        log = fit.fit_appearance(scene, torch.as_tensor(pool.o, device=device),
+                                 torch.as_tensor(pool.d, device=device),
+                                 torch.as_tensor(pool.target, device=device), p256, steps=200,
+                                 batch=1 << 14, lam_features=lam, lam_probes=lam)
+        ref = ps.render_forward(scene, o, d, p1024)
+        ref_rgb, ref_w = ref[0].cpu().numpy(), ref[2].cpu().numpy()
+        mask = ref_w > 0.5
+        del ref
+        ms_u, out_u = timed(lambda: ps.render_forward(scene, o, d, p256))
+        psnr_u = psnr_inside(out_u[0].cpu().numpy(), ref_rgb, mask)
+
+        def two_pass(band):
+            outs = []
+            for v in range(n_views):
+                sl = slice(v * view_n, (v + 1) * view_n)
+                ps.shade_nodes(scene, cam_of[v], band, p256, out=col16)
+                outs.append(ps.render_colour_field(scene, col16, o[sl], d[sl], p256))
+            return outs
+
+        forms = {}
+        for band in (0.1, 0.25, float("inf")):
+            ms, outs = timed(lambda: two_pass(band))
+            rgb = torch.cat([x[0] for x in outs]).cpu().numpy()
+            forms[f"band{band}_uniform256"] = {
+                "ms_per_frame": ms / n_views, "psnr_db": psnr_inside(rgb, ref_rgb, mask),
+                "psnr_vs_per_sample256_db": psnr_inside(rgb, out_u[0].cpu().numpy(), mask),
+                "band": band}
+        matched = [k for k in forms if forms[k]["psnr_db"] >= psnr_u - 0.1]
+        best = min(matched or forms, key=lambda k: forms[k]["ms_per_frame"]
+                   if matched else -forms[k]["psnr_db"])
+        out[f"lambda{lam:g}"] = {
+            "fit_l2": [log[0][1], log[-1][1]],
+            "per_sample_uniform256": {"ms_per_frame": ms_u / n_views, "psnr_db": psnr_u},
+            "forms": forms, "chosen": best, "matched": bool(matched),
+            "ms_per_frame": forms[best]["ms_per_frame"], "psnr_db": forms[best]["psnr_db"],
+            "speedup_vs_per_sample256": (ms_u / n_views) / forms[best]["ms_per_frame"]}
+        del scene
+    return out
+
+
 def run_inference(args, world, rank, local):
     import numpy as np
     import torch
@@ -881,6 +948,10 @@ def run_inference(args, world, rank, local):
     march_ms = statistics.mean(b.elapsed_time(c) for _, b, c in split)
     band_nodes = int((torch.as_tensor(sc.sdf).abs() < bf["band"]).sum())
 
+    tp_tri = twopass_triplane(ps, fit, synth, base, spec, tau, o, d, cam_of, n_views,
+                              lambda fn: timed(fn, args.steps, args.warmup), device,
+                              (Rz, Ry, Rx))
+
     # end to end through the public API: pinned host rays in, rgb read back
     h_rgb = torch.empty((n, 3), dtype=torch.float32).pin_memory()
 
@@ -938,6 +1009,7 @@ def run_inference(args, world, rank, local):
             "shade_ns_per_band_node": shade_ms * 1e6 / max(band_nodes, 1),
             "note": "per view: shade every node of the band for that camera (BF16 features, "
                     "FP16 probes, FP16 MLP, FP16 colour records), then march the view's rays"},
+        "two_pass_triplane": tp_tri,
         "clocks": clk,
         "gpu_launches": 2 * args.steps,
         "training": {"appearance_l2": [fit_log[0][1], fit_log[-1][1]],
@@ -1020,6 +1092,10 @@ def inference_summary(inf):
                                         "speedup_vs_uniform256", "kernels_ms_per_view")},
         "two_pass_forms": {k: {"ms_per_frame": v["ms_per_frame"], "psnr_db": v["psnr_db"]}
                            for k, v in tp["forms"].items()},
+        "two_pass_triplane": {k: {kk: v[kk] for kk in ("per_sample_uniform256", "chosen",
+                                                         "matched", "ms_per_frame", "psnr_db",
+                                                         "speedup_vs_per_sample256", "fit_l2")}
+                              for k, v in inf["two_pass_triplane"].items()},
         "cpu_baseline": inf.get("cpu_baseline"), "clocks": inf["clocks"],
         "gpu_launches": inf["gpu_launches"], "training": inf["training"],
         "device_status": inf["device_status"],

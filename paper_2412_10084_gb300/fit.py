@@ -25,9 +25,9 @@ import dataclasses
 import torch
 
 from . import (F32, FEAT_TRIPLANE, Adam, LibraryError, RenderParams, Scene, device_status,
-               occupancy_build, proposal_backward, proposal_desc, proposal_forward,
-               proposal_param_count, render_backward, render_forward, render_params, table_words,
-               weight_histogram)
+               grid_regularizers, occupancy_build, probe_smoothness, proposal_backward,
+               proposal_desc, proposal_forward, proposal_param_count, render_backward,
+               render_forward, render_params, table_words, weight_histogram)
 
 
 def _check_device(what: str, step: int):
@@ -62,13 +62,26 @@ def trainable_grid(gd, values, grad):
 
 def fit_appearance(scene: Scene, rays_o, rays_d, target, params: RenderParams, steps=200,
                    batch=1 << 14, lr_grid=1e-2, lr_probes=1e-2, lr_mlp=2e-3, train_sdf=False,
-                   seed=0, log_every=50):
-    """Fits an FP32-stored scene in place; returns [(step, mean L2 loss)]."""
+                   seed=0, log_every=50, lam_features=0.0, lam_probes=0.0):
+    """Fits an FP32-stored scene in place; returns [(step, mean L2 loss)].
+
+    lam_features (tile tri-plane grids) and lam_probes add the paper's
+    smoothness terms L_features (Eq. 14) and L_probes (Eq. 15), with their
+    gradients from the library's kernels, to the photometric objective."""
     if (scene.feat_dtype, scene.probe_dtype, scene.mlp_dtype) != (F32, F32, F32):
         raise LibraryError("fit_appearance trains FP32 storage; convert afterwards")
     dev = scene.grid.device
     gg, gp, gm = scene.grad_buffers()
-    grid_vals, grid_grads, sdf_grads = trainable_grid(scene.descs(3)[0], scene.grid, gg)
+    gd, pd, _ = scene.descs(3)
+    grid_vals, grid_grads, sdf_grads = trainable_grid(gd, scene.grid, gg)
+    if lam_features > 0.0:
+        if gd.feat_layout != FEAT_TRIPLANE:
+            raise LibraryError("fit_appearance: lam_features needs tile tri-plane features")
+        # the regulariser call takes the raw SDF; with zero SDF weights it adds
+        # nothing to the SDF gradients (which this loop zeroes anyway)
+        n_nodes = int(gd.dims[0]) * int(gd.dims[1]) * int(gd.dims[2])
+        s_hat = sdf_grads.new_zeros(n_nodes)
+        d_hat = sdf_grads.new_zeros(n_nodes)
     opt = Adam([(grid_vals, grid_grads, lr_grid),
                 (scene.probes.view(-1), gp.view(-1), lr_probes),
                 (scene.mlp.view(-1), gm.view(-1), lr_mlp)])
@@ -84,6 +97,10 @@ def fit_appearance(scene: Scene, rays_o, rays_d, target, params: RenderParams, s
         d_rgb = (2.0 / batch) * diff
         render_backward(scene, o, d, params, d_rgb.contiguous(), logT, grads=(gg, gp, gm),
                         n_live=live)
+        if lam_features > 0.0:
+            grid_regularizers(gd, s_hat, scene.grid, gg, d_hat, 0.0, 0.0, 0.0, lam_features)
+        if lam_probes > 0.0:
+            probe_smoothness(pd, scene.probes, gp, lam_probes)
         if not train_sdf:
             sdf_grads.zero_()
         opt.step()
