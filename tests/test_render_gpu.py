@@ -190,6 +190,60 @@ def test_explicit_sample_distances():
     check_backward(sc, rays.o, rays.d, 64.0, N, t_samples=t)
 
 
+@pytest.mark.parametrize("case", ["uniform", "explicit", "view_bg", "bf16", "triplane", "l4",
+                                  "n33"])
+def test_live_extent_in_every_layout_and_placement(case):
+    """Asking the forward for the live extents changes no output bit, in each
+    grid layout and sample placement, and the extents equal the oracle's
+    (1 + the last sample with a nonzero weight) on rays away from the kinks."""
+    sc = synth.make_scene("sphere64", dims=(40, 36, 44), probe_dims=(6, 5, 7))
+    rays = synth.make_rays("sphere64", n_rays=900, seed_offset=41)
+    N, mode, bg, ts = 96, 0, (0.0, 0.0, 0.0), None
+    kw = {}
+    if case == "explicit":
+        tn, tf, hit = box_interval(rays.o, rays.d, sc.box_min, sc.box_max)
+        u = np.sort(synth.rng(42).uniform(0.0, 1.0, size=(900, N + 1)), axis=1)
+        ts = dev((tn[:, None] + 1e-3 + u * np.maximum(tf - tn - 2e-3, 0.0)[:, None])
+                 .astype(np.float32) * hit[:, None])
+    elif case == "view_bg":
+        mode, bg = 1, (0.3, 0.6, 0.9)
+    elif case == "bf16":  # BF16 features with FP32 probes: 8 channels, width 32 compiled in
+        g = synth.rng(45)
+        sc.width = 32
+        sc.probes = g.normal(0, 0.1, size=(7, 5, 6, 9, 8)).astype(np.float32)
+        sc.mlp = synth.mlp_params(3 + 8 + 3, 32, g)
+        kw = dict(feat_dtype=ps.BF16)
+    elif case == "triplane":
+        sc = synth.with_triplanes(sc, 43)
+    elif case == "l4":
+        g = synth.rng(44)
+        sc.sh_l, sc.width = 4, 32
+        sc.probes = g.normal(0, 0.1, size=(7, 5, 6, 16, 4)).astype(np.float32)
+        sc.mlp = synth.mlp_params(10, 32, g)
+    elif case == "n33":
+        N = 33
+    scene = ps.Scene.from_host(sc, **kw)
+    params = ps.render_params(64.0, N, mode, 3, bg)
+    o, d = dev(rays.o), dev(rays.d)
+    a = ps.render_forward(scene, o, d, params, ts)
+    b = ps.render_forward(scene, o, d, params, ts, want_live=True)
+    assert ps.device_status() == 0
+    for x, y in zip(a, b[:4]):
+        assert torch.equal(x, y)
+    r = oracle_forward(sc if case != "bf16" else stored_values(sc, feat_bf16=True),
+                       rays.o, rays.d, 64.0, N, dir_mode=mode, bg=bg,
+                       t_samples=None if ts is None else ts.cpu().numpy(), margin=True)
+    keep = r["margin"] > KINK_MARGIN
+    m = oracle.Model.from_scene(sc)
+    live = b[4].cpu().numpy()
+    for i in np.nonzero(keep)[0][:40]:
+        tr = oracle.render_trace(m, rays.o[i], rays.d[i], 64.0, N, dir_mode=mode,
+                                 t_samples=None if ts is None else ts[i].cpu().numpy())
+        ref = int(np.nonzero(tr["w"] > 0)[0].max() + 1) if tr["hit"] and np.any(tr["w"] > 0) \
+            else 0
+        assert live[i] == ref, (i, live[i], ref)
+
+
 def test_empty_batch_and_misses():
     sc = synth.make_scene("sphere64", dims=(16, 16, 16), probe_dims=(4, 4, 4))
     scene = ps.Scene.from_host(sc)
@@ -345,6 +399,11 @@ def test_full_size_forward_sampled_parity_and_invariants(object256):
     rgb2, depth2, wsum2, logT2 = ps.render_forward(scene, o, d, params)
     torch.cuda.synchronize()
     assert torch.equal(rgb, rgb2) and torch.equal(depth, depth2) and torch.equal(wsum, wsum2)
+    # asking for the live extents changes no output bit
+    rgb3, depth3, wsum3, logT3, live = ps.render_forward(scene, o, d, params, want_live=True)
+    assert torch.equal(rgb, rgb3) and torch.equal(depth, depth3) and torch.equal(wsum, wsum3)
+    assert torch.equal(logT, logT3)
+    assert 0 < float(live.float().mean()) < 256
     for t in (rgb, depth, wsum, logT):
         assert torch.isfinite(t).all()
     assert float(wsum.min()) >= 0.0 and float(wsum.max()) <= 1.0 + 1e-6
