@@ -67,6 +67,13 @@ WORKLOADS = {
               "object-capture cameras, tau 256, L1 loss"),
         feat="f32", probe="f32", mlp="f32", dtype="f32", base="object256", sparse=True,
         R=1024, band=0.03, tau=256.0),
+    "object512_sparse": dict(
+        desc=("sparse-grid training step, the object-capture shape sampled on a 512^3 node grid "
+              "stored as 16^3-node bricks within 0.03 of the surface (the rest read as empty "
+              "space), FP32 SDF + 3 features/node, probes 32^3 x 9 SH x 4 ch, MLP 10->32->32->3, "
+              "2^18 rays x 256 samples of the object-capture cameras, tau 128, L1 loss"),
+        feat="f32", probe="f32", mlp="f32", dtype="f32", base="object256", sparse=True,
+        R=512, band=0.03, tau=128.0),
     "inference1080": dict(
         desc=("real-time inference on the object-capture scene (256^3, probes 32^3, MLP "
               "10->32->32->3; features smooth noise over ~3 voxels) after 200 steps of "
@@ -707,8 +714,8 @@ def finish_grid_passes(gt, peak):
             "nodes": gt["nodes"], "texels": gt["texels"], "probe_coeffs": gt["probe_coeffs"],
             "sdf_slot_stride_bytes": gt["sdf_stride_bytes"], "lambdas": gt["lambdas"],
             "note": "timed after the training step, 256 MB L2 flush before each pass set"
-                    + ("; sparse grid: nodes = stored nodes, the SDF regularisers take dense "
-                       "grids and are not run" if gt["sparse"] else "")}
+                    + ("; sparse grid: nodes = stored nodes, the SDF regularisers sum the "
+                       "stored nodes' terms" if gt["sparse"] else "")}
 
 
 # ---------------------------------------------------------------------------
