@@ -82,7 +82,7 @@ class _Params(ctypes.Structure):
         ("dir_mode", ctypes.c_int32),
         ("bg", ctypes.c_double * 3),
         ("sdf_fp32", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("mlp_f16", ctypes.c_int32),
     ]
 
 
@@ -105,6 +105,8 @@ def _load():
         if _lib is None:
             lib = ctypes.CDLL(build())
             P = ctypes.c_void_p
+            lib.orc_round_f16.argtypes = [ctypes.c_double]
+            lib.orc_round_f16.restype = ctypes.c_double
             lib.orc_sh_eval.argtypes = [ctypes.c_int32, P, P]
             lib.orc_sh_grad.argtypes = [ctypes.c_int32, P, P]
             lib.orc_render_forward.argtypes = [P, P, ctypes.c_int64, P, P, P, P, P, P, P, P,
@@ -207,23 +209,28 @@ class Model:
                    sc.width, sc.n_fresnel, planes=getattr(sc, "planes", None))
 
 
-def _params(tau, n_samples, dir_mode=DIR_REFLECT, bg=(0.0, 0.0, 0.0), sdf_fp32=False):
+def _params(tau, n_samples, dir_mode=DIR_REFLECT, bg=(0.0, 0.0, 0.0), sdf_fp32=False,
+            mlp_f16=False):
     p = _Params()
     p.tau = float(tau)
     p.n_samples = int(n_samples)
     p.dir_mode = int(dir_mode)
     p.bg[:] = tuple(float(v) for v in bg)
     p.sdf_fp32 = int(bool(sdf_fp32))
+    p.mlp_f16 = int(bool(mlp_f16))
     return p
 
 
 def render_forward(model: Model, rays_o, rays_d, tau, n_samples, dir_mode=DIR_REFLECT,
                    bg=(0.0, 0.0, 0.0), t_samples=None, n_threads=1, margin=False,
-                   sdf_fp32=False):
+                   sdf_fp32=False, mlp_f16=False):
     """rgb [n,3], depth [n], wsum [n], logT_final [n] (and the per-ray
     smallest relative distance to a ReLU or alpha-clip kink if asked).
     sdf_fp32: the SDF at each point rounded as the FP32 evaluation rounds it
-    (everything else in FP64), to isolate that rounding in a comparison."""
+    (everything else in FP64), to isolate that rounding in a comparison.
+    mlp_f16: the MLP's layer-1 and layer-2 inputs rounded to binary16 as a
+    reduced-precision evaluation stores them, so that both sides take the ReLU
+    decisions on the same values (everything else in FP64)."""
     lib = _load()
     o, d = _f32(rays_o).reshape(-1, 3), _f32(rays_d).reshape(-1, 3)
     n = o.shape[0]
@@ -231,7 +238,7 @@ def render_forward(model: Model, rays_o, rays_d, tau, n_samples, dir_mode=DIR_RE
     rgb = np.zeros((n, 3))
     depth, wsum, logT = np.zeros(n), np.zeros(n), np.zeros(n)
     mg = np.full(n, np.inf) if margin else None
-    p = _params(tau, n_samples, dir_mode, bg, sdf_fp32)
+    p = _params(tau, n_samples, dir_mode, bg, sdf_fp32, mlp_f16)
     st = lib.orc_render_forward(ctypes.byref(model._s), ctypes.byref(p), n, _ptr(o), _ptr(d),
                                 _ptr(ts), _ptr(rgb), _ptr(depth), _ptr(wsum), _ptr(logT),
                                 _ptr(mg), int(n_threads))
@@ -245,10 +252,11 @@ def render_forward(model: Model, rays_o, rays_d, tau, n_samples, dir_mode=DIR_RE
 
 def render_backward(model: Model, rays_o, rays_d, d_rgb, tau, n_samples, d_depth=None,
                     d_wsum=None, dir_mode=DIR_REFLECT, bg=(0.0, 0.0, 0.0), t_samples=None,
-                    n_threads=1):
+                    n_threads=1, mlp_f16=False):
     """Gradients of sum(d_rgb*rgb + d_depth*depth + d_wsum*wsum) w.r.t. the
     SDF nodes, node features (or tile planes), probe coefficients and MLP
-    parameters."""
+    parameters (mlp_f16 as in render_forward; the rounding is taken as the
+    identity in the adjoint)."""
     lib = _load()
     o, d = _f32(rays_o).reshape(-1, 3), _f32(rays_d).reshape(-1, 3)
     n = o.shape[0]
@@ -260,7 +268,7 @@ def render_backward(model: Model, rays_o, rays_d, d_rgb, tau, n_samples, d_depth
     g_feat = np.zeros_like(model.feat if model.planes is None else model.planes)
     g_probe = np.zeros_like(model.probes)
     g_mlp = np.zeros_like(model.mlp)
-    p = _params(tau, n_samples, dir_mode, bg)
+    p = _params(tau, n_samples, dir_mode, bg, mlp_f16=mlp_f16)
     st = lib.orc_render_backward(ctypes.byref(model._s), ctypes.byref(p), n, _ptr(o), _ptr(d),
                                  _ptr(ts), _ptr(drgb), _ptr(dd), _ptr(dw), _ptr(g_sdf),
                                  _ptr(g_feat), _ptr(g_probe), _ptr(g_mlp), int(n_threads))
@@ -336,21 +344,29 @@ def render_trace(model: Model, o, d, tau, n_samples, dir_mode=DIR_REFLECT, t_sam
     return {"hit": bool(hit), "t": t, "s": s, "w": w, "C": C, "normal": nrm}
 
 
-def point_eval(model: Model, o, d, t, dir_mode=DIR_REFLECT, sdf_fp32=False):
+def point_eval(model: Model, o, d, t, dir_mode=DIR_REFLECT, sdf_fp32=False, mlp_f16=False):
     """SDF value, gradient, MLP input vector and colour at the point o + t d
-    (sdf_fp32: the SDF value rounded as the FP32 evaluation rounds it)."""
+    (sdf_fp32: the SDF value rounded as the FP32 evaluation rounds it;
+    mlp_f16: the MLP's layer inputs rounded to binary16, x returned rounded)."""
     lib = _load()
     o, d = _f32(o).reshape(3), _f32(d).reshape(3)
     s = np.zeros(1)
     g = np.zeros(3)
     x = np.zeros(model.n_s + model.n_a + model.n_fresnel)
     C = np.zeros(3)
-    p = _params(1.0, 1, dir_mode, sdf_fp32=sdf_fp32)
+    p = _params(1.0, 1, dir_mode, sdf_fp32=sdf_fp32, mlp_f16=mlp_f16)
     st = lib.orc_point_eval(ctypes.byref(model._s), ctypes.byref(p), _ptr(o), _ptr(d),
                             ctypes.c_float(t), _ptr(s), _ptr(g), _ptr(x), _ptr(C))
     if st != 0:
         raise ValueError("oracle point_eval rejected its arguments")
     return {"s": s[0], "g": g, "x": x, "C": C}
+
+
+def round_f16(v):
+    """Nearest binary16 value of each element (ties to even), as FP64."""
+    lib = _load()
+    v = np.asarray(v, np.float64)
+    return np.array([lib.orc_round_f16(float(x)) for x in v.ravel()]).reshape(v.shape)
 
 
 def sh_eval(l, r):

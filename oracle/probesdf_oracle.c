@@ -334,8 +334,25 @@ static void angular_inputs(const orc_model* m, const orc_params* p, const double
     for (int k = 1; k <= m->n_fresnel; ++k) S->x[ns + na + k - 1] = pow(1.0 - S->ndv, (double)k);
 }
 
-/* Colour MLP on S->x: two ReLU layers and a sigmoid output (Sec. 4). */
-static void mlp_colour(const orc_model* m, orc_sample* S, double* margin)
+/* Nearest binary16 value of v (ties to even): 11 significant bits, so the
+ * spacing in [2^(e-1), 2^e) is 2^(e-11); below the smallest normal 2^-14 the
+ * spacing stays 2^-24 (subnormals).  nearbyint rounds in the default
+ * to-nearest-even mode. */
+double orc_round_f16(double v)
+{
+    if (!(fabs(v) > 0.0) || isinf(v)) return v;
+    int e;
+    frexp(v, &e);
+    int q = e - 11;
+    if (q < -24) q = -24;
+    const double r = ldexp(nearbyint(ldexp(v, -q)), q);
+    return fabs(r) > 65504.0 ? copysign(INFINITY, v) : r;
+}
+
+/* Colour MLP on S->x: two ReLU layers and a sigmoid output (Sec. 4).  With
+ * f16 the inputs of layers 1 and 2 are rounded to binary16 first and kept so
+ * (the adjoint's weight gradients use the rounded values). */
+static void mlp_colour(const orc_model* m, orc_sample* S, double* margin, int f16)
 {
     const int W = m->width, nin = mlp_n_in(m);
     const double* W1 = m->mlp;
@@ -344,6 +361,8 @@ static void mlp_colour(const orc_model* m, orc_sample* S, double* margin)
     const double* b2 = W2 + W * W;
     const double* W3 = b2 + W;
     const double* b3 = W3 + 3 * W;
+    if (f16)
+        for (int i = 0; i < nin; ++i) S->x[i] = orc_round_f16(S->x[i]);
     for (int o2 = 0; o2 < W; ++o2) {
         double z = b1[o2], mag = fabs(b1[o2]);
         for (int i = 0; i < nin; ++i) {
@@ -351,7 +370,7 @@ static void mlp_colour(const orc_model* m, orc_sample* S, double* margin)
             mag += fabs(W1[o2 * nin + i] * S->x[i]);
         }
         S->z1[o2] = z;
-        S->h1[o2] = relu(z);
+        S->h1[o2] = f16 ? orc_round_f16(relu(z)) : relu(z);
         if (margin && mag > 0.0 && fabs(z) / mag < *margin) *margin = fabs(z) / mag;
     }
     for (int o2 = 0; o2 < W; ++o2) {
@@ -425,7 +444,7 @@ static void eval_point(const orc_model* m, const orc_params* p, const float o[3]
     for (int a = 0; a < 3; ++a) v[a] = -(double)d[a];
     locate_f32(x, m->bmin, scp, m->P, S->pi_, S->pf);
     angular_inputs(m, p, v, S);
-    mlp_colour(m, S, margin);
+    mlp_colour(m, S, margin, p->mlp_f16);
 }
 
 /* Sample distances of one ray.  Returns 0 for a ray that misses the box. */
@@ -1309,7 +1328,7 @@ static void shade_node(const orc_model* m, const orc_params* p, const double cam
         S->pf[a] = u - (double)pi;
     }
     angular_inputs(m, p, v, S);
-    mlp_colour(m, S, NULL);
+    mlp_colour(m, S, NULL, p->mlp_f16);
     for (int c = 0; c < 3; ++c) C[c] = S->C[c];
 }
 

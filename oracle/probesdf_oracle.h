@@ -50,8 +50,18 @@ typedef struct orc_params {
                               render kernels (weights and fused multiply-adds in FP32,
                               corner order x fastest) instead of FP64; only tests that
                               isolate FP32 rounding of s set it */
-    int32_t reserved;
+    int32_t mlp_f16;       /* 1: the colour MLP's layer-1 and layer-2 inputs (the input
+                              vector and the first hidden activations) rounded to the
+                              nearest binary16 value before their products, as a
+                              reduced-precision FP16 evaluation stores them; products,
+                              sums, the output layer and the adjoint stay FP64 (the
+                              adjoint treats the rounding as the identity) */
 } orc_params;
+
+/* v rounded to the nearest IEEE binary16 value (ties to even), returned as a
+ * double; magnitudes that round beyond the largest finite binary16 value give
+ * +-inf; zeros, infinities and NaN are returned unchanged. */
+double orc_round_f16(double v);
 
 void orc_sh_eval(int32_t l, const double r[3], double* Y);
 void orc_sh_grad(int32_t l, const double r[3], double* dY);

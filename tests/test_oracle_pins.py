@@ -345,6 +345,119 @@ def test_fp32_sdf_option_is_the_same_trilinear_value_rounded():
         assert a == b, (cell, a, b)
 
 
+def test_round_f16_is_ieee_binary16_rounding():
+    """The oracle's binary16 rounding equals numpy's IEEE half-precision
+    conversion (nearest, ties to even) on normal, subnormal, tie, overflow and
+    signed-zero inputs."""
+    g = synth.rng(43)
+    v = g.normal(size=4000) * np.exp(g.uniform(-25.0, 12.0, size=4000))
+    u = 2.0 ** -24
+    special = np.array([1 + 2.0 ** -11, 1 + 3 * 2.0 ** -11, -(1 + 2.0 ** -11), 0.5 * u, 1.5 * u,
+                        2.5 * u, 2.0 ** -14, 65504.0, 65519.99, 65520.0, -65520.0, 0.0, -0.0])
+    v = np.concatenate([v, special])
+    with np.errstate(over="ignore"):
+        ref = v.astype(np.float16).astype(np.float64)
+    got = oracle.round_f16(v)
+    np.testing.assert_array_equal(got, ref)
+    assert np.array_equal(np.signbit(got), np.signbit(ref))
+
+
+def _mlp_blocks(sc, nin):
+    p = np.asarray(sc.mlp, np.float64)
+    W = sc.width
+    o = 0
+    out = []
+    for shape in ((W, nin), (W,), (W, W), (W,), (3, W), (3,)):
+        k = int(np.prod(shape))
+        out.append((o, p[o:o + k].reshape(shape)))
+        o += k
+    return out
+
+
+def _f16(a):
+    return np.asarray(a, np.float64).astype(np.float16).astype(np.float64)
+
+
+def test_mlp_f16_option_rounds_the_inputs_of_layers_one_and_two():
+    """With the binary16 option the MLP input vector is the plain one rounded
+    by numpy's IEEE binary16 conversion, and the colour is the sigmoid output
+    layer over ReLU layers fed that rounded input and the rounded first hidden
+    activations (evaluated here with numpy matrix products); the option does
+    change colours."""
+    sc = tiny_scene(R=(9, 8, 7), width=8)
+    m = oracle.Model.from_scene(sc)
+    nin = 3 + 4 + 3
+    (_, W1), (_, b1), (_, W2), (_, b2), (_, W3), (_, b3) = _mlp_blocks(sc, nin)
+    g = synth.rng(44)
+    differ = 0
+    for _ in range(100):
+        o = g.uniform(0.05, 0.95, 3).astype(np.float32)
+        d = g.normal(size=3)
+        d = (d / np.linalg.norm(d)).astype(np.float32)
+        t = float(g.uniform(0.0, 0.05))
+        a = oracle.point_eval(m, o, d, t)
+        b = oracle.point_eval(m, o, d, t, mlp_f16=True)
+        assert a["s"] == b["s"]
+        np.testing.assert_array_equal(b["x"], _f16(a["x"]))
+        h1 = _f16(np.maximum(W1 @ b["x"] + b1, 0.0))
+        h2 = np.maximum(W2 @ h1 + b2, 0.0)
+        C = 1.0 / (1.0 + np.exp(-(W3 @ h2 + b3)))
+        np.testing.assert_allclose(b["C"], C, rtol=0.0, atol=1e-14)
+        differ += bool(np.any(b["C"] != a["C"]))
+    assert differ > 50
+
+
+def test_mlp_f16_adjoint_takes_the_rounding_as_identity():
+    """Adjoint of the binary16 option: (a) the output layer and the second
+    layer are smooth in W3, b3, W2 and b2 (the rounded values feeding them do
+    not depend on those), so their gradients equal central differences of the
+    rounded forward; (b) with one colour sample per ray the first layer's
+    weight gradient is the outer product of its bias gradient with the rounded
+    input vector."""
+    sc = tiny_scene(R=(8, 8, 8), P=(3, 3, 3), width=8)
+    m = oracle.Model.from_scene(sc)
+    nin = 3 + 4 + 3
+    tau, N = 8.0, 16
+    o, d = rays_into_box(48, 45)
+    fw = oracle.render_forward(m, o, d, tau, N, margin=True, mlp_f16=True)
+    keep = (fw["margin"] > 2e-3) & (fw["wsum"] > 0)
+    o, d = o[keep][:12], d[keep][:12]
+    assert o.shape[0] >= 6
+    g = synth.rng(46)
+    drgb = g.normal(size=(o.shape[0], 3))
+    grads = oracle.render_backward(m, o, d, drgb, tau, N, mlp_f16=True)["mlp"]
+    blocks = _mlp_blocks(sc, nin)
+    first = blocks[2][0]  # W2, b2, W3, b3 follow contiguously
+    flat = m.mlp.reshape(-1)
+    scale = np.abs(grads[first:]).max()
+    h = 1e-6
+    for i in range(first, flat.size):
+        old = flat[i]
+        flat[i] = old + h
+        lp = np.sum(oracle.render_forward(m, o, d, tau, N, mlp_f16=True)["rgb"] * drgb)
+        flat[i] = old - h
+        lm = np.sum(oracle.render_forward(m, o, d, tau, N, mlp_f16=True)["rgb"] * drgb)
+        flat[i] = old
+        assert abs((lp - lm) / (2 * h) - grads[i]) <= 1e-6 * scale + 1e-10, i
+    # (b) one colour sample per ray at given distances
+    W = sc.width
+    n_checked = 0
+    for r in range(o.shape[0]):
+        ts = np.array([[1.45, 1.9]], np.float32)  # both inside the box
+        gr = oracle.render_backward(m, o[r:r + 1], d[r:r + 1], drgb[r:r + 1], tau, 1,
+                                    t_samples=ts, mlp_f16=True)["mlp"]
+        gW1 = gr[:W * nin].reshape(W, nin)
+        gb1 = gr[W * nin:W * nin + W]
+        if not np.any(gb1):
+            continue
+        xr = oracle.point_eval(m, o[r], d[r], float(ts[0, 0]), mlp_f16=True)["x"]
+        x = oracle.point_eval(m, o[r], d[r], float(ts[0, 0]))["x"]
+        np.testing.assert_array_equal(gW1, np.outer(gb1, xr))
+        assert not np.array_equal(gW1, np.outer(gb1, x))
+        n_checked += 1
+    assert n_checked >= 3
+
+
 def test_weights_plus_final_transmittance_is_one():
     sc = tiny_scene(R=(12, 12, 12))
     m = oracle.Model.from_scene(sc)
