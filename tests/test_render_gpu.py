@@ -288,17 +288,41 @@ def test_launch_occupancy():
 
 RP_RGB_ABS = 2e-3      # reduced precision: |rgb - ref| <= 2e-3 (absolute)
 RP_GRAD_RTOL = 2e-2    # reduced precision: per tensor max|g - g_ref| <= 2e-2 max|g_ref|
+# Against the oracle whose MLP layer inputs are rounded to FP16 as the tensor
+# cores read them (both sides then take the same ReLU decisions), what is left
+# is the FP16 storage of the adjoint's dz rows (unit roundoff 2^-11 ~ 4.9e-4,
+# two roundings on the path to dx) and FP32 accumulation: gradients within
+# 2e-3 of each tensor's largest magnitude, colours within 1e-5 absolute.
+RP16_GRAD_RTOL = 2e-3
+RP16_RGB_ABS = 1e-5
 
 
-def stored_values(sc, feat_bf16=False, probe_f16=False):
+def stored_values(sc, feat_bf16=False, probe_f16=False, mlp_f16=False):
     """The scene with features / probes rounded to their storage precision:
-    the values the kernels read, given to the oracle."""
+    the values the kernels read, given to the oracle.  mlp_f16: W1 and W2 (the
+    tensor-core operands of the reduced-precision MLP) rounded to FP16; the
+    biases and the output layer stay FP32."""
     out = copy.copy(sc)
     if feat_bf16:
         out.feat = torch.as_tensor(sc.feat).bfloat16().float().numpy()
     if probe_f16:
         out.probes = sc.probes.astype(np.float16).astype(np.float32)
+    if mlp_f16:
+        W = sc.width
+        mlp = np.asarray(sc.mlp, np.float32).copy()
+        nin = (mlp.size - W * W - 5 * W - 3) // W
+        o2 = W * nin + W
+        for lo, hi in ((0, W * nin), (o2, o2 + W * W)):
+            mlp[lo:hi] = mlp[lo:hi].astype(np.float16).astype(np.float32)
+        out.mlp = mlp
     return out
+
+
+def l2_rel(gpu, ref):
+    gpu = np.asarray(gpu, np.float64)
+    ref = np.asarray(ref, np.float64)
+    nr = float(np.linalg.norm(ref))
+    return float(np.linalg.norm(gpu - ref)) / nr if nr > 0 else float(np.linalg.norm(gpu))
 
 
 def psnr(a, b):
@@ -698,3 +722,122 @@ def test_adjoint_stress_central_differences(stress512):
     rel = float(np.linalg.norm(fds - ans) / np.linalg.norm(ans))
     log_errors("adjoint stress central differences", {"l2_rel": rel})
     assert rel <= 2.5e-2, rel
+
+
+# ---------------------------------------------------------------------------
+# The human-capture configuration in reduced precision at its full size:
+# 384 x 768 x 384 FP32 SDF + 3 BF16 features per node, probes 48 x 96 x 48 x
+# 9 SH x 4 channels FP16, MLP FP16 on the tensor cores, 2^19 rays x 256
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def human384():
+    sc = synth.make_scene("human384")
+    rays = synth.make_rays("human384")
+    return sc, rays
+
+
+def test_reduced_precision_full_launch_sampled_parity(human384):
+    """The benchmark's reduced-precision launch (2^19 rays x 256 samples on the
+    full human-capture grid).  Forward: the colours of 256 random rays against
+    the FP64 oracle on the stored values (BF16 features, FP16 probes, FP16 W1
+    and W2), at the reduced-precision bar.  Adjoint: the whole launch with a
+    cotangent that is nonzero on 512 random rays, against the oracle's
+    gradients over those rays with the MLP's layer inputs rounded to FP16 as the
+    tensor-core path stores them, so that both sides take the ReLU decisions on
+    the same values (rays within the kink margin left out, as everywhere).
+    Against the oracle with FP64 layer inputs the ReLU decisions of a few
+    samples differ (FP16 rounding moves pre-activations by ~1e-3 of their
+    scale, far beyond the kink margin); those errors are logged, not held to
+    a bar."""
+    sc, rays = human384
+    tau, N = 64.0, 256
+    n = rays.o.shape[0]
+    ref_sc = stored_values(sc, feat_bf16=True, probe_f16=True, mlp_f16=True)
+    scene = ps.Scene.from_host(sc, feat_dtype=ps.BF16, probe_dtype=ps.F16, mlp_dtype=ps.F16)
+    params = ps.render_params(tau, N, 0, 3)
+    g = gpu_forward(scene, rays.o, rays.d, params)
+    for k in ("rgb", "depth", "wsum", "logT"):
+        assert np.isfinite(g[k]).all(), k
+    idx = np.sort(synth.rng(101).choice(n, 256, replace=False))
+    r = oracle_forward(ref_sc, rays.o[idx], rays.d[idx], tau, N)
+    assert np.sum(r["wsum"] > 0.5) > 20
+    err = float(np.max(np.abs(g["rgb"][idx] - r["rgb"])))
+    r16 = oracle_forward(ref_sc, rays.o[idx], rays.d[idx], tau, N, mlp_f16=True)
+    err16 = float(np.max(np.abs(g["rgb"][idx] - r16["rgb"])))
+    log_errors("reduced precision full launch forward",
+               {"rgb_max_abs": err, "psnr_vs_oracle": psnr(g["rgb"][idx], r["rgb"]),
+                "depth_rel": rel_err_elementwise(g["depth"][idx], r["depth"]),
+                "rgb_max_abs_f16_inputs": err16})
+    assert err <= RP_RGB_ABS, err
+    assert err16 <= RP16_RGB_ABS, err16
+    cand = synth.rng(102).choice(n, 1024, replace=False)
+    clean = clean_rays(ref_sc, rays.o[cand], rays.d[cand], tau, N, mlp_f16=True)
+    assert clean.size >= 512, clean.size
+    sub = np.sort(cand[clean[:512]])
+    drgb = np.zeros((n, 3), np.float32)
+    drgb[sub] = (synth.rng(103).normal(size=(sub.size, 3)) / sub.size).astype(np.float32)
+    gg = gpu_backward(scene, rays.o, rays.d, params, drgb)
+    gr = oracle_backward(ref_sc, rays.o[sub], rays.d[sub], drgb[sub].astype(np.float64), tau, N,
+                         mlp_f16=True)
+    errs = {k: rel_err_tensor(gg[k], gr[k]) for k in ("sdf", "feat", "probes", "mlp")}
+    errs.update({k + "_l2": l2_rel(gg[k], gr[k]) for k in ("sdf", "feat", "probes", "mlp")})
+    gp = oracle_backward(ref_sc, rays.o[sub], rays.d[sub], drgb[sub].astype(np.float64), tau, N)
+    errs.update({k + "_plain": rel_err_tensor(gg[k], gp[k]) for k in ("sdf", "feat", "probes", "mlp")})
+    errs["rays_hit"] = int(np.sum(oracle_forward(ref_sc, rays.o[sub], rays.d[sub], tau, N)["wsum"] > 0.5))
+    log_errors("reduced precision full launch backward", errs)
+    for k in ("sdf", "feat", "probes", "mlp"):
+        assert errs[k] <= RP16_GRAD_RTOL, (k, errs)
+
+
+# ---------------------------------------------------------------------------
+# The 1080p inference launch: 8 novel 1920 x 1080 views of the object-capture
+# scene per launch (16.6 M rays)
+# ---------------------------------------------------------------------------
+
+def test_inference_launch_sampled_parity(object256):
+    """Both forms of the 1080p inference comparison at the benchmark's launch
+    size: the FP32 uniform 256-sample render at the FP32 bars, and the BF16 /
+    FP16 render placed by 16 per-bin densities (N' = 128) at the
+    reduced-precision bar, on 256 random pixels against the FP64 oracle.  The
+    densities are seeded FP32 inputs given to both sides."""
+    sc, _ = object256
+    tau = 64.0
+    spec = synth.WORKLOADS["object256"]
+    views = [synth.image_rays(c, 1920, 1080, spec["fov"])
+             for c in synth.novel_cameras("object256", 8)]
+    o = np.concatenate([v[0] for v in views])
+    d = np.concatenate([v[1] for v in views])
+    n = o.shape[0]
+    assert n == 8 * 1920 * 1080
+    idx = np.sort(synth.rng(104).choice(n, 256, replace=False))
+
+    scene = ps.Scene.from_host(sc)
+    g = gpu_forward(scene, o, d, ps.render_params(tau, 256, 0, 3))
+    r = oracle_forward(sc, o[idx], d[idx], tau, 256)
+    r32 = oracle_forward(sc, o[idx], d[idx], tau, 256, sdf_fp32=True)
+    assert np.sum(r["wsum"] > 0.5) > 20
+    for k in ("rgb", "depth", "wsum"):
+        e = rel_err_elementwise(g[k][idx], r[k])
+        assert e <= RGB_DEPTH_RTOL, (k, e)
+        e32 = rel_err_elementwise(g[k][idx], r32[k], floor=REL_FLOOR_S32)
+        assert e32 <= RGB_DEPTH_RTOL, (k + " (FP32-rounded s, 1e-3 floor)", e32)
+    del g, scene
+    torch.cuda.empty_cache()
+
+    B, n_out = 16, 128
+    q = (0.2 + 0.8 * synth.rng(105).random(size=(n, B), dtype=np.float32)) ** 3
+    q /= q.sum(1, keepdims=True)
+    fast = ps.Scene.from_host(sc, feat_dtype=ps.BF16, probe_dtype=ps.F16, mlp_dtype=ps.F16)
+    params = ps.render_params(tau, n_out, n_fresnel=sc.n_fresnel, n_bins=B)
+    rgb, depth, wsum, _ = ps.render_forward(fast, dev(o), dev(d), params, dev(q))
+    assert ps.device_status() == 0
+    rgb, depth = rgb.cpu().numpy()[idx], depth.cpu().numpy()[idx]
+    m = oracle.Model.from_scene(stored_values(sc, feat_bf16=True, probe_f16=True))
+    t_ref = oracle.place_samples(m, o[idx], d[idx], q[idx].astype(np.float64), n_out)
+    ref = oracle.render_forward(m, o[idx], d[idx], tau, n_out, t_samples=t_ref)
+    err = float(np.max(np.abs(rgb - ref["rgb"])))
+    log_errors("inference launch reduced precision + bin densities",
+               {"rgb_max_abs": err, "psnr_vs_oracle": psnr(rgb, ref["rgb"]),
+                "depth_rel": rel_err_elementwise(depth, ref["depth"])})
+    assert err <= RP_RGB_ABS, err
