@@ -2,17 +2,20 @@
 //
 // Persistent CTAs of 4 warps.  Each warp takes rays in a grid-stride loop
 // (misses are written out at once) and walks its ray in chunks of 32 samples,
-// lane = sample.  The 4 warps advance chunk by chunk in lockstep so that their
-// 128 samples form one M = 128 tile for the tensor-core MLP:
+// lane = sample.  The warps run independently (no CTA barrier in the loop):
 //   P0  trilinear gather of 8 packed 16-byte node records per sample and the
 //       sample's opacity; where it is nonzero, normal, SH of the lookup
-//       direction, probe blend, Fresnel powers -> MLP input row (split FP16)
-//       in shared memory (a sample with alpha = 0 has weight 0, so its
-//       appearance is never evaluated);
-//   P1  layer 1 on the tensor cores; meanwhile the warp scan of the clipped
-//       log-opacities gives every sample's transmittance (Eq. 8);
-//   P2  ReLU epilogue -> layer 2 on the tensor cores -> layer 3 and sigmoid on
-//       the CUDA cores; the chunk's weights, colours and depths are summed.
+//       direction, probe blend, Fresnel powers -> the warp's 32 rows of the
+//       MLP input tile (split FP16) in shared memory (a sample with alpha = 0
+//       has weight 0, so its appearance is never evaluated);
+//   P1  layer 1 on the tensor cores, issued by the warp itself over the whole
+//       M = 128 tile into its own 32 tensor-memory columns (it reads back only
+//       its own 32 lanes, i.e. its own rows; the other rows of its result are
+//       never read); meanwhile the warp scan of the clipped log-opacities
+//       gives every sample's transmittance (Eq. 8);
+//   P2  ReLU epilogue -> layer 2 into the same columns -> layer 3 and sigmoid
+//       on the CUDA cores; the chunk's weights, colours and depths are summed.
+// A chunk without an opaque sample skips P1-P2 (its weights are all zero).
 // The log-transmittance carry between chunks uses compensated summation.
 #include "internal.h"
 #include "mlp_tc.cuh"
@@ -28,15 +31,15 @@ struct FwdLayout {
     static constexpr int oW = 0;
     static constexpr int oF32 = oW + M::kWeightBytes;
     static constexpr int oX = (oF32 + 4 * M::kF32 + 127) & ~127;
-    // the hidden tile reuses the input tile's bytes: layer 1 has read the
-    // input (its MMA completed) before the hidden rows are written, and layer
-    // 2 has completed before the next chunk writes its input rows
-    static constexpr int oH = oX;
-    static_assert(kHT >= kXT, "the hidden tile covers the input tile");
+    // the warps' MLP steps are not in step with each other, so a warp's hidden
+    // rows must not cover another warp's input rows: the tiles lie apart
+    static constexpr int oH = oX + M::kSplit * kXT;
     static constexpr int oTab = oH + M::kSplit * kHT;  // per warp: 64-float placement table
-    static constexpr int oBar = oTab + 4 * 64 * 4;
-    static constexpr int kBytes = oBar + 16;
-    static constexpr uint32_t kTmemCols = 64;  // layer 1 at column 0, layer 2 at 32
+    static constexpr int oBar = oTab + 4 * 64 * 4;       // one mbarrier per warp
+    static constexpr int kBytes = oBar + 4 * 8 + 16;
+    // 32 columns per warp: layer 1's accumulator, then layer 2's over it
+    static constexpr uint32_t kTmemCols = 128;
+    static_assert(C::W <= 32, "a warp's accumulator fits its 32 columns");
 };
 
 template <class C>
@@ -54,23 +57,23 @@ render_forward_kernel(RenderArgs A)
     uint8_t* hh = smem + L::oH;
     uint8_t* hl = hh + L::kHT;
     float* stab = reinterpret_cast<float*>(smem + L::oTab);
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::oBar);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::oBar + 8);
-    int* sbad = reinterpret_cast<int*>(smem + L::oBar + 12);
+    uint64_t* mbars = reinterpret_cast<uint64_t*>(smem + L::oBar);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::oBar + 32);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     load_mlp_tc<C>(A.mlp, wt, f32);
     if (warp == 0) tc::tmem_alloc(tslot, L::kTmemCols);
-    if (tid == 0) {
-        tc::mbar_init(mbar, 1);
-        *sbad = 0;
-    }
+    if (tid < 4) tc::mbar_init(mbars + tid, 1);
     tc::fence_smem_to_async();
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = *tslot;
-    const uint32_t t_row = tmem + (static_cast<uint32_t>(32 * warp) << 16);
+    uint64_t* mbar = mbars + warp;
+    // the warp's accumulator columns (all 128 lanes written by its MMAs) and
+    // its own 32 lanes of them
+    const uint32_t t_acc = tmem + 32u * static_cast<uint32_t>(warp);
+    const uint32_t t_row = t_acc + (static_cast<uint32_t>(32 * warp) << 16);
     uint32_t phase = 0;
     bool bad = false;
 
@@ -102,7 +105,7 @@ render_forward_kernel(RenderArgs A)
             }
             ray += stride;
         }
-        if (!__syncthreads_or(have)) break;
+        if (!have) break;  // warp-uniform: every lane holds the same ray
 
         float acc_r = 0.f, acc_g = 0.f, acc_b = 0.f, acc_d = 0.f, acc_w = 0.f;
         float carry = 0.f, comp = 0.f;  // Kahan sum of log T over chunks
@@ -112,8 +115,8 @@ render_forward_kernel(RenderArgs A)
         // and spatial features from lane l - 1; lane 0 takes them from the
         // previous chunk's lane 31, and in a ray's first chunk from point 0,
         // gathered here.  So no lane gathers a second point after its own.
-        float c_s = 0.f, c_g[3] = {0.f, 0.f, 0.f}, c_f[3] = {0.f, 0.f, 0.f};
-        if (have) {
+        float c_s, c_g[3], c_f[3];
+        {
             SampleGeom<C> P;
             eval_sdf<C>(A, R.o, R.d, span_t(sp, 0), P);
             c_s = P.s;
@@ -125,11 +128,11 @@ render_forward_kernel(RenderArgs A)
         }
         for (int base = 0; base < N; base += 32) {
             const int k = base + lane;
-            const bool active = have && k < N;
-            float t = 0.0f, lam = 0.0f;
+            const bool active = k < N;
+            float lam = 0.0f;
             // ---- P0: geometry, angular and spatial features -> input row ----
-            if (have) {
-                t = span_t(sp, k < N ? k : N - 1);
+            const float t = span_t(sp, k < N ? k : N - 1);
+            {
                 SampleGeom<C> P;  // point k + 1 (lanes past the ray's end: point N)
                 eval_sdf<C>(A, R.o, R.d, span_t(sp, k < N ? k + 1 : N), P);
                 SampleGeom<C> S;  // sample k
@@ -170,30 +173,24 @@ render_forward_kernel(RenderArgs A)
 #pragma unroll
                 for (int i = 0; i < M::K1; ++i) xin[i] = i < C::NIN ? S.x[i] : 0.0f;
                 store_row<M::K1, M::kSplit>(xh, xl, tid, 0, M::K1, xin);
-            } else {
-                zero_row<M::K1, M::kSplit>(xh, xl, tid, 0, M::K1);
             }
-            tc::fence_smem_to_async();
-            tc::fence_before();
-            // One barrier both publishes the input rows and tells whether any
-            // sample of the CTA's 128 has a nonzero opacity; a failed wait
-            // (rare) is passed on through shared memory
-            if (bad) *sbad = 1;
-            const bool run_mlp = __syncthreads_or(lam < 0.0f);
-            if (*sbad) goto done;
-            tc::fence_after();
-            // ---- P1: layer 1 on the tensor cores ----
             // Without an opaque sample every weight of the chunk is zero and
             // no colour reaches an output: the MLP is skipped (the outputs are
             // the same bits), only the transmittance carry below is updated.
-            if (run_mlp && tid == 0) {
-                mma_k<M::kSplit>(tmem + 0, xh, xl, M::w1h(wt), M::w1l(wt), 128,
-                                 (M::K1 / 8) * 128, 128, (M::K1 / 8) * 128, M::kIdescL, false);
-                tc::commit(mbar);
-            }
-            {
-                const uint32_t opaque = __ballot_sync(FULL, lam < 0.0f);
-                if (opaque) n_live = base + 32 - __clz(opaque);
+            const uint32_t opaque = __ballot_sync(FULL, lam < 0.0f);
+            if (opaque) {
+                n_live = base + 32 - __clz(opaque);
+                // ---- P1: layer 1 on the tensor cores ----
+                tc::fence_smem_to_async();
+                tc::fence_before();
+                __syncwarp();
+                tc::fence_after();
+                if (lane == 0) {
+                    mma_k<M::kSplit>(t_acc, xh, xl, M::w1h(wt), M::w1l(wt), 128,
+                                     (M::K1 / 8) * 128, 128, (M::K1 / 8) * 128, M::kIdescL,
+                                     false);
+                    tc::commit(mbar);
+                }
             }
             // transmittance of the chunk (Eq. 8): exclusive warp scan of lam
             float incl = lam;
@@ -212,36 +209,51 @@ render_forward_kernel(RenderArgs A)
                 comp = (tt - carry) - y;
                 carry = tt;
             }
-            if (!run_mlp) continue;
-            bad |= !tc::mbar_wait(mbar, phase, A.wait_polls);
-            phase ^= 1;
+            if (!opaque) continue;
+            {
+                // one decision per warp: every lane leaves, or none
+                const bool ok = __all_sync(FULL, tc::mbar_wait(mbar, phase, A.wait_polls));
+                phase ^= 1;
+                if (!ok) {
+                    bad = true;
+                    goto done;
+                }
+            }
             tc::fence_after();
             {
                 float z[W];
-                tc::tmem_ld<W>(t_row + 0, z);
+                tc::tmem_ld<W>(t_row, z);
 #pragma unroll
                 for (int o = 0; o < W; ++o) z[o] = fmaxf(z[o] + f32[M::kB1 + o], 0.0f);
                 store_row<W, M::kSplit>(hh, hl, tid, 0, W, z);
             }
+            // the layer-1 reads are complete (tcgen05.wait::ld) before the
+            // layer-2 MMA overwrites the columns
             tc::fence_smem_to_async();
             tc::fence_before();
-            __syncthreads();
+            __syncwarp();
             tc::fence_after();
             // ---- P2: layer 2 on the tensor cores, layer 3 on the CUDA cores ----
-            if (tid == 0) {
+            if (lane == 0) {
 #pragma unroll
                 for (int s = 0; s < W / 16; ++s)
-                    mma_k<M::kSplit>(tmem + 32, hh + s * 256, hl + s * 256,
+                    mma_k<M::kSplit>(t_acc, hh + s * 256, hl + s * 256,
                                      M::w2h(wt) + s * 256, M::w2l(wt) + s * 256, 128,
                                      (W / 8) * 128, 128, (W / 8) * 128, M::kIdescL, s > 0);
                 tc::commit(mbar);
             }
-            bad |= !tc::mbar_wait(mbar, phase, A.wait_polls);
-            phase ^= 1;
+            {
+                const bool ok = __all_sync(FULL, tc::mbar_wait(mbar, phase, A.wait_polls));
+                phase ^= 1;
+                if (!ok) {
+                    bad = true;
+                    goto done;
+                }
+            }
             tc::fence_after();
             {
                 float z[W];
-                tc::tmem_ld<W>(t_row + 32, z);
+                tc::tmem_ld<W>(t_row, z);
 #pragma unroll
                 for (int o = 0; o < W; ++o) z[o] = fmaxf(z[o] + f32[M::kB2 + o], 0.0f);
                 float col[3];
@@ -254,37 +266,37 @@ render_forward_kernel(RenderArgs A)
                     acc_w += wgt;
                 }
             }
+            // the layer-2 reads are complete before the next chunk's layer-1
+            // MMA (issued after this warp's next __syncwarp) overwrites them
             tc::fence_before();
         }
-        if (have) {
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                acc_r += __shfl_xor_sync(FULL, acc_r, off);
-                acc_g += __shfl_xor_sync(FULL, acc_g, off);
-                acc_b += __shfl_xor_sync(FULL, acc_b, off);
-                acc_d += __shfl_xor_sync(FULL, acc_d, off);
-                acc_w += __shfl_xor_sync(FULL, acc_w, off);
-            }
-            if (lane == 0) {
-                const float logT = carry - comp;
-                const float TN = expf(logT);
-                A.rgb[3 * ray + 0] = fmaf(TN, A.bg[0], acc_r);
-                A.rgb[3 * ray + 1] = fmaf(TN, A.bg[1], acc_g);
-                A.rgb[3 * ray + 2] = fmaf(TN, A.bg[2], acc_b);
-                A.depth[ray] = acc_d;
-                A.wsum[ray] = acc_w;
-                A.logT[ray] = logT;
-                if (A.n_live) A.n_live[ray] = n_live;
-            }
-            ray += stride;
+        for (int off = 16; off > 0; off >>= 1) {
+            acc_r += __shfl_xor_sync(FULL, acc_r, off);
+            acc_g += __shfl_xor_sync(FULL, acc_g, off);
+            acc_b += __shfl_xor_sync(FULL, acc_b, off);
+            acc_d += __shfl_xor_sync(FULL, acc_d, off);
+            acc_w += __shfl_xor_sync(FULL, acc_w, off);
         }
+        if (lane == 0) {
+            const float logT = carry - comp;
+            const float TN = expf(logT);
+            A.rgb[3 * ray + 0] = fmaf(TN, A.bg[0], acc_r);
+            A.rgb[3 * ray + 1] = fmaf(TN, A.bg[1], acc_g);
+            A.rgb[3 * ray + 2] = fmaf(TN, A.bg[2], acc_b);
+            A.depth[ray] = acc_d;
+            A.wsum[ray] = acc_w;
+            A.logT[ray] = logT;
+            if (A.n_live) A.n_live[ray] = n_live;
+        }
+        ray += stride;
     }
 done:
     bad = __syncthreads_or(bad);
     if (bad) {
-        // an MMA never signalled completion: give it one more bounded wait
-        // before the tensor memory is released, and report the failure
-        // the last commit's phase has the parity before the final flip
+        // an MMA never signalled completion: give this warp's last commit one
+        // more bounded wait before the tensor memory is released (a warp with
+        // nothing pending passes at once), and report the failure
         tc::mbar_wait(mbar, phase ^ 1u);
         if (tid == 0) atomicOr(A.status, 1);
     }
