@@ -207,13 +207,13 @@ render_backward_kernel(RenderArgs A)
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::oMisc + 32);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::oMisc + 40);
     uint32_t* tslot2 = reinterpret_cast<uint32_t*>(smem + L::oMisc + 44);
+    int* ray_counter = reinterpret_cast<int*>(smem + L::oMisc + 48);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const unsigned FULL = 0xffffffffu;
     const int N = A.n_samples;
     const float tau = A.tau;
     const int64_t stride = int64_t(gridDim.x) * 4;
-    int64_t ray = int64_t(blockIdx.x) * 4 + warp;
 
     load_mlp_tc<C>(A.mlp, wt, f32);
     for (int i = tid; i < L::kParamsPad; i += blockDim.x) gacc[i] = 0.0f;
@@ -221,11 +221,16 @@ render_backward_kernel(RenderArgs A)
         tc::tmem_alloc(tslot, L::kTmemCols, !L::kKeepBc);
         if constexpr (L::kKeepBc) tc::tmem_alloc(tslot2, L::kTmemCols2, true);
     }
-    if (tid == 0) tc::mbar_init(mbar, 1);
+    if (tid == 0) {
+        tc::mbar_init(mbar, 1);
+        *ray_counter = 0;
+    }
     {
         // gradient scale: the largest |dL/drgb| over the rays this CTA renders
+        // (warp w reads the rays b * 4 + w + i * stride; together all of them)
         float m = 0.0f;
-        for (int64_t r = ray + int64_t(lane) * stride; r < A.n_rays; r += 32 * stride)
+        for (int64_t r = int64_t(blockIdx.x) * 4 + warp + int64_t(lane) * stride; r < A.n_rays;
+             r += 32 * stride)
             m = fmaxf(m, fmaxf(fabsf(__ldg(A.d_rgb + 3 * r)),
                                fmaxf(fabsf(__ldg(A.d_rgb + 3 * r + 1)),
                                      fabsf(__ldg(A.d_rgb + 3 * r + 2)))));
@@ -284,6 +289,7 @@ render_backward_kernel(RenderArgs A)
     // processed just before it (back to front), whose SDF value lane 0 carries
     // over (s_first, valid while have_first); only a ray's first chunk, and
     // the point after the ray's last sample, gather it.
+    int64_t ray = next_cta_ray(ray_counter, stride);
     RayIn R;
     RaySpan sp;
     bool have = false, have_first = false;
@@ -293,7 +299,7 @@ render_backward_kernel(RenderArgs A)
     const int nch = (N + 31) >> 5;
     for (;;) {
         if (ch < 0) {
-            if (have) ray += stride;
+            if (have) ray = next_cta_ray(ray_counter, stride);
             have = false;
             while (ray < A.n_rays) {
                 R = load_ray(A, ray);
@@ -307,7 +313,7 @@ render_backward_kernel(RenderArgs A)
                     ch = min(nch - 1, (live - 1) >> 5);
                     break;
                 }
-                ray += stride;
+                ray = next_cta_ray(ray_counter, stride);
             }
             drgb[0] = drgb[1] = drgb[2] = 0.f;
             ddepth = dwsum = logT_end = 0.f;

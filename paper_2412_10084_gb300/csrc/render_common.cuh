@@ -499,6 +499,18 @@ __device__ __forceinline__ float dlog_phi(float tau, float s)
 
 __device__ __forceinline__ float sigmoidf(float z) { return 1.0f / (1.0f + expf(-z)); }
 
+// The rays of a persistent CTA of 4 warps are b * 4 + (j & 3) + (j >> 2) * stride,
+// j = 0, 1, ... (increasing in j).  Its warps take the next j from a counter in
+// shared memory (zeroed before the CTA's first barrier), so a warp whose rays
+// end early takes more of them.  Warp-collective; every lane gets the ray.
+__device__ __forceinline__ int64_t next_cta_ray(int* counter, int64_t stride)
+{
+    int j = 0;
+    if ((threadIdx.x & 31) == 0) j = atomicAdd(counter, 1);
+    j = __shfl_sync(0xffffffffu, j, 0);
+    return int64_t(blockIdx.x) * 4 + (j & 3) + int64_t(j >> 2) * stride;
+}
+
 // Vector reduction into global memory (no return value).
 __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d)
 {

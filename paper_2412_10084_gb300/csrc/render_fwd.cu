@@ -59,11 +59,13 @@ render_forward_kernel(RenderArgs A)
     float* stab = reinterpret_cast<float*>(smem + L::oTab);
     uint64_t* mbars = reinterpret_cast<uint64_t*>(smem + L::oBar);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::oBar + 32);
+    int* ray_counter = reinterpret_cast<int*>(smem + L::oBar + 36);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     load_mlp_tc<C>(A.mlp, wt, f32);
     if (warp == 0) tc::tmem_alloc(tslot, L::kTmemCols);
     if (tid < 4) tc::mbar_init(mbars + tid, 1);
+    if (tid == 0) *ray_counter = 0;
     tc::fence_smem_to_async();
     tc::fence_before();
     __syncthreads();
@@ -80,7 +82,7 @@ render_forward_kernel(RenderArgs A)
     const unsigned FULL = 0xffffffffu;
     const int N = A.n_samples;
     const int64_t stride = int64_t(gridDim.x) * 4;
-    int64_t ray = int64_t(blockIdx.x) * 4 + warp;
+    int64_t ray = next_cta_ray(ray_counter, stride);
 
     for (;;) {
         // this warp's next ray that hits the box; misses are finished here
@@ -103,7 +105,7 @@ render_forward_kernel(RenderArgs A)
                 A.logT[ray] = 0.0f;
                 if (A.n_live) A.n_live[ray] = 0;
             }
-            ray += stride;
+            ray = next_cta_ray(ray_counter, stride);
         }
         if (!have) break;  // warp-uniform: every lane holds the same ray
 
@@ -289,7 +291,7 @@ render_forward_kernel(RenderArgs A)
             A.logT[ray] = logT;
             if (A.n_live) A.n_live[ray] = n_live;
         }
-        ray += stride;
+        ray = next_cta_ray(ray_counter, stride);
     }
 done:
     bad = __syncthreads_or(bad);
