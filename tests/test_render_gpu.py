@@ -260,6 +260,27 @@ def test_empty_batch_and_misses():
     assert np.all(out["wsum"] == 0) and np.all(out["depth"] == 0)
 
 
+def test_per_ray_results_do_not_depend_on_the_batch(sphere64):
+    """A CTA's warps take its rays from a counter, so which warp renders a ray
+    depends on timing: every ray's outputs must still be the same bits in a
+    batch of any size (1, 3, 6, 37 rays: fewer rays than warps, CTAs with some
+    warps idle) as in the full batch, and the adjoint of a small batch must
+    match the oracle."""
+    sc, rays = sphere64
+    scene = ps.Scene.from_host(sc)
+    params = ps.render_params(64.0, 128, 0, 3)
+    full = ps.render_forward(scene, dev(rays.o), dev(rays.d), params, want_live=True)
+    assert ps.device_status() == 0
+    idx = np.nonzero(full[2].cpu().numpy() > 0.5)[0]  # rays that reach the surface first
+    for n in (1, 3, 6, 37):
+        part = ps.render_forward(scene, dev(rays.o[idx[:n]]), dev(rays.d[idx[:n]]), params,
+                                 want_live=True)
+        assert ps.device_status() == 0
+        for x, y in zip(part, full):
+            assert torch.equal(x, y[torch.as_tensor(idx[:n], device="cuda")]), n
+    check_backward(sc, rays.o[idx[:37]], rays.d[idx[:37]], 64.0, 128, min_kept=0.3)
+
+
 def test_host_validation_errors():
     sc = synth.make_scene("sphere64", dims=(16, 16, 16), probe_dims=(4, 4, 4))
     scene = ps.Scene.from_host(sc)
