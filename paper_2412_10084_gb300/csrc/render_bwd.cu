@@ -1,8 +1,12 @@
 // Adjoint of the ProbeSDF render (Sec. 3.3-3.4), sm_103a.
 //
-// Same CTA organisation as the forward: 4 warps, one ray per warp, lockstep
-// 32-sample chunks forming M = 128 tiles, but chunks are walked back to front
-// starting from the saved log T_N, and every per-sample activation is
+// Persistent CTAs of 4 warps, one ray per warp (the CTA's rays taken from a
+// shared-memory counter), lane = sample.  Unlike the forward, whose warps run
+// their own MLP steps, the 4 warps advance in lockstep 32-sample chunks whose
+// 128 samples form one M = 128 tile: the adjoint's tensor memory (activations,
+// the weight-gradient accumulator and the blended probe coefficients) has no
+// room for per-warp accumulators at 3 CTAs per SM.  Chunks are walked back to
+// front starting from the saved log T_N, and every per-sample activation is
 // recomputed (nothing per sample is stored by the forward).  Per chunk:
 //   P0  recompute geometry and features -> input row of the XH tile;
 //   P1  layer 1 (tensor cores); warp suffix sum of the clipped log-opacities
