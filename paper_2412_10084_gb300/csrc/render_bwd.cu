@@ -360,7 +360,12 @@ render_backward_kernel(RenderArgs A)
                     point_at(R.o, R.d, span_t(sp, k + 1), xw);
                     c1 = locate(xw, A.grid.bmin, A.grid.sc, A.grid.R);
                 }
-                eval_sdf<C>(A, R.o, R.d, t, S);
+                // (features apart from the SDF: gathered below for the samples
+                // with a nonzero opacity only; the others' MLP rows carry zeros)
+                if constexpr (features_apart<C>())
+                    eval_sdf_geom<C>(A, R.o, R.d, t, S);
+                else
+                    eval_sdf<C>(A, R.o, R.d, t, S);
                 s_next = __shfl_down_sync(FULL, S.s, 1);
                 if (extra) {
                     if (carried)
@@ -380,6 +385,7 @@ render_backward_kernel(RenderArgs A)
                 if constexpr (L::kKeepBc) {
                     float Bc[L::kBc];
                     if (unclipped) {
+                        if constexpr (features_apart<C>()) eval_features<C>(A, R.o, R.d, t, S);
                         eval_appearance_blend<C>(A, R.o, R.d, t, S, Bc);
                     } else {
                         zero_appearance<C>(S);
@@ -388,6 +394,7 @@ render_backward_kernel(RenderArgs A)
                     }
                     bc_store<L>(t_row, t_row2, Bc);
                 } else if (unclipped) {
+                    if constexpr (features_apart<C>()) eval_features<C>(A, R.o, R.d, t, S);
                     eval_appearance<C>(A, R.o, R.d, t, S);
                 } else {
                     zero_appearance<C>(S);

@@ -120,7 +120,10 @@ render_forward_kernel(RenderArgs A)
         float c_s, c_g[3], c_f[3];
         {
             SampleGeom<C> P;
-            eval_sdf<C>(A, R.o, R.d, span_t(sp, 0), P);
+            if constexpr (features_apart<C>())
+                eval_sdf_geom<C>(A, R.o, R.d, span_t(sp, 0), P);
+            else
+                eval_sdf<C>(A, R.o, R.d, span_t(sp, 0), P);
             c_s = P.s;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
@@ -136,13 +139,18 @@ render_forward_kernel(RenderArgs A)
             const float t = span_t(sp, k < N ? k : N - 1);
             {
                 SampleGeom<C> P;  // point k + 1 (lanes past the ray's end: point N)
-                eval_sdf<C>(A, R.o, R.d, span_t(sp, k < N ? k + 1 : N), P);
+                // (the features apart from the SDF are gathered below, for the
+                // samples with a nonzero opacity only)
+                if constexpr (features_apart<C>())
+                    eval_sdf_geom<C>(A, R.o, R.d, span_t(sp, k < N ? k + 1 : N), P);
+                else
+                    eval_sdf<C>(A, R.o, R.d, span_t(sp, k < N ? k + 1 : N), P);
                 SampleGeom<C> S;  // sample k
                 S.s = __shfl_up_sync(FULL, P.s, 1);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     S.g[a] = __shfl_up_sync(FULL, P.g[a], 1);
-                    S.x[a] = __shfl_up_sync(FULL, P.x[a], 1);
+                    S.x[a] = features_apart<C>() ? 0.0f : __shfl_up_sync(FULL, P.x[a], 1);
                 }
                 if (lane == 0) {
                     S.s = c_s;
@@ -156,7 +164,7 @@ render_forward_kernel(RenderArgs A)
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     c_g[a] = __shfl_sync(FULL, P.g[a], 31);
-                    c_f[a] = __shfl_sync(FULL, P.x[a], 31);
+                    c_f[a] = features_apart<C>() ? 0.0f : __shfl_sync(FULL, P.x[a], 31);
                 }
                 const float s_next = P.s;
                 bool opaque = false;
@@ -167,10 +175,12 @@ render_forward_kernel(RenderArgs A)
                 }
                 // a clipped opacity (alpha = 0) gives the sample weight 0: its
                 // colour, and so its appearance inputs, never reach an output
-                if (opaque)
+                if (opaque) {
+                    if constexpr (features_apart<C>()) eval_features<C>(A, R.o, R.d, t, S);
                     eval_appearance<C>(A, R.o, R.d, t, S);
-                else
+                } else {
                     zero_appearance<C>(S);
+                }
                 float xin[M::K1];
 #pragma unroll
                 for (int i = 0; i < M::K1; ++i) xin[i] = i < C::NIN ? S.x[i] : 0.0f;

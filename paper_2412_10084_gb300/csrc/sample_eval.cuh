@@ -133,6 +133,66 @@ __device__ __forceinline__ void eval_sdf(const RenderArgs& A, const float o[3], 
     S.x[2] = fs[2];
 }
 
+// Layouts that keep the spatial features apart from the SDF (the BF16 feature
+// array, the tile tri-planes) gather the features only for the samples that
+// need them: those with a nonzero opacity, known once the SDF is.
+template <class C>
+__device__ __forceinline__ constexpr bool features_apart()
+{
+    return C::FB || C::TP;
+}
+
+// eval_sdf without the spatial features (S.x[0..2] = 0): the cell, SDF value
+// and gradient, from the 8 SDF values alone (the same bits as eval_sdf).
+template <class C>
+__device__ __forceinline__ void eval_sdf_geom(const RenderArgs& A, const float o[3],
+                                              const float d[3], float t, SampleGeom<C>& S)
+{
+    static_assert(features_apart<C>(), "features stored apart from the SDF");
+    float xw[3];
+    point_at(o, d, t, xw);
+    S.cell = locate(xw, A.grid.bmin, A.grid.sc, A.grid.R);
+    Corners k;
+    gather_corners_sdf(A.grid, S.cell, k);
+    float fs[3];
+    sdf_full(A.grid, S.cell, k, S.s, S.g, fs);
+    S.x[0] = S.x[1] = S.x[2] = 0.0f;
+}
+
+// The spatial features (MLP input columns 0..2) of the point at distance t,
+// with the arithmetic of eval_sdf (so the same bits).
+template <class C>
+__device__ __forceinline__ void eval_features(const RenderArgs& A, const float o[3],
+                                              const float d[3], float t, SampleGeom<C>& S)
+{
+    static_assert(features_apart<C>(), "features stored apart from the SDF");
+    float xw[3];
+    point_at(o, d, t, xw);
+    float fs[3];
+    if constexpr (C::TP) {
+        TriAt T;
+        triplane_locate(A.grid, xw, T);
+        triplane_lookup(A.grid, T, fs);
+    } else {
+        const Cell c = locate(xw, A.grid.bmin, A.grid.sc, A.grid.R);
+        const int sx = 1, sy = A.grid.R[0], sz = A.grid.R[0] * A.grid.R[1];
+        const int off[8] = {0, sx, sy, sx + sy, sz, sz + sx, sz + sy, sz + sy + sx};
+        float w[8];
+        corner_weights(c.f, w);
+        fs[0] = fs[1] = fs[2] = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const uint2 f = __ldg(A.grid.feat16 + c.base + off[q]);
+            fs[0] = fmaf(w[q], bf16_lo(f.x), fs[0]);
+            fs[1] = fmaf(w[q], bf16_hi(f.x), fs[1]);
+            fs[2] = fmaf(w[q], bf16_lo(f.y), fs[2]);
+        }
+    }
+    S.x[0] = fs[0];
+    S.x[1] = fs[1];
+    S.x[2] = fs[2];
+}
+
 // Appearance part at world point xw seen along v (towards the viewer): normal
 // (Eq. 13) from S.g, SH lookup direction and basis, probe-blended angular
 // features (Eqs. 6-7) and Fresnel inputs (Eq. 4), the MLP input columns 3.. .
