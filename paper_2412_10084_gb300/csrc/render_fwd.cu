@@ -181,10 +181,13 @@ render_forward_kernel(RenderArgs A)
                 } else {
                     zero_appearance<C>(S);
                 }
-                float xin[M::K1];
+                // the input rows are needed only if the warp runs its MLP step
+                if (__any_sync(FULL, lam < 0.0f)) {
+                    float xin[M::K1];
 #pragma unroll
-                for (int i = 0; i < M::K1; ++i) xin[i] = i < C::NIN ? S.x[i] : 0.0f;
-                store_row<M::K1, M::kSplit>(xh, xl, tid, 0, M::K1, xin);
+                    for (int i = 0; i < M::K1; ++i) xin[i] = i < C::NIN ? S.x[i] : 0.0f;
+                    store_row<M::K1, M::kSplit>(xh, xl, tid, 0, M::K1, xin);
+                }
             }
             // Without an opaque sample every weight of the chunk is zero and
             // no colour reaches an output: the MLP is skipped (the outputs are
