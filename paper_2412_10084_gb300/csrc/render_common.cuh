@@ -178,6 +178,27 @@ __device__ __forceinline__ void point_at(const float o[3], const float d[3], flo
 // Trilinear gathers (Sec. 3.1): 8 corner records of 16 bytes each.
 // ---------------------------------------------------------------------------
 
+// Read-only 16-byte loads with an L1 eviction priority: the probe
+// coefficients (a few MB, reused by every ray) are kept over the grid's node
+// records (reused only by neighbouring samples).
+__device__ __forceinline__ float4 ldg_keep(const float4* p)
+{
+    float4 v;
+    asm("ld.global.nc.L1::evict_last.v4.f32 {%0,%1,%2,%3}, [%4];"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ float4 ldg_stream(const float4* p)
+{
+    float4 v;
+    asm("ld.global.nc.L1::evict_first.v4.f32 {%0,%1,%2,%3}, [%4];"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "l"(p));
+    return v;
+}
+
 struct Corners {
     float4 v[8];  // corner c = cx + 2 cy + 4 cz
 };
@@ -186,14 +207,14 @@ __device__ __forceinline__ void gather_corners(const GridView& g, const Cell& c,
 {
     const int sx = 1, sy = g.R[0], sz = g.R[0] * g.R[1];
     const float4* p = g.nodes + c.base;
-    k.v[0] = __ldg(p);
-    k.v[1] = __ldg(p + sx);
-    k.v[2] = __ldg(p + sy);
-    k.v[3] = __ldg(p + sx + sy);
-    k.v[4] = __ldg(p + sz);
-    k.v[5] = __ldg(p + sz + sx);
-    k.v[6] = __ldg(p + sz + sy);
-    k.v[7] = __ldg(p + sz + sy + sx);
+    k.v[0] = ldg_stream(p);
+    k.v[1] = ldg_stream(p + sx);
+    k.v[2] = ldg_stream(p + sy);
+    k.v[3] = ldg_stream(p + sx + sy);
+    k.v[4] = ldg_stream(p + sz);
+    k.v[5] = ldg_stream(p + sz + sx);
+    k.v[6] = ldg_stream(p + sz + sy);
+    k.v[7] = ldg_stream(p + sz + sy + sx);
 }
 
 __device__ __forceinline__ void corner_weights(const float f[3], float w[8])

@@ -67,7 +67,7 @@ __device__ __forceinline__ float4 probe_coeffs(const ProbeView& p, int probe, in
         const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
         return make_float4(a.x, a.y, b.x, b.y);
     } else {
-        return __ldg(p.coeffs + i);
+        return ldg_keep(p.coeffs + i);
     }
 }
 
