@@ -178,13 +178,14 @@ __device__ __forceinline__ void point_at(const float o[3], const float d[3], flo
 // Trilinear gathers (Sec. 3.1): 8 corner records of 16 bytes each.
 // ---------------------------------------------------------------------------
 
-// Read-only 16-byte loads with an L1 eviction priority: the probe
-// coefficients (a few MB, reused by every ray) are kept over the grid's node
-// records (reused only by neighbouring samples).
+// Read-only 16-byte loads with eviction priorities: the probe coefficients (a
+// few MB, reused by every ray) are kept in L1 and L2 over the grid's node
+// records (reused only by neighbouring samples), which go first in L1.
 __device__ __forceinline__ float4 ldg_keep(const float4* p)
 {
     float4 v;
-    asm("ld.global.nc.L1::evict_last.v4.f32 {%0,%1,%2,%3}, [%4];"
+    asm("{\n\t.reg .b64 pol;\n\tcreatepolicy.fractional.L2::evict_last.b64 pol, 1.0;\n\t"
+        "ld.global.nc.L1::evict_last.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], pol;\n\t}"
         : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
         : "l"(p));
     return v;
