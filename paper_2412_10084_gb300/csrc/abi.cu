@@ -404,6 +404,35 @@ int resident_ctas(const cudaFuncAttributes& fa, int threads, size_t dyn_smem, un
     return n;
 }
 
+cudaError_t set_smem_carveout(const void* func, int threads, size_t dyn_smem, unsigned tmem_cols)
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, func);
+    if (e != cudaSuccess) return e;
+    const int n = resident_ctas(fa, threads, dyn_smem, tmem_cols);
+    int dev = 0, smem_sm = 0, reserved = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (n <= 0 || smem_sm <= 0) return cudaSuccess;  // nothing to choose
+    const size_t need =
+        static_cast<size_t>(n) * (dyn_smem + fa.sharedSizeBytes + static_cast<size_t>(reserved));
+    // The shared-memory capacities an sm_100-family SM can be split into
+    // (KiB); the hint is a percentage of the largest, rounded up by the driver
+    // to the next capacity, so the smallest one that holds `need` is asked for
+    // just below its own value.
+    static const int kCapKiB[] = {0, 8, 16, 32, 64, 100, 132, 164, 196, 228};
+    int pct = 100;
+    for (int c : kCapKiB) {
+        const size_t cap = static_cast<size_t>(c) * 1024;
+        if (cap >= need && cap <= static_cast<size_t>(smem_sm)) {
+            pct = static_cast<int>((100 * cap) / static_cast<size_t>(smem_sm));
+            break;
+        }
+    }
+    return cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+}
+
 cudaError_t launch_pack(const float* sdf, const float* feat, float4* packed, int64_t n_nodes,
                         cudaStream_t stream)
 {

@@ -49,6 +49,10 @@ cudaError_t launch_backward(const RenderArgs& A, const KernelShape& ks, int grid
 // Resident CTAs per SM of a kernel from its registers and shared memory, the
 // device's per-SM limits and the tensor-memory columns each CTA allocates.
 int resident_ctas(const cudaFuncAttributes& fa, int threads, size_t dyn_smem, unsigned tmem_cols);
+// Sets the kernel's shared-memory carveout hint to the smallest split of the
+// SM's unified L1 / shared memory that holds its resident CTAs (resident_ctas),
+// so that the rest of the SM's on-chip memory serves its gathers as L1.
+cudaError_t set_smem_carveout(const void* func, int threads, size_t dyn_smem, unsigned tmem_cols);
 
 // Resident CTAs per SM (occupancy, capped by tensor-memory columns).
 cudaError_t forward_ctas_per_sm(const KernelShape& ks, int* n);

@@ -60,8 +60,11 @@ struct BwdLayout {
     static constexpr int oF32 = oW + M::kWeightBytes;
     static constexpr int oXH = (oF32 + 4 * M::kF32 + 127) & ~127;
     static constexpr int oDZ = oXH + M::kSplit * kXH;
-    static constexpr int oG = oDZ + M::kSplit * kDZ;
-    static constexpr int oTab = oG + 4 * kParamsPad;  // per warp: 64-float placement table
+    // the CTA's MLP-gradient sums are formed after the chunk loop, in the
+    // operand tiles (free by then), so they take no shared memory of their own
+    static constexpr int oG = oXH;
+    static_assert(4 * kParamsPad <= M::kSplit * (kXH + kDZ), "gradient sums fit the tiles");
+    static constexpr int oTab = oDZ + M::kSplit * kDZ;  // per warp: 64-float placement table
     static constexpr int oMisc = oTab + 4 * 64 * 4;
     static constexpr int kBytes = oMisc + 64;
     static constexpr uint32_t kTmemCols = 128;  // z1/dh1 at 0, z2/dx at 32, dW at 64..111
@@ -220,7 +223,6 @@ render_backward_kernel(RenderArgs A)
     const int64_t stride = int64_t(gridDim.x) * 4;
 
     load_mlp_tc<C>(A.mlp, wt, f32);
-    for (int i = tid; i < L::kParamsPad; i += blockDim.x) gacc[i] = 0.0f;
     if (warp == 0) {
         tc::tmem_alloc(tslot, L::kTmemCols, !L::kKeepBc);
         if constexpr (L::kKeepBc) tc::tmem_alloc(tslot2, L::kTmemCols2, true);
@@ -806,10 +808,15 @@ done:
         tc::mbar_wait(mbar, phase ^ 1u);
         if (tid == 0) atomicOr(A.status, 1);
     }
+    // the tiles are free: every MMA that read them has completed (the loop
+    // waited for each one), and so has every warp's use of the probe staging
+    const bool fold = any_chunk && !bad;
+    if (fold)
+        for (int i = tid; i < L::kParamsPad; i += blockDim.x) gacc[i] = 0.0f;
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (any_chunk && !bad) {
+    if (fold) {
         // dW1, db1, dW2, db2 from the tensor-memory accumulator (M = 64 layout:
         // row r lives in lane 32 (r / 16) + r % 16)
         float v[L::XHC];
@@ -838,7 +845,7 @@ done:
         tc::tmem_dealloc(tmem, L::kTmemCols);
         if constexpr (L::kKeepBc) tc::tmem_dealloc(*tslot2, L::kTmemCols2);
     }
-    if (any_chunk)
+    if (fold)
         for (int i = tid; i < C::kParams; i += blockDim.x) red_add(A.grad_mlp + i, gacc[i]);
 }
 
@@ -848,6 +855,9 @@ cudaError_t launch_backward_t(const RenderArgs& A, int grid_ctas, cudaStream_t s
     using L = BwdLayout<C>;
     cudaError_t e = cudaFuncSetAttribute(render_backward_kernel<C>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
+    if (e == cudaSuccess)
+        e = set_smem_carveout(reinterpret_cast<const void*>(render_backward_kernel<C>),
+                              kBwdThreads, L::kBytes, L::kTmemCols + L::kTmemCols2);
     if (e != cudaSuccess) return e;
     render_backward_kernel<C><<<grid_ctas, kBwdThreads, L::kBytes, stream>>>(A);
     return cudaGetLastError();

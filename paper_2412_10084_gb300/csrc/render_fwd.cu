@@ -326,6 +326,9 @@ cudaError_t launch_forward_t(const RenderArgs& A, int grid_ctas, cudaStream_t st
     using L = FwdLayout<C>;
     cudaError_t e = cudaFuncSetAttribute(render_forward_kernel<C>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
+    if (e == cudaSuccess)
+        e = set_smem_carveout(reinterpret_cast<const void*>(render_forward_kernel<C>),
+                              kFwdThreads, L::kBytes, L::kTmemCols);
     if (e != cudaSuccess) return e;
     render_forward_kernel<C><<<grid_ctas, kFwdThreads, L::kBytes, stream>>>(A);
     return cudaGetLastError();
