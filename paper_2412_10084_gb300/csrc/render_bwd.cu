@@ -133,9 +133,17 @@ __device__ __forceinline__ void scatter_probe_grad(const RenderArgs& A, const fl
         load(sn, yn, coefn);
         const float* Y = reinterpret_cast<const float*>(y);
 #pragma unroll
-        for (int m = 0; m < CPL; ++m)
+        for (int m = 0; m < CPL; ++m) {
+            const float2 c2 = make_float2(coef[m], coef[m]);
 #pragma unroll
-            for (int j = 0; j < L2; ++j) acc[m][j] = fmaf(coef[m], Y[j], acc[m][j]);
+            for (int j = 0; j + 1 < L2; j += 2) {
+                const float2 r = fma2(c2, make_float2(Y[j], Y[j + 1]),
+                                      make_float2(acc[m][j], acc[m][j + 1]));
+                acc[m][j] = r.x;
+                acc[m][j + 1] = r.y;
+            }
+            if constexpr (L2 % 2) acc[m][L2 - 1] = fmaf(coef[m], Y[L2 - 1], acc[m][L2 - 1]);
+        }
         if ((ends >> s) & 1u) {
             const int cell = __float_as_int(pst[s * PST + 8 + L2 + NA]);
 #pragma unroll

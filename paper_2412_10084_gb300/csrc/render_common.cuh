@@ -174,6 +174,20 @@ __device__ __forceinline__ void point_at(const float o[3], const float d[3], flo
     for (int a = 0; a < 3; ++a) x[a] = __fmaf_rn(t, d[a], o[a]);
 }
 
+// Two FP32 fused multiply-adds in one instruction (fma.rn.f32x2, sm_100
+// family): each half is rounded exactly as fmaf rounds it, so a pair gives the
+// bits of the two scalar calls in half the issue slots.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
 // ---------------------------------------------------------------------------
 // Trilinear gathers (Sec. 3.1): 8 corner records of 16 bytes each.
 // ---------------------------------------------------------------------------
@@ -400,13 +414,17 @@ __device__ __forceinline__ void sdf_full(const GridView& g, const Cell& c, const
     corner_weights(c.f, w);
     s = 0.0f;
     feat[0] = feat[1] = feat[2] = 0.0f;
+    float2 sf0 = make_float2(0.0f, 0.0f), f12 = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        s = fmaf(w[q], k.v[q].x, s);
-        feat[0] = fmaf(w[q], k.v[q].y, feat[0]);
-        feat[1] = fmaf(w[q], k.v[q].z, feat[1]);
-        feat[2] = fmaf(w[q], k.v[q].w, feat[2]);
+        const float2 wq = make_float2(w[q], w[q]);
+        sf0 = fma2(wq, make_float2(k.v[q].x, k.v[q].y), sf0);  // s, feature 0
+        f12 = fma2(wq, make_float2(k.v[q].z, k.v[q].w), f12);  // features 1, 2
     }
+    s = sf0.x;
+    feat[0] = sf0.y;
+    feat[1] = f12.x;
+    feat[2] = f12.y;
     const float fx = c.f[0], fy = c.f[1], fz = c.f[2];
     const float x0 = 1.0f - fx, y0 = 1.0f - fy, z0 = 1.0f - fz;
     // d/du_x: differences along x weighted by the (y, z) bilinear weights

@@ -227,13 +227,17 @@ __device__ __forceinline__ void eval_appearance_at(const RenderArgs& A, const fl
         for (int c = 0; c < C::NA; ++c) part[c] = 0.0f;
 #pragma unroll
         for (int j = 0; j < C::L2; ++j) {
+            const float2 y = make_float2(S.Y[j], S.Y[j]);
 #pragma unroll
             for (int cg = 0; cg < C::NA4; ++cg) {
                 const float4 bb = probe_coeffs<C>(A.probes, pidx[q], j, cg);
-                part[4 * cg + 0] = fmaf(bb.x, S.Y[j], part[4 * cg + 0]);
-                part[4 * cg + 1] = fmaf(bb.y, S.Y[j], part[4 * cg + 1]);
-                part[4 * cg + 2] = fmaf(bb.z, S.Y[j], part[4 * cg + 2]);
-                part[4 * cg + 3] = fmaf(bb.w, S.Y[j], part[4 * cg + 3]);
+                float* p4 = part + 4 * cg;
+                const float2 lo = fma2(make_float2(bb.x, bb.y), y, make_float2(p4[0], p4[1]));
+                const float2 hi = fma2(make_float2(bb.z, bb.w), y, make_float2(p4[2], p4[3]));
+                p4[0] = lo.x;
+                p4[1] = lo.y;
+                p4[2] = hi.x;
+                p4[3] = hi.y;
             }
         }
 #pragma unroll
@@ -296,22 +300,28 @@ __device__ __forceinline__ void eval_appearance_blend(const RenderArgs& A, const
     corner_weights(S.pcell.f, wq);
     int pidx[8];
     probe_corner_index(A.probes, S.pcell, pidx);
+    // channel pairs of every coefficient accumulated as float2 (paired FMAs)
+    float2 B2[C::L2 * C::NA / 2];
 #pragma unroll
-    for (int i = 0; i < C::L2 * C::NA; ++i) Bc[i] = 0.0f;
+    for (int i = 0; i < C::L2 * C::NA / 2; ++i) B2[i] = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
+        const float2 w2 = make_float2(wq[q], wq[q]);
 #pragma unroll
         for (int j = 0; j < C::L2; ++j) {
 #pragma unroll
             for (int cg = 0; cg < C::NA4; ++cg) {
                 const float4 bb = probe_coeffs<C>(A.probes, pidx[q], j, cg);
-                float* b4 = Bc + j * C::NA + 4 * cg;
-                b4[0] = fmaf(wq[q], bb.x, b4[0]);
-                b4[1] = fmaf(wq[q], bb.y, b4[1]);
-                b4[2] = fmaf(wq[q], bb.z, b4[2]);
-                b4[3] = fmaf(wq[q], bb.w, b4[3]);
+                float2* b2 = B2 + (j * C::NA + 4 * cg) / 2;
+                b2[0] = fma2(w2, make_float2(bb.x, bb.y), b2[0]);
+                b2[1] = fma2(w2, make_float2(bb.z, bb.w), b2[1]);
             }
         }
+    }
+#pragma unroll
+    for (int i = 0; i < C::L2 * C::NA / 2; ++i) {
+        Bc[2 * i] = B2[i].x;
+        Bc[2 * i + 1] = B2[i].y;
     }
 #pragma unroll
     for (int c = 0; c < C::NA; ++c) {
