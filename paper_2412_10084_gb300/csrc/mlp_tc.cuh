@@ -28,8 +28,9 @@ struct MlpTC {
     static __device__ __forceinline__ uint8_t* w1l(uint8_t* wt) { return wt + kW1; }
     static __device__ __forceinline__ uint8_t* w2h(uint8_t* wt) { return wt + kSplit * kW1; }
     static __device__ __forceinline__ uint8_t* w2l(uint8_t* wt) { return wt + kSplit * kW1 + kW2; }
-    // FP32 parameters kept for the CUDA-core parts: b1[W] b2[W] W3T[W][4] b3[4]
-    static constexpr int kB1 = 0, kB2 = W, kW3T = 2 * W, kB3 = 6 * W, kF32 = 6 * W + 4;
+    // FP32 parameters kept for the CUDA-core parts: b1[W] b2[W] W3[3][W] b3[4]
+    // (W3 row-major, so that neighbouring hidden units form pairs)
+    static constexpr int kB1 = 0, kB2 = W, kW3 = 2 * W, kB3 = 5 * W, kF32 = 5 * W + 4;
     static constexpr uint32_t kIdescL = tc::idesc_f16(128, W, 0, 0);
 };
 
@@ -65,11 +66,10 @@ __device__ __forceinline__ void load_mlp_tc(const float* __restrict__ g, uint8_t
         float v;
         if (i < M::kB2) {
             v = g[C::gB1 + i];
-        } else if (i < M::kW3T) {
+        } else if (i < M::kW3) {
             v = g[C::gB2 + (i - M::kB2)];
         } else if (i < M::kB3) {
-            const int o = (i - M::kW3T) / 4, c = (i - M::kW3T) % 4;
-            v = c < 3 ? g[C::gW3 + c * W + o] : 0.0f;
+            v = g[C::gW3 + (i - M::kW3)];
         } else {
             const int c = i - M::kB3;
             v = c < 3 ? g[C::gB3 + c] : 0.0f;
@@ -111,18 +111,48 @@ template <class C>
 __device__ __forceinline__ void mlp_layer3(const float* f32, const float* h2, float col[3])
 {
     using M = MlpTC<C>;
+    constexpr int W = C::W;
     const float4 b3 = *reinterpret_cast<const float4*>(f32 + M::kB3);
-    float z0 = b3.x, z1 = b3.y, z2 = b3.z;
+    // even and odd hidden units summed apart, one paired FMA per output and pair
+    float2 z0 = make_float2(0.0f, 0.0f), z1 = z0, z2 = z0;
 #pragma unroll
-    for (int o = 0; o < C::W; ++o) {
-        const float4 w3 = *reinterpret_cast<const float4*>(f32 + M::kW3T + 4 * o);
-        z0 = fmaf(w3.x, h2[o], z0);
-        z1 = fmaf(w3.y, h2[o], z1);
-        z2 = fmaf(w3.z, h2[o], z2);
+    for (int o = 0; o < W; o += 2) {
+        const float2 h = make_float2(h2[o], h2[o + 1]);
+        z0 = fma2(*reinterpret_cast<const float2*>(f32 + M::kW3 + o), h, z0);
+        z1 = fma2(*reinterpret_cast<const float2*>(f32 + M::kW3 + W + o), h, z1);
+        z2 = fma2(*reinterpret_cast<const float2*>(f32 + M::kW3 + 2 * W + o), h, z2);
     }
-    col[0] = sigmoidf(z0);
-    col[1] = sigmoidf(z1);
-    col[2] = sigmoidf(z2);
+    col[0] = sigmoidf(b3.x + (z0.x + z0.y));
+    col[1] = sigmoidf(b3.y + (z1.x + z1.y));
+    col[2] = sigmoidf(b3.z + (z2.x + z2.y));
+}
+
+// z = max(z + b, 0) over a row of NV hidden units (bias added in pairs).
+template <int NV>
+__device__ __forceinline__ void bias_relu(float* z, const float* b)
+{
+#pragma unroll
+    for (int o = 0; o < NV; o += 2) {
+        const float2 h = add2(make_float2(z[o], z[o + 1]), *reinterpret_cast<const float2*>(b + o));
+        z[o] = fmaxf(h.x, 0.0f);
+        z[o + 1] = fmaxf(h.y, 0.0f);
+    }
+}
+
+// bias_relu that also returns the mask of the units with z + b > 0.
+template <int NV>
+__device__ __forceinline__ uint32_t bias_relu_mask(float* z, const float* b)
+{
+    uint32_t mask = 0;
+#pragma unroll
+    for (int o = 0; o < NV; o += 2) {
+        const float2 h = add2(make_float2(z[o], z[o + 1]), *reinterpret_cast<const float2*>(b + o));
+        mask |= (h.x > 0.0f ? 1u : 0u) << o;
+        mask |= (h.y > 0.0f ? 1u : 0u) << (o + 1);
+        z[o] = fmaxf(h.x, 0.0f);
+        z[o + 1] = fmaxf(h.y, 0.0f);
+    }
+    return mask;
 }
 
 // Writes a row of NV FP32 values (NV a multiple of 8) into columns

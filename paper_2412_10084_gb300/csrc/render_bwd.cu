@@ -267,10 +267,9 @@ render_backward_kernel(RenderArgs A)
     {
         const float m = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
         float c3 = 0.0f, c2 = 0.0f;
-        for (int i = 0; i < W; ++i) {
-            const float4 w3 = *reinterpret_cast<const float4*>(f32 + M::kW3T + 4 * i);
-            c3 = fmaxf(c3, fabsf(w3.x) + fabsf(w3.y) + fabsf(w3.z));
-        }
+        for (int i = 0; i < W; ++i)
+            c3 = fmaxf(c3, fabsf(f32[M::kW3 + i]) + fabsf(f32[M::kW3 + W + i]) +
+                               fabsf(f32[M::kW3 + 2 * W + i]));
         for (int i = 0; i < W; ++i) {
             float cs = 0.0f;
             for (int o = 0; o < W; ++o) cs += fabsf(__ldg(A.mlp + C::gW2 + o * W + i));
@@ -451,12 +450,7 @@ render_backward_kernel(RenderArgs A)
             {
                 float z[W];
                 tc::tmem_ld<W>(t_row + 0, z);
-#pragma unroll
-                for (int o = 0; o < W; ++o) {
-                    const float h = z[o] + f32[M::kB1 + o];
-                    mask1 |= (h > 0.0f ? 1u : 0u) << o;
-                    z[o] = fmaxf(h, 0.0f);
-                }
+                mask1 = bias_relu_mask<W>(z, f32 + M::kB1);
                 if (!have) {
 #pragma unroll
                     for (int o = 0; o < W; ++o) z[o] = 0.0f;
@@ -484,12 +478,7 @@ render_backward_kernel(RenderArgs A)
             float col[3];
             {
                 tc::tmem_ld<W>(t_row + 32, h2);
-#pragma unroll
-                for (int o = 0; o < W; ++o) {
-                    const float h = h2[o] + f32[M::kB2 + o];
-                    mask2 |= (h > 0.0f ? 1u : 0u) << o;
-                    h2[o] = fmaxf(h, 0.0f);
-                }
+                mask2 = bias_relu_mask<W>(h2, f32 + M::kB2);
                 mlp_layer3<C>(f32, h2, col);
             }
             const float w = active ? Tk * alpha : 0.0f;
@@ -570,12 +559,18 @@ render_backward_kernel(RenderArgs A)
                 if (lane == c) accb3 += sb;
             }
             {
+                // dh2 = W3^T dz3 over pairs of hidden units (W3 row-major)
                 float dz2[W];
+                const float2 e0 = make_float2(dz3[0], dz3[0]), e1 = make_float2(dz3[1], dz3[1]);
+                const float2 e2 = make_float2(dz3[2], dz3[2]), sc2 = make_float2(s2, s2);
 #pragma unroll
-                for (int i = 0; i < W; ++i) {
-                    const float4 w3 = *reinterpret_cast<const float4*>(f32 + M::kW3T + 4 * i);
-                    const float dh2 = w3.x * dz3[0] + w3.y * dz3[1] + w3.z * dz3[2];
-                    dz2[i] = ((mask2 >> i) & 1u) ? dh2 * s2 : 0.0f;
+                for (int i = 0; i < W; i += 2) {
+                    float2 dh2 = mul2(*reinterpret_cast<const float2*>(f32 + M::kW3 + i), e0);
+                    dh2 = fma2(*reinterpret_cast<const float2*>(f32 + M::kW3 + W + i), e1, dh2);
+                    dh2 = fma2(*reinterpret_cast<const float2*>(f32 + M::kW3 + 2 * W + i), e2, dh2);
+                    dh2 = mul2(dh2, sc2);
+                    dz2[i] = ((mask2 >> i) & 1u) ? dh2.x : 0.0f;
+                    dz2[i + 1] = ((mask2 >> (i + 1)) & 1u) ? dh2.y : 0.0f;
                 }
                 store_row<W, M::kSplit>(dzh, dzl, tid, W, L::DZC, dz2);
             }
@@ -601,8 +596,13 @@ render_backward_kernel(RenderArgs A)
                 float dh1[W];
                 tc::tmem_ld<W>(t_row + 0, dh1);
                 const float r12 = s1 * inv_s2;  // dh1 arrives scaled by s2; dz1 is stored scaled by s1
+                const float2 r2 = make_float2(r12, r12);
 #pragma unroll
-                for (int i = 0; i < W; ++i) dh1[i] = ((mask1 >> i) & 1u) ? dh1[i] * r12 : 0.0f;
+                for (int i = 0; i < W; i += 2) {
+                    const float2 v = mul2(make_float2(dh1[i], dh1[i + 1]), r2);
+                    dh1[i] = ((mask1 >> i) & 1u) ? v.x : 0.0f;
+                    dh1[i + 1] = ((mask1 >> (i + 1)) & 1u) ? v.y : 0.0f;
+                }
                 store_row<W, M::kSplit>(dzh, dzl, tid, 0, L::DZC, dh1);
             }
             tc::fence_smem_to_async();
@@ -631,8 +631,15 @@ render_backward_kernel(RenderArgs A)
             tc::fence_after();
             float dx[16];
             tc::tmem_ld<16>(t_row + 32, dx);
+            {
+                const float2 is1 = make_float2(inv_s1, inv_s1);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) dx[i] *= inv_s1;
+                for (int i = 0; i < 16; i += 2) {
+                    const float2 v = mul2(make_float2(dx[i], dx[i + 1]), is1);
+                    dx[i] = v.x;
+                    dx[i + 1] = v.y;
+                }
+            }
             tc::fence_before();
             __syncthreads();  // tiles are free from here on
 

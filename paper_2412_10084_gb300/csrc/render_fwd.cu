@@ -238,8 +238,7 @@ render_forward_kernel(RenderArgs A)
             {
                 float z[W];
                 tc::tmem_ld<W>(t_row, z);
-#pragma unroll
-                for (int o = 0; o < W; ++o) z[o] = fmaxf(z[o] + f32[M::kB1 + o], 0.0f);
+                bias_relu<W>(z, f32 + M::kB1);
                 store_row<W, M::kSplit>(hh, hl, tid, 0, W, z);
             }
             // the layer-1 reads are complete (tcgen05.wait::ld) before the
@@ -269,8 +268,7 @@ render_forward_kernel(RenderArgs A)
             {
                 float z[W];
                 tc::tmem_ld<W>(t_row, z);
-#pragma unroll
-                for (int o = 0; o < W; ++o) z[o] = fmaxf(z[o] + f32[M::kB2 + o], 0.0f);
+                bias_relu<W>(z, f32 + M::kB2);
                 float col[3];
                 mlp_layer3<C>(f32, z, col);
                 if (active) {

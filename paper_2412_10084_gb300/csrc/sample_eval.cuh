@@ -217,34 +217,39 @@ __device__ __forceinline__ void eval_appearance_at(const RenderArgs& A, const fl
     corner_weights(S.pcell.f, wq);
     int pidx[8];
     probe_corner_index(A.probes, S.pcell, pidx);
-    float fa[C::NA];
+    // blended coefficients b^_j = sum_i w_i b_ij first (one weight per probe
+    // serves all of its coefficients), then F_a = sum_j Y_j b^_j
+    float2 B2[C::L2 * C::NA / 2];
 #pragma unroll
-    for (int c = 0; c < C::NA; ++c) fa[c] = 0.0f;
+    for (int i = 0; i < C::L2 * C::NA / 2; ++i) B2[i] = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        float part[C::NA];
-#pragma unroll
-        for (int c = 0; c < C::NA; ++c) part[c] = 0.0f;
+        const float2 w2 = make_float2(wq[q], wq[q]);
 #pragma unroll
         for (int j = 0; j < C::L2; ++j) {
-            const float2 y = make_float2(S.Y[j], S.Y[j]);
 #pragma unroll
             for (int cg = 0; cg < C::NA4; ++cg) {
                 const float4 bb = probe_coeffs<C>(A.probes, pidx[q], j, cg);
-                float* p4 = part + 4 * cg;
-                const float2 lo = fma2(make_float2(bb.x, bb.y), y, make_float2(p4[0], p4[1]));
-                const float2 hi = fma2(make_float2(bb.z, bb.w), y, make_float2(p4[2], p4[3]));
-                p4[0] = lo.x;
-                p4[1] = lo.y;
-                p4[2] = hi.x;
-                p4[3] = hi.y;
+                float2* b2 = B2 + (j * C::NA + 4 * cg) / 2;
+                b2[0] = fma2(w2, make_float2(bb.x, bb.y), b2[0]);
+                b2[1] = fma2(w2, make_float2(bb.z, bb.w), b2[1]);
             }
         }
+    }
+    float2 fa[C::NA / 2];
 #pragma unroll
-        for (int c = 0; c < C::NA; ++c) fa[c] = fmaf(wq[q], part[c], fa[c]);
+    for (int c = 0; c < C::NA / 2; ++c) fa[c] = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int j = 0; j < C::L2; ++j) {
+        const float2 y = make_float2(S.Y[j], S.Y[j]);
+#pragma unroll
+        for (int c = 0; c < C::NA / 2; ++c) fa[c] = fma2(y, B2[j * C::NA / 2 + c], fa[c]);
     }
 #pragma unroll
-    for (int c = 0; c < C::NA; ++c) S.x[3 + c] = fa[c];
+    for (int c = 0; c < C::NA / 2; ++c) {
+        S.x[3 + 2 * c] = fa[c].x;
+        S.x[4 + 2 * c] = fa[c].y;
+    }
     // Fresnel inputs (Eq. 4): (1 - n.v)^k, k = 1..K
     const float om = 1.0f - S.ndv;
     float pw = 1.0f;

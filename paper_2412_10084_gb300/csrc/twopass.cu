@@ -203,8 +203,7 @@ __global__ void __launch_bounds__(kFwdThreads, 4) shade_kernel(RenderArgs A, Sha
             {
                 float z[W];
                 tc::tmem_ld<W>(t_row + 0, z);
-#pragma unroll
-                for (int o = 0; o < W; ++o) z[o] = fmaxf(z[o] + f32[M::kB1 + o], 0.0f);
+                bias_relu<W>(z, f32 + M::kB1);
                 store_row<W, M::kSplit>(hh, hl, tid, 0, W, z);
             }
             tc::fence_smem_to_async();
@@ -226,8 +225,7 @@ __global__ void __launch_bounds__(kFwdThreads, 4) shade_kernel(RenderArgs A, Sha
             {
                 float z[W];
                 tc::tmem_ld<W>(t_row + 32, z);
-#pragma unroll
-                for (int o = 0; o < W; ++o) z[o] = fmaxf(z[o] + f32[M::kB2 + o], 0.0f);
+                bias_relu<W>(z, f32 + M::kB2);
                 float col[3];
                 mlp_layer3<C>(f32, z, col);
                 if (node >= 0) S.colours[node] = pack_colour(col);
