@@ -1094,6 +1094,8 @@ def inference_summary(inf):
                              "depth_mae_vs_ref": form["depth_mae_vs_ref"]},
         "uniform256_fp32": inf["uniform256_fp32"],
         "speedup_vs_uniform256": inf["speedup_vs_uniform256"],
+        "proposal_forms": {k: {"ms_per_frame": v["ms_per_frame"], "psnr_db": v["psnr_db"]}
+                           for k, v in inf["proposal_forms"].items()},
         "kernels_ms": inf["kernels_ms"], "roofline": inf["roofline"], "e2e": inf["e2e"],
         "two_pass": {k: tp[k] for k in ("chosen", "matched", "ms_per_frame", "psnr_db",
                                         "speedup_vs_uniform256", "kernels_ms_per_view")},

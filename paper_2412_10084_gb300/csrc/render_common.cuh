@@ -219,13 +219,21 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b)
 // Read-only 16-byte loads with eviction priorities: the probe coefficients (a
 // few MB, reused by every ray) are kept in L1 and L2 over the grid's node
 // records (reused only by neighbouring samples), which go first in L1.
+// The L2 evict-last policy, in an asm of its own without side effects, so
+// that one instance serves every load of a kernel (hoisted, not re-created).
+__device__ __forceinline__ uint64_t l2_evict_last()
+{
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
 __device__ __forceinline__ float4 ldg_keep(const float4* p)
 {
     float4 v;
-    asm("{\n\t.reg .b64 pol;\n\tcreatepolicy.fractional.L2::evict_last.b64 pol, 1.0;\n\t"
-        "ld.global.nc.L1::evict_last.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], pol;\n\t}"
+    asm("ld.global.nc.L1::evict_last.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
         : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-        : "l"(p));
+        : "l"(p), "l"(l2_evict_last()));
     return v;
 }
 

@@ -217,33 +217,57 @@ __device__ __forceinline__ void eval_appearance_at(const RenderArgs& A, const fl
     corner_weights(S.pcell.f, wq);
     int pidx[8];
     probe_corner_index(A.probes, S.pcell, pidx);
-    // blended coefficients b^_j = sum_i w_i b_ij first (one weight per probe
-    // serves all of its coefficients), then F_a = sum_j Y_j b^_j
-    float2 B2[C::L2 * C::NA / 2];
-#pragma unroll
-    for (int i = 0; i < C::L2 * C::NA / 2; ++i) B2[i] = make_float2(0.0f, 0.0f);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const float2 w2 = make_float2(wq[q], wq[q]);
-#pragma unroll
-        for (int j = 0; j < C::L2; ++j) {
-#pragma unroll
-            for (int cg = 0; cg < C::NA4; ++cg) {
-                const float4 bb = probe_coeffs<C>(A.probes, pidx[q], j, cg);
-                float2* b2 = B2 + (j * C::NA + 4 * cg) / 2;
-                b2[0] = fma2(w2, make_float2(bb.x, bb.y), b2[0]);
-                b2[1] = fma2(w2, make_float2(bb.z, bb.w), b2[1]);
-            }
-        }
-    }
     float2 fa[C::NA / 2];
 #pragma unroll
     for (int c = 0; c < C::NA / 2; ++c) fa[c] = make_float2(0.0f, 0.0f);
+    if constexpr (C::L2 * C::NA <= 36) {
+        // blended coefficients b^_j = sum_i w_i b_ij first (one weight per
+        // probe serves all of its coefficients), then F_a = sum_j Y_j b^_j
+        float2 B2[C::L2 * C::NA / 2];
 #pragma unroll
-    for (int j = 0; j < C::L2; ++j) {
-        const float2 y = make_float2(S.Y[j], S.Y[j]);
+        for (int i = 0; i < C::L2 * C::NA / 2; ++i) B2[i] = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int c = 0; c < C::NA / 2; ++c) fa[c] = fma2(y, B2[j * C::NA / 2 + c], fa[c]);
+        for (int q = 0; q < 8; ++q) {
+            const float2 w2 = make_float2(wq[q], wq[q]);
+#pragma unroll
+            for (int j = 0; j < C::L2; ++j) {
+#pragma unroll
+                for (int cg = 0; cg < C::NA4; ++cg) {
+                    const float4 bb = probe_coeffs<C>(A.probes, pidx[q], j, cg);
+                    float2* b2 = B2 + (j * C::NA + 4 * cg) / 2;
+                    b2[0] = fma2(w2, make_float2(bb.x, bb.y), b2[0]);
+                    b2[1] = fma2(w2, make_float2(bb.z, bb.w), b2[1]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < C::L2; ++j) {
+            const float2 y = make_float2(S.Y[j], S.Y[j]);
+#pragma unroll
+            for (int c = 0; c < C::NA / 2; ++c) fa[c] = fma2(y, B2[j * C::NA / 2 + c], fa[c]);
+        }
+    } else {
+        // wide rows (more SH coefficients or channels): one probe at a time,
+        // F_a += w_i sum_j b_ij Y_j, so only NA partial sums are live
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            float2 part[C::NA / 2];
+#pragma unroll
+            for (int c = 0; c < C::NA / 2; ++c) part[c] = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int j = 0; j < C::L2; ++j) {
+                const float2 y = make_float2(S.Y[j], S.Y[j]);
+#pragma unroll
+                for (int cg = 0; cg < C::NA4; ++cg) {
+                    const float4 bb = probe_coeffs<C>(A.probes, pidx[q], j, cg);
+                    part[2 * cg] = fma2(make_float2(bb.x, bb.y), y, part[2 * cg]);
+                    part[2 * cg + 1] = fma2(make_float2(bb.z, bb.w), y, part[2 * cg + 1]);
+                }
+            }
+            const float2 w2 = make_float2(wq[q], wq[q]);
+#pragma unroll
+            for (int c = 0; c < C::NA / 2; ++c) fa[c] = fma2(w2, part[c], fa[c]);
+        }
     }
 #pragma unroll
     for (int c = 0; c < C::NA / 2; ++c) {
