@@ -31,7 +31,25 @@ template <int B>
 struct PropShape {
     static constexpr int kIn = 7 + 2 * B;
     static constexpr int kParams = kPW * kIn + kPW + kPW * kPW + kPW + B * kPW + B;
+    // W1 rows padded to an even length in shared memory, so that every row
+    // starts 8-byte aligned and is read two inputs at a time
+    static constexpr int kInP = (kIn + 1) & ~1;
+    static_assert((kPW * kIn + kPW) % 4 == 0 && (kPW * kPW + kPW) % 4 == 0,
+                  "W2 and W3 rows start 16-byte aligned in the packed parameters");
 };
+
+// Parameters into shared memory: the packed vector, and W1 with padded rows.
+template <int B>
+__device__ __forceinline__ void load_prop_params(const float* __restrict__ g, float* sw,
+                                                 float* sw1)
+{
+    constexpr int kIn = PropShape<B>::kIn, kInP = PropShape<B>::kInP;
+    for (int i = threadIdx.x; i < PropShape<B>::kParams; i += blockDim.x) sw[i] = g[i];
+    for (int i = threadIdx.x; i < kPW * kInP; i += blockDim.x) {
+        const int u = i / kInP, j = i % kInP;
+        sw1[i] = j < kIn ? g[u * kIn + j] : 0.0f;
+    }
+}
 
 // SDF of node (x, y, z); in a sparse grid a node of a brick that is not
 // stored reads as empty_sdf.
@@ -221,10 +239,10 @@ struct PropState {
 
 template <int B>
 __device__ __forceinline__ void proposal_eval(const PropArgs& P, const float* sw,
-                                              const uint32_t* bits, int64_t ray,
-                                              PropState<B>& S)
+                                              const float* sw1, const uint32_t* bits,
+                                              int64_t ray, PropState<B>& S)
 {
-    constexpr int kIn = PropShape<B>::kIn;
+    constexpr int kIn = PropShape<B>::kIn, kInP = PropShape<B>::kInP;
     float o[3], d[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -254,29 +272,43 @@ __device__ __forceinline__ void proposal_eval(const PropArgs& P, const float* sw
     const float* b2 = W2 + kPW * kPW;
     const float* W3 = b2 + kPW;
     const float* b3 = W3 + B * kPW;
+    (void)W1;
     S.m1 = S.m2 = 0;
+    // each layer sums the even and the odd inputs apart, two per paired FMA
+    float2 xp[kInP / 2];
+#pragma unroll
+    for (int i = 0; i < kInP / 2; ++i)
+        xp[i] = make_float2(S.x[2 * i], 2 * i + 1 < kIn ? S.x[2 * i + 1] : 0.0f);
 #pragma unroll
     for (int u = 0; u < kPW; ++u) {
-        float z = b1[u];
+        float2 a = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int i = 0; i < kIn; ++i) z = fmaf(W1[u * kIn + i], S.x[i], z);
+        for (int i = 0; i < kInP / 2; ++i)
+            a = fma2(*reinterpret_cast<const float2*>(sw1 + u * kInP + 2 * i), xp[i], a);
+        const float z = b1[u] + (a.x + a.y);
         S.m1 |= (z > 0.0f ? 1u : 0u) << u;
         S.h1[u] = fmaxf(z, 0.0f);
     }
 #pragma unroll
     for (int u = 0; u < kPW; ++u) {
-        float z = b2[u];
+        float2 a = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int i = 0; i < kPW; ++i) z = fmaf(W2[u * kPW + i], S.h1[i], z);
+        for (int i = 0; i < kPW; i += 2)
+            a = fma2(*reinterpret_cast<const float2*>(W2 + u * kPW + i),
+                     make_float2(S.h1[i], S.h1[i + 1]), a);
+        const float z = b2[u] + (a.x + a.y);
         S.m2 |= (z > 0.0f ? 1u : 0u) << u;
         S.h2[u] = fmaxf(z, 0.0f);
     }
     float mx = -INFINITY, l[B];
 #pragma unroll
     for (int b = 0; b < B; ++b) {
-        float z = b3[b];
+        float2 a = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int i = 0; i < kPW; ++i) z = fmaf(W3[b * kPW + i], S.h2[i], z);
+        for (int i = 0; i < kPW; i += 2)
+            a = fma2(*reinterpret_cast<const float2*>(W3 + b * kPW + i),
+                     make_float2(S.h2[i], S.h2[i + 1]), a);
+        const float z = b3[b] + (a.x + a.y);
         l[b] = z;
         mx = fmaxf(mx, z);
     }
@@ -303,10 +335,11 @@ __global__ void proposal_fwd_kernel(PropArgs P)
 {
     constexpr int kParams = PropShape<B>::kParams;
     constexpr int kRow = 2 * B + 4;  // per ray: c_0..c_B, 1/q_0..1/q_{B-1}, hit, t_n, t_f
-    __shared__ float sw[kParams];
+    __shared__ __align__(16) float sw[kParams];
+    __shared__ __align__(16) float sw1[kPW * PropShape<B>::kInP];
     __shared__ float srow[4 * 32 * kRow];
     extern __shared__ uint32_t sbits[];
-    for (int i = threadIdx.x; i < kParams; i += blockDim.x) sw[i] = P.params[i];
+    load_prop_params<B>(P.params, sw, sw1);
     for (int i = threadIdx.x; i < occ_words(P); i += blockDim.x) sbits[i] = P.occ_bits[i];
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -325,7 +358,7 @@ __global__ void proposal_fwd_kernel(PropArgs P)
 #pragma unroll
         for (int b = 0; b < B; ++b) q[b] = 1.0f / B;
         if (live) {
-            proposal_eval<B>(P, sw, sbits, ray, S);
+            proposal_eval<B>(P, sw, sw1, sbits, ray, S);
             // mix share: a quarter on every bin, three quarters on the occupied
             // bins and their neighbours (all of it uniformly when none is
             // occupied)
@@ -418,13 +451,12 @@ __global__ void proposal_bwd_kernel(PropArgs P)
 {
     constexpr int kIn = PropShape<B>::kIn;
     constexpr int kParams = PropShape<B>::kParams;
-    __shared__ float sw[kParams];
+    __shared__ __align__(16) float sw[kParams];
+    __shared__ __align__(16) float sw1[kPW * PropShape<B>::kInP];
     __shared__ float acc[kParams];
     extern __shared__ uint32_t sbits[];
-    for (int i = threadIdx.x; i < kParams; i += blockDim.x) {
-        sw[i] = P.params[i];
-        acc[i] = 0.0f;
-    }
+    load_prop_params<B>(P.params, sw, sw1);
+    for (int i = threadIdx.x; i < kParams; i += blockDim.x) acc[i] = 0.0f;
     for (int i = threadIdx.x; i < occ_words(P); i += blockDim.x) sbits[i] = P.occ_bits[i];
     __syncthreads();
     const float* W2 = sw + kPW * kIn + kPW;
@@ -452,7 +484,7 @@ __global__ void proposal_bwd_kernel(PropArgs P)
             valid = mass >= P.min_mass;
             float ce = 0.0f;
             if (valid) {
-                proposal_eval<B>(P, sw, sbits, ray, S);
+                proposal_eval<B>(P, sw, sw1, sbits, ray, S);
 #pragma unroll
                 for (int b = 0; b < B; ++b) {
                     const float h = __ldg(P.hist + ray * B + b);
